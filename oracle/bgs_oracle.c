@@ -1,0 +1,985 @@
+/*
+ * Plain FP64 CPU oracle of the block Gauss-Seidel / SA-AMG / FGMRES solve.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the benchmark's
+ * CPU-baseline leg, never by the library.  It shares no code with the CUDA path.
+ * Compiled with -ffp-contract=off so that every product and sum is rounded on its own.
+ *
+ * Readings of the paper (it configures a library and does not spell these out):
+ *  - strength (Sec. 2.2.1 drop tolerance theta; Sec. 3.1.4 theta = 0.04): j is strong for
+ *    i != j iff a_ij^2 > theta^2 |a_ii a_jj| or a_ji^2 > theta^2 |a_ii a_jj| (symmetric test;
+ *    a missing entry counts as 0).
+ *  - aggregation (not stated in the paper): distance-2 maximal independent set over the
+ *    strength graph by synchronous rounds with keys (fmix32(i ^ salt), i); aggregates are a
+ *    root plus its strong neighbours, the rest join the neighbouring phase-1 aggregate with the
+ *    largest |a_ij| (ties to the smaller aggregate id); ids are roots ranked by node index.
+ *  - tentative prolongator: one unnormalised 1 per row (constant near-nullspace).
+ *  - filtered smoothing (Sec. 2.2.1, matrix filtering with an absolute-row-sum diagonal):
+ *    A_F keeps the diagonal and the strong entries, dropped entries are added to the diagonal,
+ *    D_F = sum_j |A_F,ij| (or diag(A_F)); P = P_tent - omega D_F^-1 A_F P_tent with
+ *    omega = (4/3) / lambda_max(D_F^-1 A_F).
+ *  - Galerkin coarse operator A_{l+1} = R_l A_l P_l, R_l = P_l^T (Eq. galerkin), l = 0..L-1.
+ *  - Chebyshev smoother on D^-1 A over [boost*lmax/ratio, boost*lmax] (Sec. 2.2.1: degree 2,
+ *    4 for the voltage blocks of the coupled solve, Sec. 3.1.5), three-term recurrence
+ *    (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1); degree k = k residual
+ *    evaluations; lambda_max by power iteration.
+ *  - coarsest level: dense LU with partial pivoting in place of the sparse direct solve.
+ *  - block Gauss-Seidel (Sec. 2.2, Eqs. hierarchical-bgs ... voltage-bgs): a forward sweep over a
+ *    permutation of the fields, one V-cycle per diagonal block, blocks after the current one ignored.
+ *  - flexible GMRES(m), right preconditioned, x0 = 0, modified Gram-Schmidt, restarted on the
+ *    true residual (Sec. 2.2, flexible GMRES).
+ */
+#include "bgs_oracle.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ST_OK 0
+#define ST_INVALID 1
+#define ST_NOCONV 3
+#define ST_BREAKDOWN 4
+#define ST_NANINF 5
+#define ST_ZEROPIV 6
+
+/* ------------------------------------------------------------------------------------ */
+/* CSR helpers                                                                           */
+/* ------------------------------------------------------------------------------------ */
+or_csr *or_csr_new(int n, int m, int nnz) {
+    or_csr *A = (or_csr *)calloc(1, sizeof(or_csr));
+    A->n = n;
+    A->m = m;
+    A->nnz = nnz;
+    A->rp = (int *)calloc((size_t)n + 1, sizeof(int));
+    A->ci = (int *)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    A->v = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    return A;
+}
+
+or_csr *or_csr_from(int n, int m, const int *rp, const int *ci, const double *v) {
+    int nnz = rp[n];
+    or_csr *A = or_csr_new(n, m, nnz);
+    memcpy(A->rp, rp, sizeof(int) * ((size_t)n + 1));
+    memcpy(A->ci, ci, sizeof(int) * (size_t)nnz);
+    memcpy(A->v, v, sizeof(double) * (size_t)nnz);
+    return A;
+}
+
+void or_csr_free(or_csr *A) {
+    if (!A) return;
+    free(A->rp);
+    free(A->ci);
+    free(A->v);
+    free(A);
+}
+
+void or_csr_info(const or_csr *A, int *n, int *m, int *nnz) {
+    *n = A->n;
+    *m = A->m;
+    *nnz = A->nnz;
+}
+
+void or_csr_copy(const or_csr *A, int *rp, int *ci, double *v) {
+    memcpy(rp, A->rp, sizeof(int) * ((size_t)A->n + 1));
+    memcpy(ci, A->ci, sizeof(int) * (size_t)A->nnz);
+    memcpy(v, A->v, sizeof(double) * (size_t)A->nnz);
+}
+
+/* y = A x, each row summed in stored order */
+void or_spmv(const or_csr *A, const double *x, double *y) {
+    for (int i = 0; i < A->n; i++) {
+        double s = 0.0;
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) s += A->v[e] * x[A->ci[e]];
+        y[i] = s;
+    }
+}
+
+/* Plain transpose; rows of the result are sorted because rows of A are visited in order. */
+or_csr *or_transpose(const or_csr *A) {
+    or_csr *T = or_csr_new(A->m, A->n, A->nnz);
+    for (int e = 0; e < A->nnz; e++) T->rp[A->ci[e] + 1]++;
+    for (int j = 0; j < A->m; j++) T->rp[j + 1] += T->rp[j];
+    int *cur = (int *)malloc(sizeof(int) * ((size_t)A->m + 1));
+    memcpy(cur, T->rp, sizeof(int) * ((size_t)A->m + 1));
+    for (int i = 0; i < A->n; i++)
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) {
+            int p = cur[A->ci[e]]++;
+            T->ci[p] = i;
+            T->v[p] = A->v[e];
+        }
+    free(cur);
+    return T;
+}
+
+/* C = A B.  Row i of C: for each stored a_ik in order, for each stored b_kj in order,
+ * acc[j] += a_ik * b_kj.  Every structural entry is kept; columns sorted. */
+or_csr *or_spgemm(const or_csr *A, const or_csr *B) {
+    int n = A->n, m = B->m;
+    int *mark = (int *)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
+    double *acc = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    int *cols = (int *)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
+    for (int j = 0; j < m; j++) mark[j] = -1;
+    /* pass 1: count */
+    int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
+    for (int i = 0; i < n; i++) {
+        int c = 0;
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) {
+            int k = A->ci[e];
+            for (int f = B->rp[k]; f < B->rp[k + 1]; f++) {
+                int j = B->ci[f];
+                if (mark[j] != i) {
+                    mark[j] = i;
+                    c++;
+                }
+            }
+        }
+        cnt[i + 1] = c;
+    }
+    for (int i = 0; i < n; i++) cnt[i + 1] += cnt[i];
+    or_csr *C = or_csr_new(n, m, cnt[n]);
+    memcpy(C->rp, cnt, sizeof(int) * ((size_t)n + 1));
+    free(cnt);
+    for (int j = 0; j < m; j++) mark[j] = -1;
+    /* pass 2: accumulate in order, then emit sorted */
+    for (int i = 0; i < n; i++) {
+        int c = 0;
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) {
+            int k = A->ci[e];
+            double a = A->v[e];
+            for (int f = B->rp[k]; f < B->rp[k + 1]; f++) {
+                int j = B->ci[f];
+                if (mark[j] != i) {
+                    mark[j] = i;
+                    acc[j] = 0.0;
+                    cols[c++] = j;
+                }
+                acc[j] += a * B->v[f];
+            }
+        }
+        /* insertion sort of the (short) column list */
+        for (int p = 1; p < c; p++) {
+            int key = cols[p], q = p - 1;
+            while (q >= 0 && cols[q] > key) {
+                cols[q + 1] = cols[q];
+                q--;
+            }
+            cols[q + 1] = key;
+        }
+        int base = C->rp[i];
+        for (int p = 0; p < c; p++) {
+            C->ci[base + p] = cols[p];
+            C->v[base + p] = acc[cols[p]];
+        }
+    }
+    free(mark);
+    free(acc);
+    free(cols);
+    return C;
+}
+
+static double lookup(const or_csr *A, int i, int j) {
+    for (int e = A->rp[i]; e < A->rp[i + 1]; e++)
+        if (A->ci[e] == j) return A->v[e];
+    return 0.0;
+}
+
+static double diag_of(const or_csr *A, int i) { return lookup(A, i, i); }
+
+/* ------------------------------------------------------------------------------------ */
+/* Strength of connection, strength graph                                                */
+/* ------------------------------------------------------------------------------------ */
+uint32_t or_fmix32(uint32_t h) {
+    /* MurmurHash3 32-bit finaliser (Appleby) */
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+/* strong[e] for each stored entry e of A: off-diagonal and passes the symmetric test */
+void or_strength_flags(const or_csr *A, double theta, unsigned char *strong) {
+    double t2 = theta * theta;
+    for (int i = 0; i < A->n; i++) {
+        double aii = diag_of(A, i);
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) {
+            int j = A->ci[e];
+            strong[e] = 0;
+            if (j == i) continue;
+            double ajj = diag_of(A, j);
+            double aij = A->v[e];
+            double aji = lookup(A, j, i);
+            double rhs = t2 * fabs(aii * ajj);
+            if (aij * aij > rhs || aji * aji > rhs) strong[e] = 1;
+        }
+    }
+}
+
+/* Undirected strength graph: edge {i, j} when a strong entry exists in row i or row j.
+ * Values carry a_ij (0 when the entry is only present as a_ji). Rows sorted. */
+or_csr *or_strength_graph(const or_csr *A, const unsigned char *strong) {
+    int n = A->n;
+    /* S_A: strong entries of A */
+    int ns = 0;
+    for (int e = 0; e < A->nnz; e++) ns += strong[e];
+    or_csr *SA = or_csr_new(n, n, ns);
+    int p = 0;
+    for (int i = 0; i < n; i++) {
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++)
+            if (strong[e]) {
+                SA->ci[p] = A->ci[e];
+                SA->v[p] = A->v[e];
+                p++;
+            }
+        SA->rp[i + 1] = p;
+    }
+    or_csr *ST = or_transpose(SA);
+    /* union of row i of S_A and row i of S_A^T */
+    int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
+    for (int i = 0; i < n; i++) {
+        int a = SA->rp[i], ae = SA->rp[i + 1], b = ST->rp[i], be = ST->rp[i + 1], c = 0;
+        while (a < ae || b < be) {
+            if (b >= be || (a < ae && SA->ci[a] < ST->ci[b])) a++;
+            else if (a >= ae || ST->ci[b] < SA->ci[a]) b++;
+            else { a++; b++; }
+            c++;
+        }
+        cnt[i + 1] = c;
+    }
+    for (int i = 0; i < n; i++) cnt[i + 1] += cnt[i];
+    or_csr *S = or_csr_new(n, n, cnt[n]);
+    memcpy(S->rp, cnt, sizeof(int) * ((size_t)n + 1));
+    free(cnt);
+    for (int i = 0; i < n; i++) {
+        int a = SA->rp[i], ae = SA->rp[i + 1], b = ST->rp[i], be = ST->rp[i + 1], q = S->rp[i];
+        while (a < ae || b < be) {
+            if (b >= be || (a < ae && SA->ci[a] < ST->ci[b])) {
+                S->ci[q] = SA->ci[a];
+                S->v[q] = SA->v[a];
+                a++;
+            } else if (a >= ae || ST->ci[b] < SA->ci[a]) {
+                S->ci[q] = ST->ci[b];
+                S->v[q] = 0.0;
+                b++;
+            } else {
+                S->ci[q] = SA->ci[a];
+                S->v[q] = SA->v[a];
+                a++;
+                b++;
+            }
+            q++;
+        }
+    }
+    or_csr_free(SA);
+    or_csr_free(ST);
+    return S;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Distance-2 maximal independent set by synchronous rounds                              */
+/* ------------------------------------------------------------------------------------ */
+static uint64_t mis_key(int i, uint32_t salt) {
+    return ((uint64_t)or_fmix32((uint32_t)i ^ salt) << 32) | (uint64_t)(uint32_t)i;
+}
+
+/* state: 0 undecided, 1 in (root), 2 out.  Round: (i) an undecided v becomes a root iff its key
+ * is larger than the key of every other undecided node within distance 2 (paths through any
+ * node); (ii) every undecided node within distance 2 of a root leaves.  Returns the round count. */
+int or_mis2(const or_csr *S, uint32_t salt, int *state) {
+    int n = S->n;
+    for (int i = 0; i < n; i++) state[i] = 0;
+    int *newin = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int rounds = 0, undecided = n;
+    while (undecided > 0) {
+        rounds++;
+        /* (i) by definition: scan the distance-2 ball of each undecided node */
+        for (int v = 0; v < n; v++) {
+            newin[v] = 0;
+            if (state[v] != 0) continue;
+            uint64_t kv = mis_key(v, salt);
+            int ok = 1;
+            for (int e = S->rp[v]; e < S->rp[v + 1] && ok; e++) {
+                int u = S->ci[e];
+                if (u != v && state[u] == 0 && mis_key(u, salt) > kv) ok = 0;
+                for (int f = S->rp[u]; f < S->rp[u + 1] && ok; f++) {
+                    int w = S->ci[f];
+                    if (w != v && state[w] == 0 && mis_key(w, salt) > kv) ok = 0;
+                }
+            }
+            newin[v] = ok;
+        }
+        for (int v = 0; v < n; v++)
+            if (newin[v]) state[v] = 1;
+        /* (ii) undecided nodes within distance 2 of a root leave */
+        for (int v = 0; v < n; v++) {
+            if (state[v] != 0) continue;
+            int near = 0;
+            for (int e = S->rp[v]; e < S->rp[v + 1] && !near; e++) {
+                int u = S->ci[e];
+                if (state[u] == 1) near = 1;
+                for (int f = S->rp[u]; f < S->rp[u + 1] && !near; f++)
+                    if (state[S->ci[f]] == 1) near = 1;
+            }
+            newin[v] = near;
+        }
+        undecided = 0;
+        for (int v = 0; v < n; v++) {
+            if (state[v] == 0 && newin[v]) state[v] = 2;
+            if (state[v] == 0) undecided++;
+        }
+    }
+    free(newin);
+    return rounds;
+}
+
+/* Aggregates from the roots: phase 1 = root + its strong neighbours; phase 2 = remaining nodes
+ * join the phase-1 aggregate of the neighbour with the largest |a_ij| (ties: smaller id).
+ * Ids: roots ranked by node index.  Returns the aggregate count, or -1 if a node is left over. */
+int or_aggregate(const or_csr *S, const int *state, int *agg) {
+    int n = S->n;
+    int *rootid = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int nagg = 0;
+    for (int i = 0; i < n; i++) rootid[i] = (state[i] == 1) ? nagg++ : -1;
+    int *ph1 = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; i++) {
+        ph1[i] = -1;
+        if (state[i] == 1) {
+            ph1[i] = rootid[i];
+            continue;
+        }
+        for (int e = S->rp[i]; e < S->rp[i + 1]; e++) {
+            int j = S->ci[e];
+            if (state[j] == 1) ph1[i] = rootid[j];
+        }
+    }
+    int bad = 0;
+    for (int i = 0; i < n; i++) {
+        if (ph1[i] >= 0) {
+            agg[i] = ph1[i];
+            continue;
+        }
+        int best = -1;
+        double bw = -1.0;
+        for (int e = S->rp[i]; e < S->rp[i + 1]; e++) {
+            int j = S->ci[e];
+            if (j == i || ph1[j] < 0) continue;
+            double w = fabs(S->v[e]);
+            if (w > bw || (w == bw && ph1[j] < best)) {
+                bw = w;
+                best = ph1[j];
+            }
+        }
+        agg[i] = best;
+        if (best < 0) bad = 1;
+    }
+    free(rootid);
+    free(ph1);
+    return bad ? -1 : nagg;
+}
+
+/* Filtered matrix values vF (pattern of A) and its smoothing diagonal dF. */
+void or_filter(const or_csr *A, const unsigned char *strong, int filter_diag, double *vF, double *dF) {
+    for (int i = 0; i < A->n; i++) {
+        double lump = 0.0;
+        int dpos = -1;
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) {
+            int j = A->ci[e];
+            if (j == i) {
+                dpos = e;
+                vF[e] = A->v[e];
+            } else if (strong[e]) {
+                vF[e] = A->v[e];
+            } else {
+                vF[e] = 0.0;
+                lump += A->v[e];
+            }
+        }
+        if (dpos >= 0) vF[dpos] = A->v[dpos] + lump;
+        if (filter_diag) {
+            double s = 0.0;
+            for (int e = A->rp[i]; e < A->rp[i + 1]; e++)
+                if (A->ci[e] == i || strong[e]) s += fabs(vF[e]);
+            dF[i] = s;
+        } else {
+            dF[i] = dpos >= 0 ? vF[dpos] : 0.0;
+        }
+    }
+}
+
+/* lambda_max(D^-1 A) by power iteration from a hashed positive start vector.
+ * v0_i = (fmix32(i ^ 0x7F4A7C15) >> 8 + 0.5) / 2^24, normalised; each step w = D^-1 A v,
+ * lambda = ||w||, v = w / lambda.  Returns the last lambda. */
+double or_power_lambda(const or_csr *A, const double *dinv, int iters) {
+    int n = A->n;
+    double *v = (double *)malloc(sizeof(double) * (size_t)n);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    double nv = 0.0;
+    for (int i = 0; i < n; i++) {
+        uint32_t u = or_fmix32((uint32_t)i ^ 0x7F4A7C15u) >> 8;
+        v[i] = ((double)u + 0.5) / 16777216.0;
+        nv += v[i] * v[i];
+    }
+    nv = sqrt(nv);
+    for (int i = 0; i < n; i++) v[i] = v[i] / nv;
+    double lam = 0.0;
+    for (int it = 0; it < iters; it++) {
+        or_spmv(A, v, w);
+        double s = 0.0;
+        for (int i = 0; i < n; i++) {
+            w[i] = dinv[i] * w[i];
+            s += w[i] * w[i];
+        }
+        lam = sqrt(s);
+        if (lam == 0.0) break;
+        for (int i = 0; i < n; i++) v[i] = w[i] / lam;
+    }
+    free(v);
+    free(w);
+    return lam;
+}
+
+/* P = P_tent - omega D_F^-1 A_F P_tent, row by row: s_J = sum of A_F(i, j) over agg(j) = J in
+ * stored order (this is A_F P_tent), p_iJ = [J == agg(i)] - c_i s_J with c_i = omega / D_F,ii. */
+or_csr *or_smooth_prolongator(const or_csr *AF, const double *dinvF, const int *agg, int nagg, double omega) {
+    int n = AF->n;
+    or_csr *Pt = or_csr_new(n, nagg, n);
+    for (int i = 0; i < n; i++) {
+        Pt->rp[i + 1] = i + 1;
+        Pt->ci[i] = agg[i];
+        Pt->v[i] = 1.0;
+    }
+    or_csr *S = or_spgemm(AF, Pt);
+    for (int i = 0; i < n; i++) {
+        double c = omega * dinvF[i];
+        for (int e = S->rp[i]; e < S->rp[i + 1]; e++) {
+            double t = (S->ci[e] == agg[i]) ? 1.0 : 0.0;
+            S->v[e] = t - c * S->v[e];
+        }
+    }
+    or_csr_free(Pt);
+    return S;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Chebyshev smoother on D^-1 A (Saad Alg. 12.1 form)                                    */
+/* ------------------------------------------------------------------------------------ */
+void or_chebyshev(const or_csr *A, const double *dinv, double lmin, double lmax, int deg,
+                  const double *b, double *x, int x_is_zero) {
+    int n = A->n;
+    if (deg <= 0) return;
+    double theta = (lmax + lmin) / 2.0, delta = (lmax - lmin) / 2.0;
+    double sigma = theta / delta, rho = 1.0 / sigma;
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *d = (double *)malloc(sizeof(double) * (size_t)n);
+    double inv_theta = 1.0 / theta;
+    if (x_is_zero) {
+        for (int i = 0; i < n; i++) r[i] = b[i];
+    } else {
+        or_spmv(A, x, r);
+        for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
+    }
+    for (int i = 0; i < n; i++) {
+        d[i] = inv_theta * (dinv[i] * r[i]);
+        x[i] = (x_is_zero ? 0.0 : x[i]) + d[i];
+    }
+    for (int k = 1; k < deg; k++) {
+        double rho_new = 1.0 / (2.0 * sigma - rho);
+        double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
+        or_spmv(A, x, r);
+        for (int i = 0; i < n; i++) {
+            double ri = b[i] - r[i];
+            d[i] = c1 * d[i] + c2 * (dinv[i] * ri);
+            x[i] = x[i] + d[i];
+        }
+        rho = rho_new;
+    }
+    free(r);
+    free(d);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Dense LU with partial pivoting (row-major, in place)                                  */
+/* ------------------------------------------------------------------------------------ */
+int or_lu_factor(int n, double *a, int *piv) {
+    for (int k = 0; k < n; k++) {
+        int p = k;
+        double best = fabs(a[(size_t)k * n + k]);
+        for (int i = k + 1; i < n; i++) {
+            double t = fabs(a[(size_t)i * n + k]);
+            if (t > best) {
+                best = t;
+                p = i;
+            }
+        }
+        piv[k] = p;
+        if (best == 0.0) return ST_ZEROPIV;
+        if (p != k)
+            for (int j = 0; j < n; j++) {
+                double t = a[(size_t)k * n + j];
+                a[(size_t)k * n + j] = a[(size_t)p * n + j];
+                a[(size_t)p * n + j] = t;
+            }
+        double akk = a[(size_t)k * n + k];
+        for (int i = k + 1; i < n; i++) {
+            double l = a[(size_t)i * n + k] / akk;
+            a[(size_t)i * n + k] = l;
+            for (int j = k + 1; j < n; j++) a[(size_t)i * n + j] -= l * a[(size_t)k * n + j];
+        }
+    }
+    return ST_OK;
+}
+
+void or_lu_solve(int n, const double *lu, const int *piv, const double *b, double *x) {
+    for (int i = 0; i < n; i++) x[i] = b[i];
+    for (int k = 0; k < n; k++)
+        if (piv[k] != k) {
+            double t = x[k];
+            x[k] = x[piv[k]];
+            x[piv[k]] = t;
+        }
+    for (int i = 0; i < n; i++) {
+        double s = x[i];
+        for (int j = 0; j < i; j++) s -= lu[(size_t)i * n + j] * x[j];
+        x[i] = s;
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        double s = x[i];
+        for (int j = i + 1; j < n; j++) s -= lu[(size_t)i * n + j] * x[j];
+        x[i] = s / lu[(size_t)i * n + i];
+    }
+}
+
+/* A^T x = b with P A = L U: U^T y = b, L^T w = y, x = P^T w */
+static void lu_solve_transposed(int n, const double *lu, const int *piv, const double *b, double *x) {
+    for (int i = 0; i < n; i++) x[i] = b[i];
+    for (int i = 0; i < n; i++) {
+        double s = x[i];
+        for (int j = 0; j < i; j++) s -= lu[(size_t)j * n + i] * x[j];
+        x[i] = s / lu[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        double s = x[i];
+        for (int j = i + 1; j < n; j++) s -= lu[(size_t)j * n + i] * x[j];
+        x[i] = s;
+    }
+    for (int k = n - 1; k >= 0; k--)
+        if (piv[k] != k) {
+            double t = x[k];
+            x[k] = x[piv[k]];
+            x[piv[k]] = t;
+        }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* SA-AMG hierarchy                                                                      */
+/* ------------------------------------------------------------------------------------ */
+or_amg *or_amg_setup(const or_csr *A0, double theta, int degree, const or_options *opt) {
+    or_amg *h = (or_amg *)calloc(1, sizeof(or_amg));
+    h->degree = degree;
+    h->A[0] = or_csr_from(A0->n, A0->m, A0->rp, A0->ci, A0->v);
+    int l = 0;
+    int maxlev = opt->max_levels < OR_MAX_LEVELS ? opt->max_levels : OR_MAX_LEVELS;
+    for (;;) {
+        or_csr *A = h->A[l];
+        int n = A->n;
+        if (n <= opt->max_coarse || l + 1 >= maxlev) break;
+        unsigned char *strong = (unsigned char *)malloc((size_t)(A->nnz > 0 ? A->nnz : 1));
+        or_strength_flags(A, theta, strong);
+        or_csr *S = or_strength_graph(A, strong);
+        int *state = (int *)malloc(sizeof(int) * (size_t)n);
+        h->mis_rounds[l] = or_mis2(S, (uint32_t)l * 0x9E3779B9u, state);
+        int *agg = (int *)malloc(sizeof(int) * (size_t)n);
+        int nagg = or_aggregate(S, state, agg);
+        free(state);
+        if (nagg < 0) {
+            h->status = ST_INVALID;
+            free(agg);
+            free(strong);
+            or_csr_free(S);
+            break;
+        }
+        if ((long long)nagg * 10 > (long long)n * 9) { /* coarsening stalled: stop here */
+            free(agg);
+            free(strong);
+            or_csr_free(S);
+            break;
+        }
+        double *vF = (double *)malloc(sizeof(double) * (size_t)(A->nnz > 0 ? A->nnz : 1));
+        double *dF = (double *)malloc(sizeof(double) * (size_t)n);
+        or_filter(A, strong, opt->filter_diag, vF, dF);
+        or_csr AF = *A;
+        AF.v = vF;
+        double *dinvF = (double *)malloc(sizeof(double) * (size_t)n);
+        for (int i = 0; i < n; i++) dinvF[i] = 1.0 / dF[i];
+        double lam = or_power_lambda(&AF, dinvF, opt->power_iters);
+        double omega = (4.0 / 3.0) / lam;
+        or_csr *P = or_smooth_prolongator(&AF, dinvF, agg, nagg, omega);
+        or_csr *R = or_transpose(P);
+        or_csr *AP = or_spgemm(A, P);
+        or_csr *Ac = or_spgemm(R, AP);
+        or_csr_free(AP);
+        free(vF);
+        free(dF);
+        free(dinvF);
+        free(strong);
+        or_csr_free(S);
+        h->agg[l] = agg;
+        h->nagg[l] = nagg;
+        h->omega[l] = omega;
+        h->P[l] = P;
+        h->R[l] = R;
+        h->A[l + 1] = Ac;
+        l++;
+    }
+    h->nlevels = l + 1;
+    /* smoothers on every level above the coarsest */
+    for (int k = 0; k + 1 < h->nlevels; k++) {
+        or_csr *A = h->A[k];
+        h->dinv[k] = (double *)malloc(sizeof(double) * (size_t)A->n);
+        for (int i = 0; i < A->n; i++) h->dinv[k][i] = 1.0 / diag_of(A, i);
+        double lam = or_power_lambda(A, h->dinv[k], opt->power_iters);
+        h->lmax[k] = opt->cheb_boost * lam;
+        h->lmin[k] = h->lmax[k] / opt->cheb_ratio;
+    }
+    /* coarsest: dense LU */
+    or_csr *Ac = h->A[h->nlevels - 1];
+    int nc = Ac->n;
+    h->nc = nc;
+    h->lu = (double *)calloc((size_t)nc * nc, sizeof(double));
+    h->piv = (int *)malloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
+    for (int i = 0; i < nc; i++)
+        for (int e = Ac->rp[i]; e < Ac->rp[i + 1]; e++) h->lu[(size_t)i * nc + Ac->ci[e]] = Ac->v[e];
+    int st = or_lu_factor(nc, h->lu, h->piv);
+    if (st != ST_OK && h->status == ST_OK) h->status = st;
+    return h;
+}
+
+void or_amg_free(or_amg *h) {
+    if (!h) return;
+    for (int l = 0; l < OR_MAX_LEVELS; l++) {
+        or_csr_free(h->A[l]);
+        or_csr_free(h->P[l]);
+        or_csr_free(h->R[l]);
+        free(h->agg[l]);
+        free(h->dinv[l]);
+    }
+    free(h->lu);
+    free(h->piv);
+    free(h);
+}
+
+static void vcycle_level(const or_amg *h, int l, const double *b, double *x, int transposed, or_csr **AT) {
+    if (l == h->nlevels - 1) {
+        if (transposed) lu_solve_transposed(h->nc, h->lu, h->piv, b, x);
+        else or_lu_solve(h->nc, h->lu, h->piv, b, x);
+        return;
+    }
+    const or_csr *A = transposed ? AT[l] : h->A[l];
+    int n = A->n, nc = h->A[l + 1]->n;
+    or_chebyshev(A, h->dinv[l], h->lmin[l], h->lmax[l], h->degree, b, x, 1);
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    or_spmv(A, x, r);
+    for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
+    double *bc = (double *)malloc(sizeof(double) * (size_t)nc);
+    double *xc = (double *)malloc(sizeof(double) * (size_t)nc);
+    or_spmv(h->R[l], r, bc);
+    vcycle_level(h, l + 1, bc, xc, transposed, AT);
+    or_spmv(h->P[l], xc, r);
+    for (int i = 0; i < n; i++) x[i] += r[i];
+    or_chebyshev(A, h->dinv[l], h->lmin[l], h->lmax[l], h->degree, b, x, 0);
+    free(r);
+    free(bc);
+    free(xc);
+}
+
+void or_vcycle(const or_amg *h, const double *b, double *x) { vcycle_level(h, 0, b, x, 0, NULL); }
+
+/* ------------------------------------------------------------------------------------ */
+/* Block Gauss-Seidel                                                                    */
+/* ------------------------------------------------------------------------------------ */
+void or_default_options(or_options *o) {
+    memset(o, 0, sizeof(*o));
+    o->restart = 50;
+    o->maxit = 1000;
+    o->rtol = 1e-8;
+    for (int k = 0; k < 8; k++) {
+        o->cheb_degree[k] = 2;
+        o->theta[k] = 0.0;     /* no dropping: the library default the paper leaves in place */
+    }
+    o->theta[0] = 0.04;        /* phi_s: the grid-searched drop tolerance (Sec. 3.1.4) */
+    o->cheb_degree[0] = 4;     /* voltage blocks: degree 4 in the coupled solve (Sec. 3.1.5) */
+    o->cheb_degree[1] = 4;
+    o->max_coarse = 5000;
+    o->max_levels = 10;
+    o->cheb_ratio = 30.0;
+    o->cheb_boost = 1.1;
+    o->power_iters = 10;
+    o->filter_diag = 1;
+}
+
+or_bgs *or_bgs_create(int F, const int *sizes, const int *const *rps, const int *const *cis,
+                      const double *const *vs, const int *nnzs, const int *order, const or_options *opt) {
+    (void)nnzs;
+    or_bgs *h = (or_bgs *)calloc(1, sizeof(or_bgs));
+    h->F = F;
+    h->opt = *opt;
+    h->offs[0] = 0;
+    for (int k = 0; k < F; k++) {
+        h->sizes[k] = sizes[k];
+        h->offs[k + 1] = h->offs[k] + sizes[k];
+        h->order[k] = order[k];
+        h->pos[order[k]] = k;
+    }
+    for (int r = 0; r < F; r++)
+        for (int c = 0; c < F; c++) {
+            int b = r * F + c;
+            if (rps[b]) h->blk[b] = or_csr_from(sizes[r], sizes[c], rps[b], cis[b], vs[b]);
+        }
+    /* full operator: row i of field r = blocks (r, 0..F-1) concatenated with column offsets */
+    int n = h->offs[F];
+    long long nnz = 0;
+    for (int b = 0; b < F * F; b++)
+        if (h->blk[b]) nnz += h->blk[b]->nnz;
+    or_csr *A = or_csr_new(n, n, (int)nnz);
+    int q = 0;
+    for (int r = 0; r < F; r++)
+        for (int i = 0; i < sizes[r]; i++) {
+            for (int c = 0; c < F; c++) {
+                or_csr *B = h->blk[r * F + c];
+                if (!B) continue;
+                for (int e = B->rp[i]; e < B->rp[i + 1]; e++) {
+                    A->ci[q] = B->ci[e] + h->offs[c];
+                    A->v[q] = B->v[e];
+                    q++;
+                }
+            }
+            A->rp[h->offs[r] + i + 1] = q;
+        }
+    h->full = A;
+    return h;
+}
+
+int or_bgs_setup(or_bgs *h) {
+    for (int k = 0; k < h->F; k++) {
+        or_csr *Akk = h->blk[k * h->F + k];
+        h->amg[k] = or_amg_setup(Akk, h->opt.theta[k], h->opt.cheb_degree[k], &h->opt);
+        if (h->amg[k]->status) h->status = h->amg[k]->status;
+    }
+    return h->status;
+}
+
+void or_bgs_free(or_bgs *h) {
+    if (!h) return;
+    for (int b = 0; b < 64; b++) or_csr_free(h->blk[b]);
+    or_csr_free(h->full);
+    for (int k = 0; k < 8; k++) or_amg_free(h->amg[k]);
+    free(h);
+}
+
+void or_full_spmv(const or_bgs *h, const double *x, double *y) { or_spmv(h->full, x, y); }
+
+/* z = M^-1 v: for k in order, r_k = v_k - sum_{pos(j) < pos(k)} A_kj z_j, z_k = V-cycle_k(r_k). */
+void or_bgs_apply(const or_bgs *h, const double *v, double *z) {
+    int F = h->F;
+    for (int p = 0; p < F; p++) {
+        int k = h->order[p];
+        int nk = h->sizes[k];
+        double *r = (double *)malloc(sizeof(double) * (size_t)nk);
+        double *t = (double *)malloc(sizeof(double) * (size_t)nk);
+        for (int i = 0; i < nk; i++) r[i] = v[h->offs[k] + i];
+        for (int q = 0; q < p; q++) {
+            int j = h->order[q];
+            or_csr *B = h->blk[k * F + j];
+            if (!B) continue;
+            or_spmv(B, z + h->offs[j], t);
+            for (int i = 0; i < nk; i++) r[i] -= t[i];
+        }
+        or_vcycle(h->amg[k], r, z + h->offs[k]);
+        free(r);
+        free(t);
+    }
+}
+
+/* Transposed preconditioner for A^T: reverse order, upper couplings transposed,
+ * V-cycle on A_kk^T (level operators transposed, same transfers, LU solved transposed). */
+void or_bgs_apply_adjoint(const or_bgs *h, const double *v, double *z) {
+    int F = h->F;
+    for (int p = F - 1; p >= 0; p--) {
+        int k = h->order[p];
+        int nk = h->sizes[k];
+        double *r = (double *)malloc(sizeof(double) * (size_t)nk);
+        for (int i = 0; i < nk; i++) r[i] = v[h->offs[k] + i];
+        for (int q = p + 1; q < F; q++) {
+            int j = h->order[q];
+            or_csr *B = h->blk[j * F + k]; /* A_jk, applied transposed: r_k -= A_jk^T z_j */
+            if (!B) continue;
+            for (int i = 0; i < B->n; i++)
+                for (int e = B->rp[i]; e < B->rp[i + 1]; e++) r[B->ci[e]] -= B->v[e] * z[h->offs[j] + i];
+        }
+        const or_amg *g = h->amg[k];
+        or_csr *AT[OR_MAX_LEVELS] = {0};
+        for (int l = 0; l + 1 < g->nlevels; l++) AT[l] = or_transpose(g->A[l]);
+        vcycle_level(g, 0, r, z + h->offs[k], 1, AT);
+        for (int l = 0; l + 1 < g->nlevels; l++) or_csr_free(AT[l]);
+        free(r);
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Flexible GMRES(m), right preconditioned, modified Gram-Schmidt                        */
+/* ------------------------------------------------------------------------------------ */
+static double nrm2(int n, const double *x) {
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += x[i] * x[i];
+    return sqrt(s);
+}
+
+int or_fgmres(int n, or_apply_fn amul, void *actx, or_apply_fn prec, void *pctx, const double *b, double *x,
+              int m, int maxit, double rtol, or_info *info) {
+    memset(info, 0, sizeof(*info));
+    for (int i = 0; i < n; i++) x[i] = 0.0;
+    double bnorm = nrm2(n, b);
+    if (bnorm == 0.0) {
+        info->converged = 1;
+        return ST_OK;
+    }
+    if (!(bnorm == bnorm) || isinf(bnorm)) {
+        info->status = ST_NANINF;
+        return ST_NANINF;
+    }
+    double *Vb = (double *)malloc(sizeof(double) * (size_t)n * (m + 1));
+    double *Zb = (double *)malloc(sizeof(double) * (size_t)n * m);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *H = (double *)calloc((size_t)(m + 1) * m, sizeof(double));
+    double *cs = (double *)malloc(sizeof(double) * (size_t)m);
+    double *sn = (double *)malloc(sizeof(double) * (size_t)m);
+    double *g = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+    double *y = (double *)malloc(sizeof(double) * (size_t)m);
+    for (int i = 0; i < n; i++) r[i] = b[i];
+    double beta = bnorm;
+    int it = 0, status = ST_NOCONV;
+    double rel = 1.0, est = 1.0;
+    for (;;) {
+        for (int i = 0; i < n; i++) Vb[i] = r[i] / beta;
+        for (int k = 0; k <= m; k++) g[k] = 0.0;
+        g[0] = beta;
+        int jend = 0, breakdown = 0, nan = 0;
+        for (int j = 0; j < m; j++) {
+            double *vj = Vb + (size_t)j * n, *zj = Zb + (size_t)j * n;
+            prec(pctx, vj, zj);
+            amul(actx, zj, w);
+            for (int i = 0; i <= j; i++) {
+                double *vi = Vb + (size_t)i * n;
+                double hij = 0.0;
+                for (int t = 0; t < n; t++) hij += w[t] * vi[t];
+                H[(size_t)i * m + j] = hij;
+                for (int t = 0; t < n; t++) w[t] -= hij * vi[t];
+            }
+            double hn = nrm2(n, w);
+            H[(size_t)(j + 1) * m + j] = hn;
+            it++;
+            if (hn == 0.0) breakdown = 1;
+            else
+                for (int t = 0; t < n; t++) Vb[(size_t)(j + 1) * n + t] = w[t] / hn;
+            for (int i = 0; i < j; i++) {
+                double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            }
+            double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+            double den = sqrt(a * a + c * c);
+            cs[j] = den == 0.0 ? 1.0 : a / den;
+            sn[j] = den == 0.0 ? 0.0 : c / den;
+            H[(size_t)j * m + j] = den;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            est = fabs(g[j + 1]) / bnorm;
+            jend = j + 1;
+            if (!(est == est)) {
+                nan = 1;
+                break;
+            }
+            if (est <= rtol || it >= maxit || breakdown) break;
+        }
+        if (nan) {
+            status = ST_NANINF;
+            break;
+        }
+        for (int i = jend - 1; i >= 0; i--) {
+            double s = g[i];
+            for (int k = i + 1; k < jend; k++) s -= H[(size_t)i * m + k] * y[k];
+            y[i] = s / H[(size_t)i * m + i];
+        }
+        for (int k = 0; k < jend; k++)
+            for (int t = 0; t < n; t++) x[t] += y[k] * Zb[(size_t)k * n + t];
+        amul(actx, x, r);
+        for (int t = 0; t < n; t++) r[t] = b[t] - r[t];
+        beta = nrm2(n, r);
+        rel = beta / bnorm;
+        if (!(rel == rel)) {
+            status = ST_NANINF;
+            break;
+        }
+        if (rel <= rtol) {
+            status = ST_OK;
+            break;
+        }
+        if (it >= maxit) {
+            status = ST_NOCONV;
+            break;
+        }
+        if (breakdown && beta == 0.0) {
+            status = ST_BREAKDOWN;
+            break;
+        }
+    }
+    info->iters = it;
+    info->converged = status == ST_OK;
+    info->status = status;
+    info->rel_true_resid = rel;
+    info->rel_est_resid = est;
+    free(Vb);
+    free(Zb);
+    free(w);
+    free(r);
+    free(H);
+    free(cs);
+    free(sn);
+    free(g);
+    free(y);
+    return status;
+}
+
+static void amul_full(void *ctx, const double *in, double *out) { or_spmv(((const or_bgs *)ctx)->full, in, out); }
+static void prec_bgs(void *ctx, const double *in, double *out) { or_bgs_apply((const or_bgs *)ctx, in, out); }
+
+typedef struct {
+    const or_bgs *h;
+    or_csr *AT;
+} adj_ctx;
+static void amul_fullT(void *ctx, const double *in, double *out) { or_spmv(((adj_ctx *)ctx)->AT, in, out); }
+static void prec_bgsT(void *ctx, const double *in, double *out) { or_bgs_apply_adjoint(((adj_ctx *)ctx)->h, in, out); }
+
+int or_bgs_solve(const or_bgs *h, const double *b, double *x, or_info *info) {
+    int n = h->offs[h->F];
+    return or_fgmres(n, amul_full, (void *)h, prec_bgs, (void *)h, b, x, h->opt.restart, h->opt.maxit,
+                     h->opt.rtol, info);
+}
+
+int or_bgs_solve_adjoint(const or_bgs *h, const double *g, double *lam, or_info *info) {
+    int n = h->offs[h->F];
+    adj_ctx c = {h, or_transpose(h->full)};
+    int st = or_fgmres(n, amul_fullT, &c, prec_bgsT, &c, g, lam, h->opt.restart, h->opt.maxit, h->opt.rtol, info);
+    or_csr_free(c.AT);
+    return st;
+}
+
+/* dL/da_ij = -lambda_i x_j on the pattern of block A (row offset roff, column offset coff) */
+void or_grad_values(const or_csr *A, int roff, int coff, const double *lam, const double *x, double *g) {
+    for (int i = 0; i < A->n; i++)
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) g[e] = -(lam[roff + i] * x[coff + A->ci[e]]);
+}
