@@ -1,0 +1,151 @@
+/*
+ * bgs.h - C ABI of the GB300 block Gauss-Seidel / SA-AMG / FGMRES solver (libbgs.so).
+ *
+ * The library solves A x = b for a coupled multi-field system given as an F x F grid of
+ * CSR blocks (F <= 8).  It is the method of "Multi-physics Preconditioning for Thermally
+ * Activated Batteries" (Phillips): flexible GMRES (Sec. 2.2, flexible GMRES) right-
+ * preconditioned by one forward block Gauss-Seidel sweep over a permutation of the fields
+ * (Sec. 2.2, Eqs. hierarchical-bgs, non-voltage-bgs, voltage-bgs), with one smoothed-
+ * aggregation AMG V-cycle per diagonal block (Sec. 2.2.1, Eq. galerkin: Chebyshev smoothing,
+ * filtered prolongator smoothing, Galerkin coarse operators, a direct coarsest solve).
+ *
+ * Conventions for every entry point:
+ *  - Return value: a status code (BGS_OK = 0, see below).  No C++ exception crosses the ABI.
+ *  - Pointers marked "host or device" may point to either; the library copies them with
+ *    cudaMemcpyDefault on the handle's stream.  Pointers marked "device" must be device memory.
+ *  - Vectors over all fields are field-blocked: x = [x_0; x_1; ...; x_{F-1}], x_k of length
+ *    field_sizes[k].
+ *  - CSR: rowptr has nrows+1 int32 entries starting at 0; col/val have nnz entries; within a
+ *    row the columns are strictly increasing and in [0, ncols).  nnz < 2^31.
+ *  - The caller keeps ownership of everything it passes; the library copies what it keeps.
+ *  - One handle is used from one host thread at a time; all work goes to the handle's stream.
+ */
+#ifndef BGS_H
+#define BGS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BGS_OK 0
+#define BGS_INVALID_ARG 1     /* malformed CSR, bad order, missing diagonal, size mismatch */
+#define BGS_NOT_SETUP 2       /* solve before setup */
+#define BGS_NO_CONVERGENCE 3  /* maxit reached; x holds the last iterate, info is filled */
+#define BGS_BREAKDOWN 4       /* Arnoldi breakdown without convergence */
+#define BGS_NAN_INF 5         /* NaN or Inf in the input or in a residual norm */
+#define BGS_ZERO_PIVOT 6      /* the coarsest-level LU met a zero pivot */
+#define BGS_CUDA_ERROR 7      /* a CUDA call failed */
+#define BGS_OOM 8             /* device allocation failed */
+#define BGS_INTERNAL 9        /* an internal consistency check failed */
+
+typedef struct bgs_ctx *bgs_handle;
+
+/* One CSR block; pointers host or device.  nrows == 0 and nnz == 0 with NULL pointers
+ * denotes a zero block. */
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    const int32_t *rowptr;
+    const int32_t *col;
+    const double *val;
+} bgs_csr;
+
+typedef struct {
+    int restart;            /* FGMRES restart length m (Sec. 2.2; default 50) */
+    int maxit;              /* total FGMRES iterations (default 1000) */
+    double rtol;            /* stop when ||b - A x|| / ||b|| <= rtol, true residual (default 1e-8) */
+    int precision;          /* 0: FP64 hierarchy; 1: FP32 hierarchy + BF16 coupling values */
+    int graph;              /* 1: replay the preconditioner sweep as a captured CUDA graph */
+    int autotune;           /* 1: pick the SpMV variant per level operator by timing */
+    int cheb_degree[8];     /* Chebyshev degree per field id (Sec. 2.2.1: 2; voltage blocks 4, Sec. 3.1.5) */
+    double theta[8];        /* strength drop tolerance per field id (Sec. 3.1.4: 0.04 for phi_s) */
+    int max_coarse;         /* stop coarsening at this many rows (Sec. 2.2.1: 5000) */
+    int max_levels;         /* at most this many levels (default 10) */
+    double cheb_ratio;      /* lambda_min = lambda_max / ratio (default 30) */
+    double cheb_boost;      /* lambda_max = boost * power-iteration estimate (default 1.1) */
+    int power_iters;        /* power iterations for the eigenvalue estimates (default 10) */
+    int filter_diag;        /* smoothing diagonal of the filtered matrix: 1 absolute row sum
+                               (Sec. 2.2.1), 0 its plain diagonal */
+} bgs_options;
+
+typedef struct {
+    int iters;              /* FGMRES iterations (preconditioner applications) */
+    int converged;          /* 1 if the true relative residual reached rtol */
+    int status;             /* same as the return value */
+    int restarts;
+    double rel_true_resid;  /* ||b - A x|| / ||b|| of the returned x, in FP64 */
+    double rel_est_resid;   /* last Arnoldi residual estimate */
+    double t_setup_ms;      /* bgs_setup wall time */
+    double t_solve_ms;      /* this solve's wall time */
+} bgs_info;
+
+/* Fills *opt with the defaults listed above. */
+int bgs_default_options(bgs_options *opt);
+
+/* Builds the block operator (Sec. 2.2, Eq. block-splitting).
+ *  field_sizes: F entries (host).  blocks: F*F row-major bgs_csr (host array; block (r, c) has
+ *  field_sizes[r] rows and field_sizes[c] columns, or is a zero block).  Every diagonal block
+ *  is non-empty, square and stores its diagonal.  order: F entries (host), a permutation of
+ *  0..F-1: the sweep visits fields in this order.  opt: NULL for defaults.  cuda_stream: a
+ *  cudaStream_t or NULL for the default stream.  The CSR arrays are copied (host or device).
+ *  On success *out owns device memory until bgs_destroy. */
+int bgs_create(bgs_handle *out, int nfields, const int64_t *field_sizes, const bgs_csr *blocks,
+               const int *order, const bgs_options *opt, void *cuda_stream);
+
+/* Builds the SA-AMG hierarchy of every diagonal block (Sec. 2.2.1): strength filter, MIS-2
+ * aggregation, smoothed prolongator, Galerkin coarse operators, Chebyshev bounds, coarsest LU. */
+int bgs_setup(bgs_handle h);
+
+/* Solves A x = b by FGMRES(m) with the block Gauss-Seidel preconditioner, x0 = 0.
+ * b, x: host or device, length sum(field_sizes).  info may be NULL. */
+int bgs_solve(bgs_handle h, const double *b, double *x, bgs_info *info);
+
+/* Solves A^T lambda = g with the transposed preconditioner: the sweep in reverse order over the
+ * transposed couplings, V-cycles on the transposed diagonal blocks (same transfers).  This is an
+ * extension; the paper has no adjoint.  g, lambda: host or device. */
+int bgs_solve_adjoint(bgs_handle h, const double *g, double *lambda, bgs_info *info);
+
+/* Gradient of a scalar loss through the solve with respect to the stored values of block
+ * (row_field, col_field): dvals[e] = -lambda_i * x_j for stored entry e = (i, j) (extension,
+ * no counterpart in the paper).  lambda, x: device, full length; dvals: device, nnz of the block. */
+int bgs_grad_values(bgs_handle h, int row_field, int col_field, const double *lambda, const double *x,
+                    double *dvals);
+
+/* One application of the preconditioner z = M^-1 v (device pointers, full length). */
+int bgs_apply_preconditioner(bgs_handle h, const double *v, double *z);
+
+/* One V-cycle of field k's hierarchy from x = 0: x = V_k(b) (device pointers, field length). */
+int bgs_apply_vcycle(bgs_handle h, int field, const double *b, double *x);
+
+/* y = A x with the assembled FP64 operator (device pointers, full length). */
+int bgs_full_spmv(bgs_handle h, const double *x, double *y);
+
+/* Hierarchy introspection (host outputs; any pointer may be NULL).  Level 0 is the block. */
+int bgs_num_levels(bgs_handle h, int field, int *nlevels);
+int bgs_level_info(bgs_handle h, int field, int level, int64_t *rows, int64_t *nnz, int64_t *p_nnz,
+                   int *nagg, int *mis_rounds, double *omega, double *lmin, double *lmax);
+/* which: 0 level operator A_l, 1 prolongator P_l, 2 restriction R_l.  rowptr/col/val: host
+ * arrays sized by bgs_level_info (rows+1 / nnz / nnz; P_l has rows(l) rows and nagg columns). */
+int bgs_level_copy(bgs_handle h, int field, int level, int which, int32_t *rowptr, int32_t *col, double *val);
+/* Aggregate id of every node of level `level` (host array of rows(level) entries). */
+int bgs_level_aggregates(bgs_handle h, int field, int level, int32_t *agg);
+
+/* Per-kernel-class timing of the last solve when enabled (bgs_set_profiling(h, 1)): launches,
+ * summed CUDA-event milliseconds and algorithmic bytes.  kernel_class: 0 full SpMV, 1 Chebyshev
+ * step (all levels), 2 Arnoldi orthogonalisation, 3 coupling SpMV. */
+int bgs_set_profiling(bgs_handle h, int on);
+int bgs_kernel_stats(bgs_handle h, int kernel_class, int64_t *launches, double *ms, double *bytes);
+
+/* Stateless y = A x for a device CSR in FP64 (K1): the same SpMV kernel the solver uses.
+ * lanes: threads per row (1, 2, 4, 8, 16 or 32), or 0 for the built-in choice. */
+int bgs_csr_spmv(int64_t nrows, int64_t nnz, const int32_t *rowptr, const int32_t *col, const double *val,
+                 const double *x, double *y, int lanes, void *cuda_stream);
+
+void bgs_destroy(bgs_handle h);
+const char *bgs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -609,13 +609,28 @@ or_amg *or_amg_setup(const or_csr *A0, double theta, int degree, const or_option
         double *vF = (double *)malloc(sizeof(double) * (size_t)(A->nnz > 0 ? A->nnz : 1));
         double *dF = (double *)malloc(sizeof(double) * (size_t)n);
         or_filter(A, strong, opt->filter_diag, vF, dF);
-        or_csr AF = *A;
-        AF.v = vF;
+        /* A_F as its own matrix: the dropped entries leave the pattern (they would only add
+         * structural zeros to P and to the coarse operators) */
+        int nf = 0;
+        for (int i = 0; i < n; i++)
+            for (int e = A->rp[i]; e < A->rp[i + 1]; e++) nf += (A->ci[e] == i) || strong[e];
+        or_csr *AF = or_csr_new(n, n, nf);
+        nf = 0;
+        for (int i = 0; i < n; i++) {
+            for (int e = A->rp[i]; e < A->rp[i + 1]; e++)
+                if (A->ci[e] == i || strong[e]) {
+                    AF->ci[nf] = A->ci[e];
+                    AF->v[nf] = vF[e];
+                    nf++;
+                }
+            AF->rp[i + 1] = nf;
+        }
         double *dinvF = (double *)malloc(sizeof(double) * (size_t)n);
         for (int i = 0; i < n; i++) dinvF[i] = 1.0 / dF[i];
-        double lam = or_power_lambda(&AF, dinvF, opt->power_iters);
+        double lam = or_power_lambda(AF, dinvF, opt->power_iters);
         double omega = (4.0 / 3.0) / lam;
-        or_csr *P = or_smooth_prolongator(&AF, dinvF, agg, nagg, omega);
+        or_csr *P = or_smooth_prolongator(AF, dinvF, agg, nagg, omega);
+        or_csr_free(AF);
         or_csr *R = or_transpose(P);
         or_csr *AP = or_spgemm(A, P);
         or_csr *Ac = or_spgemm(R, AP);

@@ -1,0 +1,326 @@
+"""Python binding of libbgs (GB300 block Gauss-Seidel / SA-AMG / FGMRES solver).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.  The names follow
+the C ABI in include/bgs.h.  PyTorch supplies device memory and the CUDA stream.  There is no
+CPU fallback: importing the binding without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbgs.so")
+
+OK, INVALID_ARG, NOT_SETUP, NO_CONVERGENCE, BREAKDOWN, NAN_INF, ZERO_PIVOT, CUDA_ERROR, OOM, INTERNAL = range(10)
+FIELD_MAX = 8
+
+
+class bgs_csr(C.Structure):
+    _fields_ = [("nrows", C.c_int64), ("ncols", C.c_int64), ("nnz", C.c_int64),
+                ("rowptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class bgs_options(C.Structure):
+    _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("rtol", C.c_double), ("precision", C.c_int),
+                ("graph", C.c_int), ("autotune", C.c_int), ("cheb_degree", C.c_int * 8),
+                ("theta", C.c_double * 8), ("max_coarse", C.c_int), ("max_levels", C.c_int),
+                ("cheb_ratio", C.c_double), ("cheb_boost", C.c_double), ("power_iters", C.c_int),
+                ("filter_diag", C.c_int)]
+
+
+class bgs_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("status", C.c_int), ("restarts", C.c_int),
+                ("rel_true_resid", C.c_double), ("rel_est_resid", C.c_double),
+                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BGSError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libbgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libbgs.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        sig = {
+            "bgs_default_options": (i32, [C.POINTER(bgs_options)]),
+            "bgs_create": (i32, [C.POINTER(vp), i32, C.POINTER(C.c_int64), C.POINTER(bgs_csr), C.POINTER(C.c_int),
+                                 C.POINTER(bgs_options), vp]),
+            "bgs_setup": (i32, [vp]),
+            "bgs_solve": (i32, [vp, vp, vp, C.POINTER(bgs_info)]),
+            "bgs_solve_adjoint": (i32, [vp, vp, vp, C.POINTER(bgs_info)]),
+            "bgs_grad_values": (i32, [vp, i32, i32, vp, vp, vp]),
+            "bgs_apply_preconditioner": (i32, [vp, vp, vp]),
+            "bgs_apply_vcycle": (i32, [vp, i32, vp, vp]),
+            "bgs_full_spmv": (i32, [vp, vp, vp]),
+            "bgs_num_levels": (i32, [vp, i32, C.POINTER(C.c_int)]),
+            "bgs_level_info": (i32, [vp, i32, i32, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64),
+                                     C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(dbl), C.POINTER(dbl),
+                                     C.POINTER(dbl)]),
+            "bgs_level_copy": (i32, [vp, i32, i32, i32, vp, vp, vp]),
+            "bgs_level_aggregates": (i32, [vp, i32, i32, vp]),
+            "bgs_set_profiling": (i32, [vp, i32]),
+            "bgs_kernel_stats": (i32, [vp, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
+            "bgs_csr_spmv": (i32, [i64, i64, vp, vp, vp, vp, vp, i32, vp]),
+            "bgs_destroy": (None, [vp]),
+            "bgs_status_string": (C.c_char_p, [i32]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(st: int) -> str:
+    return lib().bgs_status_string(int(st)).decode()
+
+
+def _check(st, what):
+    if st != OK:
+        raise BGSError(st, what)
+
+
+def _ptr(a):
+    """Data pointer of a torch tensor or a numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ---------------------------------------------------------------------------------------------
+# Direct entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------------------------
+def bgs_default_options(**overrides) -> bgs_options:
+    o = bgs_options()
+    _check(lib().bgs_default_options(C.byref(o)), "bgs_default_options")
+    for k, v in overrides.items():
+        if k in ("cheb_degree", "theta"):
+            arr = getattr(o, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def bgs_csr_spmv(nrows, nnz, rowptr, col, val, x, y, lanes=0, stream=None) -> int:
+    return lib().bgs_csr_spmv(int(nrows), int(nnz), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(x), _ptr(y),
+                              int(lanes), _stream_ptr(stream))
+
+
+class Solver:
+    """Owns one bgs handle.  blocks: F x F list of CSR-like objects (rowptr/col/val arrays,
+    numpy or torch, host or device) or None for zero blocks."""
+
+    def __init__(self, blocks, field_sizes, order, options: bgs_options | None = None, stream=None, **opts):
+        F = len(field_sizes)
+        self.F = F
+        self.field_sizes = [int(s) for s in field_sizes]
+        self.n = sum(self.field_sizes)
+        self.offsets = np.concatenate([[0], np.cumsum(self.field_sizes)]).astype(np.int64)
+        self.options = options if options is not None else bgs_default_options(**opts)
+        arr = (bgs_csr * (F * F))()
+        keep = []
+        for r in range(F):
+            for c in range(F):
+                B = blocks[r][c]
+                if B is None:
+                    continue
+                rp, ci, v = B.rowptr, B.col, B.val
+                keep += [rp, ci, v]
+                nnz = int(rp[-1])
+                arr[r * F + c] = bgs_csr(self.field_sizes[r], self.field_sizes[c], nnz, _ptr(rp), _ptr(ci), _ptr(v))
+        self._stream = _stream_ptr(stream)
+        h = C.c_void_p()
+        sizes = (C.c_int64 * F)(*self.field_sizes)
+        ordr = (C.c_int * F)(*[int(k) for k in order])
+        _check(lib().bgs_create(C.byref(h), F, sizes, arr, ordr, C.byref(self.options), self._stream),
+               "bgs_create")
+        self.h = h
+        self.order = list(order)
+        del keep
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                lib().bgs_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    def close(self):
+        self.__del__()
+
+    def bgs_setup(self):
+        _check(lib().bgs_setup(self.h), "bgs_setup")
+
+    setup = bgs_setup
+
+    def bgs_solve(self, b, x, check=True) -> bgs_info:
+        info = bgs_info()
+        st = lib().bgs_solve(self.h, _ptr(b), _ptr(x), C.byref(info))
+        if check and st not in (OK, NO_CONVERGENCE):
+            _check(st, "bgs_solve")
+        return info
+
+    def bgs_solve_adjoint(self, g, lam, check=True) -> bgs_info:
+        info = bgs_info()
+        st = lib().bgs_solve_adjoint(self.h, _ptr(g), _ptr(lam), C.byref(info))
+        if check and st not in (OK, NO_CONVERGENCE):
+            _check(st, "bgs_solve_adjoint")
+        return info
+
+    def bgs_grad_values(self, row_field, col_field, lam, x, dvals):
+        _check(lib().bgs_grad_values(self.h, row_field, col_field, _ptr(lam), _ptr(x), _ptr(dvals)),
+               "bgs_grad_values")
+
+    def bgs_apply_preconditioner(self, v, z):
+        _check(lib().bgs_apply_preconditioner(self.h, _ptr(v), _ptr(z)), "bgs_apply_preconditioner")
+
+    def bgs_apply_vcycle(self, field, b, x):
+        _check(lib().bgs_apply_vcycle(self.h, int(field), _ptr(b), _ptr(x)), "bgs_apply_vcycle")
+
+    def bgs_full_spmv(self, x, y):
+        _check(lib().bgs_full_spmv(self.h, _ptr(x), _ptr(y)), "bgs_full_spmv")
+
+    def bgs_num_levels(self, field) -> int:
+        n = C.c_int()
+        _check(lib().bgs_num_levels(self.h, int(field), C.byref(n)), "bgs_num_levels")
+        return n.value
+
+    def bgs_level_info(self, field, level) -> dict:
+        rows, nnz, pnnz = C.c_int64(), C.c_int64(), C.c_int64()
+        nagg, rounds = C.c_int(), C.c_int()
+        om, lo, hi = C.c_double(), C.c_double(), C.c_double()
+        _check(lib().bgs_level_info(self.h, int(field), int(level), C.byref(rows), C.byref(nnz), C.byref(pnnz),
+                                    C.byref(nagg), C.byref(rounds), C.byref(om), C.byref(lo), C.byref(hi)),
+               "bgs_level_info")
+        return dict(rows=rows.value, nnz=nnz.value, p_nnz=pnnz.value, nagg=nagg.value, mis_rounds=rounds.value,
+                    omega=om.value, lmin=lo.value, lmax=hi.value)
+
+    def bgs_level_copy(self, field, level, which):
+        """which: 0 A_l, 1 P_l, 2 R_l -> (rowptr, col, val) numpy arrays."""
+        info = self.bgs_level_info(field, level)
+        if which == 0:
+            n, nnz = info["rows"], info["nnz"]
+        elif which == 1:
+            n, nnz = info["rows"], info["p_nnz"]
+        else:
+            n, nnz = info["nagg"], info["p_nnz"]
+        rp = np.zeros(n + 1, dtype=np.int32)
+        ci = np.zeros(max(nnz, 1), dtype=np.int32)
+        v = np.zeros(max(nnz, 1), dtype=np.float64)
+        _check(lib().bgs_level_copy(self.h, int(field), int(level), int(which), _ptr(rp), _ptr(ci), _ptr(v)),
+               "bgs_level_copy")
+        return rp, ci[:nnz], v[:nnz]
+
+    def bgs_level_aggregates(self, field, level):
+        info = self.bgs_level_info(field, level)
+        agg = np.zeros(info["rows"], dtype=np.int32)
+        _check(lib().bgs_level_aggregates(self.h, int(field), int(level), _ptr(agg)), "bgs_level_aggregates")
+        return agg
+
+    def bgs_set_profiling(self, on=True):
+        _check(lib().bgs_set_profiling(self.h, 1 if on else 0), "bgs_set_profiling")
+
+    def bgs_kernel_stats(self, kernel_class) -> dict:
+        n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+        _check(lib().bgs_kernel_stats(self.h, int(kernel_class), C.byref(n), C.byref(ms), C.byref(by)),
+               "bgs_kernel_stats")
+        return dict(launches=n.value, ms=ms.value, bytes=by.value)
+
+
+KERNEL_CLASSES = {"full_spmv": 0, "chebyshev": 1, "arnoldi": 2, "coupling": 3}
+
+
+def solver_for_system(system, order=None, device=True, **opts):
+    """Solver over a battery_system.CoupledSystem; the CSR blocks are passed from host memory
+    (the library copies them) unless device=True, in which case they are staged as torch tensors."""
+    import torch
+
+    class _B:
+        pass
+
+    blocks = []
+    keep = []
+    for r in range(5):
+        row = []
+        for c in range(5):
+            B = system.blocks.get((r, c))
+            if B is None:
+                row.append(None)
+                continue
+            o = _B()
+            if device:
+                o.rowptr = torch.from_numpy(B.rowptr).cuda()
+                o.col = torch.from_numpy(B.col).cuda()
+                o.val = torch.from_numpy(B.val).cuda()
+                o.rowptr_host = B.rowptr
+            else:
+                o.rowptr, o.col, o.val = B.rowptr, B.col, B.val
+            keep.append(o)
+            row.append(o)
+        blocks.append(row)
+
+    class _RP:
+        def __init__(self, o):
+            self.rowptr, self.col, self.val = o.rowptr, o.col, o.val
+
+    # the nnz is read from rowptr[-1]: take it from the host copy for device tensors
+    blocks2 = []
+    for row in blocks:
+        r2 = []
+        for o in row:
+            if o is None:
+                r2.append(None)
+                continue
+            w = _RP(o)
+            if device:
+                w.rowptr = _Rowptr(o.rowptr, int(o.rowptr_host[-1]))
+            r2.append(w)
+        blocks2.append(r2)
+    s = Solver(blocks2, system.field_sizes, order if order is not None else list(range(5)), **opts)
+    torch.cuda.synchronize()
+    return s
+
+
+class _Rowptr:
+    """A device rowptr tensor that reports its last element without a device read."""
+
+    def __init__(self, t, last):
+        self.t, self.last = t, last
+
+    def __getitem__(self, i):
+        if i == -1:
+            return self.last
+        raise IndexError
+
+    def data_ptr(self):
+        return self.t.data_ptr()

@@ -1,0 +1,1025 @@
+// SA-AMG setup on the device (Sec. 2.2.1, Eq. galerkin): strength filter (K3), MIS-2 rounds
+// (K4), aggregation (K5), tentative + smoothed prolongator (K6), transpose (K8), two-pass
+// hash SpGEMM for A_F P_tent, A P and R (A P) (K7), power iteration (K9) and the coarsest dense
+// LU with an explicit inverse (K12).
+//
+// Integer decisions (strength, MIS-2, aggregates) follow the exact rules:
+//  * j strong for i != j iff a_ij^2 > theta^2 |a_ii a_jj| or a_ji^2 > theta^2 |a_ii a_jj|, each
+//    product rounded separately (no fused multiply-add), a missing entry counting as 0;
+//  * MIS-2 by synchronous rounds with keys (fmix32(i ^ salt), i), salt = level * 0x9E3779B9;
+//  * aggregates = root + strong neighbours, then the leftover nodes join the neighbouring
+//    phase-1 aggregate with the largest |a_ij| (ties to the smaller id); ids by root index.
+// SpGEMM accumulates every output entry in the order of the left operand's row, so the
+// products are summed in a fixed order (mul and add rounded separately).
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+namespace bgs {
+
+// ==========================================================================================
+// Strength of connection
+// ==========================================================================================
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__device__ __forceinline__ int find_in_row(const int *ci, int s, int e, int col) {
+    int lo = s, hi = e - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int c = ci[mid];
+        if (c == col) return mid;
+        if (c < col) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+__global__ void k_strength(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
+                           const double *__restrict__ diag, double t2, uint8_t *strong, int *flags) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double aii = diag[i];
+        if (aii == 0.0) atomicOr(flags, 2);
+        for (int e = rp[i]; e < rp[i + 1]; e++) {
+            const int j = ci[e];
+            if (j == i) {
+                strong[e] = 0;
+                continue;
+            }
+            const int f = find_in_row(ci, rp[j], rp[j + 1], i);
+            if (f < 0) atomicOr(flags, 1);   // structurally non-symmetric
+            const double aji = f >= 0 ? v[f] : 0.0;
+            const double aij = v[e];
+            const double rhs = __dmul_rn(t2, fabs(__dmul_rn(aii, diag[j])));
+            strong[e] = (__dmul_rn(aij, aij) > rhs || __dmul_rn(aji, aji) > rhs) ? 1 : 0;
+        }
+    }
+}
+
+__global__ void k_count_flag(int n, const int *rp, const uint8_t *flag, int *cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int e = rp[i]; e < rp[i + 1]; e++) c += flag[e];
+        cnt[i] = c;
+    }
+}
+
+__global__ void k_fill_flag(int n, const int *rp, const int *ci, const double *v, const uint8_t *flag, const int *orp,
+                            int *oci, double *ov) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int q = orp[i];
+        for (int e = rp[i]; e < rp[i + 1]; e++)
+            if (flag[e]) {
+                oci[q] = ci[e];
+                ov[q] = v[e];
+                q++;
+            }
+    }
+}
+
+// union of two sorted rows (A, B); values from A, 0 where only B has the column
+__global__ void k_merge_count(int n, const int *arp, const int *aci, const int *brp, const int *bci, int *cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int a = arp[i], ae = arp[i + 1], b = brp[i], be = brp[i + 1], c = 0;
+        while (a < ae || b < be) {
+            if (b >= be || (a < ae && aci[a] < bci[b])) a++;
+            else if (a >= ae || bci[b] < aci[a]) b++;
+            else { a++; b++; }
+            c++;
+        }
+        cnt[i] = c;
+    }
+}
+__global__ void k_merge_fill(int n, const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
+                             const int *orp, int *oci, double *ov) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int a = arp[i], ae = arp[i + 1], b = brp[i], be = brp[i + 1], q = orp[i];
+        while (a < ae || b < be) {
+            if (b >= be || (a < ae && aci[a] < bci[b])) { oci[q] = aci[a]; ov[q] = av[a]; a++; }
+            else if (a >= ae || bci[b] < aci[a]) { oci[q] = bci[b]; ov[q] = 0.0; b++; }
+            else { oci[q] = aci[a]; ov[q] = av[a]; a++; b++; }
+            q++;
+        }
+    }
+}
+
+// ==========================================================================================
+// Transpose with sorted rows
+// ==========================================================================================
+__global__ void k_tr_count(int64_t nnz, const int *ci, int *cnt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[ci[e]], 1);
+}
+__global__ void k_tr_fill(int n, const int *rp, const int *ci, const double *v, const int *trp, int *cur, int *tci,
+                          double *tv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int e = rp[i]; e < rp[i + 1]; e++) {
+            int c = ci[e];
+            int p = trp[c] + atomicAdd(&cur[c], 1);
+            tci[p] = i;
+            if (v) tv[p] = v[e];
+        }
+}
+// rank sort of each row (keys distinct): one warp per row, reading the unsorted copy
+__global__ void k_row_rank_sort(int n, const int *rp, const int *ici, const double *iv, int *oci, double *ov) {
+    const int lane = threadIdx.x & 31;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += (gridDim.x * blockDim.x) >> 5) {
+        const int s = rp[r], e = rp[r + 1];
+        for (int t = s + lane; t < e; t += 32) {
+            const int k = ici[t];
+            int rank = 0;
+            for (int q = s; q < e; q++) rank += ici[q] < k;
+            oci[s + rank] = k;
+            if (iv) ov[s + rank] = iv[t];
+        }
+    }
+}
+
+void transpose_csr(const CsrView &A, DCsr &T, Scratch &sc, cudaStream_t s) {
+    T.n = A.m;
+    T.m = A.n;
+    T.nnz = A.nnz;
+    T.rp.alloc((size_t)A.m + 1, s);
+    CK(cudaMemsetAsync(T.rp.p, 0, sizeof(int) * ((size_t)A.m + 1), s));
+    if (A.nnz > 0) {
+        k_tr_count<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.nnz, A.ci, T.rp.p);
+        CK_LAUNCH();
+    }
+    scan_exclusive(T.rp.p, T.rp.p, A.m, sc, s);
+    DBuf<int> cur((size_t)A.m + 1, s), tci((size_t)std::max<int64_t>(A.nnz, 1), s);
+    DBuf<double> tv;
+    if (A.v) tv.alloc((size_t)std::max<int64_t>(A.nnz, 1), s);
+    CK(cudaMemsetAsync(cur.p, 0, sizeof(int) * ((size_t)A.m + 1), s));
+    T.ci.alloc((size_t)A.nnz, s);
+    if (A.v) T.v.alloc((size_t)A.nnz, s);
+    if (A.n > 0 && A.nnz > 0) {
+        k_tr_fill<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, T.rp.p, cur.p, tci.p, tv.p);
+        CK_LAUNCH();
+        k_row_rank_sort<<<grid_for((int64_t)A.m * 32, 256), 256, 0, s>>>(A.m, T.rp.p, tci.p, tv.p, T.ci.p, T.v.p);
+        CK_LAUNCH();
+    }
+}
+
+// ==========================================================================================
+// Strength graph
+// ==========================================================================================
+// S: undirected strength graph without the diagonal, values a_ij (0 where only a_ji is stored).
+static void strength_graph(const CsrView &A, const uint8_t *strong, bool asym, DCsr &S, Scratch &sc,
+                           cudaStream_t s) {
+    const int n = A.n;
+    DCsr SA;
+    SA.n = SA.m = n;
+    SA.rp.alloc((size_t)n + 1, s);
+    k_count_flag<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, strong, SA.rp.p);
+    CK_LAUNCH();
+    SA.nnz = scan_exclusive(SA.rp.p, SA.rp.p, n, sc, s);
+    SA.ci.alloc((size_t)SA.nnz, s);
+    SA.v.alloc((size_t)SA.nnz, s);
+    k_fill_flag<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, strong, SA.rp.p, SA.ci.p, SA.v.p);
+    CK_LAUNCH();
+    if (!asym) {   // symmetric pattern: the symmetric test makes S_A symmetric already
+        S = std::move(SA);
+        return;
+    }
+    DCsr ST;
+    transpose_csr(view(SA), ST, sc, s);
+    S.n = S.m = n;
+    S.rp.alloc((size_t)n + 1, s);
+    k_merge_count<<<grid_for(n, 256), 256, 0, s>>>(n, SA.rp.p, SA.ci.p, ST.rp.p, ST.ci.p, S.rp.p);
+    CK_LAUNCH();
+    S.nnz = scan_exclusive(S.rp.p, S.rp.p, n, sc, s);
+    S.ci.alloc((size_t)S.nnz, s);
+    S.v.alloc((size_t)S.nnz, s);
+    k_merge_fill<<<grid_for(n, 256), 256, 0, s>>>(n, SA.rp.p, SA.ci.p, SA.v.p, ST.rp.p, ST.ci.p, S.rp.p, S.ci.p,
+                                                   S.v.p);
+    CK_LAUNCH();
+}
+
+// ==========================================================================================
+// MIS-2 rounds and aggregation
+// ==========================================================================================
+__device__ __forceinline__ unsigned long long mis_key1(int i, uint32_t salt) {
+    return ((((unsigned long long)fmix32((uint32_t)i ^ salt)) << 32) | (unsigned long long)(uint32_t)i) + 1ull;
+}
+
+// m1[v] = max key over undecided nodes of the closed neighbourhood of v (0: none)
+__global__ void k_mis_m1(int n, const int *rp, const int *ci, const int *state, uint32_t salt,
+                         unsigned long long *m1) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        unsigned long long m = state[v] == 0 ? mis_key1(v, salt) : 0ull;
+        for (int e = rp[v]; e < rp[v + 1]; e++) {
+            int u = ci[e];
+            if (state[u] == 0) {
+                unsigned long long k = mis_key1(u, salt);
+                m = k > m ? k : m;
+            }
+        }
+        m1[v] = m;
+    }
+}
+// undecided v becomes a root iff the maximum over its distance-2 ball is its own key
+__global__ void k_mis_select(int n, const int *rp, const int *ci, int *state, uint32_t salt,
+                             const unsigned long long *m1) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (state[v] != 0) continue;
+        unsigned long long m = m1[v];
+        for (int e = rp[v]; e < rp[v + 1]; e++) {
+            unsigned long long k = m1[ci[e]];
+            m = k > m ? k : m;
+        }
+        if (m == mis_key1(v, salt)) state[v] = 1;
+    }
+}
+__global__ void k_mis_f1(int n, const int *rp, const int *ci, const int *state, int *f1) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int f = state[v] == 1;
+        for (int e = rp[v]; e < rp[v + 1] && !f; e++) f = state[ci[e]] == 1;
+        f1[v] = f;
+    }
+}
+__global__ void k_mis_out(int n, const int *rp, const int *ci, int *state, const int *f1, int *undecided) {
+    int local = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (state[v] != 0) continue;
+        int f = f1[v];
+        for (int e = rp[v]; e < rp[v + 1] && !f; e++) f = f1[ci[e]];
+        if (f) state[v] = 2;
+        else local++;
+    }
+    if (local) atomicAdd(undecided, local);
+}
+
+static int mis2(const DCsr &S, uint32_t salt, int *state, Scratch &sc, cudaStream_t s) {
+    const int n = S.n;
+    DBuf<unsigned long long> m1((size_t)n, s);
+    DBuf<int> f1((size_t)n, s);
+    CK(cudaMemsetAsync(state, 0, sizeof(int) * (size_t)n, s));
+    const int g = grid_for(n, 256);
+    int rounds = 0;
+    for (;;) {
+        rounds++;
+        k_mis_m1<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, salt, m1.p);
+        k_mis_select<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, salt, m1.p);
+        k_mis_f1<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, f1.p);
+        CK(cudaMemsetAsync(sc.flags.p + 4, 0, sizeof(int), s));
+        k_mis_out<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, f1.p, sc.flags.p + 4);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(sc.h_flags + 4, sc.flags.p + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (sc.h_flags[4] == 0) break;
+        if (rounds > n + 1) throw Error(BGS_INTERNAL, "MIS-2 did not terminate");
+    }
+    return rounds;
+}
+
+__global__ void k_root_flag(int n, const int *state, int *f) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) f[i] = state[i] == 1;
+}
+__global__ void k_phase1(int n, const int *rp, const int *ci, const int *state, const int *rootid, int *ph1) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int a = -1;
+        if (state[i] == 1) a = rootid[i];
+        else
+            for (int e = rp[i]; e < rp[i + 1]; e++)
+                if (state[ci[e]] == 1) a = rootid[ci[e]];
+        ph1[i] = a;
+    }
+}
+__global__ void k_phase2(int n, const int *rp, const int *ci, const double *v, const int *ph1, int *agg, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int a = ph1[i];
+        if (a < 0) {
+            double bw = -1.0;
+            for (int e = rp[i]; e < rp[i + 1]; e++) {
+                int j = ci[e];
+                int pj = ph1[j];
+                if (j == i || pj < 0) continue;
+                double w = fabs(v[e]);
+                if (w > bw || (w == bw && pj < a)) {
+                    bw = w;
+                    a = pj;
+                }
+            }
+            if (a < 0) atomicOr(bad, 1);
+        }
+        agg[i] = a;
+    }
+}
+
+static int aggregate(const DCsr &S, const int *state, int *agg, Scratch &sc, cudaStream_t s) {
+    const int n = S.n;
+    DBuf<int> rootid((size_t)n + 1, s), ph1((size_t)n, s);
+    const int g = grid_for(n, 256);
+    k_root_flag<<<g, 256, 0, s>>>(n, state, rootid.p);
+    CK_LAUNCH();
+    int nagg = (int)scan_exclusive(rootid.p, rootid.p, n, sc, s);
+    k_phase1<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, rootid.p, ph1.p);
+    CK(cudaMemsetAsync(sc.flags.p + 5, 0, sizeof(int), s));
+    k_phase2<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, S.v.p, ph1.p, agg, sc.flags.p + 5);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(sc.h_flags + 5, sc.flags.p + 5, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return sc.h_flags[5] ? -1 : nagg;
+}
+
+// ==========================================================================================
+// Filtered matrix (compact: diagonal + strong entries, dropped entries lumped on the diagonal)
+// ==========================================================================================
+__global__ void k_filter_count(int n, const int *rp, const int *ci, const uint8_t *strong, int *cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int e = rp[i]; e < rp[i + 1]; e++) c += (ci[e] == i) || strong[e];
+        cnt[i] = c;
+    }
+}
+__global__ void k_filter_fill(int n, const int *rp, const int *ci, const double *v, const uint8_t *strong,
+                              const int *frp, int *fci, double *fv, double *dinvF, int filter_diag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double lump = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; e++)
+            if (ci[e] != i && !strong[e]) lump += v[e];
+        int q = frp[i];
+        double dg = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; e++) {
+            if (ci[e] == i) {
+                fci[q] = i;
+                fv[q] = v[e] + lump;
+                dg = fv[q];
+                q++;
+            } else if (strong[e]) {
+                fci[q] = ci[e];
+                fv[q] = v[e];
+                q++;
+            }
+        }
+        if (filter_diag) {
+            double sabs = 0.0;
+            for (int t = frp[i]; t < q; t++) sabs += fabs(fv[t]);
+            dg = sabs;
+        }
+        dinvF[i] = 1.0 / dg;
+    }
+}
+
+// ==========================================================================================
+// Power iteration: lambda_max(D^-1 A), start v0_i = ((fmix32(i ^ 0x7F4A7C15) >> 8) + 0.5) / 2^24
+// ==========================================================================================
+__global__ void k_power_start(int n, double *v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t u = fmix32((uint32_t)i ^ 0x7F4A7C15u) >> 8;
+        v[i] = ((double)u + 0.5) / 16777216.0;
+    }
+}
+
+static double power_lambda(const CsrView &A, const double *dinv, int iters, Scratch &sc, cudaStream_t s) {
+    const int n = A.n;
+    DBuf<double> v((size_t)n, s), w((size_t)n, s);
+    k_power_start<<<grid_for(n, 256), 256, 0, s>>>(n, v.p);
+    CK_LAUNCH();
+    dev_dot(v.p, v.p, n, sc.scal.p, sc, s);
+    scale_by_inv_dev(v.p, sc.scal.p, v.p, n, true, s);
+    for (int it = 0; it < iters; it++) {
+        spmv_scaled(A, dinv, v.p, w.p, s);
+        dev_dot(w.p, w.p, n, sc.scal.p + 1, sc, s);
+        scale_by_inv_dev(w.p, sc.scal.p + 1, v.p, n, true, s);
+    }
+    CK(cudaMemcpyAsync(sc.h_scal + 1, sc.scal.p + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return std::sqrt(sc.h_scal[1]);
+}
+
+// ==========================================================================================
+// Hash SpGEMM C = A B (two passes; warp per row; shared-memory tables, global tables for big rows)
+// ==========================================================================================
+constexpr int SG_WARPS = 8;
+constexpr int SG_SYM_T = 2048;
+constexpr int SG_NUM_T = 1024;
+
+__device__ __forceinline__ unsigned nextpow2u(unsigned x) {
+    x = x < 2 ? 2 : x;
+    return 1u << (32 - __clz(x - 1));
+}
+
+__device__ __forceinline__ int tbl_insert(int *keys, unsigned mask, int col, bool &ins) {
+    unsigned h = ((unsigned)col * 2654435761u) & mask;
+    for (unsigned t = 0; t <= mask; t++) {
+        int k = ((volatile int *)keys)[h];
+        if (k == col) { ins = false; return (int)h; }
+        if (k == -1) {
+            int old = atomicCAS(&keys[h], -1, col);
+            if (old == -1) { ins = true; return (int)h; }
+            if (old == col) { ins = false; return (int)h; }
+        }
+        h = (h + 1) & mask;
+    }
+    ins = false;
+    return -1;
+}
+
+__global__ void k_sg_ub(int n, const int *arp, const int *aci, const int *brp, int *ub) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        long long u = 0;
+        for (int e = arp[i]; e < arp[i + 1]; e++) u += brp[aci[e] + 1] - brp[aci[e]];
+        ub[i] = (int)(u > 0x3fffffff ? 0x3fffffff : u);
+    }
+}
+
+// symbolic: distinct column count per row; rows that overflow the shared table get -1
+__global__ void __launch_bounds__(SG_WARPS * 32) k_sg_sym(int n, const int *arp, const int *aci, const int *brp,
+                                                          const int *bci, const int *ub, int *cnt) {
+    extern __shared__ int sg_smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *keys = sg_smem + wib * SG_SYM_T;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+        const int u = ub[row];
+        if (u == 0) {
+            if (lane == 0) cnt[row] = 0;
+            continue;
+        }
+        const unsigned T = min((unsigned)SG_SYM_T, nextpow2u(2u * (unsigned)u));
+        const unsigned mask = T - 1;
+        for (unsigned t = lane; t < T; t += 32) keys[t] = -1;
+        __syncwarp();
+        int mine = 0, total = 0;
+        bool over = false;
+        for (int e = arp[row]; e < arp[row + 1]; e++) {
+            const int k = aci[e];
+            for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) {
+                bool ins;
+                if (tbl_insert(keys, mask, bci[f], ins) < 0) over = true;
+                mine += ins;
+            }
+            __syncwarp();
+            total = __reduce_add_sync(0xffffffffu, mine);
+            over = __any_sync(0xffffffffu, over);
+            if (over || (T == SG_SYM_T && total > (int)(T / 2))) {
+                over = true;
+                break;
+            }
+        }
+        if (lane == 0) cnt[row] = over ? -1 : total;
+        __syncwarp();
+    }
+}
+
+// symbolic for big rows: global table per row
+__global__ void k_sg_sym_big(int nbig, const int *rows, const long long *toff, int *gkeys, const int *arp,
+                             const int *aci, const int *brp, const int *bci, int *cnt) {
+    const int lane = threadIdx.x & 31;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbig; b += (gridDim.x * blockDim.x) >> 5) {
+        const int row = rows[b];
+        int *keys = gkeys + toff[b];
+        const unsigned T = (unsigned)(toff[b + 1] - toff[b]);
+        const unsigned mask = T - 1;
+        for (unsigned t = lane; t < T; t += 32) keys[t] = -1;
+        __syncwarp();
+        int mine = 0;
+        for (int e = arp[row]; e < arp[row + 1]; e++) {
+            const int k = aci[e];
+            for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) {
+                bool ins;
+                tbl_insert(keys, mask, bci[f], ins);
+                mine += ins;
+            }
+            __syncwarp();
+        }
+        int total = __reduce_add_sync(0xffffffffu, mine);
+        if (lane == 0) cnt[row] = total;
+    }
+}
+
+// numeric accumulate + in-place compaction + rank sort into the output row
+__device__ void sg_numeric_row(int row, int *keys, double *vals, unsigned T, const int *arp, const int *aci,
+                               const double *av, const int *brp, const int *bci, const double *bv, const int *crp,
+                               int *cci, double *cv) {
+    const int lane = threadIdx.x & 31;
+    const unsigned mask = T - 1;
+    for (unsigned t = lane; t < T; t += 32) {
+        keys[t] = -1;
+        vals[t] = 0.0;
+    }
+    __syncwarp();
+    for (int e = arp[row]; e < arp[row + 1]; e++) {
+        const int k = aci[e];
+        const double a = av[e];
+        for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) {
+            bool ins;
+            const int sl = tbl_insert(keys, mask, bci[f], ins);
+            vals[sl] = __dadd_rn(vals[sl], __dmul_rn(a, bv[f]));
+        }
+        __syncwarp();
+    }
+    int wpos = 0;
+    for (unsigned base = 0; base < T; base += 32) {
+        const unsigned sl = base + lane;
+        const int k = sl < T ? keys[sl] : -1;
+        const double v = sl < T ? vals[sl] : 0.0;
+        const unsigned bal = __ballot_sync(0xffffffffu, k != -1);
+        const int pos = wpos + __popc(bal & ((1u << lane) - 1u));
+        __syncwarp();
+        if (k != -1) {
+            keys[pos] = k;
+            vals[pos] = v;
+        }
+        wpos += __popc(bal);
+        __syncwarp();
+    }
+    const int c = wpos;
+    const int out = crp[row];
+    for (int t = lane; t < c; t += 32) {
+        const int kt = keys[t];
+        int rank = 0;
+        for (int q = 0; q < c; q++) rank += keys[q] < kt;
+        cci[out + rank] = kt;
+        cv[out + rank] = vals[t];
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *arp, const int *aci, const double *av,
+                                                          const int *brp, const int *bci, const double *bv,
+                                                          const int *crp, int *cci, double *cv) {
+    extern __shared__ double sg_nsm[];
+    const int wib = threadIdx.x >> 5;
+    double *vals = sg_nsm + wib * SG_NUM_T;
+    int *keys = (int *)(sg_nsm + SG_WARPS * SG_NUM_T) + wib * SG_NUM_T;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+        const int c = crp[row + 1] - crp[row];
+        if (c == 0 || c > SG_NUM_T / 2) continue;
+        const unsigned T = nextpow2u(2u * (unsigned)c);
+        sg_numeric_row(row, keys, vals, T, arp, aci, av, brp, bci, bv, crp, cci, cv);
+    }
+}
+
+__global__ void k_sg_num_big(int nbig, const int *rows, const long long *toff, int *gkeys, double *gvals,
+                             const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
+                             const double *bv, const int *crp, int *cci, double *cv) {
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbig; b += (gridDim.x * blockDim.x) >> 5) {
+        const unsigned T = (unsigned)(toff[b + 1] - toff[b]);
+        sg_numeric_row(rows[b], gkeys + toff[b], gvals + toff[b], T, arp, aci, av, brp, bci, bv, crp, cci, cv);
+    }
+}
+
+__global__ void k_big_mark(int n, const int *cnt, int limit, int *flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flag[i] = (cnt[i] < 0 || cnt[i] > limit) ? 1 : 0;
+}
+__global__ void k_big_list(int n, const int *flag, const int *pos, int *rows) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (flag[i]) rows[pos[i]] = i;
+}
+// table sizes nextpow2(2 * size) for the big rows (size = ub for symbolic, cnt for numeric)
+__global__ void k_big_tsize(int nbig, const int *rows, const int *size, long long *toff) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbig; b += gridDim.x * blockDim.x) {
+        unsigned s = (unsigned)size[rows[b]];
+        unsigned t = 2;
+        while (t < 2u * s) t <<= 1;
+        toff[b] = (long long)t;
+    }
+}
+__global__ void k_ll_excl_scan_small(long long *a, int n) {
+    // n is small (number of big rows); one thread
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        long long s = 0;
+        for (int i = 0; i < n; i++) {
+            long long t = a[i];
+            a[i] = s;
+            s += t;
+        }
+        a[n] = s;
+    }
+}
+
+static int collect_big(int n, const int *cnt, int limit, DBuf<int> &rows, Scratch &sc, cudaStream_t s) {
+    DBuf<int> flag((size_t)n + 1, s);
+    k_big_mark<<<grid_for(n, 256), 256, 0, s>>>(n, cnt, limit, flag.p);
+    CK_LAUNCH();
+    DBuf<int> pos((size_t)n + 1, s);
+    int nbig = (int)scan_exclusive(flag.p, pos.p, n, sc, s);
+    rows.alloc((size_t)std::max(nbig, 1), s);
+    if (nbig) {
+        k_big_list<<<grid_for(n, 256), 256, 0, s>>>(n, flag.p, pos.p, rows.p);
+        CK_LAUNCH();
+    }
+    return nbig;
+}
+
+static long long big_tables(int nbig, const int *rows, const int *size, DBuf<long long> &toff, cudaStream_t s) {
+    toff.alloc((size_t)nbig + 1, s);
+    k_big_tsize<<<grid_for(nbig, 256), 256, 0, s>>>(nbig, rows, size, toff.p);
+    CK_LAUNCH();
+    if (nbig > 100000) throw Error(BGS_INTERNAL, "too many long SpGEMM rows");
+    k_ll_excl_scan_small<<<1, 1, 0, s>>>(toff.p, nbig);
+    CK_LAUNCH();
+    long long total = 0;
+    CK(cudaMemcpyAsync(&total, toff.p + nbig, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return total;
+}
+
+__global__ void k_row_lengths(int n, const int *rp, int *len) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) len[i] = rp[i + 1] - rp[i];
+}
+
+static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cudaStream_t s) {
+    const int n = A.n;
+    C.n = n;
+    C.m = B.m;
+    C.rp.alloc((size_t)n + 1, s);
+    if (n == 0) {
+        C.nnz = 0;
+        CK(cudaMemsetAsync(C.rp.p, 0, sizeof(int), s));
+        return;
+    }
+    DBuf<int> ub((size_t)n, s);
+    k_sg_ub<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, ub.p);
+    CK_LAUNCH();
+    const int blocks = grid_for((int64_t)n * 32, SG_WARPS * 32, kSMs * 8);
+    const size_t sym_smem = sizeof(int) * SG_WARPS * SG_SYM_T;
+    k_sg_sym<<<blocks, SG_WARPS * 32, sym_smem, s>>>(n, A.rp, A.ci, B.rp, B.ci, ub.p, C.rp.p);
+    CK_LAUNCH();
+    // rows whose distinct count overflowed the shared table
+    {
+        DBuf<int> rows;
+        int nbig = collect_big(n, C.rp.p, 1 << 30, rows, sc, s);
+        if (nbig) {
+            DBuf<long long> toff;
+            long long tot = big_tables(nbig, rows.p, ub.p, toff, s);
+            DBuf<int> gk((size_t)tot, s);
+            k_sg_sym_big<<<grid_for((int64_t)nbig * 32, 256), 256, 0, s>>>(nbig, rows.p, toff.p, gk.p, A.rp, A.ci,
+                                                                            B.rp, B.ci, C.rp.p);
+            CK_LAUNCH();
+        }
+    }
+    C.nnz = scan_exclusive(C.rp.p, C.rp.p, n, sc, s);
+    C.ci.alloc((size_t)C.nnz, s);
+    C.v.alloc((size_t)C.nnz, s);
+    const size_t num_smem = (sizeof(double) + sizeof(int)) * SG_WARPS * SG_NUM_T;
+    k_sg_num<<<blocks, SG_WARPS * 32, num_smem, s>>>(n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p);
+    CK_LAUNCH();
+    // rows too long for the shared table
+    {
+        DBuf<int> cnt((size_t)n, s), rows;
+        k_row_lengths<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp.p, cnt.p);
+        CK_LAUNCH();
+        int nbig = collect_big(n, cnt.p, SG_NUM_T / 2, rows, sc, s);
+        if (nbig) {
+            DBuf<long long> toff;
+            long long tot = big_tables(nbig, rows.p, cnt.p, toff, s);
+            DBuf<int> gk((size_t)tot, s);
+            DBuf<double> gv((size_t)tot, s);
+            k_sg_num_big<<<grid_for((int64_t)nbig * 32, 256), 256, 0, s>>>(
+                nbig, rows.p, toff.p, gk.p, gv.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p);
+            CK_LAUNCH();
+        }
+    }
+}
+
+
+// ==========================================================================================
+// Prolongator: P_tent (iota, agg, 1) and the damped smoothing transform
+// ==========================================================================================
+__global__ void k_ptent(int n, const int *agg, int *rp, int *ci, double *v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
+        rp[i] = i;
+        if (i < n) {
+            ci[i] = agg[i];
+            v[i] = 1.0;
+        }
+    }
+}
+// p_iJ = [J == agg(i)] - (omega * dinvF_i) * s_iJ
+__global__ void k_psmooth(int n, const int *rp, const int *ci, double *v, const int *agg, const double *dinvF,
+                          double omega) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double c = omega * dinvF[i];
+        const int a = agg[i];
+        for (int e = rp[i]; e < rp[i + 1]; e++) {
+            const double t = ci[e] == a ? 1.0 : 0.0;
+            v[e] = t - __dmul_rn(c, v[e]);
+        }
+    }
+}
+
+// ==========================================================================================
+// Coarsest level: dense LU with partial pivoting (column-major), explicit inverse (row-major)
+// ==========================================================================================
+__global__ void k_to_dense_cm(int n, const int *rp, const int *ci, const double *v, double *a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int e = rp[i]; e < rp[i + 1]; e++) a[(size_t)ci[e] * n + i] = v[e];
+}
+
+constexpr int LU_NB = 32;
+constexpr int LU_T = 1024;
+
+__global__ void __launch_bounds__(LU_T) k_lu_panel(double *a, int n, int k0, int nb, int *piv, int *status) {
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    __shared__ int sp;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int j = k0; j < k0 + nb; j++) {
+        double *colj = a + (size_t)j * n;
+        double best = -1.0;
+        int bi = n;
+        for (int i = j + tid; i < n; i += LU_T) {
+            double t = fabs(colj[i]);
+            if (t > best) { best = t; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { sv[w] = best; si[w] = bi; }
+        __syncthreads();
+        if (w == 0) {
+            best = sv[lane];
+            bi = si[lane];
+            for (int o = 16; o > 0; o >>= 1) {
+                double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                sp = bi;
+                piv[j] = bi;
+                if (!(best > 0.0)) *status = 1;
+            }
+        }
+        __syncthreads();
+        const int p = sp;
+        if (p != j)
+            for (int c = k0 + tid; c < k0 + nb; c += LU_T) {
+                double t = a[(size_t)c * n + j];
+                a[(size_t)c * n + j] = a[(size_t)c * n + p];
+                a[(size_t)c * n + p] = t;
+            }
+        __syncthreads();
+        const double pivot = colj[j];
+        if (pivot != 0.0)
+            for (int i = j + 1 + tid; i < n; i += LU_T) colj[i] = colj[i] / pivot;
+        __syncthreads();
+        const int ncols = k0 + nb - (j + 1);
+        const int nrows = n - (j + 1);
+        for (int64_t t = tid; t < (int64_t)ncols * nrows; t += LU_T) {
+            const int c = j + 1 + (int)(t / nrows);
+            const int i = j + 1 + (int)(t % nrows);
+            a[(size_t)c * n + i] -= colj[i] * a[(size_t)c * n + j];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_lu_swap(double *a, int n, int k0, int nb, const int *piv) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        if (c >= k0 && c < k0 + nb) continue;
+        double *col = a + (size_t)c * n;
+        for (int j = k0; j < k0 + nb; j++) {
+            int p = piv[j];
+            if (p != j) {
+                double t = col[j];
+                col[j] = col[p];
+                col[p] = t;
+            }
+        }
+    }
+}
+
+__global__ void k_lu_trsm(double *a, int n, int k0, int nb) {
+    __shared__ double L[LU_NB][LU_NB];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        int r = t % nb, c = t / nb;
+        L[r][c] = a[(size_t)(k0 + c) * n + (k0 + r)];
+    }
+    __syncthreads();
+    for (int c = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        double *col = a + (size_t)c * n + k0;
+        double x[LU_NB];
+        for (int r = 0; r < nb; r++) x[r] = col[r];
+        for (int r = 0; r < nb; r++) {
+            double s = x[r];
+            for (int t = 0; t < r; t++) s -= L[r][t] * x[t];
+            x[r] = s;
+        }
+        for (int r = 0; r < nb; r++) col[r] = x[r];
+    }
+}
+
+// A22 -= L21 U12: 64 x 64 output tiles, 256 threads each computing 4 x 4
+__global__ void __launch_bounds__(256) k_lu_gemm(double *a, int n, int k0, int nb) {
+    __shared__ double Ls[64][LU_NB + 1];
+    __shared__ double Us[LU_NB][64 + 1];
+    const int r0 = k0 + nb + blockIdx.x * 64, c0 = k0 + nb + blockIdx.y * 64;
+    for (int t = threadIdx.x; t < 64 * nb; t += 256) {
+        int r = t % 64, k = t / 64;
+        Ls[r][k] = (r0 + r < n) ? a[(size_t)(k0 + k) * n + r0 + r] : 0.0;
+    }
+    for (int t = threadIdx.x; t < 64 * nb; t += 256) {
+        int k = t % nb, c = t / nb;
+        Us[k][c] = (c0 + c < n) ? a[(size_t)(c0 + c) * n + k0 + k] : 0.0;
+    }
+    __syncthreads();
+    const int tr = (threadIdx.x % 16) * 4, tc = (threadIdx.x / 16) * 4;
+    double acc[4][4] = {};
+    for (int k = 0; k < nb; k++) {
+        double lv[4], uv[4];
+        for (int q = 0; q < 4; q++) { lv[q] = Ls[tr + q][k]; uv[q] = Us[k][tc + q]; }
+        for (int p = 0; p < 4; p++)
+            for (int q = 0; q < 4; q++) acc[p][q] += lv[p] * uv[q];
+    }
+    for (int q = 0; q < 4; q++) {
+        const int c = c0 + tc + q;
+        if (c >= n) continue;
+        for (int p = 0; p < 4; p++) {
+            const int r = r0 + tr + p;
+            if (r < n) a[(size_t)c * n + r] -= acc[p][q];
+        }
+    }
+}
+
+// one block per column c of the inverse: x = U^-1 L^-1 P e_c, written to row-major W[i][c]
+__global__ void k_lu_inverse(const double *a, const int *piv, int n, double *W) {
+    extern __shared__ double xs[];
+    const int c = blockIdx.x;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = (i == c) ? 1.0 : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < n; k++) {
+            int p = piv[k];
+            if (p != k) {
+                double t = xs[k];
+                xs[k] = xs[p];
+                xs[p] = t;
+            }
+        }
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+        const double xj = xs[j];
+        const double *col = a + (size_t)j * n;
+        if (xj != 0.0)
+            for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) xs[i] -= col[i] * xj;
+        __syncthreads();
+    }
+    for (int j = n - 1; j >= 0; j--) {
+        const double *col = a + (size_t)j * n;
+        const double xj = xs[j] / col[j];
+        __syncthreads();
+        if (threadIdx.x == 0) xs[j] = xj;
+        if (xj != 0.0)
+            for (int i = threadIdx.x; i < j; i += blockDim.x) xs[i] -= col[i] * xj;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) W[(size_t)i * n + c] = xs[i];
+}
+
+static int dense_inverse(const DCsr &Ac, DBuf<double> &W, Scratch &sc, cudaStream_t s) {
+    const int n = Ac.n;
+    DBuf<double> a((size_t)n * n, s);
+    DBuf<int> piv((size_t)n, s);
+    CK(cudaMemsetAsync(a.p, 0, sizeof(double) * (size_t)n * n, s));
+    k_to_dense_cm<<<grid_for(n, 256), 256, 0, s>>>(n, Ac.rp.p, Ac.ci.p, Ac.v.p, a.p);
+    CK_LAUNCH();
+    CK(cudaMemsetAsync(sc.flags.p + 6, 0, sizeof(int), s));
+    for (int k0 = 0; k0 < n; k0 += LU_NB) {
+        const int nb = std::min(LU_NB, n - k0);
+        k_lu_panel<<<1, LU_T, 0, s>>>(a.p, n, k0, nb, piv.p, sc.flags.p + 6);
+        CK_LAUNCH();
+        k_lu_swap<<<grid_for(n, 256), 256, 0, s>>>(a.p, n, k0, nb, piv.p);
+        CK_LAUNCH();
+        const int rest = n - k0 - nb;
+        if (rest > 0) {
+            k_lu_trsm<<<grid_for(rest, 128), 128, 0, s>>>(a.p, n, k0, nb);
+            CK_LAUNCH();
+            dim3 g((rest + 63) / 64, (rest + 63) / 64);
+            k_lu_gemm<<<g, 256, 0, s>>>(a.p, n, k0, nb);
+            CK_LAUNCH();
+        }
+    }
+    W.alloc((size_t)n * n, s);
+    const size_t smem = sizeof(double) * (size_t)n;
+    if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_lu_inverse<<<n, 256, smem, s>>>(a.p, piv.p, n, W.p);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(sc.h_flags + 6, sc.flags.p + 6, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return sc.h_flags[6] ? BGS_ZERO_PIVOT : BGS_OK;
+}
+
+__global__ void k_dense_transpose(int n, const double *in, double *out) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n), j = (int)(t % n);
+        out[(size_t)j * n + i] = in[t];
+    }
+}
+
+void Hier::build_inv_T(cudaStream_t s) {
+    invT.alloc((size_t)nc * nc, s);
+    if (nc > 0) {
+        k_dense_transpose<<<grid_for((int64_t)nc * nc, 256), 256, 0, s>>>(nc, inv.p, invT.p);
+        CK_LAUNCH();
+    }
+}
+
+// ==========================================================================================
+// Hierarchy construction
+// ==========================================================================================
+void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
+    static bool attrs = false;
+    if (!attrs) {
+        CK(cudaFuncSetAttribute(k_sg_sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(int) * SG_WARPS * SG_SYM_T)));
+        CK(cudaFuncSetAttribute(k_sg_num, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((sizeof(double) + sizeof(int)) * SG_WARPS * SG_NUM_T)));
+        attrs = true;
+    }
+    H.degree = p.degree;
+    H.L.reserve(32);
+    const double t2 = p.theta * p.theta;
+    for (int l = 0;; l++) {
+        Level &Lv = H.L[l];
+        DCsr &A = Lv.A;
+        const int n = A.n;
+        if (n <= p.max_coarse || l + 1 >= p.max_levels) break;
+        DBuf<double> diag((size_t)n, s);
+        extract_diag(view(A), diag.p, s);
+        DBuf<uint8_t> strong((size_t)std::max<int64_t>(A.nnz, 1), s);
+        CK(cudaMemsetAsync(sc.flags.p + 7, 0, sizeof(int), s));
+        k_strength<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, diag.p, t2, strong.p, sc.flags.p + 7);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(sc.h_flags + 7, sc.flags.p + 7, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const int sflags = sc.h_flags[7];
+        if (sflags & 2) throw Error(BGS_ZERO_PIVOT, "zero diagonal entry in a level operator");
+        DCsr S;
+        strength_graph(view(A), strong.p, (sflags & 1) != 0, S, sc, s);
+        DBuf<int> state((size_t)n, s);
+        const uint32_t salt = (uint32_t)l * 0x9E3779B9u;
+        const int rounds = mis2(S, salt, state.p, sc, s);
+        DBuf<int> agg((size_t)n, s);
+        const int nagg = aggregate(S, state.p, agg.p, sc, s);
+        if (nagg < 0) throw Error(BGS_INTERNAL, "aggregation left a node unassigned");
+        if ((long long)nagg * 10 > (long long)n * 9) break;   // coarsening stalled
+        // filtered matrix and its smoothing diagonal
+        DCsr AF;
+        AF.n = AF.m = n;
+        AF.rp.alloc((size_t)n + 1, s);
+        k_filter_count<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, strong.p, AF.rp.p);
+        CK_LAUNCH();
+        AF.nnz = scan_exclusive(AF.rp.p, AF.rp.p, n, sc, s);
+        AF.ci.alloc((size_t)AF.nnz, s);
+        AF.v.alloc((size_t)AF.nnz, s);
+        DBuf<double> dinvF((size_t)n, s);
+        k_filter_fill<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, strong.p, AF.rp.p, AF.ci.p, AF.v.p,
+                                                       dinvF.p, p.filter_diag);
+        CK_LAUNCH();
+        const double lamF = power_lambda(view(AF), dinvF.p, p.power_iters, sc, s);
+        const double omega = (4.0 / 3.0) / lamF;
+        // P = P_tent - omega D_F^-1 A_F P_tent
+        DCsr Pt;
+        Pt.n = n;
+        Pt.m = nagg;
+        Pt.nnz = n;
+        Pt.rp.alloc((size_t)n + 1, s);
+        Pt.ci.alloc((size_t)n, s);
+        Pt.v.alloc((size_t)n, s);
+        k_ptent<<<grid_for(n + 1, 256), 256, 0, s>>>(n, agg.p, Pt.rp.p, Pt.ci.p, Pt.v.p);
+        CK_LAUNCH();
+        spgemm(view(AF), view(Pt), Lv.P, sc, s);
+        k_psmooth<<<grid_for(n, 256), 256, 0, s>>>(n, Lv.P.rp.p, Lv.P.ci.p, Lv.P.v.p, agg.p, dinvF.p, omega);
+        CK_LAUNCH();
+        transpose_csr(view(Lv.P), Lv.R, sc, s);
+        DCsr AP;
+        spgemm(view(A), view(Lv.P), AP, sc, s);
+        H.L.emplace_back();
+        Level &Lv2 = H.L[l];
+        spgemm(view(Lv2.R), view(AP), H.L[l + 1].A, sc, s);
+        Lv2.agg = std::move(agg);
+        Lv2.nagg = nagg;
+        Lv2.mis_rounds = rounds;
+        Lv2.omega = omega;
+    }
+    // Chebyshev bounds on every level above the coarsest
+    for (size_t k = 0; k + 1 < H.L.size(); k++) {
+        Level &Lv = H.L[k];
+        const int n = Lv.A.n;
+        DBuf<double> diag((size_t)n, s);
+        extract_diag(view(Lv.A), diag.p, s);
+        Lv.dinv.alloc((size_t)n, s);
+        reciprocal(diag.p, Lv.dinv.p, n, s);
+        const double lam = power_lambda(view(Lv.A), Lv.dinv.p, p.power_iters, sc, s);
+        Lv.lmax = p.cheb_boost * lam;
+        Lv.lmin = Lv.lmax / p.cheb_ratio;
+    }
+    H.nc = H.L.back().A.n;
+    H.status = dense_inverse(H.L.back().A, H.inv, sc, s);
+}
+
+}  // namespace bgs

@@ -1,0 +1,860 @@
+// C ABI of libbgs: block operator (Sec. 2.2, Eq. block-splitting), SA-AMG setup per diagonal
+// block (Sec. 2.2.1), the forward block Gauss-Seidel sweep (Eqs. hierarchical-bgs, non-voltage-bgs,
+// voltage-bgs) and flexible GMRES (Sec. 2.2) with CGS2 Arnoldi on the device.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <cstdlib>
+#include <memory>
+#include <type_traits>
+
+#include "internal.h"
+
+using namespace bgs;
+
+namespace {
+
+struct KStats {
+    int64_t launches = 0;
+    double ms = 0.0, bytes = 0.0;
+};
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int cls = 0;
+    double bytes = 0.0;
+};
+
+}  // namespace
+
+struct bgs_ctx {
+    cudaStream_t s = nullptr;
+    int F = 0;
+    int64_t sizes[8] = {}, offs[9] = {};
+    int order[8] = {}, pos[8] = {};
+    bgs_options opt{};
+    std::vector<DCsr> blk;          // F*F input copies (n == 0: zero block)
+    DCsr full, fullT;
+    DCsr lower[8], upperT[8];
+    Hier H[8];
+    bool setup_done = false, adjoint_ready = false;
+    Scratch sc;
+    DBuf<double> V, Z, w, r, x, bvec, hdev;
+    double t_setup_ms = 0.0;
+    // profiling
+    bool prof = false;
+    std::vector<EventPair> ev;
+    size_t ev_used = 0;
+    KStats stats[4];
+};
+
+namespace {
+
+int64_t total_n(const bgs_ctx *h) { return h->offs[h->F]; }
+
+// ------------------------------------------------------------------ profiling helpers
+struct Prof {
+    bgs_ctx *h;
+    EventPair *p = nullptr;
+    Prof(bgs_ctx *hh, int cls, double bytes) : h(hh) {
+        if (!h->prof) return;
+        if (h->ev_used == h->ev.size()) {
+            EventPair e;
+            CK(cudaEventCreate(&e.a));
+            CK(cudaEventCreate(&e.b));
+            h->ev.push_back(e);
+        }
+        p = &h->ev[h->ev_used++];
+        p->cls = cls;
+        p->bytes = bytes;
+        CK(cudaEventRecord(p->a, h->s));
+    }
+    ~Prof() {
+        if (p) cudaEventRecord(p->b, h->s);
+    }
+};
+
+void prof_collect(bgs_ctx *h) {
+    if (!h->prof) return;
+    CK(cudaStreamSynchronize(h->s));
+    for (size_t i = 0; i < h->ev_used; i++) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->ev[i].a, h->ev[i].b));
+        KStats &k = h->stats[h->ev[i].cls];
+        k.launches++;
+        k.ms += ms;
+        k.bytes += h->ev[i].bytes;
+    }
+    h->ev_used = 0;
+}
+
+double spmv_bytes(const DCsr &A, int vbytes, int xbytes, int extra_vectors) {
+    return (double)A.nnz * (vbytes + 4) + 4.0 * (A.n + 1) + (double)xbytes * A.n * (2 + extra_vectors);
+}
+
+// ------------------------------------------------------------------ typed buffer access
+template <class XT>
+struct Buf;
+template <>
+struct Buf<double> {
+    static double *b(Level &L) { return L.b.p; }
+    static double *x0(Level &L) { return L.x0.p; }
+    static double *x1(Level &L) { return L.x1.p; }
+    static double *d(Level &L) { return L.d.p; }
+    static double *r(Level &L) { return L.r.p; }
+    static const double *dinv(Level &L) { return L.dinv.p; }
+    static void alloc(Level &L, int n, cudaStream_t s) {
+        L.b.alloc(n, s); L.x0.alloc(n, s); L.x1.alloc(n, s); L.d.alloc(n, s); L.r.alloc(n, s);
+    }
+};
+template <>
+struct Buf<float> {
+    static float *b(Level &L) { return L.fb.p; }
+    static float *x0(Level &L) { return L.fx0.p; }
+    static float *x1(Level &L) { return L.fx1.p; }
+    static float *d(Level &L) { return L.fd.p; }
+    static float *r(Level &L) { return L.fr.p; }
+    static const float *dinv(Level &L) { return L.dinvf.p; }
+    static void alloc(Level &L, int n, cudaStream_t s) {
+        L.fb.alloc(n, s); L.fx0.alloc(n, s); L.fx1.alloc(n, s); L.fd.alloc(n, s); L.fr.alloc(n, s);
+    }
+};
+template <class VT>
+const VT *vals(const DCsr &A);
+template <>
+const double *vals<double>(const DCsr &A) { return A.v.p; }
+template <>
+const float *vals<float>(const DCsr &A) { return A.vf.p; }
+
+// ------------------------------------------------------------------ V-cycle (Sec. 2.2.1)
+template <class VT, class XT>
+XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
+    cudaStream_t s = h->s;
+    Level &Lv = H.L[l];
+    const int n = Lv.A.n;
+    XT *b = Buf<XT>::b(Lv), *x0 = Buf<XT>::x0(Lv), *x1 = Buf<XT>::x1(Lv), *d = Buf<XT>::d(Lv),
+       *r = Buf<XT>::r(Lv);
+    if (l == (int)H.L.size() - 1) {
+        dense_gemv<XT>(n, transposed ? H.inv_T().p : H.inv.p, b, x0, false, s);
+        return x0;
+    }
+    const DCsr &A = transposed ? Lv.AT : Lv.A;
+    const VT *av = vals<VT>(A);
+    const XT *dinv = Buf<XT>::dinv(Lv);
+    const double theta = (Lv.lmax + Lv.lmin) / 2.0, delta = (Lv.lmax - Lv.lmin) / 2.0;
+    const double sigma = theta / delta, inv_theta = 1.0 / theta;
+    const int deg = H.degree;
+    const int vb = sizeof(VT), xb = sizeof(XT);
+    const double cbytes = spmv_bytes(A, vb, xb, 4);
+    // pre-smoothing from x = 0
+    cheb_first<XT>(n, b, dinv, inv_theta, x0, d, s);
+    XT *cur = x0, *oth = x1;
+    double rho = 1.0 / sigma;
+    for (int k = 1; k < deg; k++) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        Prof pf(h, 1, cbytes);
+        cheb_step<VT, XT>(A, av, b, dinv, cur, oth, d, rn * rho, 2.0 * rn / delta, false, s);
+        std::swap(cur, oth);
+        rho = rn;
+    }
+    // residual, restriction, coarse correction, prolongation
+    spmv_resid<VT, XT>(A, av, b, cur, r, s);
+    Level &C = H.L[l + 1];
+    spmv_store<VT, XT>(Lv.R, vals<VT>(Lv.R), r, Buf<XT>::b(C), s);
+    XT *xc = vcycle<VT, XT>(h, H, l + 1, transposed);
+    spmv_addto<VT, XT>(Lv.P, vals<VT>(Lv.P), xc, cur, s);
+    // post-smoothing
+    rho = 1.0 / sigma;
+    {
+        Prof pf(h, 1, cbytes);
+        cheb_step<VT, XT>(A, av, b, dinv, cur, oth, d, 0.0, inv_theta, true, s);
+    }
+    std::swap(cur, oth);
+    for (int k = 1; k < deg; k++) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        Prof pf(h, 1, cbytes);
+        cheb_step<VT, XT>(A, av, b, dinv, cur, oth, d, rn * rho, 2.0 * rn / delta, false, s);
+        std::swap(cur, oth);
+        rho = rn;
+    }
+    return cur;
+}
+
+template <class XT>
+void copy_in(const double *src, XT *dst, int64_t n, cudaStream_t s);
+template <>
+void copy_in<double>(const double *src, double *dst, int64_t n, cudaStream_t s) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+}
+template <>
+void copy_in<float>(const double *src, float *dst, int64_t n, cudaStream_t s) { copy_d2f(src, dst, n, s); }
+template <class XT>
+void copy_out(const XT *src, double *dst, int64_t n, cudaStream_t s);
+template <>
+void copy_out<double>(const double *src, double *dst, int64_t n, cudaStream_t s) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+}
+template <>
+void copy_out<float>(const float *src, double *dst, int64_t n, cudaStream_t s) { copy_f2d(src, dst, n, s); }
+
+// ------------------------------------------------------------------ block Gauss-Seidel sweep
+template <class VT, class XT, class CVT>
+void sweep(bgs_ctx *h, const double *v, double *z, bool transposed) {
+    cudaStream_t s = h->s;
+    for (int p = 0; p < h->F; p++) {
+        const int k = transposed ? h->order[h->F - 1 - p] : h->order[p];
+        Hier &H = h->H[k];
+        Level &L0 = H.L[0];
+        const int64_t nk = h->sizes[k];
+        XT *b0 = Buf<XT>::b(L0);
+        const DCsr &C = transposed ? h->upperT[k] : h->lower[k];
+        if (C.nnz > 0) {
+            Prof pf(h, 3, spmv_bytes(C, sizeof(CVT), 8, 1));
+            const CVT *cv;
+            if constexpr (std::is_same<CVT, double>::value) cv = C.v.p;
+            else cv = C.vb.p;
+            coupling_sub<CVT, XT>(C, cv, v + h->offs[k], z, b0, s);
+        } else {
+            copy_in<XT>(v + h->offs[k], b0, nk, s);
+        }
+        XT *xk = vcycle<VT, XT>(h, H, 0, transposed);
+        copy_out<XT>(xk, z + h->offs[k], nk, s);
+    }
+}
+
+void apply_prec(bgs_ctx *h, const double *v, double *z, bool transposed) {
+    if (h->opt.precision == 1) sweep<float, float, __nv_bfloat16>(h, v, z, transposed);
+    else sweep<double, double, double>(h, v, z, transposed);
+}
+
+void full_spmv(bgs_ctx *h, const double *x, double *y, bool transposed) {
+    const DCsr &A = transposed ? h->fullT : h->full;
+    Prof pf(h, 0, spmv_bytes(A, 8, 8, 0));
+    spmv_store<double, double>(A, A.v.p, x, y, h->s);
+}
+
+double host_dot(bgs_ctx *h, const double *a, const double *b, int64_t n) {
+    dev_dot(a, b, n, h->sc.scal.p + 8, h->sc, h->s);
+    CK(cudaMemcpyAsync(h->sc.h_scal + 8, h->sc.scal.p + 8, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return h->sc.h_scal[8];
+}
+
+// ------------------------------------------------------------------ FGMRES(m)
+int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
+    cudaStream_t s = h->s;
+    const int64_t n = total_n(h);
+    const int m = h->opt.restart;
+    const double rtol = h->opt.rtol;
+    const int maxit = h->opt.maxit;
+    double *V = h->V.p, *Z = h->Z.p, *w = h->w.p, *r = h->r.p, *x = h->x.p, *b = h->bvec.p;
+    bgs_info inf{};
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    const double bn2 = host_dot(h, b, b, n);
+    const double bnorm = std::sqrt(bn2);
+    if (!std::isfinite(bnorm)) {
+        inf.status = BGS_NAN_INF;
+        if (info) *info = inf;
+        return BGS_NAN_INF;
+    }
+    if (bnorm == 0.0) {
+        inf.converged = 1;
+        inf.status = BGS_OK;
+        if (info) *info = inf;
+        return BGS_OK;
+    }
+    std::vector<double> Hm((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
+    CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    double beta = bnorm, rel = 1.0, est = 1.0;
+    int it = 0, status = BGS_NO_CONVERGENCE, restarts = 0;
+    double *hd = h->hdev.p, *hh = h->sc.h_scal;
+    for (;;) {
+        scale_copy(r, 1.0 / beta, V, n, s);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jend = 0;
+        bool breakdown = false, nan = false;
+        for (int j = 0; j < m; j++) {
+            double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
+            apply_prec(h, vj, zj, adjoint);
+            full_spmv(h, zj, w, adjoint);
+            {
+                Prof pf(h, 2, 8.0 * n * (3.0 * (j + 1) + 5.0));
+                arnoldi_dots(V, n, j + 1, w, n, hd, h->sc, s);
+                arnoldi_update_dots(V, n, j + 1, hd, w, n, hd + 80, h->sc, s);
+                arnoldi_update_norm(V, n, j + 1, hd + 80, w, n, hd + 160, h->sc, s);
+            }
+            CK(cudaMemcpyAsync(hh, hd, sizeof(double) * 161, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int i = 0; i <= j; i++) Hm[(size_t)i * m + j] = hh[i] + hh[80 + i];
+            const double hn = std::sqrt(hh[160]);
+            Hm[(size_t)(j + 1) * m + j] = hn;
+            it++;
+            if (hn == 0.0) breakdown = true;
+            else scale_copy(w, 1.0 / hn, V + (size_t)(j + 1) * n, n, s);
+            for (int i = 0; i < j; i++) {
+                const double a = Hm[(size_t)i * m + j], c = Hm[(size_t)(i + 1) * m + j];
+                Hm[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+                Hm[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            }
+            const double a = Hm[(size_t)j * m + j], c = Hm[(size_t)(j + 1) * m + j];
+            const double den = std::sqrt(a * a + c * c);
+            cs[j] = den == 0.0 ? 1.0 : a / den;
+            sn[j] = den == 0.0 ? 0.0 : c / den;
+            Hm[(size_t)j * m + j] = den;
+            Hm[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            est = std::fabs(g[j + 1]) / bnorm;
+            jend = j + 1;
+            if (!std::isfinite(est)) {
+                nan = true;
+                break;
+            }
+            if (est <= rtol || it >= maxit || breakdown) break;
+        }
+        if (nan) {
+            status = BGS_NAN_INF;
+            break;
+        }
+        for (int i = jend - 1; i >= 0; i--) {
+            double t = g[i];
+            for (int k = i + 1; k < jend; k++) t -= Hm[(size_t)i * m + k] * y[k];
+            y[i] = t / Hm[(size_t)i * m + i];
+        }
+        multi_axpy(Z, n, jend, y.data(), x, n, s);
+        const DCsr &A = adjoint ? h->fullT : h->full;
+        spmv_resid<double, double>(A, A.v.p, b, x, r, s);
+        beta = std::sqrt(host_dot(h, r, r, n));
+        rel = beta / bnorm;
+        if (!std::isfinite(rel)) {
+            status = BGS_NAN_INF;
+            break;
+        }
+        if (rel <= rtol) {
+            status = BGS_OK;
+            break;
+        }
+        if (it >= maxit) {
+            status = BGS_NO_CONVERGENCE;
+            break;
+        }
+        if (breakdown && beta == 0.0) {
+            status = BGS_BREAKDOWN;
+            break;
+        }
+        restarts++;
+    }
+    inf.iters = it;
+    inf.converged = status == BGS_OK;
+    inf.status = status;
+    inf.restarts = restarts;
+    inf.rel_true_resid = rel;
+    inf.rel_est_resid = est;
+    if (info) *info = inf;
+    return status;
+}
+
+// ------------------------------------------------------------------ helpers for create/setup
+void copy_block(const bgs_csr &in, int64_t nr, int64_t nc, DCsr &out, cudaStream_t s) {
+    out.n = (int)nr;
+    out.m = (int)nc;
+    out.nnz = in.nnz;
+    out.rp.alloc((size_t)nr + 1, s);
+    out.ci.alloc((size_t)in.nnz, s);
+    out.v.alloc((size_t)in.nnz, s);
+    CK(cudaMemcpyAsync(out.rp.p, in.rowptr, sizeof(int) * ((size_t)nr + 1), cudaMemcpyDefault, s));
+    if (in.nnz) {
+        CK(cudaMemcpyAsync(out.ci.p, in.col, sizeof(int) * (size_t)in.nnz, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(out.v.p, in.val, sizeof(double) * (size_t)in.nnz, cudaMemcpyDefault, s));
+    }
+}
+
+__global__ void k_shift_rowptr(int n, const int *in, int off, int *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = in[i] + off;
+}
+
+// vertical stack of row blocks into one CSR
+void vstack(const std::vector<DCsr *> &parts, int ncols, DCsr &C, cudaStream_t s) {
+    int64_t n = 0, nnz = 0;
+    for (auto *p : parts) {
+        n += p->n;
+        nnz += p->nnz;
+    }
+    if (nnz >= INT32_MAX) throw Error(BGS_INVALID_ARG, "operator has 2^31 or more entries");
+    C.n = (int)n;
+    C.m = ncols;
+    C.nnz = nnz;
+    C.rp.alloc((size_t)n + 1, s);
+    C.ci.alloc((size_t)nnz, s);
+    C.v.alloc((size_t)nnz, s);
+    int64_t r0 = 0, e0 = 0;
+    for (auto *p : parts) {
+        if (p->n) {
+            k_shift_rowptr<<<grid_for(p->n, 256), 256, 0, s>>>(p->n, p->rp.p, (int)e0, C.rp.p + r0);
+            CK_LAUNCH();
+        }
+        if (p->nnz) {
+            CK(cudaMemcpyAsync(C.ci.p + e0, p->ci.p, sizeof(int) * p->nnz, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(C.v.p + e0, p->v.p, sizeof(double) * p->nnz, cudaMemcpyDeviceToDevice, s));
+        }
+        r0 += p->n;
+        e0 += p->nnz;
+    }
+    int last = (int)nnz;
+    CK(cudaMemcpyAsync(C.rp.p + n, &last, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+}
+
+void build_adjoint(bgs_ctx *h) {
+    if (h->adjoint_ready) return;
+    cudaStream_t s = h->s;
+    transpose_csr(view(h->full), h->fullT, h->sc, s);
+    for (int k = 0; k < h->F; k++) {
+        // rows of field k: sum over pos(j) > pos(k) of A_jk^T (global columns)
+        std::vector<DCsr> tr;
+        std::vector<CsrView> parts;
+        std::vector<int> offs;
+        tr.reserve(h->F);
+        for (int j = 0; j < h->F; j++) {
+            if (h->pos[j] <= h->pos[k]) continue;
+            DCsr &B = h->blk[(size_t)j * h->F + k];
+            if (B.nnz == 0) continue;
+            tr.emplace_back();
+            transpose_csr(view(B), tr.back(), h->sc, s);
+        }
+        size_t t = 0;
+        for (int j = 0; j < h->F; j++) {
+            if (h->pos[j] <= h->pos[k]) continue;
+            DCsr &B = h->blk[(size_t)j * h->F + k];
+            if (B.nnz == 0) continue;
+            parts.push_back(view(tr[t++]));
+            offs.push_back((int)h->offs[j]);
+        }
+        concat_rows((int)h->sizes[k], (int)parts.size(), parts.data(), offs.data(), h->upperT[k], h->sc, s);
+        h->upperT[k].m = (int)total_n(h);
+        if (h->opt.precision == 1 && h->upperT[k].nnz) {
+            h->upperT[k].vb.alloc((size_t)h->upperT[k].nnz, s);
+            convert_d2bf(h->upperT[k].v.p, h->upperT[k].vb.p, h->upperT[k].nnz, s);
+        }
+        Hier &H = h->H[k];
+        for (size_t l = 0; l + 1 < H.L.size(); l++) {
+            transpose_csr(view(H.L[l].A), H.L[l].AT, h->sc, s);
+            if (h->opt.precision == 1) {
+                H.L[l].AT.vf.alloc((size_t)H.L[l].AT.nnz, s);
+                convert_d2f(H.L[l].AT.v.p, H.L[l].AT.vf.p, H.L[l].AT.nnz, s);
+            }
+        }
+        H.build_inv_T(s);
+    }
+    CK(cudaStreamSynchronize(s));
+    h->adjoint_ready = true;
+}
+
+template <class F>
+int guarded(F &&f) {
+    try {
+        return f();
+    } catch (const Error &e) {
+        if (getenv("BGS_VERBOSE")) fprintf(stderr, "libbgs: %s\n", e.what());
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        return BGS_OOM;
+    } catch (...) {
+        return BGS_INTERNAL;
+    }
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+int bgs_default_options(bgs_options *o) {
+    if (!o) return BGS_INVALID_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->restart = 50;
+    o->maxit = 1000;
+    o->rtol = 1e-8;
+    o->precision = 0;
+    o->graph = 0;
+    o->autotune = 0;
+    for (int k = 0; k < 8; k++) {
+        o->cheb_degree[k] = 2;
+        o->theta[k] = 0.0;
+    }
+    o->theta[0] = 0.04;
+    o->cheb_degree[0] = 4;
+    o->cheb_degree[1] = 4;
+    o->max_coarse = 5000;
+    o->max_levels = 10;
+    o->cheb_ratio = 30.0;
+    o->cheb_boost = 1.1;
+    o->power_iters = 10;
+    o->filter_diag = 1;
+    return BGS_OK;
+}
+
+const char *bgs_status_string(int st) {
+    switch (st) {
+        case BGS_OK: return "ok";
+        case BGS_INVALID_ARG: return "invalid argument";
+        case BGS_NOT_SETUP: return "bgs_setup has not run";
+        case BGS_NO_CONVERGENCE: return "no convergence within maxit";
+        case BGS_BREAKDOWN: return "Arnoldi breakdown";
+        case BGS_NAN_INF: return "NaN or Inf encountered";
+        case BGS_ZERO_PIVOT: return "zero pivot in the coarsest LU or a zero diagonal";
+        case BGS_CUDA_ERROR: return "CUDA error";
+        case BGS_OOM: return "device out of memory";
+        case BGS_INTERNAL: return "internal error";
+        default: return "unknown status";
+    }
+}
+
+int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *blocks, const int *order,
+               const bgs_options *opt, void *stream) {
+    if (!out || !sizes || !blocks || !order || F < 1 || F > 8) return BGS_INVALID_ARG;
+    *out = nullptr;
+    bgs_options o;
+    if (opt) o = *opt;
+    else bgs_default_options(&o);
+    if (o.restart < 1 || o.restart > 63 || o.maxit < 1 || !(o.rtol > 0) || o.max_coarse < 1 || o.max_levels < 1 ||
+        o.precision < 0 || o.precision > 1 || o.power_iters < 1 || !(o.cheb_ratio > 1.0) || !(o.cheb_boost > 0))
+        return BGS_INVALID_ARG;
+    // host-side shape checks
+    int seen[8] = {};
+    for (int p = 0; p < F; p++) {
+        if (order[p] < 0 || order[p] >= F || seen[order[p]]) return BGS_INVALID_ARG;
+        seen[order[p]] = 1;
+    }
+    int64_t tot = 0;
+    for (int k = 0; k < F; k++) {
+        if (sizes[k] < 1 || sizes[k] >= INT32_MAX) return BGS_INVALID_ARG;
+        tot += sizes[k];
+        if (o.cheb_degree[k] < 1 || o.theta[k] < 0) return BGS_INVALID_ARG;
+    }
+    if (tot >= INT32_MAX) return BGS_INVALID_ARG;
+    for (int r = 0; r < F; r++)
+        for (int c = 0; c < F; c++) {
+            const bgs_csr &B = blocks[r * F + c];
+            const bool zero = B.nrows == 0 && B.nnz == 0;
+            if (r == c && zero) return BGS_INVALID_ARG;
+            if (zero) continue;
+            if (B.nrows != sizes[r] || B.ncols != sizes[c] || B.nnz < 0 || B.nnz >= INT32_MAX || !B.rowptr)
+                return BGS_INVALID_ARG;
+            if (B.nnz > 0 && (!B.col || !B.val)) return BGS_INVALID_ARG;
+        }
+    std::unique_ptr<bgs_ctx> h(new bgs_ctx());
+    return guarded([&]() -> int {
+        h->s = (cudaStream_t)stream;
+        h->F = F;
+        h->opt = o;
+        h->offs[0] = 0;
+        for (int k = 0; k < F; k++) {
+            h->sizes[k] = sizes[k];
+            h->offs[k + 1] = h->offs[k] + sizes[k];
+            h->order[k] = order[k];
+            h->pos[order[k]] = k;
+        }
+        cudaStream_t s = h->s;
+        h->sc.init(s);
+        h->blk.resize((size_t)F * F);
+        for (int r = 0; r < F; r++)
+            for (int c = 0; c < F; c++) {
+                const bgs_csr &B = blocks[r * F + c];
+                DCsr &D = h->blk[(size_t)r * F + c];
+                if (B.nrows == 0 && B.nnz == 0) {
+                    D.n = (int)sizes[r];
+                    D.m = (int)sizes[c];
+                    D.nnz = 0;
+                    D.rp.alloc((size_t)sizes[r] + 1, s);
+                    CK(cudaMemsetAsync(D.rp.p, 0, sizeof(int) * ((size_t)sizes[r] + 1), s));
+                    continue;
+                }
+                copy_block(B, sizes[r], sizes[c], D, s);
+                int st = validate_csr(view(D), r == c, h->sc, s);
+                if (st) return st;
+            }
+        // full operator, field-blocked rows
+        std::vector<DCsr> rowblocks((size_t)F);
+        for (int r = 0; r < F; r++) {
+            std::vector<CsrView> parts;
+            std::vector<int> offs;
+            for (int c = 0; c < F; c++) {
+                DCsr &B = h->blk[(size_t)r * F + c];
+                if (B.nnz == 0) continue;
+                parts.push_back(view(B));
+                offs.push_back((int)h->offs[c]);
+            }
+            concat_rows((int)sizes[r], (int)parts.size(), parts.data(), offs.data(), rowblocks[r], h->sc, s);
+        }
+        std::vector<DCsr *> rb;
+        for (auto &x : rowblocks) rb.push_back(&x);
+        vstack(rb, (int)tot, h->full, s);
+        rowblocks.clear();
+        // lower couplings per field: blocks (k, j) with pos(j) < pos(k), global columns
+        for (int k = 0; k < F; k++) {
+            std::vector<CsrView> parts;
+            std::vector<int> offs;
+            for (int j = 0; j < F; j++) {
+                if (h->pos[j] >= h->pos[k]) continue;
+                DCsr &B = h->blk[(size_t)k * F + j];
+                if (B.nnz == 0) continue;
+                parts.push_back(view(B));
+                offs.push_back((int)h->offs[j]);
+            }
+            concat_rows((int)sizes[k], (int)parts.size(), parts.data(), offs.data(), h->lower[k], h->sc, s);
+            h->lower[k].m = (int)tot;
+        }
+        CK(cudaStreamSynchronize(s));
+        *out = h.release();
+        return BGS_OK;
+    });
+}
+
+int bgs_setup(bgs_handle h) {
+    if (!h) return BGS_INVALID_ARG;
+    return guarded([&]() -> int {
+        cudaStream_t s = h->s;
+        CK(cudaStreamSynchronize(s));
+        const double t0 = now_ms();
+        const bool mixed = h->opt.precision == 1;
+        for (int k = 0; k < h->F; k++) {
+            Hier &H = h->H[k];
+            H = Hier();
+            H.L.reserve(32);
+            H.L.emplace_back();
+            DCsr &B = h->blk[(size_t)k * h->F + k];
+            DCsr &A0 = H.L[0].A;
+            A0.n = B.n;
+            A0.m = B.m;
+            A0.nnz = B.nnz;
+            A0.rp.alloc((size_t)B.n + 1, s);
+            A0.ci.alloc((size_t)B.nnz, s);
+            A0.v.alloc((size_t)B.nnz, s);
+            CK(cudaMemcpyAsync(A0.rp.p, B.rp.p, sizeof(int) * ((size_t)B.n + 1), cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(A0.ci.p, B.ci.p, sizeof(int) * B.nnz, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(A0.v.p, B.v.p, sizeof(double) * B.nnz, cudaMemcpyDeviceToDevice, s));
+            AmgParams p{h->opt.theta[k], h->opt.cheb_degree[k], h->opt.max_coarse, h->opt.max_levels,
+                        h->opt.power_iters, h->opt.filter_diag, h->opt.cheb_ratio, h->opt.cheb_boost};
+            amg_build(H, p, h->sc, s);
+            if (H.status) return H.status;
+            for (size_t l = 0; l < H.L.size(); l++) {
+                Level &Lv = H.L[l];
+                if (mixed) {
+                    Buf<float>::alloc(Lv, Lv.A.n, s);
+                    if (l + 1 < H.L.size()) {
+                        for (DCsr *M : {&Lv.A, &Lv.P, &Lv.R}) {
+                            M->vf.alloc((size_t)M->nnz, s);
+                            convert_d2f(M->v.p, M->vf.p, M->nnz, s);
+                        }
+                        Lv.dinvf.alloc((size_t)Lv.A.n, s);
+                        convert_d2f(Lv.dinv.p, Lv.dinvf.p, Lv.A.n, s);
+                    }
+                } else {
+                    Buf<double>::alloc(Lv, Lv.A.n, s);
+                }
+            }
+            if (mixed && h->lower[k].nnz) {
+                h->lower[k].vb.alloc((size_t)h->lower[k].nnz, s);
+                convert_d2bf(h->lower[k].v.p, h->lower[k].vb.p, h->lower[k].nnz, s);
+            }
+        }
+        const int64_t n = total_n(h);
+        const int m = h->opt.restart;
+        h->V.alloc((size_t)n * (m + 1), s);
+        h->Z.alloc((size_t)n * m, s);
+        h->w.alloc((size_t)n, s);
+        h->r.alloc((size_t)n, s);
+        h->x.alloc((size_t)n, s);
+        h->bvec.alloc((size_t)n, s);
+        h->hdev.alloc(256, s);
+        h->adjoint_ready = false;
+        CK(cudaStreamSynchronize(s));
+        h->t_setup_ms = now_ms() - t0;
+        h->setup_done = true;
+        return BGS_OK;
+    });
+}
+
+static int solve_common(bgs_handle h, const double *b, double *x, bgs_info *info, bool adjoint) {
+    if (!h || !b || !x) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    return guarded([&]() -> int {
+        cudaStream_t s = h->s;
+        const int64_t n = total_n(h);
+        if (adjoint) build_adjoint(h);
+        CK(cudaStreamSynchronize(s));
+        const double t0 = now_ms();
+        for (auto &k : h->stats) k = KStats();
+        CK(cudaMemcpyAsync(h->bvec.p, b, sizeof(double) * n, cudaMemcpyDefault, s));
+        bgs_info inf{};
+        int st = fgmres(h, adjoint, &inf);
+        CK(cudaMemcpyAsync(x, h->x.p, sizeof(double) * n, cudaMemcpyDefault, s));
+        CK(cudaStreamSynchronize(s));
+        inf.t_solve_ms = now_ms() - t0;
+        inf.t_setup_ms = h->t_setup_ms;
+        prof_collect(h);
+        if (info) *info = inf;
+        return st;
+    });
+}
+
+int bgs_solve(bgs_handle h, const double *b, double *x, bgs_info *info) {
+    return solve_common(h, b, x, info, false);
+}
+
+int bgs_solve_adjoint(bgs_handle h, const double *g, double *lambda, bgs_info *info) {
+    return solve_common(h, g, lambda, info, true);
+}
+
+int bgs_grad_values(bgs_handle h, int rf, int cf, const double *lambda, const double *x, double *dvals) {
+    if (!h || rf < 0 || cf < 0 || rf >= h->F || cf >= h->F || !lambda || !x || !dvals) return BGS_INVALID_ARG;
+    return guarded([&]() -> int {
+        DCsr &B = h->blk[(size_t)rf * h->F + cf];
+        grad_outer(view(B), lambda + h->offs[rf], x + h->offs[cf], dvals, h->s);
+        CK(cudaStreamSynchronize(h->s));
+        return BGS_OK;
+    });
+}
+
+int bgs_apply_preconditioner(bgs_handle h, const double *v, double *z) {
+    if (!h || !v || !z) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    return guarded([&]() -> int {
+        apply_prec(h, v, z, false);
+        CK(cudaStreamSynchronize(h->s));
+        return BGS_OK;
+    });
+}
+
+int bgs_apply_vcycle(bgs_handle h, int field, const double *b, double *x) {
+    if (!h || field < 0 || field >= h->F || !b || !x) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    return guarded([&]() -> int {
+        Hier &H = h->H[field];
+        const int64_t n = h->sizes[field];
+        if (h->opt.precision == 1) {
+            copy_in<float>(b, Buf<float>::b(H.L[0]), n, h->s);
+            float *r = vcycle<float, float>(h, H, 0, false);
+            copy_out<float>(r, x, n, h->s);
+        } else {
+            copy_in<double>(b, Buf<double>::b(H.L[0]), n, h->s);
+            double *r = vcycle<double, double>(h, H, 0, false);
+            copy_out<double>(r, x, n, h->s);
+        }
+        CK(cudaStreamSynchronize(h->s));
+        return BGS_OK;
+    });
+}
+
+int bgs_full_spmv(bgs_handle h, const double *x, double *y) {
+    if (!h || !x || !y) return BGS_INVALID_ARG;
+    return guarded([&]() -> int {
+        spmv_store<double, double>(h->full, h->full.v.p, x, y, h->s);
+        CK(cudaStreamSynchronize(h->s));
+        return BGS_OK;
+    });
+}
+
+int bgs_num_levels(bgs_handle h, int field, int *nlevels) {
+    if (!h || field < 0 || field >= h->F || !nlevels) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    *nlevels = (int)h->H[field].L.size();
+    return BGS_OK;
+}
+
+int bgs_level_info(bgs_handle h, int field, int level, int64_t *rows, int64_t *nnz, int64_t *p_nnz, int *nagg,
+                   int *mis_rounds, double *omega, double *lmin, double *lmax) {
+    if (!h || field < 0 || field >= h->F) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    Hier &H = h->H[field];
+    if (level < 0 || level >= (int)H.L.size()) return BGS_INVALID_ARG;
+    Level &L = H.L[level];
+    if (rows) *rows = L.A.n;
+    if (nnz) *nnz = L.A.nnz;
+    if (p_nnz) *p_nnz = L.P.nnz;
+    if (nagg) *nagg = L.nagg;
+    if (mis_rounds) *mis_rounds = L.mis_rounds;
+    if (omega) *omega = L.omega;
+    if (lmin) *lmin = L.lmin;
+    if (lmax) *lmax = L.lmax;
+    return BGS_OK;
+}
+
+int bgs_level_copy(bgs_handle h, int field, int level, int which, int32_t *rowptr, int32_t *col, double *val) {
+    if (!h || field < 0 || field >= h->F || which < 0 || which > 2) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    Hier &H = h->H[field];
+    if (level < 0 || level >= (int)H.L.size()) return BGS_INVALID_ARG;
+    if (which > 0 && level + 1 >= (int)H.L.size()) return BGS_INVALID_ARG;
+    return guarded([&]() -> int {
+        Level &L = H.L[level];
+        const DCsr &M = which == 0 ? L.A : (which == 1 ? L.P : L.R);
+        cudaStream_t s = h->s;
+        if (rowptr) CK(cudaMemcpyAsync(rowptr, M.rp.p, sizeof(int) * ((size_t)M.n + 1), cudaMemcpyDeviceToHost, s));
+        if (col && M.nnz) CK(cudaMemcpyAsync(col, M.ci.p, sizeof(int) * M.nnz, cudaMemcpyDeviceToHost, s));
+        if (val && M.nnz) CK(cudaMemcpyAsync(val, M.v.p, sizeof(double) * M.nnz, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return BGS_OK;
+    });
+}
+
+int bgs_level_aggregates(bgs_handle h, int field, int level, int32_t *agg) {
+    if (!h || field < 0 || field >= h->F || !agg) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    Hier &H = h->H[field];
+    if (level < 0 || level + 1 >= (int)H.L.size()) return BGS_INVALID_ARG;
+    return guarded([&]() -> int {
+        Level &L = H.L[level];
+        CK(cudaMemcpyAsync(agg, L.agg.p, sizeof(int) * (size_t)L.A.n, cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        return BGS_OK;
+    });
+}
+
+int bgs_set_profiling(bgs_handle h, int on) {
+    if (!h) return BGS_INVALID_ARG;
+    h->prof = on != 0;
+    return BGS_OK;
+}
+
+int bgs_kernel_stats(bgs_handle h, int cls, int64_t *launches, double *ms, double *bytes) {
+    if (!h || cls < 0 || cls > 3) return BGS_INVALID_ARG;
+    if (launches) *launches = h->stats[cls].launches;
+    if (ms) *ms = h->stats[cls].ms;
+    if (bytes) *bytes = h->stats[cls].bytes;
+    return BGS_OK;
+}
+
+int bgs_csr_spmv(int64_t nrows, int64_t nnz, const int32_t *rowptr, const int32_t *col, const double *val,
+                 const double *x, double *y, int lanes, void *stream) {
+    if (nrows < 0 || nnz < 0 || nrows >= INT32_MAX || nnz >= INT32_MAX) return BGS_INVALID_ARG;
+    if (nrows > 0 && (!rowptr || !x || !y)) return BGS_INVALID_ARG;
+    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
+        return BGS_INVALID_ARG;
+    return guarded([&]() -> int {
+        CsrView A{(int)nrows, 0, nnz, rowptr, col, val};
+        spmv_f64(A, lanes, x, y, (cudaStream_t)stream);
+        return BGS_OK;
+    });
+}
+
+void bgs_destroy(bgs_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->s);
+    for (auto &e : h->ev) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    cudaStream_t s = h->s;
+    delete h;
+    cudaStreamSynchronize(s);
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Shared device/host utilities of libbgs (GB300, sm_103a).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/bgs.h"
+
+namespace bgs {
+
+// ------------------------------------------------------------------------------------------
+// Errors: thrown inside the library, turned into status codes at the C ABI.
+// ------------------------------------------------------------------------------------------
+struct Error : std::runtime_error {
+    int status;
+    Error(int s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+inline void cuda_check(cudaError_t e, const char *file, int line) {
+    if (e == cudaSuccess) return;
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s at %s:%d", cudaGetErrorString(e), file, line);
+    throw Error(e == cudaErrorMemoryAllocation ? BGS_OOM : BGS_CUDA_ERROR, buf);
+}
+#define CK(x) ::bgs::cuda_check((x), __FILE__, __LINE__)
+#define CK_LAUNCH() ::bgs::cuda_check(cudaGetLastError(), __FILE__, __LINE__)
+
+// ------------------------------------------------------------------------------------------
+// Device buffers: stream-ordered allocation, freed on the stream they were allocated on.
+// ------------------------------------------------------------------------------------------
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    DBuf() = default;
+    DBuf(size_t count, cudaStream_t st) { alloc(count, st); }
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; s = o.s;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void alloc(size_t count, cudaStream_t st) {
+        release();
+        s = st;
+        n = count;
+        if (count) CK(cudaMallocAsync((void **)&p, count * sizeof(T), st));
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    T *get() const { return p; }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// A device CSR matrix.  Values in FP64 always; FP32 / BF16 copies exist in mixed precision.
+struct DCsr {
+    int n = 0, m = 0;       // rows, columns
+    int64_t nnz = 0;
+    DBuf<int> rp, ci;
+    DBuf<double> v;
+    DBuf<float> vf;
+    DBuf<__nv_bfloat16> vb;
+    int lanes = 0;          // SpMV threads per row chosen for this matrix
+};
+
+// ------------------------------------------------------------------------------------------
+// Launch helpers
+// ------------------------------------------------------------------------------------------
+constexpr int kSMs = 152;
+
+inline int grid_for(int64_t work, int block, int max_blocks = kSMs * 16) {
+    int64_t g = (work + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(double x) { return (float)x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
+template <class T>
+__device__ __forceinline__ T from_d(double x);
+template <>
+__device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_d<float>(double x) { return (float)x; }
+
+// read-only cached load
+template <class T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 ldg(const __nv_bfloat16 *p) { return *p; }
+
+}  // namespace bgs

@@ -1,0 +1,131 @@
+// Host-side interfaces between the translation units of libbgs.
+#pragma once
+#include "common.cuh"
+
+namespace bgs {
+
+// Non-owning CSR view (FP64 values).
+struct CsrView {
+    int n = 0, m = 0;
+    int64_t nnz = 0;
+    const int *rp = nullptr, *ci = nullptr;
+    const double *v = nullptr;
+};
+inline CsrView view(const DCsr &A) { return CsrView{A.n, A.m, A.nnz, A.rp.p, A.ci.p, A.v.p}; }
+
+// Reusable device scratch for reductions and flags (one per handle).
+struct Scratch {
+    DBuf<double> partial;   // per-block partial sums
+    DBuf<double> scal;      // device scalars
+    DBuf<int> flags;        // device integer flags / counters
+    DBuf<int> iscan;        // scan block sums
+    DBuf<double> pinned_dummy;
+    double *h_scal = nullptr;  // pinned host mirror
+    int *h_flags = nullptr;
+    void init(cudaStream_t s);
+    ~Scratch();
+};
+
+// ---------------------------------------------------------------- util.cu
+// out[0..n] = exclusive scan of in[0..n-1] (out[n] = total); in and out may alias.
+// Returns the total (synchronises the stream).  Throws if the total exceeds INT32_MAX.
+int64_t scan_exclusive(const int *in, int *out, int64_t n, Scratch &sc, cudaStream_t s);
+// sum of squares / dot products into a device scalar (deterministic two-pass reduction).
+void dev_dot(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s);
+void dev_fill_int(int *p, int value, int64_t n, cudaStream_t s);
+void dev_fill_double(double *p, double value, int64_t n, cudaStream_t s);
+// Validation of one CSR (device arrays); returns 0 or BGS_INVALID_ARG.  Checks monotone rowptr,
+// rowptr[0] = 0, rowptr[n] = nnz, columns in range and strictly increasing, and (need_diag) that
+// every row stores its diagonal.
+int validate_csr(const CsrView &A, bool need_diag, Scratch &sc, cudaStream_t s);
+// C = row-wise concatenation of blocks: row i of C = row i of parts[0] (columns + offs[0]), then
+// row i of parts[1] ... (all parts have n rows; columns stay sorted if offsets increase).
+void concat_rows(int n, int nparts, const CsrView *parts, const int *col_offs, DCsr &C, Scratch &sc,
+                 cudaStream_t s);
+void convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
+void convert_d2bf(const double *in, __nv_bfloat16 *out, int64_t n, cudaStream_t s);
+void copy_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
+void copy_f2d(const float *in, double *out, int64_t n, cudaStream_t s);
+void extract_diag(const CsrView &A, double *diag, cudaStream_t s);
+void reciprocal(const double *in, double *out, int64_t n, cudaStream_t s);
+// dvals[e] = -lam[roff + i] * x[coff + j]
+void grad_outer(const CsrView &A, const double *lam, const double *x, double *dvals, cudaStream_t s);
+
+// ---------------------------------------------------------------- spmv.cu
+int choose_lanes(int64_t nrows, int64_t nnz);
+// y = A x (FP64)
+void spmv_f64(const CsrView &A, int lanes, const double *x, double *y, cudaStream_t s);
+// generic kernels on a level operator, VT = matrix value type, XT = vector type
+template <class VT, class XT>
+void spmv_store(const DCsr &A, const VT *val, const XT *x, XT *y, cudaStream_t s);
+template <class VT, class XT>
+void spmv_resid(const DCsr &A, const VT *val, const XT *b, const XT *x, XT *r, cudaStream_t s);
+template <class VT, class XT>
+void spmv_addto(const DCsr &A, const VT *val, const XT *x, XT *y, cudaStream_t s);
+template <class VT, class XT>
+void cheb_step(const DCsr &A, const VT *val, const XT *b, const XT *dinv, const XT *xin, XT *xout, XT *d,
+               double c1, double c2, bool first, cudaStream_t s);
+template <class XT>
+void cheb_first(int n, const XT *b, const XT *dinv, double inv_theta, XT *x, XT *d, cudaStream_t s);
+// r = v - L z (L with global columns into z), v/z FP64, output typed
+template <class VT, class XT>
+void coupling_sub(const DCsr &L, const VT *val, const double *v, const double *z, XT *r, cudaStream_t s);
+// w_i = dinv_i * (A v)_i (FP64, power iteration)
+void spmv_scaled(const CsrView &A, const double *dinv, const double *v, double *w, cudaStream_t s);
+// y = W x, W dense column-major n x n in FP64 (transposed = 0) or y = W^T x (transposed = 1)
+template <class XT>
+void dense_gemv(int n, const double *W, const XT *x, XT *y, bool transposed, cudaStream_t s);
+
+// ---------------------------------------------------------------- krylov.cu
+// h[k] = V_k . w for k < cnt (V column-major with leading dimension ld); h[cnt] = w . w
+void arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, Scratch &sc,
+                  cudaStream_t s);
+// w -= V h; then h2[k] = V_k . w, h2[cnt] = w . w
+void arnoldi_update_dots(const double *V, int64_t ld, int cnt, const double *h, double *w, int64_t n, double *h2,
+                         Scratch &sc, cudaStream_t s);
+// w -= V h; h2[0] = w . w
+void arnoldi_update_norm(const double *V, int64_t ld, int cnt, const double *h, double *w, int64_t n,
+                         double *nrm2, Scratch &sc, cudaStream_t s);
+// x += sum_k y_k Z_k (y host values)
+void multi_axpy(const double *Z, int64_t ld, int cnt, const double *y_host, double *x, int64_t n, cudaStream_t s);
+void scale_copy(const double *in, double alpha, double *out, int64_t n, cudaStream_t s);
+// out = in / *dev_scalar
+void scale_by_inv_dev(const double *in, const double *dev_scalar, double *out, int64_t n, bool sqrt_first,
+                      cudaStream_t s);
+
+// ---------------------------------------------------------------- amg_setup.cu
+struct Level {
+    DCsr A, P, R, AT;
+    DBuf<int> agg;
+    int nagg = 0, mis_rounds = 0;
+    double omega = 0.0;
+    DBuf<double> dinv;
+    DBuf<float> dinvf;
+    double lmin = 0.0, lmax = 0.0;
+    // V-cycle work vectors (FP64 or FP32 by precision)
+    DBuf<double> b, x0, x1, d, r;
+    DBuf<float> fb, fx0, fx1, fd, fr;
+};
+
+struct Hier {
+    std::vector<Level> L;
+    int degree = 2;
+    int nc = 0;
+    DBuf<double> inv;      // dense inverse of the coarsest operator, row-major nc x nc
+    DBuf<double> invT;     // its transpose (adjoint V-cycle), built on first use
+    int status = 0;
+    const DBuf<double> &inv_T() const { return invT; }
+    void build_inv_T(cudaStream_t s);
+};
+
+struct AmgParams {
+    double theta;
+    int degree, max_coarse, max_levels, power_iters, filter_diag;
+    double cheb_ratio, cheb_boost;
+};
+
+// Builds the hierarchy on the level-0 operator already stored in H.L[0].A.
+void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s);
+void transpose_csr(const CsrView &A, DCsr &T, Scratch &sc, cudaStream_t s);
+
+}  // namespace bgs

@@ -1,0 +1,358 @@
+// Scans, reductions, validation, block assembly and small element-wise kernels.
+#include <climits>
+
+#include "internal.h"
+
+namespace bgs {
+
+void Scratch::init(cudaStream_t s) {
+    partial.alloc(kSMs * 8 * 72, s);
+    scal.alloc(256, s);
+    flags.alloc(64, s);
+    iscan.alloc(1 << 16, s);
+    CK(cudaMallocHost((void **)&h_scal, 256 * sizeof(double)));
+    CK(cudaMallocHost((void **)&h_flags, 64 * sizeof(int)));
+}
+
+Scratch::~Scratch() {
+    if (h_scal) cudaFreeHost(h_scal);
+    if (h_flags) cudaFreeHost(h_flags);
+}
+
+// ------------------------------------------------------------------------------------------
+// Exclusive scan (int32 counts -> int32 offsets, int64 block totals)
+// ------------------------------------------------------------------------------------------
+constexpr int SCAN_T = 1024, SCAN_I = 4, SCAN_B = SCAN_T * SCAN_I;
+
+__device__ long long block_excl_scan(long long v, long long *sm_warp, long long *total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long t = (lane < (int)(blockDim.x >> 5)) ? sm_warp[lane] : 0;
+        long long u = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, u, o);
+            if (lane >= o) u += y;
+        }
+        if (lane < (int)(blockDim.x >> 5)) sm_warp[lane] = u - t;
+        if (lane == 31) *total = u;
+    }
+    __syncthreads();
+    long long r = sm_warp[w] + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_sums(const int *__restrict__ in, int64_t n, long long *bsums) {
+    __shared__ long long sw[32];
+    __shared__ long long tot;
+    int64_t base = (int64_t)blockIdx.x * SCAN_B + threadIdx.x * SCAN_I;
+    long long v = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++)
+        if (base + k < n) v += in[base + k];
+    block_excl_scan(v, sw, &tot);
+    if (threadIdx.x == 0) bsums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_ll_single(long long *a, int n) {
+    // exclusive scan of up to SCAN_B long longs in one block
+    __shared__ long long sw[32];
+    __shared__ long long tot;
+    int base = threadIdx.x * SCAN_I;
+    long long v[SCAN_I], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++) {
+        v[k] = (base + k < n) ? a[base + k] : 0;
+        s += v[k];
+    }
+    long long off = block_excl_scan(s, sw, &tot);
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++) {
+        if (base + k < n) a[base + k] = off;
+        off += v[k];
+    }
+    if (threadIdx.x == 0) a[n] = tot;
+}
+
+__global__ void k_scan_apply(const int *in, int *out, int64_t n, const long long *boffs, long long *total) {
+    __shared__ long long sw[32];
+    __shared__ long long tot;
+    int64_t base = (int64_t)blockIdx.x * SCAN_B + threadIdx.x * SCAN_I;
+    int v[SCAN_I];
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        s += v[k];
+    }
+    long long off = block_excl_scan(s, sw, &tot) + boffs[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++) {
+        if (base + k < n) out[base + k] = (int)off;
+        off += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        long long t = boffs[blockIdx.x] + tot;
+        *total = t;
+        out[n] = (int)(t > INT_MAX ? INT_MAX : t);
+    }
+}
+
+int64_t scan_exclusive(const int *in, int *out, int64_t n, Scratch &sc, cudaStream_t s) {
+    if (n == 0) {
+        CK(cudaMemsetAsync(out, 0, sizeof(int), s));
+        return 0;
+    }
+    int64_t nb = (n + SCAN_B - 1) / SCAN_B;
+    if (nb + 1 > SCAN_B) throw Error(BGS_INTERNAL, "scan too large");
+    long long *bs = (long long *)sc.iscan.p;   // needs nb + 1 entries
+    if ((size_t)(nb + 2) * sizeof(long long) > sc.iscan.bytes()) throw Error(BGS_INTERNAL, "scan scratch");
+    long long *total = bs + nb + 1;
+    if ((size_t)(nb + 2) * sizeof(long long) > sc.iscan.bytes() - sizeof(long long))
+        throw Error(BGS_INTERNAL, "scan scratch");
+    k_scan_sums<<<(unsigned)nb, SCAN_T, 0, s>>>(in, n, bs);
+    CK_LAUNCH();
+    k_scan_ll_single<<<1, SCAN_T, 0, s>>>(bs, (int)nb);
+    CK_LAUNCH();
+    k_scan_apply<<<(unsigned)nb, SCAN_T, 0, s>>>(in, out, n, bs, total);
+    CK_LAUNCH();
+    long long h = 0;
+    CK(cudaMemcpyAsync(&h, total, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h > INT_MAX) throw Error(BGS_INVALID_ARG, "more than 2^31-1 entries");
+    return h;
+}
+
+// ------------------------------------------------------------------------------------------
+// Deterministic dot product
+// ------------------------------------------------------------------------------------------
+__device__ double block_sum(double v) {
+    __shared__ double sw[32];
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sw[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = (lane < (int)(blockDim.x >> 5)) ? sw[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;  // valid in thread 0
+}
+
+__global__ void k_dot_partial(const double *__restrict__ a, const double *__restrict__ b, int64_t n, double *part) {
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += a[i] * b[i];
+    double t = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_reduce_final(const double *part, int g, double *out) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < g; i += blockDim.x) acc += part[i];
+    double t = block_sum(acc);
+    if (threadIdx.x == 0) *out = t;
+}
+
+void dev_dot(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s) {
+    int g = grid_for(n, 256, kSMs * 4);
+    k_dot_partial<<<g, 256, 0, s>>>(a, b, n, sc.partial.p);
+    CK_LAUNCH();
+    k_reduce_final<<<1, 256, 0, s>>>(sc.partial.p, g, out);
+    CK_LAUNCH();
+}
+
+// ------------------------------------------------------------------------------------------
+// Small element-wise kernels
+// ------------------------------------------------------------------------------------------
+template <class T>
+__global__ void k_fill(T *p, T v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+void dev_fill_int(int *p, int value, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_fill<int><<<grid_for(n, 256), 256, 0, s>>>(p, value, n);
+    CK_LAUNCH();
+}
+void dev_fill_double(double *p, double value, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_fill<double><<<grid_for(n, 256), 256, 0, s>>>(p, value, n);
+    CK_LAUNCH();
+}
+
+template <class A, class B>
+__global__ void k_convert(const A *in, B *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (B)in[i];
+}
+__global__ void k_convert_bf(const double *in, __nv_bfloat16 *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __double2bfloat16(in[i]);
+}
+void convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_convert<double, float><<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    CK_LAUNCH();
+}
+void copy_d2f(const double *in, float *out, int64_t n, cudaStream_t s) { convert_d2f(in, out, n, s); }
+void copy_f2d(const float *in, double *out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_convert<float, double><<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    CK_LAUNCH();
+}
+void convert_d2bf(const double *in, __nv_bfloat16 *out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_convert_bf<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    CK_LAUNCH();
+}
+
+__global__ void k_reciprocal(const double *in, double *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = 1.0 / in[i];
+}
+void reciprocal(const double *in, double *out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_reciprocal<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    CK_LAUNCH();
+}
+
+__global__ void k_extract_diag(int n, const int *rp, const int *ci, const double *v, double *d) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double x = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; e++)
+            if (ci[e] == i) {
+                x = v[e];
+                break;
+            }
+        d[i] = x;
+    }
+}
+void extract_diag(const CsrView &A, double *diag, cudaStream_t s) {
+    if (A.n <= 0) return;
+    k_extract_diag<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, diag);
+    CK_LAUNCH();
+}
+
+__global__ void k_grad_outer(int n, const int *rp, const int *ci, const double *lam, const double *x, double *g) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double li = lam[i];
+        for (int e = rp[i]; e < rp[i + 1]; e++) g[e] = -(li * x[ci[e]]);
+    }
+}
+void grad_outer(const CsrView &A, const double *lam, const double *x, double *dvals, cudaStream_t s) {
+    if (A.n <= 0) return;
+    k_grad_outer<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp, A.ci, lam, x, dvals);
+    CK_LAUNCH();
+}
+
+// ------------------------------------------------------------------------------------------
+// Validation
+// ------------------------------------------------------------------------------------------
+__global__ void k_validate(int n, int m, int64_t nnz, const int *rp, const int *ci, const double *v, int need_diag,
+                           int *flag) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (rp[0] != 0 || (int64_t)rp[n] != nnz) atomicOr(flag, 1);
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int s = rp[i], e = rp[i + 1];
+        if (s < 0 || e < s || (int64_t)e > nnz) {
+            atomicOr(flag, 2);
+            continue;
+        }
+        int prev = -1, has_diag = 0;
+        for (int k = s; k < e; k++) {
+            int c = ci[k];
+            if (c < 0 || c >= m || c <= prev) atomicOr(flag, 4);
+            double x = v[k];
+            if (!(x == x) || x - x != 0.0) atomicOr(flag, 16);
+            if (c == i) has_diag = 1;
+            prev = c;
+        }
+        if (need_diag && !has_diag) atomicOr(flag, 8);
+    }
+}
+
+int validate_csr(const CsrView &A, bool need_diag, Scratch &sc, cudaStream_t s) {
+    CK(cudaMemsetAsync(sc.flags.p, 0, sizeof(int), s));
+    if (A.n > 0) {
+        k_validate<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.m, A.nnz, A.rp, A.ci, A.v, need_diag ? 1 : 0,
+                                                       sc.flags.p);
+        CK_LAUNCH();
+    }
+    CK(cudaMemcpyAsync(sc.h_flags, sc.flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int f = sc.h_flags[0];
+    if (f & 16) return BGS_NAN_INF;
+    return f ? BGS_INVALID_ARG : BGS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Row-wise concatenation of blocks (assembly of the full operator / coupling rows)
+// ------------------------------------------------------------------------------------------
+struct Parts {
+    const int *rp[8];
+    const int *ci[8];
+    const double *v[8];
+    int off[8];
+    int np;
+};
+
+__global__ void k_concat_count(int n, Parts P, int *cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int p = 0; p < P.np; p++) c += P.rp[p][i + 1] - P.rp[p][i];
+        cnt[i] = c;
+    }
+}
+
+__global__ void k_concat_fill(int n, Parts P, const int *rp, int *ci, double *v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int q = rp[i];
+        for (int p = 0; p < P.np; p++)
+            for (int e = P.rp[p][i]; e < P.rp[p][i + 1]; e++) {
+                ci[q] = P.ci[p][e] + P.off[p];
+                v[q] = P.v[p][e];
+                q++;
+            }
+    }
+}
+
+void concat_rows(int n, int nparts, const CsrView *parts, const int *col_offs, DCsr &C, Scratch &sc,
+                 cudaStream_t s) {
+    Parts P{};
+    P.np = nparts;
+    for (int p = 0; p < nparts; p++) {
+        P.rp[p] = parts[p].rp;
+        P.ci[p] = parts[p].ci;
+        P.v[p] = parts[p].v;
+        P.off[p] = col_offs[p];
+    }
+    C.n = n;
+    C.rp.alloc((size_t)n + 1, s);
+    if (nparts == 0 || n == 0) {
+        CK(cudaMemsetAsync(C.rp.p, 0, sizeof(int) * ((size_t)n + 1), s));
+        C.nnz = 0;
+        return;
+    }
+    k_concat_count<<<grid_for(n, 256), 256, 0, s>>>(n, P, C.rp.p);
+    CK_LAUNCH();
+    C.nnz = scan_exclusive(C.rp.p, C.rp.p, n, sc, s);
+    C.ci.alloc((size_t)C.nnz, s);
+    C.v.alloc((size_t)C.nnz, s);
+    k_concat_fill<<<grid_for(n, 256), 256, 0, s>>>(n, P, C.rp.p, C.ci.p, C.v.p);
+    CK_LAUNCH();
+}
+
+}  // namespace bgs

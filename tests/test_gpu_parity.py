@@ -1,0 +1,232 @@
+"""GPU parity tests: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Integer results (strength decisions, MIS-2, aggregates) must match bit for bit; floating-point
+results within tolerances derived from the arithmetic (documented per test)."""
+import numpy as np
+import pytest
+
+import battery_system as bs
+import oracle
+from battery_system import spec
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bgs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_13079_gb300 import _build
+    _build.build()
+    import paper_2602_13079_gb300 as m
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def opts_kw(**kw):
+    return kw
+
+
+def make_pair(bgs, system, order=None, **kw):
+    order = list(order if order is not None else spec.WORKLOAD_ORDER)
+    s = bgs.solver_for_system(system, order=order, **kw)
+    s.setup()
+    o = oracle.bgs_for_system(system, order=order, opts=oracle.default_options(
+        **{k: v for k, v in kw.items() if k not in ("precision", "graph", "autotune")}))
+    return s, o
+
+
+# ------------------------------------------------------------------------------------- SpMV
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8, 16, 32])
+def test_csr_spmv_matches_oracle(bgs, lanes):
+    rng = np.random.default_rng(lanes)
+    n = 20_011                                  # several blocks and a ragged tail
+    lens = rng.integers(0, 40, n)
+    lens[::97] = 0                               # empty rows
+    lens[5] = 700                                # one long row
+    rp = np.zeros(n + 1, dtype=np.int32)
+    np.cumsum(lens, out=rp[1:])
+    col = np.concatenate([np.sort(rng.choice(n, l, replace=False)) for l in lens]).astype(np.int32)
+    val = rng.standard_normal(rp[-1])
+    x = rng.standard_normal(n)
+    A = oracle.CSR(rp, col, val, n, n)
+    ref = oracle.spmv(A, x)
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = bgs.bgs_csr_spmv(n, rp[-1], dev(rp), dev(col), dev(val), dev(x), y, lanes)
+    torch.cuda.synchronize()
+    assert st == 0
+    rows = np.repeat(np.arange(n), lens)
+    scale = np.bincount(rows, weights=np.abs(val * x[col]), minlength=n)
+    # FP64 sums of the same products in another order: |diff| <= len * eps * sum |a x|
+    tol = 64 * np.finfo(float).eps * (lens + 1) * scale + 1e-300
+    assert np.all(np.abs(y.cpu().numpy() - ref) <= tol)
+
+
+def test_full_operator_spmv(bgs):
+    s = bs.assemble("C1")
+    g, o = bgs.solver_for_system(s), oracle.bgs_for_system(s, setup=False)
+    x = np.random.default_rng(1).standard_normal(s.ndof)
+    y = torch.zeros(s.ndof, dtype=torch.float64, device="cuda")
+    g.bgs_full_spmv(dev(x), y)
+    ref = o.full_matvec(x)
+    assert np.allclose(y.cpu().numpy(), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+# ------------------------------------------------------------------------------------- setup
+SETUP_CASES = [
+    ("C1-mc100", lambda: bs.assemble("C1"), dict(max_coarse=100)),
+    ("3D-17x13x11", lambda: bs.assemble(grid=bs.Grid(3, 17, 13, 11), seed=2), dict(max_coarse=60)),
+    ("3D-24", lambda: bs.assemble(grid=bs.Grid(3, 24, 24, 24), seed=1), dict()),
+    ("stack-8x8x40", lambda: bs.assemble(grid=bs.Grid(3, 8, 8, 40), stack=True, seed=3), dict(max_coarse=80)),
+]
+
+
+@pytest.mark.parametrize("name,mk,kw", SETUP_CASES, ids=[c[0] for c in SETUP_CASES])
+def test_hierarchy_parity(bgs, name, mk, kw):
+    system = mk()
+    g, o = make_pair(bgs, system, **kw)
+    for k in range(5):
+        oa = o.amg(k)
+        nl = g.bgs_num_levels(k)
+        assert nl == oa.nlevels, (k, nl, oa.sizes())
+        for l in range(nl):
+            info = g.bgs_level_info(k, l)
+            assert info["rows"] == oa.sizes()[l]
+            if l + 1 < nl:
+                # integer decisions: bit-exact
+                assert info["nagg"] == oa.nagg(l)
+                assert info["mis_rounds"] == oa.mis_rounds(l)
+                assert np.array_equal(g.bgs_level_aggregates(k, l), oa.aggregates(l)), (k, l)
+                assert abs(info["omega"] - oa.omega(l)) <= 1e-12 * abs(oa.omega(l))
+                lo, hi = oa.cheb_bounds(l)
+                assert abs(info["lmax"] - hi) <= 1e-10 * hi and abs(info["lmin"] - lo) <= 1e-10 * lo
+                for which, ref in ((1, oa.prolongator(l)), (2, oa.restriction(l))):
+                    rp, ci, v = g.bgs_level_copy(k, l, which)
+                    assert np.array_equal(rp, ref.rowptr) and np.array_equal(ci, ref.col)
+                    assert np.abs(v - ref.val).max() <= 1e-12 * max(1.0, np.abs(ref.val).max())
+            rp, ci, v = g.bgs_level_copy(k, l, 0)
+            ref = oa.level_matrix(l)
+            assert np.array_equal(rp, ref.rowptr) and np.array_equal(ci, ref.col), (k, l)
+            assert np.abs(v - ref.val).max() <= 1e-11 * np.abs(ref.val).max(), (k, l)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_vcycle_and_sweep_parity(bgs, precision):
+    system = bs.assemble(grid=bs.Grid(3, 17, 13, 11), seed=2)
+    g, o = make_pair(bgs, system, max_coarse=60, precision=precision)
+    rng = np.random.default_rng(3)
+    # FP64: the same arithmetic up to summation order; FP32 hierarchy: single-precision error
+    tol = 1e-10 if precision == 0 else 2e-4
+    for k in range(5):
+        n = system.ncells
+        b = rng.standard_normal(n)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        g.bgs_apply_vcycle(k, dev(b), x)
+        ref = o.amg(k).vcycle(b)
+        err = np.linalg.norm(x.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err <= tol, (k, err)
+    v = rng.standard_normal(system.ndof)
+    z = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+    g.bgs_apply_preconditioner(dev(v), z)
+    ref = o.apply(v)
+    err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err <= (1e-10 if precision == 0 else 5e-3), err
+
+
+# ------------------------------------------------------------------------------------- solve
+@pytest.mark.parametrize("order", [spec.WORKLOAD_ORDER, spec.PAPER_ORDER], ids=["workload", "paper"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_parity(bgs, order, precision):
+    system = bs.assemble("C1")
+    g, o = make_pair(bgs, system, order=order, max_coarse=100, precision=precision)
+    xr, ir = o.solve(system.b)
+    assert ir.converged
+    x = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+    info = g.bgs_solve(dev(system.b), x)
+    xh = x.cpu().numpy()
+    assert info.converged and info.status == 0
+    true_rel = np.linalg.norm(system.b - o.full_matvec(xh)) / np.linalg.norm(system.b)
+    assert true_rel <= 1e-8 and abs(true_rel - info.rel_true_resid) <= 1e-3 * true_rel + 1e-15
+    assert np.linalg.norm(xh - xr) <= 1e-6 * np.linalg.norm(xr)
+    if precision == 0:
+        assert abs(info.iters - ir.iters) <= 2
+
+
+def test_solve_3d_default_options_and_host_buffers(bgs):
+    system = bs.assemble(grid=bs.Grid(3, 24, 24, 24), seed=1)
+    g, o = make_pair(bgs, system)
+    xr, ir = o.solve(system.b)
+    x = np.zeros(system.ndof)                     # host in, host out through the C ABI
+    info = g.bgs_solve(system.b, x)
+    assert info.converged
+    assert np.linalg.norm(system.b - o.full_matvec(x)) <= 1e-8 * np.linalg.norm(system.b)
+    assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr)
+
+
+def test_adjoint_parity_and_gradient(bgs):
+    system = bs.assemble(grid=bs.Grid(3, 10, 9, 8), seed=4)
+    g, o = make_pair(bgs, system, max_coarse=40, rtol=1e-12)
+    rng = np.random.default_rng(5)
+    gvec = rng.standard_normal(system.ndof)
+    lam_ref, ir = o.solve_adjoint(gvec)
+    lam = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+    info = g.bgs_solve_adjoint(dev(gvec), lam)
+    assert info.converged and ir.converged
+    lh = lam.cpu().numpy()
+    assert np.linalg.norm(lh - lam_ref) <= 1e-9 * np.linalg.norm(lam_ref)
+    x = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+    g.bgs_solve(dev(system.b), x)
+    assert abs(gvec @ x.cpu().numpy() - lh @ system.b) <= 1e-9 * abs(gvec @ x.cpu().numpy())
+    # dL/dA on the pattern of every stored block
+    for (r, c), blk in system.blocks.items():
+        d = torch.zeros(blk.nnz, dtype=torch.float64, device="cuda")
+        g.bgs_grad_values(r, c, lam, x, d)
+        n = system.ncells
+        rows = np.repeat(np.arange(blk.nrows), np.diff(blk.rowptr))
+        ref = -(lh[r * n + rows] * x.cpu().numpy()[c * n + blk.col])
+        assert np.array_equal(d.cpu().numpy(), ref)
+
+
+# ------------------------------------------------------------------------------------- errors
+def test_error_statuses(bgs):
+    system = bs.assemble(grid=bs.Grid(3, 6, 6, 6), seed=1)
+    # unsorted columns in a diagonal block -> INVALID_ARG
+    bad = bs.assemble(grid=bs.Grid(3, 6, 6, 6), seed=1)
+    B = bad.blocks[(0, 0)]
+    B.col[1], B.col[2] = B.col[2], B.col[1]
+    with pytest.raises(bgs.BGSError) as e:
+        bgs.solver_for_system(bad)
+    assert e.value.status == bgs.INVALID_ARG
+    # a missing diagonal entry -> INVALID_ARG
+    bad2 = bs.assemble(grid=bs.Grid(3, 6, 6, 6), seed=1)
+    B = bad2.blocks[(2, 2)]
+    keep = np.ones(B.nnz, dtype=bool)
+    keep[np.nonzero(B.col == 0)[0][0]] = False   # row 0's diagonal
+    rows = np.repeat(np.arange(B.nrows), np.diff(B.rowptr))
+    B.col, B.val = B.col[keep], B.val[keep]
+    B.rowptr = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=B.nrows))]).astype(np.int32)
+    with pytest.raises(bgs.BGSError) as e:
+        bgs.solver_for_system(bad2)
+    assert e.value.status == bgs.INVALID_ARG
+    g = bgs.solver_for_system(system, max_coarse=20)
+    x = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+    with pytest.raises(bgs.BGSError) as e:
+        g.bgs_solve(dev(system.b), x)
+    assert e.value.status == bgs.NOT_SETUP
+    g.setup()
+    bn = system.b.copy()
+    bn[7] = np.nan
+    with pytest.raises(bgs.BGSError) as e:
+        g.bgs_solve(dev(bn), x)
+    assert e.value.status == bgs.NAN_INF
+    g2 = bgs.solver_for_system(system, max_coarse=20, maxit=1)
+    g2.setup()
+    info = g2.bgs_solve(dev(system.b), x)
+    assert info.status == bgs.NO_CONVERGENCE and info.iters == 1 and not info.converged
+    # zero right-hand side: x = 0, converged, no iterations
+    info = g.bgs_solve(torch.zeros(system.ndof, dtype=torch.float64, device="cuda"), x)
+    assert info.converged and info.iters == 0 and float(x.abs().max()) == 0.0
