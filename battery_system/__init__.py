@@ -239,6 +239,31 @@ class CoupledSystem:
             A[r * n:(r + 1) * n, c * n:(c + 1) * n] = blk.to_dense()
         return A
 
+    def full_csr(self) -> CSR:
+        """The field-blocked full operator as one CSR (rows of field r list blocks (r, 0..4) in order)."""
+        n = self.ncells
+        F = spec.NFIELDS
+        counts = np.zeros(self.ndof, dtype=np.int64)
+        for (r, c), blk in self.blocks.items():
+            counts[r * n:(r + 1) * n] += np.diff(blk.rowptr)
+        rowptr = np.zeros(self.ndof + 1, dtype=np.int64)
+        np.cumsum(counts, out=rowptr[1:])
+        col = np.empty(int(rowptr[-1]), dtype=np.int32)
+        val = np.empty(int(rowptr[-1]))
+        cursor = rowptr[:-1].copy()
+        for r in range(F):
+            for c in range(F):
+                blk = self.blocks.get((r, c))
+                if blk is None:
+                    continue
+                lens = np.diff(blk.rowptr).astype(np.int64)
+                start = np.repeat(cursor[r * n:(r + 1) * n], lens)
+                within = np.arange(blk.nnz) - np.repeat(blk.rowptr[:-1].astype(np.int64), lens)
+                col[start + within] = blk.col + c * n
+                val[start + within] = blk.val
+                cursor[r * n:(r + 1) * n] += lens
+        return CSR(rowptr.astype(np.int32), col, val, self.ndof, self.ndof)
+
     def matvec(self, x: np.ndarray) -> np.ndarray:
         n = self.ncells
         y = np.zeros(self.ndof)

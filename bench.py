@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the end-to-end electrochemical solve on one GB300 (or N replicas).
+
+One step = bgs_create (from device-resident CSR blocks) + bgs_setup + bgs_solve to a true
+relative residual of 1e-8 on the 3D 128^3 five-field layered system (10.5M DOFs, seed 1).
+`value` is the plain-method FP64 setup+solve seconds per step; the mixed-precision form
+(FP32 hierarchy, BF16 coupling values, FP64 Krylov) is timed the same way and reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+For N > 1 the driver launches one rank per GPU with torchrun; every rank solves its own copy
+(replicas: the solve has no data-parallel split on one node here), rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "setup+solve sec to rtol 1e-8 at 10.5M DOFs, mixed vs FP64 on same GB300; SpMV HBM GB/s"
+WORKLOAD = "C4"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--config", default=WORKLOAD)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-profile", action="store_true")
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline): bounded sample
+# --------------------------------------------------------------------------------------------
+def oracle_sample(seed):
+    """The FP64 oracle's setup+solve on the 3D 64^3 system (1.31M DOFs, 1/8 of the workload),
+    single-threaded; returns (seconds, scaled seconds for 10.5M DOFs, iterations)."""
+    import battery_system as bs
+    import oracle
+    system = bs.assemble("C2", seed=seed)
+    t0 = time.perf_counter()
+    o = oracle.bgs_for_system(system)
+    x, info = o.solve(system.b)
+    dt = time.perf_counter() - t0
+    scale = (5 * 128 ** 3) / system.ndof
+    return dt, dt * scale, info.iters, bool(info.converged)
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    times = []
+    for _ in range(args.warmup):
+        oracle_sample(args.seed)
+    for _ in range(args.steps):
+        dt, scaled, iters, conv = oracle_sample(args.seed)
+        times.append(scaled)
+    v = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded layered battery system)",
+            "config": {"workload": "C4: 3D 128^3, 5 fields, 10.5M DOFs (projected from the 64^3 sample)",
+                       "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": "oracle setup+solve on 3D 64^3 (1.31M DOFs, seed 1), x8 DOF scaling"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------------------------
+class _Blk:
+    pass
+
+
+def device_blocks(system, torch, pinned=False):
+    blocks = []
+    nbytes = 0
+    for r in range(5):
+        row = []
+        for c in range(5):
+            B = system.blocks.get((r, c))
+            if B is None:
+                row.append(None)
+                continue
+            o = _Blk()
+            if pinned:
+                o.rowptr = torch.from_numpy(B.rowptr).pin_memory()
+                o.col = torch.from_numpy(B.col).pin_memory()
+                o.val = torch.from_numpy(B.val).pin_memory()
+                last = int(B.rowptr[-1])
+            else:
+                o.rowptr = torch.from_numpy(B.rowptr).cuda()
+                o.col = torch.from_numpy(B.col).cuda()
+                o.val = torch.from_numpy(B.val).cuda()
+                last = int(B.rowptr[-1])
+            nbytes += B.rowptr.nbytes + B.col.nbytes + B.val.nbytes
+            from paper_2602_13079_gb300 import _Rowptr
+            o.rowptr = _Rowptr(o.rowptr, last)
+            row.append(o)
+        blocks.append(row)
+    return blocks, nbytes
+
+
+def gpu_arm(args, rank, world):
+    import torch
+    import battery_system as bs
+    from battery_system import spec
+    import paper_2602_13079_gb300 as bgs
+    from paper_2602_13079_gb300 import _build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    _build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def allmax(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    tg = time.perf_counter()
+    system = bs.assemble(args.config, seed=args.seed)
+    t_gen = time.perf_counter() - tg
+    sizes = system.field_sizes
+    order = list(spec.WORKLOAD_ORDER)
+    blocks, mat_bytes = device_blocks(system, torch)
+    b = torch.from_numpy(system.b).cuda()
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+
+    def step(precision, prof=False):
+        s = bgs.Solver(blocks, sizes, order, precision=precision)
+        s.setup()
+        if prof:
+            s.bgs_set_profiling(True)
+        info = s.bgs_solve(b, x)
+        stats = {k: s.bgs_kernel_stats(v) for k, v in bgs.KERNEL_CLASSES.items()} if prof else None
+        s.close()
+        return info, stats
+
+    def timed(precision):
+        for _ in range(args.warmup):
+            step(precision)
+        barrier()
+        torch.cuda.synchronize()
+        l0 = bgs.bgs_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(step(precision)[0])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / args.steps
+        launches = bgs.bgs_launch_count() - l0
+        return allmax(ms), infos, launches
+
+    clk = Clocks(local)
+    ms64, inf64, launches64 = timed(0)
+    x64 = x.cpu().numpy()
+    msmx, infmx, launchesmx = timed(1)
+    xmx = x.cpu().numpy()
+    clocks = clk.stop()
+
+    def summary(ms, infos, xs):
+        i = infos[-1]
+        rel = float(np.linalg.norm(system.b - system.matvec(xs)) / np.linalg.norm(system.b))
+        return {"s_per_step": ms / 1e3, "setup_s": statistics.mean(k.t_setup_ms for k in infos) / 1e3,
+                "solve_s": statistics.mean(k.t_solve_ms for k in infos) / 1e3, "iters": i.iters,
+                "converged": bool(i.converged), "rel_true_resid_host_check": rel}
+
+    arm64 = summary(ms64, inf64, x64)
+    armmx = summary(msmx, infmx, xmx)
+    armmx["rel_diff_vs_fp64"] = float(np.linalg.norm(xmx - x64) / np.linalg.norm(x64))
+
+    # per-kernel-class timing inside a solve (CUDA events on the library stream)
+    prof = None
+    if not args.no_profile:
+        _, prof = step(0, prof=True)
+
+    # standalone FP64 CSR SpMV of the full operator (L2 flushed before every launch)
+    A = system.full_csr()
+    rp, ci, va = (torch.from_numpy(a).cuda() for a in (A.rowptr, A.col, A.val))
+    xs = torch.rand(A.nrows, dtype=torch.float64, device="cuda")
+    ys = torch.zeros_like(xs)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    spmv_ms = []
+    for it in range(13):
+        flush.fill_(float(it))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = bgs.bgs_csr_spmv(A.nrows, A.nnz, rp, ci, va, xs, ys, 0, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert st == 0
+        if it >= 3:
+            spmv_ms.append(e0.elapsed_time(e1))
+    spmv_bytes = A.nnz * 12 + 4 * (A.nrows + 1) + 8 * A.nrows * 2
+    spmv_gbs = spmv_bytes / (statistics.median(spmv_ms) * 1e-3) / 1e9
+    del rp, ci, va, xs, ys, flush
+
+    # end to end through the C ABI from pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hblocks, hbytes = device_blocks(system, torch, pinned=True)
+        bh = torch.from_numpy(system.b).pin_memory()
+        xh = torch.zeros_like(bh).pin_memory()
+
+        def hstep():
+            s = bgs.Solver(hblocks, sizes, order, precision=0)
+            s.setup()
+            s.bgs_solve(bh, xh)
+            s.close()
+
+        hstep()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = allmax((time.perf_counter() - t0) / args.steps)
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(hbytes + bh.numel() * 8),
+               "d2h_bytes_per_step": int(xh.numel() * 8), "precision": "fp64"}
+
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if prof:
+        dom = max(prof, key=lambda k: prof[k]["ms"])
+        d = prof[dom]
+        ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_kind": peak_kind, "traffic": None,
+                "launches": d["launches"], "avg_launch_ms": d["ms"] / max(d["launches"], 1),
+                "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
+                "classes": {k: {"launches": v["launches"], "ms": v["ms"],
+                                "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                            for k, v in prof.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, scaled, iters, conv = oracle_sample(args.seed)
+        cpu = {"value": scaled, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle setup+solve on 3D 64^3 (1.31M DOFs, seed {args.seed}) took {dt:.1f} s "
+                         f"({iters} iterations), x8 DOF scaling to 10.5M"}
+
+    if rank == 0:
+        v = ms64 / 1e3
+        line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded layered battery system)",
+                "config": {"workload": "C4: 3D 128^3 layered system, 5 fields (phi_s, phi_e, p, c1, c2), "
+                                       f"{system.ndof} DOFs, {system.nnz} nnz, seed {args.seed}",
+                           "order": "[phi_s, phi_e] -> p -> [c1, c2]", "rtol": 1e-8, "restart": 50,
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (matrix 1.4 GB)", "generation_s": t_gen},
+                "fp64": arm64, "mixed": armmx,
+                "mixed_speedup_vs_fp64": ms64 / msmx,
+                "spmv_full_fp64": {"GBps": spmv_gbs, "ms": statistics.median(spmv_ms), "bytes": spmv_bytes,
+                                   "frac_of_measured_peak": spmv_gbs / peak},
+                "gpu_launches": int(launches64 // max(args.steps, 1)) * args.steps,
+                "gpu_launches_per_step": int(launches64 // max(args.steps, 1)),
+                "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    gpu_arm(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -133,7 +133,9 @@ int bgs_level_aggregates(bgs_handle h, int field, int level, int32_t *agg);
 
 /* Per-kernel-class timing of the last solve when enabled (bgs_set_profiling(h, 1)): launches,
  * summed CUDA-event milliseconds and algorithmic bytes.  kernel_class: 0 full SpMV, 1 Chebyshev
- * step (all levels), 2 Arnoldi orthogonalisation, 3 coupling SpMV. */
+ * step on the finest level, 2 Arnoldi orthogonalisation, 3 coupling SpMV, 4 Chebyshev steps on
+ * the coarser levels.  Algorithmic bytes: matrix values + column indices + row pointers + each
+ * vector read or written once. */
 int bgs_set_profiling(bgs_handle h, int on);
 int bgs_kernel_stats(bgs_handle h, int kernel_class, int64_t *launches, double *ms, double *bytes);
 
@@ -141,6 +143,9 @@ int bgs_kernel_stats(bgs_handle h, int kernel_class, int64_t *launches, double *
  * lanes: threads per row (1, 2, 4, 8, 16 or 32), or 0 for the built-in choice. */
 int bgs_csr_spmv(int64_t nrows, int64_t nnz, const int32_t *rowptr, const int32_t *col, const double *val,
                  const double *x, double *y, int lanes, void *cuda_stream);
+
+/* Number of kernels this library has launched in the process so far (all handles). */
+int64_t bgs_launch_count(void);
 
 void bgs_destroy(bgs_handle h);
 const char *bgs_status_string(int status);

@@ -77,6 +77,7 @@ def lib():
             "bgs_set_profiling": (i32, [vp, i32]),
             "bgs_kernel_stats": (i32, [vp, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
             "bgs_csr_spmv": (i32, [i64, i64, vp, vp, vp, vp, vp, i32, vp]),
+            "bgs_launch_count": (C.c_int64, []),
             "bgs_destroy": (None, [vp]),
             "bgs_status_string": (C.c_char_p, [i32]),
         }
@@ -132,6 +133,10 @@ def bgs_default_options(**overrides) -> bgs_options:
 def bgs_csr_spmv(nrows, nnz, rowptr, col, val, x, y, lanes=0, stream=None) -> int:
     return lib().bgs_csr_spmv(int(nrows), int(nnz), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(x), _ptr(y),
                               int(lanes), _stream_ptr(stream))
+
+
+def bgs_launch_count() -> int:
+    return int(lib().bgs_launch_count())
 
 
 class Solver:
@@ -257,7 +262,7 @@ class Solver:
         return dict(launches=n.value, ms=ms.value, bytes=by.value)
 
 
-KERNEL_CLASSES = {"full_spmv": 0, "chebyshev": 1, "arnoldi": 2, "coupling": 3}
+KERNEL_CLASSES = {"full_spmv": 0, "chebyshev_fine": 1, "arnoldi": 2, "coupling": 3, "chebyshev_coarse": 4}
 
 
 def solver_for_system(system, order=None, device=True, **opts):

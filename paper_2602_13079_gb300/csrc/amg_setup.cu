@@ -266,8 +266,11 @@ static int mis2(const DCsr &S, uint32_t salt, int *state, Scratch &sc, cudaStrea
     for (;;) {
         rounds++;
         k_mis_m1<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, salt, m1.p);
+        CK_LAUNCH();
         k_mis_select<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, salt, m1.p);
+        CK_LAUNCH();
         k_mis_f1<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, f1.p);
+        CK_LAUNCH();
         CK(cudaMemsetAsync(sc.flags.p + 4, 0, sizeof(int), s));
         k_mis_out<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, f1.p, sc.flags.p + 4);
         CK_LAUNCH();
@@ -321,6 +324,7 @@ static int aggregate(const DCsr &S, const int *state, int *agg, Scratch &sc, cud
     CK_LAUNCH();
     int nagg = (int)scan_exclusive(rootid.p, rootid.p, n, sc, s);
     k_phase1<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, rootid.p, ph1.p);
+    CK_LAUNCH();
     CK(cudaMemsetAsync(sc.flags.p + 5, 0, sizeof(int), s));
     k_phase2<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, S.v.p, ph1.p, agg, sc.flags.p + 5);
     CK_LAUNCH();
@@ -498,7 +502,7 @@ __global__ void k_sg_sym_big(int nbig, const int *rows, const long long *toff, i
 // numeric accumulate + in-place compaction + rank sort into the output row
 __device__ void sg_numeric_row(int row, int *keys, double *vals, unsigned T, const int *arp, const int *aci,
                                const double *av, const int *brp, const int *bci, const double *bv, const int *crp,
-                               int *cci, double *cv) {
+                               int *cci, double *cv, int *err) {
     const int lane = threadIdx.x & 31;
     const unsigned mask = T - 1;
     for (unsigned t = lane; t < T; t += 32) {
@@ -533,6 +537,10 @@ __device__ void sg_numeric_row(int row, int *keys, double *vals, unsigned T, con
     }
     const int c = wpos;
     const int out = crp[row];
+    if (c != crp[row + 1] - out) {   // must equal the symbolic count; never write past the row
+        if (lane == 0) atomicOr(err, 1);
+        return;
+    }
     for (int t = lane; t < c; t += 32) {
         const int kt = keys[t];
         int rank = 0;
@@ -545,7 +553,7 @@ __device__ void sg_numeric_row(int row, int *keys, double *vals, unsigned T, con
 
 __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *arp, const int *aci, const double *av,
                                                           const int *brp, const int *bci, const double *bv,
-                                                          const int *crp, int *cci, double *cv) {
+                                                          const int *crp, int *cci, double *cv, int *err) {
     extern __shared__ double sg_nsm[];
     const int wib = threadIdx.x >> 5;
     double *vals = sg_nsm + wib * SG_NUM_T;
@@ -554,16 +562,16 @@ __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *arp,
         const int c = crp[row + 1] - crp[row];
         if (c == 0 || c > SG_NUM_T / 2) continue;
         const unsigned T = nextpow2u(2u * (unsigned)c);
-        sg_numeric_row(row, keys, vals, T, arp, aci, av, brp, bci, bv, crp, cci, cv);
+        sg_numeric_row(row, keys, vals, T, arp, aci, av, brp, bci, bv, crp, cci, cv, err);
     }
 }
 
 __global__ void k_sg_num_big(int nbig, const int *rows, const long long *toff, int *gkeys, double *gvals,
                              const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
-                             const double *bv, const int *crp, int *cci, double *cv) {
+                             const double *bv, const int *crp, int *cci, double *cv, int *err) {
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbig; b += (gridDim.x * blockDim.x) >> 5) {
         const unsigned T = (unsigned)(toff[b + 1] - toff[b]);
-        sg_numeric_row(rows[b], gkeys + toff[b], gvals + toff[b], T, arp, aci, av, brp, bci, bv, crp, cci, cv);
+        sg_numeric_row(rows[b], gkeys + toff[b], gvals + toff[b], T, arp, aci, av, brp, bci, bv, crp, cci, cv, err);
     }
 }
 
@@ -662,7 +670,9 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
     C.ci.alloc((size_t)C.nnz, s);
     C.v.alloc((size_t)C.nnz, s);
     const size_t num_smem = (sizeof(double) + sizeof(int)) * SG_WARPS * SG_NUM_T;
-    k_sg_num<<<blocks, SG_WARPS * 32, num_smem, s>>>(n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p);
+    CK(cudaMemsetAsync(sc.flags.p + 8, 0, sizeof(int), s));
+    k_sg_num<<<blocks, SG_WARPS * 32, num_smem, s>>>(n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
+                                                     sc.flags.p + 8);
     CK_LAUNCH();
     // rows too long for the shared table
     {
@@ -676,10 +686,14 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
             DBuf<int> gk((size_t)tot, s);
             DBuf<double> gv((size_t)tot, s);
             k_sg_num_big<<<grid_for((int64_t)nbig * 32, 256), 256, 0, s>>>(
-                nbig, rows.p, toff.p, gk.p, gv.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p);
+                nbig, rows.p, toff.p, gk.p, gv.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
+                sc.flags.p + 8);
             CK_LAUNCH();
         }
     }
+    CK(cudaMemcpyAsync(sc.h_flags + 8, sc.flags.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (sc.h_flags[8]) throw Error(BGS_INTERNAL, "SpGEMM numeric count differs from the symbolic count");
 }
 
 

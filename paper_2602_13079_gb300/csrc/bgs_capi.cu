@@ -46,7 +46,7 @@ struct bgs_ctx {
     bool prof = false;
     std::vector<EventPair> ev;
     size_t ev_used = 0;
-    KStats stats[4];
+    KStats stats[5];
 };
 
 namespace {
@@ -147,13 +147,14 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     const int deg = H.degree;
     const int vb = sizeof(VT), xb = sizeof(XT);
     const double cbytes = spmv_bytes(A, vb, xb, 4);
+    const int ccls = l == 0 ? 1 : 4;   // fine-level vs coarse-level Chebyshev steps
     // pre-smoothing from x = 0
     cheb_first<XT>(n, b, dinv, inv_theta, x0, d, s);
     XT *cur = x0, *oth = x1;
     double rho = 1.0 / sigma;
     for (int k = 1; k < deg; k++) {
         const double rn = 1.0 / (2.0 * sigma - rho);
-        Prof pf(h, 1, cbytes);
+        Prof pf(h, ccls, cbytes);
         cheb_step<VT, XT>(A, av, b, dinv, cur, oth, d, rn * rho, 2.0 * rn / delta, false, s);
         std::swap(cur, oth);
         rho = rn;
@@ -167,13 +168,13 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     // post-smoothing
     rho = 1.0 / sigma;
     {
-        Prof pf(h, 1, cbytes);
+        Prof pf(h, ccls, cbytes);
         cheb_step<VT, XT>(A, av, b, dinv, cur, oth, d, 0.0, inv_theta, true, s);
     }
     std::swap(cur, oth);
     for (int k = 1; k < deg; k++) {
         const double rn = 1.0 / (2.0 * sigma - rho);
-        Prof pf(h, 1, cbytes);
+        Prof pf(h, ccls, cbytes);
         cheb_step<VT, XT>(A, av, b, dinv, cur, oth, d, rn * rho, 2.0 * rn / delta, false, s);
         std::swap(cur, oth);
         rho = rn;
@@ -825,7 +826,7 @@ int bgs_set_profiling(bgs_handle h, int on) {
 }
 
 int bgs_kernel_stats(bgs_handle h, int cls, int64_t *launches, double *ms, double *bytes) {
-    if (!h || cls < 0 || cls > 3) return BGS_INVALID_ARG;
+    if (!h || cls < 0 || cls > 4) return BGS_INVALID_ARG;
     if (launches) *launches = h->stats[cls].launches;
     if (ms) *ms = h->stats[cls].ms;
     if (bytes) *bytes = h->stats[cls].bytes;
@@ -844,6 +845,8 @@ int bgs_csr_spmv(int64_t nrows, int64_t nnz, const int32_t *rowptr, const int32_
         return BGS_OK;
     });
 }
+
+int64_t bgs_launch_count(void) { return (int64_t)launch_count(); }
 
 void bgs_destroy(bgs_handle h) {
     if (!h) return;

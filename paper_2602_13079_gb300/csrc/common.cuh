@@ -29,7 +29,9 @@ inline void cuda_check(cudaError_t e, const char *file, int line) {
     throw Error(e == cudaErrorMemoryAllocation ? BGS_OOM : BGS_CUDA_ERROR, buf);
 }
 #define CK(x) ::bgs::cuda_check((x), __FILE__, __LINE__)
-#define CK_LAUNCH() ::bgs::cuda_check(cudaGetLastError(), __FILE__, __LINE__)
+// every kernel launch is followed by CK_LAUNCH(): it checks the launch and counts it
+void count_launch();
+#define CK_LAUNCH() (::bgs::count_launch(), ::bgs::cuda_check(cudaGetLastError(), __FILE__, __LINE__))
 
 // ------------------------------------------------------------------------------------------
 // Device buffers: stream-ordered allocation, freed on the stream they were allocated on.

@@ -27,6 +27,7 @@ struct Scratch {
 };
 
 // ---------------------------------------------------------------- util.cu
+long long launch_count();
 // out[0..n] = exclusive scan of in[0..n-1] (out[n] = total); in and out may alias.
 // Returns the total (synchronises the stream).  Throws if the total exceeds INT32_MAX.
 int64_t scan_exclusive(const int *in, int *out, int64_t n, Scratch &sc, cudaStream_t s);

@@ -1,9 +1,14 @@
 // Scans, reductions, validation, block assembly and small element-wise kernels.
+#include <atomic>
 #include <climits>
 
 #include "internal.h"
 
 namespace bgs {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void Scratch::init(cudaStream_t s) {
     partial.alloc(kSMs * 8 * 72, s);
@@ -64,23 +69,28 @@ __global__ void k_scan_sums(const int *__restrict__ in, int64_t n, long long *bs
 }
 
 __global__ void k_scan_ll_single(long long *a, int n) {
-    // exclusive scan of up to SCAN_B long longs in one block
+    // exclusive scan of n long longs in one block, chunk by chunk with a running carry
     __shared__ long long sw[32];
     __shared__ long long tot;
-    int base = threadIdx.x * SCAN_I;
-    long long v[SCAN_I], s = 0;
+    long long carry = 0;
+    for (int c0 = 0; c0 < n; c0 += SCAN_B) {
+        const int base = c0 + threadIdx.x * SCAN_I;
+        long long v[SCAN_I], s = 0;
 #pragma unroll
-    for (int k = 0; k < SCAN_I; k++) {
-        v[k] = (base + k < n) ? a[base + k] : 0;
-        s += v[k];
-    }
-    long long off = block_excl_scan(s, sw, &tot);
+        for (int k = 0; k < SCAN_I; k++) {
+            v[k] = (base + k < n) ? a[base + k] : 0;
+            s += v[k];
+        }
+        long long off = block_excl_scan(s, sw, &tot) + carry;
 #pragma unroll
-    for (int k = 0; k < SCAN_I; k++) {
-        if (base + k < n) a[base + k] = off;
-        off += v[k];
+        for (int k = 0; k < SCAN_I; k++) {
+            if (base + k < n) a[base + k] = off;
+            off += v[k];
+        }
+        carry += tot;
+        __syncthreads();
     }
-    if (threadIdx.x == 0) a[n] = tot;
+    if (threadIdx.x == 0) a[n] = carry;
 }
 
 __global__ void k_scan_apply(const int *in, int *out, int64_t n, const long long *boffs, long long *total) {
@@ -112,13 +122,10 @@ int64_t scan_exclusive(const int *in, int *out, int64_t n, Scratch &sc, cudaStre
         CK(cudaMemsetAsync(out, 0, sizeof(int), s));
         return 0;
     }
-    int64_t nb = (n + SCAN_B - 1) / SCAN_B;
-    if (nb + 1 > SCAN_B) throw Error(BGS_INTERNAL, "scan too large");
-    long long *bs = (long long *)sc.iscan.p;   // needs nb + 1 entries
-    if ((size_t)(nb + 2) * sizeof(long long) > sc.iscan.bytes()) throw Error(BGS_INTERNAL, "scan scratch");
+    const int64_t nb = (n + SCAN_B - 1) / SCAN_B;
+    long long *bs = (long long *)sc.iscan.p;   // nb + 1 block offsets, then the total
+    if ((size_t)(nb + 2) * sizeof(long long) > sc.iscan.bytes()) throw Error(BGS_INTERNAL, "scan too large");
     long long *total = bs + nb + 1;
-    if ((size_t)(nb + 2) * sizeof(long long) > sc.iscan.bytes() - sizeof(long long))
-        throw Error(BGS_INTERNAL, "scan scratch");
     k_scan_sums<<<(unsigned)nb, SCAN_T, 0, s>>>(in, n, bs);
     CK_LAUNCH();
     k_scan_ll_single<<<1, SCAN_T, 0, s>>>(bs, (int)nb);
