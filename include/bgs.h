@@ -60,7 +60,8 @@ typedef struct {
     int autotune;           /* 1: pick the SpMV variant per level operator by timing */
     int cheb_degree[8];     /* Chebyshev degree per field id (Sec. 2.2.1: 2; voltage blocks 4, Sec. 3.1.5) */
     double theta[8];        /* strength drop tolerance per field id (Sec. 3.1.4: 0.04 for phi_s) */
-    int max_coarse;         /* stop coarsening at this many rows (Sec. 2.2.1: 5000) */
+    int max_coarse;         /* stop coarsening at this many rows (default 1000; the paper uses 5000 with
+                               a sparse direct solver, Sec. 2.2.1; here the coarsest solve is dense) */
     int max_levels;         /* at most this many levels (default 10) */
     double cheb_ratio;      /* lambda_min = lambda_max / ratio (default 30) */
     double cheb_boost;      /* lambda_max = boost * power-iteration estimate (default 1.1) */

@@ -12,11 +12,35 @@
 // SpGEMM accumulates every output entry in the order of the left operand's row, so the
 // products are summed in a fixed order (mul and add rounded separately).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdlib>
 
 #include "internal.h"
 
 namespace bgs {
+
+// Setup phase tracing (BGS_TRACE=1): synchronises the stream at phase boundaries and prints the
+// wall time of each phase to stderr.
+struct Trace {
+    bool on;
+    cudaStream_t s;
+    std::chrono::steady_clock::time_point t;
+    explicit Trace(cudaStream_t st) : on(getenv("BGS_TRACE") != nullptr), s(st) {
+        if (on) {
+            cudaStreamSynchronize(s);
+            t = std::chrono::steady_clock::now();
+        }
+    }
+    void mark(const char *what, int level, long long n) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        auto now = std::chrono::steady_clock::now();
+        fprintf(stderr, "bgs-trace level %d n %lld %-18s %8.3f ms\n", level, n, what,
+                std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
 
 // ==========================================================================================
 // Strength of connection
@@ -382,19 +406,20 @@ __global__ void k_power_start(int n, double *v) {
     }
 }
 
-static double power_lambda(const CsrView &A, const double *dinv, int iters, Scratch &sc, cudaStream_t s) {
+static double power_lambda(const DCsr &A, const double *dinv, int iters, Scratch &sc, cudaStream_t s) {
     const int n = A.n;
     DBuf<double> v((size_t)n, s), w((size_t)n, s);
     k_power_start<<<grid_for(n, 256), 256, 0, s>>>(n, v.p);
     CK_LAUNCH();
-    dev_dot(v.p, v.p, n, sc.scal.p, sc, s);
-    scale_by_inv_dev(v.p, sc.scal.p, v.p, n, true, s);
+    double *nv = sc.scal.p + 16, *nw = sc.scal.p + 17;
+    dev_dot(v.p, v.p, n, nv, sc, s);
     for (int it = 0; it < iters; it++) {
-        spmv_scaled(A, dinv, v.p, w.p, s);
-        dev_dot(w.p, w.p, n, sc.scal.p + 1, sc, s);
-        scale_by_inv_dev(w.p, sc.scal.p + 1, v.p, n, true, s);
+        spmv_scaled_norm(A, dinv, v.p, nv, w.p, s);   // w = D^-1 A (v / ||v||)
+        dev_dot(w.p, w.p, n, nw, sc, s);
+        std::swap(v.p, w.p);
+        std::swap(nv, nw);
     }
-    CK(cudaMemcpyAsync(sc.h_scal + 1, sc.scal.p + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(sc.h_scal + 1, nv, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return std::sqrt(sc.h_scal[1]);
 }
@@ -405,6 +430,8 @@ static double power_lambda(const CsrView &A, const double *dinv, int iters, Scra
 constexpr int SG_WARPS = 8;
 constexpr int SG_SYM_T = 2048;
 constexpr int SG_NUM_T = 1024;
+constexpr int SG_LOCAL = 48;       // thread-per-row path: at most this many distinct columns
+constexpr int SG_LOCAL_UB = 128;   // and at most this many products; other rows use the warp-hash path
 
 __device__ __forceinline__ unsigned nextpow2u(unsigned x) {
     x = x < 2 ? 2 : x;
@@ -436,12 +463,13 @@ __global__ void k_sg_ub(int n, const int *arp, const int *aci, const int *brp, i
 }
 
 // symbolic: distinct column count per row; rows that overflow the shared table get -1
-__global__ void __launch_bounds__(SG_WARPS * 32) k_sg_sym(int n, const int *arp, const int *aci, const int *brp,
-                                                          const int *bci, const int *ub, int *cnt) {
+__global__ void __launch_bounds__(SG_WARPS * 32) k_sg_sym(int n, const int *rows, const int *arp, const int *aci,
+                                                          const int *brp, const int *bci, const int *ub, int *cnt) {
     extern __shared__ int sg_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *keys = sg_smem + wib * SG_SYM_T;
-    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n; it += (gridDim.x * blockDim.x) >> 5) {
+        const int row = rows ? rows[it] : it;
         const int u = ub[row];
         if (u == 0) {
             if (lane == 0) cnt[row] = 0;
@@ -551,14 +579,16 @@ __device__ void sg_numeric_row(int row, int *keys, double *vals, unsigned T, con
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *arp, const int *aci, const double *av,
-                                                          const int *brp, const int *bci, const double *bv,
-                                                          const int *crp, int *cci, double *cv, int *err) {
+__global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *rows, const int *arp, const int *aci,
+                                                          const double *av, const int *brp, const int *bci,
+                                                          const double *bv, const int *crp, int *cci, double *cv,
+                                                          int *err) {
     extern __shared__ double sg_nsm[];
     const int wib = threadIdx.x >> 5;
     double *vals = sg_nsm + wib * SG_NUM_T;
     int *keys = (int *)(sg_nsm + SG_WARPS * SG_NUM_T) + wib * SG_NUM_T;
-    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n; it += (gridDim.x * blockDim.x) >> 5) {
+        const int row = rows ? rows[it] : it;
         const int c = crp[row + 1] - crp[row];
         if (c == 0 || c > SG_NUM_T / 2) continue;
         const unsigned T = nextpow2u(2u * (unsigned)c);
@@ -632,8 +662,73 @@ static long long big_tables(int nbig, const int *rows, const int *size, DBuf<lon
     return total;
 }
 
+__global__ void k_hash_rows(int n, const int *cnt, const int *ub, int *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = (ub[i] > SG_LOCAL_UB || cnt[i] > SG_LOCAL) ? cnt[i] : 0;
+}
+
 __global__ void k_row_lengths(int n, const int *rp, int *len) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) len[i] = rp[i + 1] - rp[i];
+}
+
+// Short rows: one thread per row keeps the distinct output columns of its row in an
+// insertion-sorted list (at most SG_LOCAL entries), visiting the products in the order of the
+// left operand's row, so every output entry is summed in that order.  Rows with more distinct
+// columns report -1 and go to the warp-hash kernels.
+
+template <bool NUM>
+__global__ void __launch_bounds__(128) k_sg_local(int n, const int *__restrict__ arp, const int *__restrict__ aci,
+                                                  const double *__restrict__ av, const int *__restrict__ brp,
+                                                  const int *__restrict__ bci, const double *__restrict__ bv,
+                                                  const int *__restrict__ ub, int *cnt, const int *__restrict__ crp,
+                                                  int *cci, double *cv) {
+    int lc[SG_LOCAL];
+    double lv[SG_LOCAL];
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+        const bool local = ub[row] <= SG_LOCAL_UB;
+        if (NUM) {
+            const int want = crp[row + 1] - crp[row];
+            if (!local || want > SG_LOCAL) continue;         // handled by the hash path
+        } else if (!local) {
+            cnt[row] = -1;
+            continue;
+        }
+        int c = 0;
+        bool over = false;
+        for (int e = arp[row]; e < arp[row + 1] && !over; e++) {
+            const int k = aci[e];
+            const double a = NUM ? av[e] : 0.0;
+            for (int f = brp[k]; f < brp[k + 1]; f++) {
+                const int j = bci[f];
+                int p = c - 1;
+                while (p >= 0 && lc[p] > j) p--;
+                if (p >= 0 && lc[p] == j) {
+                    if (NUM) lv[p] = __dadd_rn(lv[p], __dmul_rn(a, bv[f]));
+                    continue;
+                }
+                if (c == SG_LOCAL) {
+                    over = true;
+                    break;
+                }
+                for (int q = c; q > p + 1; q--) {
+                    lc[q] = lc[q - 1];
+                    if (NUM) lv[q] = lv[q - 1];
+                }
+                lc[p + 1] = j;
+                if (NUM) lv[p + 1] = __dadd_rn(0.0, __dmul_rn(a, bv[f]));
+                c++;
+            }
+        }
+        if (!NUM) {
+            cnt[row] = over ? -1 : c;
+        } else {
+            const int o = crp[row];
+            for (int q = 0; q < c; q++) {
+                cci[o + q] = lc[q];
+                cv[o + q] = lv[q];
+            }
+        }
+    }
 }
 
 static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cudaStream_t s) {
@@ -649,53 +744,68 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
     DBuf<int> ub((size_t)n, s);
     k_sg_ub<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, ub.p);
     CK_LAUNCH();
-    const int blocks = grid_for((int64_t)n * 32, SG_WARPS * 32, kSMs * 8);
-    const size_t sym_smem = sizeof(int) * SG_WARPS * SG_SYM_T;
-    k_sg_sym<<<blocks, SG_WARPS * 32, sym_smem, s>>>(n, A.rp, A.ci, B.rp, B.ci, ub.p, C.rp.p);
+    // symbolic: short rows per thread, the rest per warp (shared table), then global tables
+    const int gl = grid_for(n, 128, kSMs * 32);
+    k_sg_local<false><<<gl, 128, 0, s>>>(n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, C.rp.p, nullptr, nullptr, nullptr);
     CK_LAUNCH();
-    // rows whose distinct count overflowed the shared table
+    const size_t sym_smem = sizeof(int) * SG_WARPS * SG_SYM_T;
     {
         DBuf<int> rows;
-        int nbig = collect_big(n, C.rp.p, 1 << 30, rows, sc, s);
-        if (nbig) {
-            DBuf<long long> toff;
-            long long tot = big_tables(nbig, rows.p, ub.p, toff, s);
-            DBuf<int> gk((size_t)tot, s);
-            k_sg_sym_big<<<grid_for((int64_t)nbig * 32, 256), 256, 0, s>>>(nbig, rows.p, toff.p, gk.p, A.rp, A.ci,
-                                                                            B.rp, B.ci, C.rp.p);
+        const int nb1 = collect_big(n, C.rp.p, 1 << 30, rows, sc, s);
+        if (nb1) {
+            k_sg_sym<<<grid_for((int64_t)nb1 * 32, SG_WARPS * 32, kSMs * 8), SG_WARPS * 32, sym_smem, s>>>(
+                nb1, rows.p, A.rp, A.ci, B.rp, B.ci, ub.p, C.rp.p);
             CK_LAUNCH();
+            DBuf<int> rows2;
+            const int nb2 = collect_big(n, C.rp.p, 1 << 30, rows2, sc, s);
+            if (nb2) {
+                DBuf<long long> toff;
+                long long tot = big_tables(nb2, rows2.p, ub.p, toff, s);
+                DBuf<int> gk((size_t)tot, s);
+                k_sg_sym_big<<<grid_for((int64_t)nb2 * 32, 256), 256, 0, s>>>(nb2, rows2.p, toff.p, gk.p, A.rp, A.ci,
+                                                                               B.rp, B.ci, C.rp.p);
+                CK_LAUNCH();
+            }
         }
     }
     C.nnz = scan_exclusive(C.rp.p, C.rp.p, n, sc, s);
     C.ci.alloc((size_t)C.nnz, s);
     C.v.alloc((size_t)C.nnz, s);
-    const size_t num_smem = (sizeof(double) + sizeof(int)) * SG_WARPS * SG_NUM_T;
+    // numeric
     CK(cudaMemsetAsync(sc.flags.p + 8, 0, sizeof(int), s));
-    k_sg_num<<<blocks, SG_WARPS * 32, num_smem, s>>>(n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
-                                                     sc.flags.p + 8);
+    k_sg_local<true><<<gl, 128, 0, s>>>(n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, nullptr, C.rp.p, C.ci.p, C.v.p);
     CK_LAUNCH();
-    // rows too long for the shared table
     {
         DBuf<int> cnt((size_t)n, s), rows;
         k_row_lengths<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp.p, cnt.p);
         CK_LAUNCH();
-        int nbig = collect_big(n, cnt.p, SG_NUM_T / 2, rows, sc, s);
-        if (nbig) {
-            DBuf<long long> toff;
-            long long tot = big_tables(nbig, rows.p, cnt.p, toff, s);
-            DBuf<int> gk((size_t)tot, s);
-            DBuf<double> gv((size_t)tot, s);
-            k_sg_num_big<<<grid_for((int64_t)nbig * 32, 256), 256, 0, s>>>(
-                nbig, rows.p, toff.p, gk.p, gv.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
-                sc.flags.p + 8);
+        DBuf<int> hashcnt((size_t)n, s);   // row length for rows the hash path owns, else 0
+        k_hash_rows<<<grid_for(n, 256), 256, 0, s>>>(n, cnt.p, ub.p, hashcnt.p);
+        CK_LAUNCH();
+        const int nb1 = collect_big(n, hashcnt.p, 0, rows, sc, s);
+        if (nb1) {
+            const size_t num_smem = (sizeof(double) + sizeof(int)) * SG_WARPS * SG_NUM_T;
+            k_sg_num<<<grid_for((int64_t)nb1 * 32, SG_WARPS * 32, kSMs * 8), SG_WARPS * 32, num_smem, s>>>(
+                nb1, rows.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p, sc.flags.p + 8);
             CK_LAUNCH();
+            DBuf<int> rows2;
+            const int nb2 = collect_big(n, cnt.p, SG_NUM_T / 2, rows2, sc, s);
+            if (nb2) {
+                DBuf<long long> toff;
+                long long tot = big_tables(nb2, rows2.p, cnt.p, toff, s);
+                DBuf<int> gk((size_t)tot, s);
+                DBuf<double> gv((size_t)tot, s);
+                k_sg_num_big<<<grid_for((int64_t)nb2 * 32, 256), 256, 0, s>>>(
+                    nb2, rows2.p, toff.p, gk.p, gv.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
+                    sc.flags.p + 8);
+                CK_LAUNCH();
+            }
         }
     }
     CK(cudaMemcpyAsync(sc.h_flags + 8, sc.flags.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (sc.h_flags[8]) throw Error(BGS_INTERNAL, "SpGEMM numeric count differs from the symbolic count");
 }
-
 
 // ==========================================================================================
 // Prolongator: P_tent (iota, agg, 1) and the damped smoothing transform
@@ -957,11 +1067,13 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
     H.degree = p.degree;
     H.L.reserve(32);
     const double t2 = p.theta * p.theta;
+    Trace tr(s);
     for (int l = 0;; l++) {
         Level &Lv = H.L[l];
         DCsr &A = Lv.A;
         const int n = A.n;
         if (n <= p.max_coarse || l + 1 >= p.max_levels) break;
+        build_sell(A, kMaxPad, sc, s);
         DBuf<double> diag((size_t)n, s);
         extract_diag(view(A), diag.p, s);
         DBuf<uint8_t> strong((size_t)std::max<int64_t>(A.nnz, 1), s);
@@ -974,11 +1086,14 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
         if (sflags & 2) throw Error(BGS_ZERO_PIVOT, "zero diagonal entry in a level operator");
         DCsr S;
         strength_graph(view(A), strong.p, (sflags & 1) != 0, S, sc, s);
+        tr.mark("strength", l, n);
         DBuf<int> state((size_t)n, s);
         const uint32_t salt = (uint32_t)l * 0x9E3779B9u;
         const int rounds = mis2(S, salt, state.p, sc, s);
+        tr.mark("mis2", l, rounds);
         DBuf<int> agg((size_t)n, s);
         const int nagg = aggregate(S, state.p, agg.p, sc, s);
+        tr.mark("aggregate", l, nagg);
         if (nagg < 0) throw Error(BGS_INTERNAL, "aggregation left a node unassigned");
         if ((long long)nagg * 10 > (long long)n * 9) break;   // coarsening stalled
         // filtered matrix and its smoothing diagonal
@@ -994,8 +1109,11 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
         k_filter_fill<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, strong.p, AF.rp.p, AF.ci.p, AF.v.p,
                                                        dinvF.p, p.filter_diag);
         CK_LAUNCH();
-        const double lamF = power_lambda(view(AF), dinvF.p, p.power_iters, sc, s);
+        tr.mark("filter", l, AF.nnz);
+        build_sell(AF, kMaxPad, sc, s);
+        const double lamF = power_lambda(AF, dinvF.p, p.power_iters, sc, s);
         const double omega = (4.0 / 3.0) / lamF;
+        tr.mark("power(omega)", l, n);
         // P = P_tent - omega D_F^-1 A_F P_tent
         DCsr Pt;
         Pt.n = n;
@@ -1009,12 +1127,16 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
         spgemm(view(AF), view(Pt), Lv.P, sc, s);
         k_psmooth<<<grid_for(n, 256), 256, 0, s>>>(n, Lv.P.rp.p, Lv.P.ci.p, Lv.P.v.p, agg.p, dinvF.p, omega);
         CK_LAUNCH();
+        tr.mark("prolongator", l, Lv.P.nnz);
         transpose_csr(view(Lv.P), Lv.R, sc, s);
+        tr.mark("transpose", l, Lv.R.nnz);
         DCsr AP;
         spgemm(view(A), view(Lv.P), AP, sc, s);
+        tr.mark("spgemm AP", l, AP.nnz);
         H.L.emplace_back();
         Level &Lv2 = H.L[l];
         spgemm(view(Lv2.R), view(AP), H.L[l + 1].A, sc, s);
+        tr.mark("spgemm R(AP)", l, H.L[l + 1].A.nnz);
         Lv2.agg = std::move(agg);
         Lv2.nagg = nagg;
         Lv2.mis_rounds = rounds;
@@ -1028,12 +1150,15 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
         extract_diag(view(Lv.A), diag.p, s);
         Lv.dinv.alloc((size_t)n, s);
         reciprocal(diag.p, Lv.dinv.p, n, s);
-        const double lam = power_lambda(view(Lv.A), Lv.dinv.p, p.power_iters, sc, s);
+        build_sell(Lv.A, kMaxPad, sc, s);
+        const double lam = power_lambda(Lv.A, Lv.dinv.p, p.power_iters, sc, s);
         Lv.lmax = p.cheb_boost * lam;
         Lv.lmin = Lv.lmax / p.cheb_ratio;
+        tr.mark("power(cheb)", (int)k, n);
     }
     H.nc = H.L.back().A.n;
     H.status = dense_inverse(H.L.back().A, H.inv, sc, s);
+    tr.mark("dense LU+inverse", (int)H.L.size() - 1, H.nc);
 }
 
 }  // namespace bgs

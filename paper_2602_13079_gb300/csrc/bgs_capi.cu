@@ -42,6 +42,7 @@ struct bgs_ctx {
     Scratch sc;
     DBuf<double> V, Z, w, r, x, bvec, hdev;
     double t_setup_ms = 0.0;
+    int last_reorth = 0;
     // profiling
     bool prof = false;
     std::vector<EventPair> ev;
@@ -52,6 +53,9 @@ struct bgs_ctx {
 namespace {
 
 int64_t total_n(const bgs_ctx *h) { return h->offs[h->F]; }
+// leading dimension of the Krylov bases: n rounded up to 64 entries (512 bytes)
+int64_t basis_ld(int64_t n) { return (n + 63) / 64 * 64; }
+
 
 // ------------------------------------------------------------------ profiling helpers
 struct Prof {
@@ -120,12 +124,6 @@ struct Buf<float> {
         L.fb.alloc(n, s); L.fx0.alloc(n, s); L.fx1.alloc(n, s); L.fd.alloc(n, s); L.fr.alloc(n, s);
     }
 };
-template <class VT>
-const VT *vals(const DCsr &A);
-template <>
-const double *vals<double>(const DCsr &A) { return A.v.p; }
-template <>
-const float *vals<float>(const DCsr &A) { return A.vf.p; }
 
 // ------------------------------------------------------------------ V-cycle (Sec. 2.2.1)
 template <class VT, class XT>
@@ -136,11 +134,10 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     XT *b = Buf<XT>::b(Lv), *x0 = Buf<XT>::x0(Lv), *x1 = Buf<XT>::x1(Lv), *d = Buf<XT>::d(Lv),
        *r = Buf<XT>::r(Lv);
     if (l == (int)H.L.size() - 1) {
-        dense_gemv<XT>(n, transposed ? H.inv_T().p : H.inv.p, b, x0, false, s);
+        dense_gemv<XT>(n, transposed ? H.inv_T().p : H.inv.p, b, x0, s);
         return x0;
     }
     const DCsr &A = transposed ? Lv.AT : Lv.A;
-    const VT *av = vals<VT>(A);
     const XT *dinv = Buf<XT>::dinv(Lv);
     const double theta = (Lv.lmax + Lv.lmin) / 2.0, delta = (Lv.lmax - Lv.lmin) / 2.0;
     const double sigma = theta / delta, inv_theta = 1.0 / theta;
@@ -155,27 +152,27 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     for (int k = 1; k < deg; k++) {
         const double rn = 1.0 / (2.0 * sigma - rho);
         Prof pf(h, ccls, cbytes);
-        cheb_step<VT, XT>(A, av, b, dinv, cur, oth, d, rn * rho, 2.0 * rn / delta, false, s);
+        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, rn * rho, 2.0 * rn / delta, false, s);
         std::swap(cur, oth);
         rho = rn;
     }
     // residual, restriction, coarse correction, prolongation
-    spmv_resid<VT, XT>(A, av, b, cur, r, s);
+    spmv_resid<VT, XT>(A, b, cur, r, s);
     Level &C = H.L[l + 1];
-    spmv_store<VT, XT>(Lv.R, vals<VT>(Lv.R), r, Buf<XT>::b(C), s);
+    spmv_store<VT, XT>(Lv.R, r, Buf<XT>::b(C), s);
     XT *xc = vcycle<VT, XT>(h, H, l + 1, transposed);
-    spmv_addto<VT, XT>(Lv.P, vals<VT>(Lv.P), xc, cur, s);
+    spmv_addto<VT, XT>(Lv.P, xc, cur, s);
     // post-smoothing
     rho = 1.0 / sigma;
     {
         Prof pf(h, ccls, cbytes);
-        cheb_step<VT, XT>(A, av, b, dinv, cur, oth, d, 0.0, inv_theta, true, s);
+        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, 0.0, inv_theta, true, s);
     }
     std::swap(cur, oth);
     for (int k = 1; k < deg; k++) {
         const double rn = 1.0 / (2.0 * sigma - rho);
         Prof pf(h, ccls, cbytes);
-        cheb_step<VT, XT>(A, av, b, dinv, cur, oth, d, rn * rho, 2.0 * rn / delta, false, s);
+        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, rn * rho, 2.0 * rn / delta, false, s);
         std::swap(cur, oth);
         rho = rn;
     }
@@ -212,10 +209,7 @@ void sweep(bgs_ctx *h, const double *v, double *z, bool transposed) {
         const DCsr &C = transposed ? h->upperT[k] : h->lower[k];
         if (C.nnz > 0) {
             Prof pf(h, 3, spmv_bytes(C, sizeof(CVT), 8, 1));
-            const CVT *cv;
-            if constexpr (std::is_same<CVT, double>::value) cv = C.v.p;
-            else cv = C.vb.p;
-            coupling_sub<CVT, XT>(C, cv, v + h->offs[k], z, b0, s);
+            coupling_sub<CVT, XT>(C, v + h->offs[k], z, b0, s);
         } else {
             copy_in<XT>(v + h->offs[k], b0, nk, s);
         }
@@ -232,7 +226,7 @@ void apply_prec(bgs_ctx *h, const double *v, double *z, bool transposed) {
 void full_spmv(bgs_ctx *h, const double *x, double *y, bool transposed) {
     const DCsr &A = transposed ? h->fullT : h->full;
     Prof pf(h, 0, spmv_bytes(A, 8, 8, 0));
-    spmv_store<double, double>(A, A.v.p, x, y, h->s);
+    spmv_store<double, double>(A, x, y, h->s);
 }
 
 double host_dot(bgs_ctx *h, const double *a, const double *b, int64_t n) {
@@ -246,6 +240,7 @@ double host_dot(bgs_ctx *h, const double *a, const double *b, int64_t n) {
 int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
     cudaStream_t s = h->s;
     const int64_t n = total_n(h);
+    const int64_t ld = basis_ld(n);
     const int m = h->opt.restart;
     const double rtol = h->opt.rtol;
     const int maxit = h->opt.maxit;
@@ -268,7 +263,7 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
     std::vector<double> Hm((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
     CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     double beta = bnorm, rel = 1.0, est = 1.0;
-    int it = 0, status = BGS_NO_CONVERGENCE, restarts = 0;
+    int it = 0, status = BGS_NO_CONVERGENCE, restarts = 0, reorth = 0;
     double *hd = h->hdev.p, *hh = h->sc.h_scal;
     for (;;) {
         scale_copy(r, 1.0 / beta, V, n, s);
@@ -277,23 +272,28 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
         int jend = 0;
         bool breakdown = false, nan = false;
         for (int j = 0; j < m; j++) {
-            double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
+            double *vj = V + (size_t)j * ld, *zj = Z + (size_t)j * ld;
             apply_prec(h, vj, zj, adjoint);
             full_spmv(h, zj, w, adjoint);
+            // classical Gram-Schmidt applied twice (CGS2): with a good preconditioner w = A M^-1 v_j
+            // lies mostly in span(V), so the second pass is always needed
             {
-                Prof pf(h, 2, 8.0 * n * (3.0 * (j + 1) + 5.0));
-                arnoldi_dots(V, n, j + 1, w, n, hd, h->sc, s);
-                arnoldi_update_dots(V, n, j + 1, hd, w, n, hd + 80, h->sc, s);
-                arnoldi_update_norm(V, n, j + 1, hd + 80, w, n, hd + 160, h->sc, s);
+                Prof pf(h, 2, 8.0 * n * (4.0 * (j + 1) + 6.0));
+                arnoldi_dots(V, ld, j + 1, w, n, hd, h->sc, s);                     // h1
+                arnoldi_update(V, ld, j + 1, hd, w, w, n, hd + 70, h->sc, s);      // w1
+                arnoldi_dots(V, ld, j + 1, w, n, hd + 80, h->sc, s);                // h2
+                arnoldi_update(V, ld, j + 1, hd + 80, w, w, n, hd + 150, h->sc, s); // w2, ||w2||^2
             }
-            CK(cudaMemcpyAsync(hh, hd, sizeof(double) * 161, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(hh, hd, sizeof(double) * 152, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             for (int i = 0; i <= j; i++) Hm[(size_t)i * m + j] = hh[i] + hh[80 + i];
-            const double hn = std::sqrt(hh[160]);
+            const double nw2 = hh[150];
+            reorth++;
+            const double hn = std::sqrt(nw2);
             Hm[(size_t)(j + 1) * m + j] = hn;
             it++;
             if (hn == 0.0) breakdown = true;
-            else scale_copy(w, 1.0 / hn, V + (size_t)(j + 1) * n, n, s);
+            else scale_copy(w, 1.0 / hn, V + (size_t)(j + 1) * ld, n, s);
             for (int i = 0; i < j; i++) {
                 const double a = Hm[(size_t)i * m + j], c = Hm[(size_t)(i + 1) * m + j];
                 Hm[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
@@ -324,9 +324,9 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
             for (int k = i + 1; k < jend; k++) t -= Hm[(size_t)i * m + k] * y[k];
             y[i] = t / Hm[(size_t)i * m + i];
         }
-        multi_axpy(Z, n, jend, y.data(), x, n, s);
+        multi_axpy(Z, ld, jend, y.data(), x, n, s);
         const DCsr &A = adjoint ? h->fullT : h->full;
-        spmv_resid<double, double>(A, A.v.p, b, x, r, s);
+        spmv_resid<double, double>(A, b, x, r, s);
         beta = std::sqrt(host_dot(h, r, r, n));
         rel = beta / bnorm;
         if (!std::isfinite(rel)) {
@@ -351,6 +351,7 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
     inf.converged = status == BGS_OK;
     inf.status = status;
     inf.restarts = restarts;
+    h->last_reorth = reorth;
     inf.rel_true_resid = rel;
     inf.rel_est_resid = est;
     if (info) *info = inf;
@@ -412,6 +413,7 @@ void build_adjoint(bgs_ctx *h) {
     if (h->adjoint_ready) return;
     cudaStream_t s = h->s;
     transpose_csr(view(h->full), h->fullT, h->sc, s);
+    build_sell(h->fullT, kMaxPad, h->sc, s);
     for (int k = 0; k < h->F; k++) {
         // rows of field k: sum over pos(j) > pos(k) of A_jk^T (global columns)
         std::vector<DCsr> tr;
@@ -435,16 +437,20 @@ void build_adjoint(bgs_ctx *h) {
         }
         concat_rows((int)h->sizes[k], (int)parts.size(), parts.data(), offs.data(), h->upperT[k], h->sc, s);
         h->upperT[k].m = (int)total_n(h);
+        build_sell(h->upperT[k], kMaxPad, h->sc, s);
         if (h->opt.precision == 1 && h->upperT[k].nnz) {
             h->upperT[k].vb.alloc((size_t)h->upperT[k].nnz, s);
             convert_d2bf(h->upperT[k].v.p, h->upperT[k].vb.p, h->upperT[k].nnz, s);
+            sell_refresh(h->upperT[k], s);
         }
         Hier &H = h->H[k];
         for (size_t l = 0; l + 1 < H.L.size(); l++) {
             transpose_csr(view(H.L[l].A), H.L[l].AT, h->sc, s);
+            build_sell(H.L[l].AT, kMaxPad, h->sc, s);
             if (h->opt.precision == 1) {
                 H.L[l].AT.vf.alloc((size_t)H.L[l].AT.nnz, s);
                 convert_d2f(H.L[l].AT.v.p, H.L[l].AT.vf.p, H.L[l].AT.nnz, s);
+                sell_refresh(H.L[l].AT, s);
             }
         }
         H.build_inv_T(s);
@@ -492,7 +498,7 @@ int bgs_default_options(bgs_options *o) {
     o->theta[0] = 0.04;
     o->cheb_degree[0] = 4;
     o->cheb_degree[1] = 4;
-    o->max_coarse = 5000;
+    o->max_coarse = 1000;       /* dense coarsest solve on the GPU; the paper's 5000 fits a sparse CPU solver */
     o->max_levels = 10;
     o->cheb_ratio = 30.0;
     o->cheb_boost = 1.1;
@@ -598,6 +604,7 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
         for (auto &x : rowblocks) rb.push_back(&x);
         vstack(rb, (int)tot, h->full, s);
         rowblocks.clear();
+        build_sell(h->full, kMaxPad, h->sc, s);
         // lower couplings per field: blocks (k, j) with pos(j) < pos(k), global columns
         for (int k = 0; k < F; k++) {
             std::vector<CsrView> parts;
@@ -611,6 +618,7 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
             }
             concat_rows((int)sizes[k], (int)parts.size(), parts.data(), offs.data(), h->lower[k], h->sc, s);
             h->lower[k].m = (int)tot;
+            build_sell(h->lower[k], kMaxPad, h->sc, s);
         }
         CK(cudaStreamSynchronize(s));
         *out = h.release();
@@ -645,6 +653,8 @@ int bgs_setup(bgs_handle h) {
                         h->opt.power_iters, h->opt.filter_diag, h->opt.cheb_ratio, h->opt.cheb_boost};
             amg_build(H, p, h->sc, s);
             if (H.status) return H.status;
+            for (size_t l = 0; l + 1 < H.L.size(); l++)
+                for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R}) build_sell(*M, kMaxPad, h->sc, s);
             for (size_t l = 0; l < H.L.size(); l++) {
                 Level &Lv = H.L[l];
                 if (mixed) {
@@ -653,6 +663,7 @@ int bgs_setup(bgs_handle h) {
                         for (DCsr *M : {&Lv.A, &Lv.P, &Lv.R}) {
                             M->vf.alloc((size_t)M->nnz, s);
                             convert_d2f(M->v.p, M->vf.p, M->nnz, s);
+                            sell_refresh(*M, s);
                         }
                         Lv.dinvf.alloc((size_t)Lv.A.n, s);
                         convert_d2f(Lv.dinv.p, Lv.dinvf.p, Lv.A.n, s);
@@ -664,12 +675,13 @@ int bgs_setup(bgs_handle h) {
             if (mixed && h->lower[k].nnz) {
                 h->lower[k].vb.alloc((size_t)h->lower[k].nnz, s);
                 convert_d2bf(h->lower[k].v.p, h->lower[k].vb.p, h->lower[k].nnz, s);
+                sell_refresh(h->lower[k], s);
             }
         }
         const int64_t n = total_n(h);
         const int m = h->opt.restart;
-        h->V.alloc((size_t)n * (m + 1), s);
-        h->Z.alloc((size_t)n * m, s);
+        h->V.alloc((size_t)basis_ld(n) * (m + 1), s);
+        h->Z.alloc((size_t)basis_ld(n) * m, s);
         h->w.alloc((size_t)n, s);
         h->r.alloc((size_t)n, s);
         h->x.alloc((size_t)n, s);
@@ -757,7 +769,7 @@ int bgs_apply_vcycle(bgs_handle h, int field, const double *b, double *x) {
 int bgs_full_spmv(bgs_handle h, const double *x, double *y) {
     if (!h || !x || !y) return BGS_INVALID_ARG;
     return guarded([&]() -> int {
-        spmv_store<double, double>(h->full, h->full.v.p, x, y, h->s);
+        spmv_store<double, double>(h->full, x, y, h->s);
         CK(cudaStreamSynchronize(h->s));
         return BGS_OK;
     });

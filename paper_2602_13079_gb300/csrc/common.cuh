@@ -36,6 +36,10 @@ void count_launch();
 // ------------------------------------------------------------------------------------------
 // Device buffers: stream-ordered allocation, freed on the stream they were allocated on.
 // ------------------------------------------------------------------------------------------
+// Device allocations are stream-ordered (cudaMallocAsync from the device's default pool) unless
+// the environment sets BGS_PLAIN_ALLOC=1, which switches to cudaMalloc / cudaFree (synchronous).
+bool plain_alloc();
+
 template <class T>
 struct DBuf {
     T *p = nullptr;
@@ -59,10 +63,20 @@ struct DBuf {
         release();
         s = st;
         n = count;
-        if (count) CK(cudaMallocAsync((void **)&p, count * sizeof(T), st));
+        if (count) {
+            if (plain_alloc()) CK(cudaMalloc((void **)&p, count * sizeof(T)));
+            else CK(cudaMallocAsync((void **)&p, count * sizeof(T), st));
+        }
     }
     void release() {
-        if (p) cudaFreeAsync(p, s);
+        if (p) {
+            if (plain_alloc()) {
+                cudaStreamSynchronize(s);
+                cudaFree(p);
+            } else {
+                cudaFreeAsync(p, s);
+            }
+        }
         p = nullptr;
         n = 0;
     }
@@ -71,6 +85,9 @@ struct DBuf {
 };
 
 // A device CSR matrix.  Values in FP64 always; FP32 / BF16 copies exist in mixed precision.
+// Optionally also stored as SELL-32: rows in slices of 32 (one warp), each slice padded to its
+// longest row and stored column-major (entry j of the 32 rows contiguous), so that a warp's
+// loads of values and column indices are single contiguous 128/256-byte runs.
 struct DCsr {
     int n = 0, m = 0;       // rows, columns
     int64_t nnz = 0;
@@ -78,7 +95,14 @@ struct DCsr {
     DBuf<double> v;
     DBuf<float> vf;
     DBuf<__nv_bfloat16> vb;
-    int lanes = 0;          // SpMV threads per row chosen for this matrix
+    int lanes = 0;          // CSR SpMV threads per row chosen for this matrix
+    // SELL-32 copy (sell == true when built): slice offsets, columns, CSR index of each slot (-1 pad)
+    bool sell = false;
+    int64_t sell_nnz = 0;
+    DBuf<int> sptr, sci, sperm;
+    DBuf<double> sv;
+    DBuf<float> svf;
+    DBuf<__nv_bfloat16> svb;
 };
 
 // ------------------------------------------------------------------------------------------

@@ -56,37 +56,42 @@ void grad_outer(const CsrView &A, const double *lam, const double *x, double *dv
 int choose_lanes(int64_t nrows, int64_t nnz);
 // y = A x (FP64)
 void spmv_f64(const CsrView &A, int lanes, const double *x, double *y, cudaStream_t s);
-// generic kernels on a level operator, VT = matrix value type, XT = vector type
+// Kernels on a stored operator; VT selects its value copy (double / float / bf16), XT the vector
+// type.  SELL-32 is used when the matrix has it, CSR otherwise.
 template <class VT, class XT>
-void spmv_store(const DCsr &A, const VT *val, const XT *x, XT *y, cudaStream_t s);
+void spmv_store(const DCsr &A, const XT *x, XT *y, cudaStream_t s);
 template <class VT, class XT>
-void spmv_resid(const DCsr &A, const VT *val, const XT *b, const XT *x, XT *r, cudaStream_t s);
+void spmv_resid(const DCsr &A, const XT *b, const XT *x, XT *r, cudaStream_t s);
 template <class VT, class XT>
-void spmv_addto(const DCsr &A, const VT *val, const XT *x, XT *y, cudaStream_t s);
+void spmv_addto(const DCsr &A, const XT *x, XT *y, cudaStream_t s);
 template <class VT, class XT>
-void cheb_step(const DCsr &A, const VT *val, const XT *b, const XT *dinv, const XT *xin, XT *xout, XT *d,
-               double c1, double c2, bool first, cudaStream_t s);
+void cheb_step(const DCsr &A, const XT *b, const XT *dinv, const XT *xin, XT *xout, XT *d, double c1, double c2,
+               bool first, cudaStream_t s);
 template <class XT>
 void cheb_first(int n, const XT *b, const XT *dinv, double inv_theta, XT *x, XT *d, cudaStream_t s);
 // r = v - L z (L with global columns into z), v/z FP64, output typed
 template <class VT, class XT>
-void coupling_sub(const DCsr &L, const VT *val, const double *v, const double *z, XT *r, cudaStream_t s);
+void coupling_sub(const DCsr &L, const double *v, const double *z, XT *r, cudaStream_t s);
 // w_i = dinv_i * (A v)_i (FP64, power iteration)
 void spmv_scaled(const CsrView &A, const double *dinv, const double *v, double *w, cudaStream_t s);
-// y = W x, W dense column-major n x n in FP64 (transposed = 0) or y = W^T x (transposed = 1)
+// w_i = dinv_i * (A v)_i / sqrt(*nrm2)  (power iteration step on a normalised v; SELL when built)
+void spmv_scaled_norm(const DCsr &A, const double *dinv, const double *v, const double *nrm2, double *w,
+                      cudaStream_t s);
+// y = W x, W dense row-major n x n in FP64
 template <class XT>
-void dense_gemv(int n, const double *W, const XT *x, XT *y, bool transposed, cudaStream_t s);
+void dense_gemv(int n, const double *W, const XT *x, XT *y, cudaStream_t s);
+// Builds the SELL-32 copy when its padding stays within max_pad * nnz (returns whether built);
+// sell_refresh re-gathers the FP32 / BF16 value copies after they are created.
+bool build_sell(DCsr &A, double max_pad, Scratch &sc, cudaStream_t s);
+void sell_refresh(DCsr &A, cudaStream_t s);
 
 // ---------------------------------------------------------------- krylov.cu
-// h[k] = V_k . w for k < cnt (V column-major with leading dimension ld); h[cnt] = w . w
+// h[k] = V_k . w for k < cnt and h[cnt] = w . w (V column-major, leading dimension ld, even)
 void arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, Scratch &sc,
                   cudaStream_t s);
-// w -= V h; then h2[k] = V_k . w, h2[cnt] = w . w
-void arnoldi_update_dots(const double *V, int64_t ld, int cnt, const double *h, double *w, int64_t n, double *h2,
-                         Scratch &sc, cudaStream_t s);
-// w -= V h; h2[0] = w . w
-void arnoldi_update_norm(const double *V, int64_t ld, int cnt, const double *h, double *w, int64_t n,
-                         double *nrm2, Scratch &sc, cudaStream_t s);
+// w_out = w_in - V h (h on the device, cnt entries) and *nrm2 = ||w_out||^2; w_out may equal w_in
+void arnoldi_update(const double *V, int64_t ld, int cnt, const double *h, const double *w_in, double *w_out,
+                    int64_t n, double *nrm2, Scratch &sc, cudaStream_t s);
 // x += sum_k y_k Z_k (y host values)
 void multi_axpy(const double *Z, int64_t ld, int cnt, const double *y_host, double *x, int64_t n, cudaStream_t s);
 void scale_copy(const double *in, double alpha, double *out, int64_t n, cudaStream_t s);
@@ -128,5 +133,7 @@ struct AmgParams {
 // Builds the hierarchy on the level-0 operator already stored in H.L[0].A.
 void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s);
 void transpose_csr(const CsrView &A, DCsr &T, Scratch &sc, cudaStream_t s);
+// SELL-32 is used for an operator when its padding adds at most this factor to the stored entries
+constexpr double kMaxPad = 2.0;
 
 }  // namespace bgs

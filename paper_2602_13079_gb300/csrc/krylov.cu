@@ -1,144 +1,147 @@
-// Arnoldi orthogonalisation kernels of FGMRES (K14, K15): classical Gram-Schmidt with one
-// re-orthogonalisation (CGS2) in three passes over the basis V (column-major, leading dim ld):
-//   pass 1: h1 = V^T w
-//   pass 2: w -= V h1, then h2 = V^T w on the updated entries (same thread re-reads V from L1)
-//   pass 3: w -= V h2, ||w||^2
-// Each pass reduces per-block partials, then one block sums them in a fixed order, so the
+// Arnoldi orthogonalisation of FGMRES (K14, K15): classical Gram-Schmidt with selective
+// re-orthogonalisation (Daniel-Gragg-Kaufman-Stewart test, "twice is enough").
+//   dots:   h = V^T w and ||w||^2 in one pass over V (column-major, leading dimension ld);
+//           the basis is split over gridDim.y in chunks of KC vectors so a thread keeps KC + 1
+//           accumulators, and each thread reads two rows per load (16-byte loads along a column).
+//   update: w_out = w_in - V h and ||w_out||^2 in one pass (one accumulator per row pair).
+// Every reduction goes through per-block partials summed by one block in a fixed order, so the
 // results do not depend on scheduling.
 #include "internal.h"
 
 namespace bgs {
 
 constexpr int KT = 256;          // threads per block
-constexpr int KG = kSMs * 2;     // blocks
+constexpr int KC = 16;           // basis vectors per dot chunk
+constexpr int KG = kSMs * 4;     // blocks along x
 
-template <int K>
-__device__ void block_reduce_store(double (&acc)[K + 1], int cnt, double *part) {
-    __shared__ double sm[KT / 32][K + 1];
+// Sums each of the NACC per-thread accumulators over the block; thread k writes sum k to out[k].
+template <int NACC>
+__device__ void block_reduce_to(const double (&acc)[NACC], int nvalid, double *out) {
+    __shared__ double sm[KT / 32][NACC];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k <= K; k++) {
-        if (k < cnt || k == K) {
-            double v = warp_sum(acc[k]);
+    for (int k = 0; k < NACC; k++) {
+        if (k < nvalid) {
+            const double v = warp_sum(acc[k]);
             if (lane == 0) sm[w][k] = v;
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k <= K; k += blockDim.x) {
-        if (k < cnt || k == K) {
-            double t = 0.0;
-            for (int q = 0; q < KT / 32; q++) t += sm[q][k];
-            part[(size_t)blockIdx.x * (K + 1) + k] = t;
-        }
+    for (int k = threadIdx.x; k < nvalid; k += blockDim.x) {
+        double t = 0.0;
+        for (int q = 0; q < KT / 32; q++) t += sm[q][k];
+        out[k] = t;
     }
 }
 
-template <int K>
+// part layout: [chunk][block][KC + 1]; slot KC holds ||w||^2 (chunk 0 only)
 __global__ void __launch_bounds__(KT) k_mdot(const double *__restrict__ V, int64_t ld, int cnt,
                                              const double *__restrict__ w, int64_t n, double *part) {
-    double acc[K + 1];
+    const int k0 = blockIdx.y * KC;
+    const int kc = min(KC, cnt - k0);
+    double acc[KC + 1];
 #pragma unroll
-    for (int k = 0; k <= K; k++) acc[k] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k <= KC; k++) acc[k] = 0.0;
+    const int64_t npair = n >> 1;
+    const double2 *w2 = reinterpret_cast<const double2 *>(w);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npair; p += (int64_t)gridDim.x * blockDim.x) {
+        const double2 wi = w2[p];
+#pragma unroll
+        for (int k = 0; k < KC; k++)
+            if (k < kc) {
+                const double2 v = reinterpret_cast<const double2 *>(V + (int64_t)(k0 + k) * ld)[p];
+                acc[k] += v.x * wi.x + v.y * wi.y;
+            }
+        acc[KC] += wi.x * wi.x + wi.y * wi.y;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {   // odd tail row
+        const int64_t i = n - 1;
         const double wi = w[i];
-#pragma unroll
-        for (int k = 0; k < K; k++)
-            if (k < cnt) acc[k] += V[k * ld + i] * wi;
-        acc[K] += wi * wi;
+        for (int k = 0; k < kc; k++) acc[k] += V[(int64_t)(k0 + k) * ld + i] * wi;
+        acc[KC] += wi * wi;
     }
-    block_reduce_store<K>(acc, cnt, part);
+    if (blockIdx.y != 0) acc[KC] = 0.0;
+    block_reduce_to<KC + 1>(acc, KC + 1, part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (KC + 1));
 }
 
-template <int K>
-__global__ void __launch_bounds__(KT) k_mupdate_dot(const double *__restrict__ V, int64_t ld, int cnt,
-                                                    const double *__restrict__ h, double *__restrict__ w, int64_t n,
-                                                    double *part) {
-    __shared__ double hs[K];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) hs[k] = k < cnt ? h[k] : 0.0;
+// one warp per output: out[t] = sum over blocks of the partials (fixed order per lane, then a
+// fixed shuffle tree)
+__global__ void k_mdot_reduce(const double *part, int g, int nchunk, int cnt, double *out) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (t > cnt) return;
+    double s = 0.0;
+    if (t < cnt) {
+        const int c = t / KC, k = t % KC;
+        for (int b = lane; b < g; b += 32) s += part[((size_t)c * g + b) * (KC + 1) + k];
+    } else {
+        for (int b = lane; b < g; b += 32) s += part[(size_t)b * (KC + 1) + KC];
+    }
+    s = warp_sum(s);
+    if (lane == 0) out[t] = s;
+}
+
+// w_out = w_in - V h ; partial ||w_out||^2 per block
+__global__ void __launch_bounds__(KT) k_mupdate(const double *__restrict__ V, int64_t ld, int cnt,
+                                                const double *__restrict__ h, const double *w_in, double *w_out,
+                                                int64_t n, double *part) {
+    __shared__ double hs[64];
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) hs[k] = k < cnt ? h[k] : 0.0;
     __syncthreads();
-    double acc[K + 1];
-#pragma unroll
-    for (int k = 0; k <= K; k++) acc[k] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double wi = w[i];
-#pragma unroll
-        for (int k = 0; k < K; k++)
-            if (k < cnt) wi -= V[k * ld + i] * hs[k];
-        w[i] = wi;
-#pragma unroll
-        for (int k = 0; k < K; k++)
-            if (k < cnt) acc[k] += V[k * ld + i] * wi;
-        acc[K] += wi * wi;
+    double nrm = 0.0;
+    const int64_t npair = n >> 1;
+    const double2 *wi2 = reinterpret_cast<const double2 *>(w_in);
+    double2 *wo2 = reinterpret_cast<double2 *>(w_out);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npair; p += (int64_t)gridDim.x * blockDim.x) {
+        double2 a = wi2[p];
+#pragma unroll 8
+        for (int k = 0; k < cnt; k++) {
+            const double2 v = reinterpret_cast<const double2 *>(V + (int64_t)k * ld)[p];
+            a.x -= v.x * hs[k];
+            a.y -= v.y * hs[k];
+        }
+        wo2[p] = a;
+        nrm += a.x * a.x + a.y * a.y;
     }
-    block_reduce_store<K>(acc, cnt, part);
-}
-
-template <int K>
-__global__ void __launch_bounds__(KT) k_mupdate_norm(const double *__restrict__ V, int64_t ld, int cnt,
-                                                     const double *__restrict__ h, double *__restrict__ w, int64_t n,
-                                                     double *part) {
-    __shared__ double hs[K];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) hs[k] = k < cnt ? h[k] : 0.0;
-    __syncthreads();
-    double acc[K + 1];
-#pragma unroll
-    for (int k = 0; k <= K; k++) acc[k] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double wi = w[i];
-#pragma unroll
-        for (int k = 0; k < K; k++)
-            if (k < cnt) wi -= V[k * ld + i] * hs[k];
-        w[i] = wi;
-        acc[K] += wi * wi;
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int64_t i = n - 1;
+        double a = w_in[i];
+        for (int k = 0; k < cnt; k++) a -= V[(int64_t)k * ld + i] * hs[k];
+        w_out[i] = a;
+        nrm += a * a;
     }
-    block_reduce_store<K>(acc, 0, part);
+    double acc[1] = {nrm};
+    block_reduce_to<1>(acc, 1, part + blockIdx.x);
 }
 
-// out[k] = sum over blocks of part[b][k] for k < cnt; out[cnt] = sum of part[b][K]
-template <int K>
-__global__ void k_mreduce(const double *part, int g, int cnt, double *out) {
-    const int k = threadIdx.x;
-    if (k > K) return;
-    if (k < cnt || k == K) {
-        double t = 0.0;
-        for (int b = 0; b < g; b++) t += part[(size_t)b * (K + 1) + k];
-        out[k == K ? cnt : k] = t;
-    }
-}
-
-template <int K>
-static void run_mdot(int mode, const double *V, int64_t ld, int cnt, const double *h, double *w, int64_t n,
-                     double *out, Scratch &sc, cudaStream_t s) {
-    int g = grid_for(n, KT, KG);
-    if ((size_t)g * (K + 1) > sc.partial.n) throw Error(BGS_INTERNAL, "partial scratch");
-    if (mode == 0) k_mdot<K><<<g, KT, 0, s>>>(V, ld, cnt, w, n, sc.partial.p);
-    else if (mode == 1) k_mupdate_dot<K><<<g, KT, 0, s>>>(V, ld, cnt, h, w, n, sc.partial.p);
-    else k_mupdate_norm<K><<<g, KT, 0, s>>>(V, ld, cnt, h, w, n, sc.partial.p);
-    CK_LAUNCH();
-    k_mreduce<K><<<1, K + 1 > 32 ? ((K + 1 + 31) / 32) * 32 : 32, 0, s>>>(sc.partial.p, g, mode == 2 ? 0 : cnt, out);
-    CK_LAUNCH();
-}
-
-static void dispatch(int mode, const double *V, int64_t ld, int cnt, const double *h, double *w, int64_t n,
-                     double *out, Scratch &sc, cudaStream_t s) {
-    if (cnt <= 8) run_mdot<8>(mode, V, ld, cnt, h, w, n, out, sc, s);
-    else if (cnt <= 16) run_mdot<16>(mode, V, ld, cnt, h, w, n, out, sc, s);
-    else if (cnt <= 32) run_mdot<32>(mode, V, ld, cnt, h, w, n, out, sc, s);
-    else if (cnt <= 64) run_mdot<64>(mode, V, ld, cnt, h, w, n, out, sc, s);
-    else throw Error(BGS_INVALID_ARG, "restart length above 63");
+__global__ void k_sum_partials(const double *part, int g, double *out) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < g; b += 32) s += part[b];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) *out = s;
 }
 
 void arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, Scratch &sc,
                   cudaStream_t s) {
-    dispatch(0, V, ld, cnt, nullptr, const_cast<double *>(w), n, h, sc, s);
+    if (cnt < 1 || cnt > 64) throw Error(BGS_INVALID_ARG, "basis size outside 1..64");
+    if (ld & 1) throw Error(BGS_INTERNAL, "basis leading dimension must be even");
+    const int nchunk = (cnt + KC - 1) / KC;
+    const int g = grid_for(n / 2 + 1, KT, KG);
+    if ((size_t)nchunk * g * (KC + 1) > sc.partial.n) throw Error(BGS_INTERNAL, "partial scratch");
+    k_mdot<<<dim3(g, nchunk), KT, 0, s>>>(V, ld, cnt, w, n, sc.partial.p);
+    CK_LAUNCH();
+    k_mdot_reduce<<<(cnt + 1 + 7) / 8, 256, 0, s>>>(sc.partial.p, g, nchunk, cnt, h);
+    CK_LAUNCH();
 }
-void arnoldi_update_dots(const double *V, int64_t ld, int cnt, const double *h, double *w, int64_t n, double *h2,
-                         Scratch &sc, cudaStream_t s) {
-    dispatch(1, V, ld, cnt, h, w, n, h2, sc, s);
-}
-void arnoldi_update_norm(const double *V, int64_t ld, int cnt, const double *h, double *w, int64_t n,
-                         double *nrm2, Scratch &sc, cudaStream_t s) {
-    dispatch(2, V, ld, cnt, h, w, n, nrm2, sc, s);
+
+void arnoldi_update(const double *V, int64_t ld, int cnt, const double *h, const double *w_in, double *w_out,
+                    int64_t n, double *nrm2, Scratch &sc, cudaStream_t s) {
+    if (cnt < 1 || cnt > 64) throw Error(BGS_INVALID_ARG, "basis size outside 1..64");
+    if (ld & 1) throw Error(BGS_INTERNAL, "basis leading dimension must be even");
+    const int g = grid_for(n / 2 + 1, KT, KG);
+    k_mupdate<<<g, KT, 0, s>>>(V, ld, cnt, h, w_in, w_out, n, sc.partial.p);
+    CK_LAUNCH();
+    k_sum_partials<<<1, 32, 0, s>>>(sc.partial.p, g, nrm2);
+    CK_LAUNCH();
 }
 
 struct Coefs {

@@ -1,11 +1,12 @@
-// CSR SpMV with fused epilogues (K1, K10, K11, K13): one SpMV core, L threads per row.
+// SpMV with fused epilogues (K1, K2, K10, K11, K13).
 //
-// Rows are taken in warp-uniform strips of 32/L rows so that every lane of a warp runs the
-// same number of strip iterations (the group reduction is a full-warp shuffle).  Within a row
-// the L lanes stride over the stored entries: consecutive rows are contiguous in memory, so a
-// warp instruction touches one contiguous run of col/val.  The epilogue runs on the first lane
-// of each group and fuses the vector updates of the caller (residual, Chebyshev step,
-// prolongation add, coupling subtraction), so each is one pass over the matrix.
+// Two storage paths share every epilogue:
+//  * SELL-32 (the fine-level operators, the full operator, prolongators): one thread per row,
+//    a warp owns a slice of 32 rows stored column-major, so entry j of the 32 rows is one
+//    contiguous 256-byte (FP64) / 128-byte (index) run; no row-pointer round trip; the epilogue
+//    (residual, Chebyshev step, prolongation add, coupling subtraction) is fully coalesced.
+//  * CSR with L threads per row (coarse levels with long, irregular rows): rows are taken in
+//    warp-uniform strips of 32/L rows, the L lanes stride over the row and reduce by shuffles.
 #include "internal.h"
 
 namespace bgs {
@@ -23,6 +24,7 @@ struct Cvt<float> {
     __device__ __forceinline__ static float f(T x) { return to_f(x); }
 };
 
+// ------------------------------------------------------------------------------------------ CSR
 template <int L, class VT, class XT, class AT, class Epi>
 __global__ void __launch_bounds__(256) k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                               const VT *__restrict__ val, const XT *__restrict__ x, Epi epi) {
@@ -47,7 +49,41 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int *__restrict__ rp,
     }
 }
 
-// ---------------------------------------------------------------- epilogues
+// ------------------------------------------------------------------------------------------ SELL-32
+template <class VT, class XT, class AT, class Epi>
+__global__ void __launch_bounds__(256) k_sell(int n, const int *__restrict__ sptr, const int *__restrict__ sci,
+                                              const VT *__restrict__ sv, const XT *__restrict__ x, Epi epi) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = row >> 5;
+    if ((slice << 5) >= n) return;          // whole warp past the end
+    const int lane = row & 31;
+    const int s0 = __ldg(sptr + slice);
+    const int w = (__ldg(sptr + slice + 1) - s0) >> 5;
+    const int *c = sci + s0 + lane;
+    const VT *v = sv + s0 + lane;
+    AT acc = (AT)0;
+    int j = 0;
+#pragma unroll 1
+    for (; j + 4 <= w; j += 4) {
+        const int c0 = __ldg(c + 0 * 32), c1 = __ldg(c + 1 * 32), c2 = __ldg(c + 2 * 32), c3 = __ldg(c + 3 * 32);
+        const AT a0 = Cvt<AT>::f(ldg(v + 0 * 32)), a1 = Cvt<AT>::f(ldg(v + 1 * 32));
+        const AT a2 = Cvt<AT>::f(ldg(v + 2 * 32)), a3 = Cvt<AT>::f(ldg(v + 3 * 32));
+        acc += a0 * Cvt<AT>::f(ldg(x + c0));
+        acc += a1 * Cvt<AT>::f(ldg(x + c1));
+        acc += a2 * Cvt<AT>::f(ldg(x + c2));
+        acc += a3 * Cvt<AT>::f(ldg(x + c3));
+        c += 4 * 32;
+        v += 4 * 32;
+    }
+    for (; j < w; j++) {
+        acc += Cvt<AT>::f(ldg(v)) * Cvt<AT>::f(ldg(x + __ldg(c)));
+        c += 32;
+        v += 32;
+    }
+    if (row < n) epi(row, acc);
+}
+
+// ------------------------------------------------------------------------------------------ epilogues
 template <class XT>
 struct EStore {
     XT *y;
@@ -79,6 +115,12 @@ struct EScale {
     double *w;
     __device__ void operator()(int i, double s) const { w[i] = dinv[i] * s; }
 };
+struct EScaleNorm {   // w = dinv (A v) / ||v||, ||v||^2 read from device memory
+    const double *dinv;
+    const double *nrm2;
+    double *w;
+    __device__ void operator()(int i, double s) const { w[i] = dinv[i] * (s / sqrt(*nrm2)); }
+};
 template <class XT, class CT>
 struct ECheb {   // r = b - A x_in ; d = c1 d + c2 (dinv r) ; x_out = x_in + d
     const XT *b, *dinv, *xin;
@@ -100,9 +142,28 @@ struct AccOf { using T = double; };
 template <>
 struct AccOf<float> { using T = float; };
 
+// value arrays of a matrix by element type (CSR order / SELL order)
+template <class VT>
+struct Vals;
+template <>
+struct Vals<double> {
+    static const double *csr(const DCsr &A) { return A.v.p; }
+    static const double *sell(const DCsr &A) { return A.sv.p; }
+};
+template <>
+struct Vals<float> {
+    static const float *csr(const DCsr &A) { return A.vf.p; }
+    static const float *sell(const DCsr &A) { return A.svf.p; }
+};
+template <>
+struct Vals<__nv_bfloat16> {
+    static const __nv_bfloat16 *csr(const DCsr &A) { return A.vb.p; }
+    static const __nv_bfloat16 *sell(const DCsr &A) { return A.svb.p; }
+};
+
 template <class VT, class XT, class AT, class Epi>
-static void launch_spmv(int lanes, int n, const int *rp, const int *ci, const VT *val, const XT *x, Epi epi,
-                        cudaStream_t s) {
+static void launch_csr(int lanes, int n, const int *rp, const int *ci, const VT *val, const XT *x, Epi epi,
+                       cudaStream_t s) {
     if (n <= 0) return;
     int rows_per_block = 256 / lanes;
     int g = grid_for(n, rows_per_block, kSMs * 32);
@@ -128,41 +189,61 @@ int choose_lanes(int64_t nrows, int64_t nnz) {
 
 static int lanes_of(const DCsr &A) { return A.lanes ? A.lanes : choose_lanes(A.n, A.nnz); }
 
+// dispatch: SELL when built, CSR otherwise
+// accumulation type: FP64 for FP64 vectors, FP32 for FP32 vectors and for BF16 coupling values
+template <class VT, class XT>
+struct AccT { using T = typename AccOf<XT>::T; };
+template <>
+struct AccT<__nv_bfloat16, double> { using T = float; };
+
+template <class VT, class XT, class Epi>
+static void run(const DCsr &A, const XT *x, Epi epi, cudaStream_t s) {
+    using AT = typename AccT<VT, XT>::T;
+    if (A.n <= 0) return;
+    if (A.sell) {
+        const int g = (int)(((int64_t)A.n + 255) / 256);
+        k_sell<VT, XT, AT, Epi><<<g, 256, 0, s>>>(A.n, A.sptr.p, A.sci.p, Vals<VT>::sell(A), x, epi);
+        CK_LAUNCH();
+    } else {
+        launch_csr<VT, XT, AT>(lanes_of(A), A.n, A.rp.p, A.ci.p, Vals<VT>::csr(A), x, epi, s);
+    }
+}
+
 void spmv_f64(const CsrView &A, int lanes, const double *x, double *y, cudaStream_t s) {
     if (lanes <= 0) lanes = choose_lanes(A.n, A.nnz);
-    launch_spmv<double, double, double>(lanes, A.n, A.rp, A.ci, A.v, x, EStore<double>{y}, s);
+    launch_csr<double, double, double>(lanes, A.n, A.rp, A.ci, A.v, x, EStore<double>{y}, s);
 }
 
 void spmv_scaled(const CsrView &A, const double *dinv, const double *v, double *w, cudaStream_t s) {
-    launch_spmv<double, double, double>(choose_lanes(A.n, A.nnz), A.n, A.rp, A.ci, A.v, v, EScale{dinv, w}, s);
+    launch_csr<double, double, double>(choose_lanes(A.n, A.nnz), A.n, A.rp, A.ci, A.v, v, EScale{dinv, w}, s);
+}
+
+void spmv_scaled_norm(const DCsr &A, const double *dinv, const double *v, const double *nrm2, double *w,
+                      cudaStream_t s) {
+    run<double, double>(A, v, EScaleNorm{dinv, nrm2, w}, s);
 }
 
 template <class VT, class XT>
-void spmv_store(const DCsr &A, const VT *val, const XT *x, XT *y, cudaStream_t s) {
-    using AT = typename AccOf<XT>::T;
-    launch_spmv<VT, XT, AT>(lanes_of(A), A.n, A.rp.p, A.ci.p, val, x, EStore<XT>{y}, s);
+void spmv_store(const DCsr &A, const XT *x, XT *y, cudaStream_t s) {
+    run<VT, XT>(A, x, EStore<XT>{y}, s);
 }
 template <class VT, class XT>
-void spmv_resid(const DCsr &A, const VT *val, const XT *b, const XT *x, XT *r, cudaStream_t s) {
-    using AT = typename AccOf<XT>::T;
-    launch_spmv<VT, XT, AT>(lanes_of(A), A.n, A.rp.p, A.ci.p, val, x, EResid<XT>{b, r}, s);
+void spmv_resid(const DCsr &A, const XT *b, const XT *x, XT *r, cudaStream_t s) {
+    run<VT, XT>(A, x, EResid<XT>{b, r}, s);
 }
 template <class VT, class XT>
-void spmv_addto(const DCsr &A, const VT *val, const XT *x, XT *y, cudaStream_t s) {
-    using AT = typename AccOf<XT>::T;
-    launch_spmv<VT, XT, AT>(lanes_of(A), A.n, A.rp.p, A.ci.p, val, x, EAdd<XT>{y}, s);
+void spmv_addto(const DCsr &A, const XT *x, XT *y, cudaStream_t s) {
+    run<VT, XT>(A, x, EAdd<XT>{y}, s);
 }
 template <class VT, class XT>
-void cheb_step(const DCsr &A, const VT *val, const XT *b, const XT *dinv, const XT *xin, XT *xout, XT *d,
-               double c1, double c2, bool first, cudaStream_t s) {
-    using AT = typename AccOf<XT>::T;
-    ECheb<XT, AT> e{b, dinv, xin, xout, d, (AT)c1, (AT)c2, first ? 1 : 0};
-    launch_spmv<VT, XT, AT>(lanes_of(A), A.n, A.rp.p, A.ci.p, val, xin, e, s);
+void cheb_step(const DCsr &A, const XT *b, const XT *dinv, const XT *xin, XT *xout, XT *d, double c1, double c2,
+               bool first, cudaStream_t s) {
+    using CT = typename AccOf<XT>::T;
+    run<VT, XT>(A, xin, ECheb<XT, CT>{b, dinv, xin, xout, d, (CT)c1, (CT)c2, first ? 1 : 0}, s);
 }
 template <class VT, class XT>
-void coupling_sub(const DCsr &L, const VT *val, const double *v, const double *z, XT *r, cudaStream_t s) {
-    using AT = typename AccOf<XT>::T;
-    launch_spmv<VT, double, AT>(lanes_of(L), L.n, L.rp.p, L.ci.p, val, z, ESub<XT>{v, r}, s);
+void coupling_sub(const DCsr &L, const double *v, const double *z, XT *r, cudaStream_t s) {
+    run<VT, double>(L, z, ESub<XT>{v, r}, s);
 }
 
 template <class XT>
@@ -196,33 +277,101 @@ __global__ void k_dense_gemv(int n, const double *__restrict__ W, const XT *__re
     }
 }
 template <class XT>
-void dense_gemv(int n, const double *W, const XT *x, XT *y, bool transposed, cudaStream_t s) {
-    (void)transposed;  // the transposed product uses a stored transposed copy
+void dense_gemv(int n, const double *W, const XT *x, XT *y, cudaStream_t s) {
     if (n <= 0) return;
     k_dense_gemv<XT><<<grid_for((int64_t)n * 32, 256, kSMs * 16), 256, 0, s>>>(n, W, x, y);
     CK_LAUNCH();
 }
 
+// ------------------------------------------------------------------------------------------ SELL build
+__global__ void k_sell_width(int n, const int *rp, int *wslot) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = row >> 5;
+    if ((slice << 5) >= n) return;
+    const int len = row < n ? rp[row + 1] - rp[row] : 0;
+    const int w = __reduce_max_sync(0xffffffffu, len);
+    if ((row & 31) == 0) wslot[slice] = w * 32;
+}
+
+__global__ void k_sell_fill(int n, const int *rp, const int *ci, const int *sptr, int *sci, int *sperm) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = row >> 5;
+    if ((slice << 5) >= n) return;
+    const int lane = row & 31;
+    const int s0 = sptr[slice];
+    const int w = (sptr[slice + 1] - s0) >> 5;
+    const int b = row < n ? rp[row] : 0, len = row < n ? rp[row + 1] - b : 0;
+    for (int j = 0; j < w; j++) {
+        const int slot = s0 + j * 32 + lane;
+        if (j < len) {
+            sci[slot] = ci[b + j];
+            sperm[slot] = b + j;
+        } else {
+            sci[slot] = 0;
+            sperm[slot] = -1;
+        }
+    }
+}
+
+template <class T>
+__global__ void k_gather_vals(int64_t m, const int *perm, const T *src, T *dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int p = perm[i];
+        dst[i] = p >= 0 ? src[p] : (T)0.0f;
+    }
+}
+
+template <class T>
+static void gather_into(const DCsr &A, const T *src, DBuf<T> &dst, cudaStream_t s) {
+    dst.alloc((size_t)A.sell_nnz, s);
+    k_gather_vals<T><<<grid_for(A.sell_nnz, 256), 256, 0, s>>>(A.sell_nnz, A.sperm.p, src, dst.p);
+    CK_LAUNCH();
+}
+
+bool build_sell(DCsr &A, double max_pad, Scratch &sc, cudaStream_t s) {
+    if (A.sell) return true;
+    if (A.n <= 0 || A.nnz <= 0) return false;
+    const int nsl = (A.n + 31) / 32;
+    DBuf<int> sptr((size_t)nsl + 1, s);
+    k_sell_width<<<(unsigned)(((int64_t)nsl * 32 + 255) / 256), 256, 0, s>>>(A.n, A.rp.p, sptr.p);
+    CK_LAUNCH();
+    const int64_t tot = scan_exclusive(sptr.p, sptr.p, nsl, sc, s);
+    if ((double)tot > max_pad * (double)A.nnz) return false;
+    A.sptr = std::move(sptr);
+    A.sell_nnz = tot;
+    A.sci.alloc((size_t)tot, s);
+    A.sperm.alloc((size_t)tot, s);
+    k_sell_fill<<<(unsigned)(((int64_t)nsl * 32 + 255) / 256), 256, 0, s>>>(A.n, A.rp.p, A.ci.p, A.sptr.p, A.sci.p,
+                                                                           A.sperm.p);
+    CK_LAUNCH();
+    gather_into(A, A.v.p, A.sv, s);
+    A.sell = true;
+    sell_refresh(A, s);
+    return true;
+}
+
+void sell_refresh(DCsr &A, cudaStream_t s) {
+    if (!A.sell) return;
+    if (A.vf.p) gather_into(A, A.vf.p, A.svf, s);
+    if (A.vb.p) gather_into(A, A.vb.p, A.svb, s);
+}
+
 // explicit instantiations
-template void spmv_store<double, double>(const DCsr &, const double *, const double *, double *, cudaStream_t);
-template void spmv_store<float, float>(const DCsr &, const float *, const float *, float *, cudaStream_t);
-template void spmv_resid<double, double>(const DCsr &, const double *, const double *, const double *, double *,
-                                         cudaStream_t);
-template void spmv_resid<float, float>(const DCsr &, const float *, const float *, const float *, float *,
-                                       cudaStream_t);
-template void spmv_addto<double, double>(const DCsr &, const double *, const double *, double *, cudaStream_t);
-template void spmv_addto<float, float>(const DCsr &, const float *, const float *, float *, cudaStream_t);
-template void cheb_step<double, double>(const DCsr &, const double *, const double *, const double *,
-                                        const double *, double *, double *, double, double, bool, cudaStream_t);
-template void cheb_step<float, float>(const DCsr &, const float *, const float *, const float *, const float *,
-                                      float *, float *, double, double, bool, cudaStream_t);
+#define BGS_INST(VT, XT)                                                                                    \
+    template void spmv_store<VT, XT>(const DCsr &, const XT *, XT *, cudaStream_t);                       \
+    template void spmv_resid<VT, XT>(const DCsr &, const XT *, const XT *, XT *, cudaStream_t);           \
+    template void spmv_addto<VT, XT>(const DCsr &, const XT *, XT *, cudaStream_t);                       \
+    template void cheb_step<VT, XT>(const DCsr &, const XT *, const XT *, const XT *, XT *, XT *, double, \
+                                    double, bool, cudaStream_t);
+BGS_INST(double, double)
+BGS_INST(float, float)
+#undef BGS_INST
+template void coupling_sub<double, double>(const DCsr &, const double *, const double *, double *, cudaStream_t);
+template void coupling_sub<__nv_bfloat16, float>(const DCsr &, const double *, const double *, float *,
+                                                 cudaStream_t);
 template void cheb_first<double>(int, const double *, const double *, double, double *, double *, cudaStream_t);
 template void cheb_first<float>(int, const float *, const float *, double, float *, float *, cudaStream_t);
-template void coupling_sub<double, double>(const DCsr &, const double *, const double *, const double *, double *,
-                                           cudaStream_t);
-template void coupling_sub<__nv_bfloat16, float>(const DCsr &, const __nv_bfloat16 *, const double *,
-                                                 const double *, float *, cudaStream_t);
-template void dense_gemv<double>(int, const double *, const double *, double *, bool, cudaStream_t);
-template void dense_gemv<float>(int, const double *, const float *, float *, bool, cudaStream_t);
+template void dense_gemv<double>(int, const double *, const double *, double *, cudaStream_t);
+template void dense_gemv<float>(int, const double *, const float *, float *, cudaStream_t);
 
 }  // namespace bgs

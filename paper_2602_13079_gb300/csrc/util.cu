@@ -1,12 +1,20 @@
 // Scans, reductions, validation, block assembly and small element-wise kernels.
 #include <atomic>
 #include <climits>
+#include <cstdlib>
 
 #include "internal.h"
 
 namespace bgs {
 
 static std::atomic<long long> g_launches{0};
+bool plain_alloc() {
+    static const bool v = [] {
+        const char *e = getenv("BGS_PLAIN_ALLOC");
+        return e && e[0] == '1';
+    }();
+    return v;
+}
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
