@@ -145,6 +145,14 @@ int bgs_kernel_stats(bgs_handle h, int kernel_class, int64_t *launches, double *
 int bgs_csr_spmv(int64_t nrows, int64_t nnz, const int32_t *rowptr, const int32_t *col, const double *val,
                  const double *x, double *y, int lanes, void *cuda_stream);
 
+/* Block dot products of one Arnoldi step (K14, Sec. 2.2 flexible GMRES orthogonalisation):
+ * h[k] = V_k . w for k < cnt and h[cnt] = w . w.  V: device, column-major, vector k at V + k*ld,
+ * ld even and >= n; w: device, n entries; h: device, cnt + 1 entries; 1 <= cnt <= 64.  Per-block
+ * partial sums go through device scratch that the call allocates and frees on the stream
+ * (stream-ordered).  The sums are taken in a fixed order (run-to-run reproducible). */
+int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h,
+                     void *cuda_stream);
+
 /* Number of kernels this library has launched in the process so far (all handles). */
 int64_t bgs_launch_count(void);
 

@@ -858,6 +858,16 @@ int bgs_csr_spmv(int64_t nrows, int64_t nnz, const int32_t *rowptr, const int32_
     });
 }
 
+int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, void *stream) {
+    if (!V || !w || !h || n < 1 || cnt < 1 || cnt > 64 || ld < n || (ld & 1)) return BGS_INVALID_ARG;
+    return guarded([&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        DBuf<double> part(arnoldi_dots_scratch(cnt, n), s);
+        arnoldi_dots_into(V, ld, cnt, w, n, h, part.p, part.n, s);
+        return BGS_OK;
+    });
+}
+
 int64_t bgs_launch_count(void) { return (int64_t)launch_count(); }
 
 void bgs_destroy(bgs_handle h) {

@@ -89,6 +89,11 @@ void sell_refresh(DCsr &A, cudaStream_t s);
 // h[k] = V_k . w for k < cnt and h[cnt] = w . w (V column-major, leading dimension ld, even)
 void arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, Scratch &sc,
                   cudaStream_t s);
+// the same with a caller-provided partial-sum buffer of partial_cap doubles; the buffer needs
+// arnoldi_dots_scratch(cnt, n) doubles (at most 4 * 608 * 17) and need not be cleared
+void arnoldi_dots_into(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, double *partial,
+                       size_t partial_cap, cudaStream_t s);
+size_t arnoldi_dots_scratch(int cnt, int64_t n);
 // w_out = w_in - V h (h on the device, cnt entries) and *nrm2 = ||w_out||^2; w_out may equal w_in
 void arnoldi_update(const double *V, int64_t ld, int cnt, const double *h, const double *w_in, double *w_out,
                     int64_t n, double *nrm2, Scratch &sc, cudaStream_t s);

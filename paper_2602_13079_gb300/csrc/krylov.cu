@@ -120,17 +120,28 @@ __global__ void k_sum_partials(const double *part, int g, double *out) {
     if (threadIdx.x == 0) *out = s;
 }
 
-void arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, Scratch &sc,
-                  cudaStream_t s) {
-    if (cnt < 1 || cnt > 64) throw Error(BGS_INVALID_ARG, "basis size outside 1..64");
-    if (ld & 1) throw Error(BGS_INTERNAL, "basis leading dimension must be even");
+size_t arnoldi_dots_scratch(int cnt, int64_t n) {
     const int nchunk = (cnt + KC - 1) / KC;
     const int g = grid_for(n / 2 + 1, KT, KG);
-    if ((size_t)nchunk * g * (KC + 1) > sc.partial.n) throw Error(BGS_INTERNAL, "partial scratch");
-    k_mdot<<<dim3(g, nchunk), KT, 0, s>>>(V, ld, cnt, w, n, sc.partial.p);
+    return (size_t)nchunk * g * (KC + 1);
+}
+
+void arnoldi_dots_into(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, double *partial,
+                       size_t partial_cap, cudaStream_t s) {
+    if (cnt < 1 || cnt > 64) throw Error(BGS_INVALID_ARG, "basis size outside 1..64");
+    if (ld & 1) throw Error(BGS_INVALID_ARG, "basis leading dimension must be even");
+    const int nchunk = (cnt + KC - 1) / KC;
+    const int g = grid_for(n / 2 + 1, KT, KG);
+    if ((size_t)nchunk * g * (KC + 1) > partial_cap) throw Error(BGS_INTERNAL, "partial scratch too small");
+    k_mdot<<<dim3(g, nchunk), KT, 0, s>>>(V, ld, cnt, w, n, partial);
     CK_LAUNCH();
-    k_mdot_reduce<<<(cnt + 1 + 7) / 8, 256, 0, s>>>(sc.partial.p, g, nchunk, cnt, h);
+    k_mdot_reduce<<<(cnt + 1 + 7) / 8, 256, 0, s>>>(partial, g, nchunk, cnt, h);
     CK_LAUNCH();
+}
+
+void arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, Scratch &sc,
+                  cudaStream_t s) {
+    arnoldi_dots_into(V, ld, cnt, w, n, h, sc.partial.p, sc.partial.n, s);
 }
 
 void arnoldi_update(const double *V, int64_t ld, int cnt, const double *h, const double *w_in, double *w_out,

@@ -66,6 +66,25 @@ def test_csr_spmv_matches_oracle(bgs, lanes):
     assert np.all(np.abs(y.cpu().numpy() - ref) <= tol)
 
 
+@pytest.mark.parametrize("cnt", [1, 7, 16, 17, 50, 64])
+def test_arnoldi_dots_match_fp64_dot_products(bgs, cnt):
+    rng = np.random.default_rng(cnt)
+    n = 100_003                                  # odd: exercises the tail row
+    ld = n + 1
+    V = rng.standard_normal((cnt, ld))
+    w = rng.standard_normal(n)
+    h = torch.zeros(cnt + 1, dtype=torch.float64, device="cuda")
+    assert bgs.bgs_arnoldi_dots(dev(V), ld, cnt, dev(w), n, h) == 0
+    torch.cuda.synchronize()
+    ref = np.concatenate([V[:, :n] @ w, [w @ w]])
+    # FP64 sums of n products in another order: |diff| <= n eps sum |v w|
+    scale = np.concatenate([np.abs(V[:, :n]) @ np.abs(w), [w @ w]])
+    assert np.all(np.abs(h.cpu().numpy() - ref) <= 4 * n * np.finfo(float).eps * scale)
+    bad = torch.zeros(66, dtype=torch.float64, device="cuda")
+    assert bgs.bgs_arnoldi_dots(dev(V), ld, 65, dev(w), n, bad) == bgs.INVALID_ARG
+    assert bgs.bgs_arnoldi_dots(dev(V), n, cnt, dev(w), n, h) == bgs.INVALID_ARG   # odd leading dimension
+
+
 def test_full_operator_spmv(bgs):
     s = bs.assemble("C1")
     g, o = bgs.solver_for_system(s), oracle.bgs_for_system(s, setup=False)
