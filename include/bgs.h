@@ -153,6 +153,20 @@ int bgs_csr_spmv(int64_t nrows, int64_t nnz, const int32_t *rowptr, const int32_
 int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h,
                      void *cuda_stream);
 
+/* bgs_arnoldi_dots without any device allocation (the paper has no counterpart: this is a
+ * library convenience).  For callers that cannot allocate device memory when they need the dots:
+ * work inside a captured or frozen execution context, memory fully pre-reserved by the caller's
+ * own pool, or hosts that forbid allocation after start-up.  Same arguments, results and limits
+ * as bgs_arnoldi_dots (1 <= cnt <= 64, ld even and >= n; anything else returns BGS_INVALID_ARG).
+ * The partial sums go to one fixed array of 330,752 bytes inside the library's device image,
+ * held by every GPU that loads the library until the process exits.  The first call on each
+ * device looks up that array's address (cudaGetSymbolAddress with the device current), so make
+ * the first call on a device before any stream capture.  All calls share the array: calls whose
+ * GPU work overlaps (different streams, threads or processes sharing the context) race and give
+ * wrong results; serialise them. */
+int bgs_arnoldi_dots_noalloc(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h,
+                             void *cuda_stream);
+
 /* Number of kernels this library has launched in the process so far (all handles). */
 int64_t bgs_launch_count(void);
 

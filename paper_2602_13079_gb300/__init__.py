@@ -78,6 +78,7 @@ def lib():
             "bgs_kernel_stats": (i32, [vp, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
             "bgs_csr_spmv": (i32, [i64, i64, vp, vp, vp, vp, vp, i32, vp]),
             "bgs_arnoldi_dots": (i32, [vp, i64, i32, vp, i64, vp, vp]),
+            "bgs_arnoldi_dots_noalloc": (i32, [vp, i64, i32, vp, i64, vp, vp]),
             "bgs_launch_count": (C.c_int64, []),
             "bgs_destroy": (None, [vp]),
             "bgs_status_string": (C.c_char_p, [i32]),
@@ -139,6 +140,13 @@ def bgs_csr_spmv(nrows, nnz, rowptr, col, val, x, y, lanes=0, stream=None) -> in
 def bgs_arnoldi_dots(V, ld, cnt, w, n, h, stream=None) -> int:
     """h[k] = V_k . w (k < cnt), h[cnt] = w . w; device tensors, V column-major with leading dim ld."""
     return lib().bgs_arnoldi_dots(_ptr(V), int(ld), int(cnt), _ptr(w), int(n), _ptr(h), _stream_ptr(stream))
+
+
+def bgs_arnoldi_dots_noalloc(V, ld, cnt, w, n, h, stream=None) -> int:
+    """Same as bgs_arnoldi_dots, but allocates no device memory: for callers that cannot allocate
+    at that point.  Calls share one fixed scratch array, so do not overlap calls on the GPU."""
+    return lib().bgs_arnoldi_dots_noalloc(_ptr(V), int(ld), int(cnt), _ptr(w), int(n), _ptr(h),
+                                          _stream_ptr(stream))
 
 
 def bgs_launch_count() -> int:
