@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--no-profile", action="store_true")
     p.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler")
     p.add_argument("--arms", default="both", choices=["both", "fp64", "mixed"])
+    p.add_argument("--graph", type=int, default=None, help="override the library default (CUDA graph sweep)")
     return p.parse_args()
 
 
@@ -214,8 +215,10 @@ def gpu_arm(args, rank, world):
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
 
+    extra = {} if args.graph is None else {"graph": args.graph}
+
     def step(precision, prof=False):
-        s = bgs.Solver(blocks, sizes, order, precision=precision)
+        s = bgs.Solver(blocks, sizes, order, precision=precision, **extra)
         s.setup()
         if prof:
             s.bgs_set_profiling(True)
@@ -310,7 +313,7 @@ def gpu_arm(args, rank, world):
         xh = torch.zeros_like(bh).pin_memory()
 
         def hstep():
-            s = bgs.Solver(hblocks, sizes, order, precision=0)
+            s = bgs.Solver(hblocks, sizes, order, precision=0, **extra)
             s.setup()
             s.bgs_solve(bh, xh)
             s.close()
@@ -357,7 +360,8 @@ def gpu_arm(args, rank, world):
                                        f"{system.ndof} DOFs, {system.nnz} nnz, seed {args.seed}",
                            "order": "[phi_s, phi_e] -> p -> [c1, c2]", "rtol": 1e-8, "restart": 50,
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "l2": "inputs larger than L2 (matrix 1.4 GB)", "generation_s": t_gen},
+                           "l2": "inputs larger than L2 (matrix 1.4 GB)", "generation_s": t_gen,
+                           "graph": int(bgs.bgs_default_options(**extra).graph)},
                 "fp64": arm64, "mixed": armmx,
                 "mixed_speedup_vs_fp64": (ms64 / msmx) if msmx else None,
                 "spmv_full_fp64": {"GBps": spmv_gbs, "ms": statistics.median(spmv_ms), "bytes": spmv_bytes,

@@ -56,7 +56,7 @@ typedef struct {
     int maxit;              /* total FGMRES iterations (default 1000) */
     double rtol;            /* stop when ||b - A x|| / ||b|| <= rtol, true residual (default 1e-8) */
     int precision;          /* 0: FP64 hierarchy; 1: FP32 hierarchy + BF16 coupling values */
-    int graph;              /* 1: replay the preconditioner sweep as a captured CUDA graph */
+    int graph;              /* 1 (default): replay the preconditioner sweep as a captured CUDA graph */
     int autotune;           /* 1: pick the SpMV variant per level operator by timing */
     int cheb_degree[8];     /* Chebyshev degree per field id (Sec. 2.2.1: 2; voltage blocks 4, Sec. 3.1.5) */
     double theta[8];        /* strength drop tolerance per field id (Sec. 3.1.4: 0.04 for phi_s) */

@@ -44,6 +44,13 @@ struct bgs_ctx {
     double t_setup_ms = 0.0;
     int last_reorth = 0;
     // profiling
+    // CUDA graph of one preconditioner sweep (forward, adjoint): captured once on an internal
+    // stream with fixed staging vectors gv -> gz, replayed every FGMRES iteration
+    cudaStream_t gs = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long glaunches[2] = {0, 0};
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    DBuf<double> gv, gz;
     bool prof = false;
     std::vector<EventPair> ev;
     size_t ev_used = 0;
@@ -229,6 +236,64 @@ void full_spmv(bgs_ctx *h, const double *x, double *y, bool transposed) {
     spmv_store<double, double>(A, x, y, h->s);
 }
 
+void drop_graphs(bgs_ctx *h) {
+    for (int a = 0; a < 2; a++)
+        if (h->gexec[a]) {
+            cudaGraphExecDestroy(h->gexec[a]);
+            h->gexec[a] = nullptr;
+        }
+}
+
+// z = M^-1 v through the captured graph (captured on first use for this direction)
+void apply_prec_graph(bgs_ctx *h, const double *v, double *z, bool adjoint) {
+    const int a = adjoint ? 1 : 0;
+    const int64_t n = total_n(h);
+    if (!h->gs) {
+        CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->gev[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->gev[1], cudaEventDisableTiming));
+    }
+    if (!h->gv.p) {
+        h->gv.alloc((size_t)n, h->s);
+        h->gz.alloc((size_t)n, h->s);
+        CK(cudaStreamSynchronize(h->s));
+    }
+    if (!h->gexec[a]) {
+        cudaStream_t saved = h->s;
+        const bool saved_prof = h->prof;
+        h->s = h->gs;
+        h->prof = false;
+        const long long l0 = launch_count();
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal));
+        try {
+            apply_prec(h, h->gv.p, h->gz.p, adjoint);
+        } catch (...) {
+            cudaStreamEndCapture(h->gs, &g);
+            if (g) cudaGraphDestroy(g);
+            h->s = saved;
+            h->prof = saved_prof;
+            throw;
+        }
+        CK(cudaStreamEndCapture(h->gs, &g));
+        h->s = saved;
+        h->prof = saved_prof;
+        h->glaunches[a] = launch_count() - l0;
+        const cudaError_t e = cudaGraphInstantiate(&h->gexec[a], g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+    }
+    cudaStream_t s = h->s;
+    CK(cudaMemcpyAsync(h->gv.p, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaEventRecord(h->gev[0], s));
+    CK(cudaStreamWaitEvent(h->gs, h->gev[0], 0));
+    CK(cudaGraphLaunch(h->gexec[a], h->gs));
+    for (long long i = 0; i < h->glaunches[a]; i++) count_launch();
+    CK(cudaEventRecord(h->gev[1], h->gs));
+    CK(cudaStreamWaitEvent(s, h->gev[1], 0));
+    CK(cudaMemcpyAsync(z, h->gz.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+}
+
 double host_dot(bgs_ctx *h, const double *a, const double *b, int64_t n) {
     dev_dot(a, b, n, h->sc.scal.p + 8, h->sc, h->s);
     CK(cudaMemcpyAsync(h->sc.h_scal + 8, h->sc.scal.p + 8, sizeof(double), cudaMemcpyDeviceToHost, h->s));
@@ -273,7 +338,8 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
         bool breakdown = false, nan = false;
         for (int j = 0; j < m; j++) {
             double *vj = V + (size_t)j * ld, *zj = Z + (size_t)j * ld;
-            apply_prec(h, vj, zj, adjoint);
+            if (h->opt.graph && !h->prof) apply_prec_graph(h, vj, zj, adjoint);
+            else apply_prec(h, vj, zj, adjoint);
             full_spmv(h, zj, w, adjoint);
             // classical Gram-Schmidt applied twice (CGS2): with a good preconditioner w = A M^-1 v_j
             // lies mostly in span(V), so the second pass is always needed
@@ -489,7 +555,7 @@ int bgs_default_options(bgs_options *o) {
     o->maxit = 1000;
     o->rtol = 1e-8;
     o->precision = 0;
-    o->graph = 0;
+    o->graph = 1;
     o->autotune = 0;
     for (int k = 0; k < 8; k++) {
         o->cheb_degree[k] = 2;
@@ -688,6 +754,7 @@ int bgs_setup(bgs_handle h) {
         h->bvec.alloc((size_t)n, s);
         h->hdev.alloc(256, s);
         h->adjoint_ready = false;
+        drop_graphs(h);
         CK(cudaStreamSynchronize(s));
         h->t_setup_ms = now_ms() - t0;
         h->setup_done = true;
@@ -873,6 +940,11 @@ int64_t bgs_launch_count(void) { return (int64_t)launch_count(); }
 void bgs_destroy(bgs_handle h) {
     if (!h) return;
     cudaStreamSynchronize(h->s);
+    if (h->gs) cudaStreamSynchronize(h->gs);
+    drop_graphs(h);
+    for (auto &e : h->gev)
+        if (e) cudaEventDestroy(e);
+    if (h->gs) cudaStreamDestroy(h->gs);
     for (auto &e : h->ev) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);

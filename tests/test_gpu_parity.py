@@ -175,6 +175,25 @@ def test_solve_parity(bgs, order, precision):
         assert abs(info.iters - ir.iters) <= 2
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_is_bit_identical(bgs, precision):
+    """The captured preconditioner graph runs the same kernels in the same order as direct
+    launches, so the whole solve (forward and adjoint) must agree bit for bit."""
+    system = bs.assemble(grid=bs.Grid(3, 17, 13, 11), seed=2)
+    out = []
+    for graph in (0, 1):
+        g = bgs.solver_for_system(system, max_coarse=60, precision=precision, graph=graph)
+        g.setup()
+        x = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+        info = g.bgs_solve(dev(system.b), x)
+        lam = torch.zeros_like(x)
+        info_a = g.bgs_solve_adjoint(dev(system.b), lam)
+        out.append((x.cpu().numpy(), info.iters, lam.cpu().numpy(), info_a.iters))
+        g.close()
+    assert out[0][1] == out[1][1] and out[0][3] == out[1][3]
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])
+
+
 def test_solve_3d_default_options_and_host_buffers(bgs):
     system = bs.assemble(grid=bs.Grid(3, 24, 24, 24), seed=1)
     g, o = make_pair(bgs, system)
