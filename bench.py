@@ -28,6 +28,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "setup+solve sec to rtol 1e-8 at 10.5M DOFs, mixed vs FP64 on same GB300; SpMV HBM GB/s"
+# DRAM bytes (read + write) of one finest-level FP64 Chebyshev-step launch on the 128^3 phi_s block,
+# from the ncu capture in profiles/k_sell_cheb_phi_s_128cubed.md; None once that kernel changes
+CHEB_FINE_TRAFFIC_BYTES = 264.757248e6
 WORKLOAD = "C4"
 
 
@@ -45,6 +48,8 @@ def parse():
     p.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler")
     p.add_argument("--arms", default="both", choices=["both", "fp64", "mixed"])
     p.add_argument("--graph", type=int, default=None, help="override the library default (CUDA graph sweep)")
+    p.add_argument("--profile-case", default=None, choices=["vcycle", "arnoldi", "spmv"],
+                   help="run one small kernel case for an ncu capture and exit")
     return p.parse_args()
 
 
@@ -271,9 +276,10 @@ def gpu_arm(args, rank, world):
         armmx["rel_diff_vs_fp64"] = float(np.linalg.norm(xmx - x64) / np.linalg.norm(x64))
 
     # per-kernel-class timing inside a solve (CUDA events on the library stream)
-    prof = None
+    prof = prof_mx = None
     if not args.no_profile:
         _, prof = step(0, prof=True)
+        _, prof_mx = step(1, prof=True)
 
     # FP64 SpMV of the full operator (L2 flushed before every launch): the standalone CSR entry
     # point and the solver's own operator (SELL-32); algorithmic bytes count stored entries only
@@ -333,16 +339,24 @@ def gpu_arm(args, rank, world):
     peak, peak_kind = measured_peaks()
     roof = None
     if prof:
-        dom = max(prof, key=lambda k: prof[k]["ms"])
-        d = prof[dom]
+        # Dominant kernel: the fused Chebyshev step k_sell<ECheb> (top share of the ncu launch list,
+        # profiles/launch_list_c4_fp64_step.md); its HBM-bound launches are the finest-level ones.
+        d = prof["chebyshev_fine"]
         ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_kind": peak_kind, "traffic": None,
+        roof = {"bound": "hbm", "kernel": "k_sell<double,double,double,ECheb> (Chebyshev step, finest level, FP64)",
+                "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_kind": peak_kind,
+                "traffic": CHEB_FINE_TRAFFIC_BYTES, "traffic_source": "ncu --set full, one phi_s launch "
+                "(profiles/k_sell_cheb_phi_s_128cubed.md)",
                 "launches": d["launches"], "avg_launch_ms": d["ms"] / max(d["launches"], 1),
                 "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
+                "note": "FP64 pipe 81% busy vs DRAM 61% under ncu: co-bound by GB300's FP64 FMA rate",
                 "classes": {k: {"launches": v["launches"], "ms": v["ms"],
                                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                             for k, v in prof.items()}}
+        if prof_mx:
+            roof["classes_mixed"] = {k: {"launches": v["launches"], "ms": v["ms"],
+                                         "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                                     for k, v in prof_mx.items()}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -375,8 +389,58 @@ def gpu_arm(args, rank, world):
         dist.destroy_process_group()
 
 
+def profile_case(args):
+    """Small, self-contained cases for single-kernel ncu captures (inputs larger than L2, a few
+    GB on the device): one V-cycle on the 128^3 phi_s block alone; one Arnoldi dot/update pass
+    over 16 basis vectors of 10.5M entries; one SpMV with the 128^3 full operator."""
+    import torch
+    import battery_system as bs
+    import paper_2602_13079_gb300 as bgs
+    from paper_2602_13079_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    if args.profile_case == "arnoldi":
+        n, cnt = 5 * 128 ** 3, 16
+        V = torch.rand((cnt, n), dtype=torch.float64, device="cuda")
+        w = torch.rand(n, dtype=torch.float64, device="cuda")
+        h = torch.zeros(cnt + 1, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            assert bgs.bgs_arnoldi_dots(V, n, cnt, w, n, h) == 0
+        torch.cuda.synchronize()
+        print("arnoldi case done", float(h[-1]))
+        return
+    system = bs.assemble(args.config, seed=args.seed)
+    if args.profile_case == "vcycle":
+        B = system.blocks[(0, 0)]
+
+        class _B:
+            pass
+        o = _B()
+        o.rowptr, o.col, o.val = B.rowptr, B.col, B.val
+        s = bgs.Solver([[o]], [B.nrows], [0])
+        s.setup()
+        b = torch.from_numpy(system.b[:B.nrows].copy()).cuda()
+        x = torch.zeros_like(b)
+        for _ in range(2):
+            s.bgs_apply_vcycle(0, b, x)
+        torch.cuda.synchronize()
+        print("vcycle case done", float(x.norm()))
+    else:
+        blocks, _ = device_blocks(system, torch)
+        s = bgs.Solver(blocks, system.field_sizes, list(range(5)))
+        xs = torch.rand(system.ndof, dtype=torch.float64, device="cuda")
+        ys = torch.zeros_like(xs)
+        for _ in range(2):
+            s.bgs_full_spmv(xs, ys)
+        torch.cuda.synchronize()
+        print("spmv case done", float(ys.norm()))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

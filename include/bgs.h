@@ -57,7 +57,8 @@ typedef struct {
     double rtol;            /* stop when ||b - A x|| / ||b|| <= rtol, true residual (default 1e-8) */
     int precision;          /* 0: FP64 hierarchy; 1: FP32 hierarchy + BF16 coupling values */
     int graph;              /* 1 (default): replay the preconditioner sweep as a captured CUDA graph */
-    int autotune;           /* 1: pick the SpMV variant per level operator by timing */
+    int autotune;           /* 1 (default): pick SELL-32 or CSR (1..32 lanes per row) per stored operator by
+                               timing at setup; choices cached per process by operator shape */
     int cheb_degree[8];     /* Chebyshev degree per field id (Sec. 2.2.1: 2; voltage blocks 4, Sec. 3.1.5) */
     double theta[8];        /* strength drop tolerance per field id (Sec. 3.1.4: 0.04 for phi_s) */
     int max_coarse;         /* stop coarsening at this many rows (default 1000; the paper uses 5000 with
@@ -166,6 +167,11 @@ int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int6
  * wrong results; serialise them. */
 int bgs_arnoldi_dots_noalloc(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h,
                              void *cuda_stream);
+
+/* The library allocates device memory stream-ordered from its own pool on each device; freed
+ * memory stays cached there for later handles.  This returns the cached memory of the current
+ * device to the driver (it synchronises the device first). */
+int bgs_release_cached_memory(void);
 
 /* Number of kernels this library has launched in the process so far (all handles). */
 int64_t bgs_launch_count(void);

@@ -80,6 +80,7 @@ def lib():
             "bgs_arnoldi_dots": (i32, [vp, i64, i32, vp, i64, vp, vp]),
             "bgs_arnoldi_dots_noalloc": (i32, [vp, i64, i32, vp, i64, vp, vp]),
             "bgs_launch_count": (C.c_int64, []),
+            "bgs_release_cached_memory": (i32, []),
             "bgs_destroy": (None, [vp]),
             "bgs_status_string": (C.c_char_p, [i32]),
         }
@@ -147,6 +148,10 @@ def bgs_arnoldi_dots_noalloc(V, ld, cnt, w, n, h, stream=None) -> int:
     at that point.  Calls share one fixed scratch array, so do not overlap calls on the GPU."""
     return lib().bgs_arnoldi_dots_noalloc(_ptr(V), int(ld), int(cnt), _ptr(w), int(n), _ptr(h),
                                           _stream_ptr(stream))
+
+
+def bgs_release_cached_memory() -> int:
+    return lib().bgs_release_cached_memory()
 
 
 def bgs_launch_count() -> int:
@@ -343,3 +348,74 @@ class _Rowptr:
 
     def data_ptr(self):
         return self.t.data_ptr()
+
+
+# ---------------------------------------------------------------------------------------------
+# Differentiable solve: x = A(vals)^-1 b with gradients for b and the stored block values
+# ---------------------------------------------------------------------------------------------
+class _Block:
+    def __init__(self, rowptr, col, val, last):
+        self.rowptr = _Rowptr(rowptr, last) if hasattr(rowptr, "data_ptr") else rowptr
+        self.col, self.val = col, val
+
+
+def _autograd_fn():
+    import torch
+
+    class BGSSolve(torch.autograd.Function):
+        """forward: bgs_create + bgs_setup + bgs_solve.  backward: bgs_solve_adjoint gives
+        lambda = A^-T g (so dL/db = lambda) and bgs_grad_values gives dL/dA = -lambda x^T on the
+        stored pattern of every block (the adjoint and the gradient kernel are extensions; the
+        paper has no adjoint)."""
+
+        @staticmethod
+        def forward(ctx, meta, b, *vals):
+            keys, patterns, sizes, order, opts = meta
+            F = len(sizes)
+            blocks = [[None] * F for _ in range(F)]
+            for (r, c), v in zip(keys, vals):
+                rp, ci, last = patterns[(r, c)]
+                blocks[r][c] = _Block(rp, ci, v.detach().contiguous(), last)
+            solver = Solver(blocks, sizes, order, **opts)
+            solver.setup()
+            x = torch.zeros_like(b)
+            info = solver.bgs_solve(b.detach().contiguous(), x)
+            ctx.solver, ctx.keys, ctx.nnz = solver, keys, [patterns[k][2] for k in keys]
+            ctx.info = info
+            ctx.save_for_backward(x)
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            (x,) = ctx.saved_tensors
+            solver = ctx.solver
+            lam = torch.zeros_like(gx)
+            solver.bgs_solve_adjoint(gx.detach().contiguous(), lam)
+            grads = []
+            for (r, c), nnz in zip(ctx.keys, ctx.nnz):
+                d = torch.empty(nnz, dtype=torch.float64, device=gx.device)
+                solver.bgs_grad_values(r, c, lam, x, d)
+                grads.append(d)
+            ctx.solver = None
+            return (None, lam, *grads)
+
+    return BGSSolve
+
+
+_BGSSolve = None
+
+
+def bgs_solve_autograd(patterns, values, b, field_sizes, order, **opts):
+    """Differentiable x = A^-1 b.  patterns: {(r, c): (rowptr, col)} device int32 tensors;
+    values: {(r, c): float64 device tensor} (may require grad); b: float64 device tensor."""
+    global _BGSSolve
+    if _BGSSolve is None:
+        _BGSSolve = _autograd_fn()
+    keys = sorted(values.keys())
+    pats = {}
+    for k in keys:
+        rp, ci = patterns[k]
+        last = int(rp[-1].item()) if hasattr(rp, "item") else int(rp[-1])
+        pats[k] = (rp, ci, last)
+    meta = (keys, pats, [int(s) for s in field_sizes], list(order), dict(opts))
+    return _BGSSolve.apply(meta, b, *[values[k] for k in keys])

@@ -454,6 +454,62 @@ __device__ __forceinline__ int tbl_insert(int *keys, unsigned mask, int col, boo
     return -1;
 }
 
+
+// Accumulate the products of one row into a hash table, one warp: lanes take 32 entries of the
+// left operand's row at a time and walk their right-operand rows in step.  Lanes of one step that
+// hit the same column are grouped (__match_any_sync); the group leader adds the group's values
+// in lane order (= left-operand order) and updates the table once, so no two lanes race on a
+// slot and the sums are reproducible.  Returns this lane's count of new columns; sets over if
+// the table's limit is passed (symbolic pass with a capped shared table).
+template <bool NUM>
+__device__ int sg_accumulate(int row, int *keys, double *vals, unsigned T, bool capped, double *sv, const int *arp,
+                             const int *aci, const double *av, const int *brp, const int *bci, const double *bv,
+                             bool &over) {
+    const int lane = threadIdx.x & 31;
+    const unsigned mask = T - 1;
+    int mine = 0;
+    const int rb = arp[row], re = arp[row + 1];
+    for (int e0 = rb; e0 < re; e0 += 32) {
+        const int e = e0 + lane;
+        const bool has = e < re;
+        const int k = has ? aci[e] : 0;
+        const double a = (NUM && has) ? av[e] : 0.0;
+        const int bs = has ? brp[k] : 0;
+        const int len = has ? brp[k + 1] - bs : 0;
+        const int maxlen = __reduce_max_sync(0xffffffffu, len);
+        for (int q = 0; q < maxlen; q++) {
+            const bool act = q < len;
+            const int j = act ? bci[bs + q] : -1;
+            const unsigned grp = __match_any_sync(0xffffffffu, j);
+            const int leader = __ffs(grp) - 1;
+            if (NUM) sv[lane] = act ? __dmul_rn(a, bv[bs + q]) : 0.0;
+            __syncwarp();
+            if (act && lane == leader) {
+                double sum = 0.0;
+                if (NUM)
+                    for (unsigned g = grp; g; g &= g - 1) sum = __dadd_rn(sum, sv[__ffs(g) - 1]);
+                bool ins;
+                const int sl = tbl_insert(keys, mask, j, ins);
+                if (sl < 0) over = true;
+                else {
+                    if (NUM) vals[sl] = __dadd_rn(vals[sl], sum);
+                    mine += ins;
+                }
+            }
+            __syncwarp();
+            if (capped) {
+                const int total = __reduce_add_sync(0xffffffffu, mine);
+                if (__any_sync(0xffffffffu, over) || total > (int)(T / 2)) {
+                    over = true;
+                    return mine;
+                }
+            }
+        }
+    }
+    over = __any_sync(0xffffffffu, over);
+    return mine;
+}
+
 __global__ void k_sg_ub(int n, const int *arp, const int *aci, const int *brp, int *ub) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         long long u = 0;
@@ -476,26 +532,12 @@ __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_sym(int n, const int *rows
             continue;
         }
         const unsigned T = min((unsigned)SG_SYM_T, nextpow2u(2u * (unsigned)u));
-        const unsigned mask = T - 1;
         for (unsigned t = lane; t < T; t += 32) keys[t] = -1;
         __syncwarp();
-        int mine = 0, total = 0;
         bool over = false;
-        for (int e = arp[row]; e < arp[row + 1]; e++) {
-            const int k = aci[e];
-            for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) {
-                bool ins;
-                if (tbl_insert(keys, mask, bci[f], ins) < 0) over = true;
-                mine += ins;
-            }
-            __syncwarp();
-            total = __reduce_add_sync(0xffffffffu, mine);
-            over = __any_sync(0xffffffffu, over);
-            if (over || (T == SG_SYM_T && total > (int)(T / 2))) {
-                over = true;
-                break;
-            }
-        }
+        const int mine = sg_accumulate<false>(row, keys, nullptr, T, T == (unsigned)SG_SYM_T, nullptr, arp, aci,
+                                              nullptr, brp, bci, nullptr, over);
+        const int total = __reduce_add_sync(0xffffffffu, mine);
         if (lane == 0) cnt[row] = over ? -1 : total;
         __syncwarp();
     }
@@ -509,44 +551,31 @@ __global__ void k_sg_sym_big(int nbig, const int *rows, const long long *toff, i
         const int row = rows[b];
         int *keys = gkeys + toff[b];
         const unsigned T = (unsigned)(toff[b + 1] - toff[b]);
-        const unsigned mask = T - 1;
         for (unsigned t = lane; t < T; t += 32) keys[t] = -1;
         __syncwarp();
-        int mine = 0;
-        for (int e = arp[row]; e < arp[row + 1]; e++) {
-            const int k = aci[e];
-            for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) {
-                bool ins;
-                tbl_insert(keys, mask, bci[f], ins);
-                mine += ins;
-            }
-            __syncwarp();
-        }
-        int total = __reduce_add_sync(0xffffffffu, mine);
+        bool over = false;
+        const int mine = sg_accumulate<false>(row, keys, nullptr, T, false, nullptr, arp, aci, nullptr, brp, bci,
+                                              nullptr, over);
+        const int total = __reduce_add_sync(0xffffffffu, mine);
         if (lane == 0) cnt[row] = total;
     }
 }
 
 // numeric accumulate + in-place compaction + rank sort into the output row
-__device__ void sg_numeric_row(int row, int *keys, double *vals, unsigned T, const int *arp, const int *aci,
-                               const double *av, const int *brp, const int *bci, const double *bv, const int *crp,
-                               int *cci, double *cv, int *err) {
+__device__ void sg_numeric_row(int row, int *keys, double *vals, unsigned T, double *sv, const int *arp,
+                               const int *aci, const double *av, const int *brp, const int *bci, const double *bv,
+                               const int *crp, int *cci, double *cv, int *err) {
     const int lane = threadIdx.x & 31;
-    const unsigned mask = T - 1;
     for (unsigned t = lane; t < T; t += 32) {
         keys[t] = -1;
         vals[t] = 0.0;
     }
     __syncwarp();
-    for (int e = arp[row]; e < arp[row + 1]; e++) {
-        const int k = aci[e];
-        const double a = av[e];
-        for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) {
-            bool ins;
-            const int sl = tbl_insert(keys, mask, bci[f], ins);
-            vals[sl] = __dadd_rn(vals[sl], __dmul_rn(a, bv[f]));
-        }
-        __syncwarp();
+    bool over = false;
+    sg_accumulate<true>(row, keys, vals, T, false, sv, arp, aci, av, brp, bci, bv, over);
+    if (over) {
+        if (lane == 0) atomicOr(err, 1);
+        return;
     }
     int wpos = 0;
     for (unsigned base = 0; base < T; base += 32) {
@@ -586,22 +615,25 @@ __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *rows
     extern __shared__ double sg_nsm[];
     const int wib = threadIdx.x >> 5;
     double *vals = sg_nsm + wib * SG_NUM_T;
-    int *keys = (int *)(sg_nsm + SG_WARPS * SG_NUM_T) + wib * SG_NUM_T;
+    double *sv = sg_nsm + SG_WARPS * SG_NUM_T + wib * 32;
+    int *keys = (int *)(sg_nsm + SG_WARPS * (SG_NUM_T + 32)) + wib * SG_NUM_T;
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n; it += (gridDim.x * blockDim.x) >> 5) {
         const int row = rows ? rows[it] : it;
         const int c = crp[row + 1] - crp[row];
         if (c == 0 || c > SG_NUM_T / 2) continue;
         const unsigned T = nextpow2u(2u * (unsigned)c);
-        sg_numeric_row(row, keys, vals, T, arp, aci, av, brp, bci, bv, crp, cci, cv, err);
+        sg_numeric_row(row, keys, vals, T, sv, arp, aci, av, brp, bci, bv, crp, cci, cv, err);
     }
 }
 
 __global__ void k_sg_num_big(int nbig, const int *rows, const long long *toff, int *gkeys, double *gvals,
                              const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
                              const double *bv, const int *crp, int *cci, double *cv, int *err) {
+    __shared__ double svb[8][32];
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbig; b += (gridDim.x * blockDim.x) >> 5) {
         const unsigned T = (unsigned)(toff[b + 1] - toff[b]);
-        sg_numeric_row(rows[b], gkeys + toff[b], gvals + toff[b], T, arp, aci, av, brp, bci, bv, crp, cci, cv, err);
+        sg_numeric_row(rows[b], gkeys + toff[b], gvals + toff[b], T, svb[(threadIdx.x >> 5) & 7], arp, aci, av, brp,
+                       bci, bv, crp, cci, cv, err);
     }
 }
 
@@ -784,7 +816,7 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
         CK_LAUNCH();
         const int nb1 = collect_big(n, hashcnt.p, 0, rows, sc, s);
         if (nb1) {
-            const size_t num_smem = (sizeof(double) + sizeof(int)) * SG_WARPS * SG_NUM_T;
+            const size_t num_smem = sizeof(double) * SG_WARPS * (SG_NUM_T + 32) + sizeof(int) * SG_WARPS * SG_NUM_T;
             k_sg_num<<<grid_for((int64_t)nb1 * 32, SG_WARPS * 32, kSMs * 8), SG_WARPS * 32, num_smem, s>>>(
                 nb1, rows.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p, sc.flags.p + 8);
             CK_LAUNCH();
@@ -890,12 +922,9 @@ __global__ void __launch_bounds__(LU_T) k_lu_panel(double *a, int n, int k0, int
         if (pivot != 0.0)
             for (int i = j + 1 + tid; i < n; i += LU_T) colj[i] = colj[i] / pivot;
         __syncthreads();
-        const int ncols = k0 + nb - (j + 1);
-        const int nrows = n - (j + 1);
-        for (int64_t t = tid; t < (int64_t)ncols * nrows; t += LU_T) {
-            const int c = j + 1 + (int)(t / nrows);
-            const int i = j + 1 + (int)(t % nrows);
-            a[(size_t)c * n + i] -= colj[i] * a[(size_t)c * n + j];
+        for (int i = j + 1 + tid; i < n; i += LU_T) {
+            const double l = colj[i];
+            for (int c = j + 1; c < k0 + nb; c++) a[(size_t)c * n + i] -= l * a[(size_t)c * n + j];
         }
         __syncthreads();
     }
@@ -1061,7 +1090,7 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
         CK(cudaFuncSetAttribute(k_sg_sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(int) * SG_WARPS * SG_SYM_T)));
         CK(cudaFuncSetAttribute(k_sg_num, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)((sizeof(double) + sizeof(int)) * SG_WARPS * SG_NUM_T)));
+                                (int)(sizeof(double) * SG_WARPS * (SG_NUM_T + 32) + sizeof(int) * SG_WARPS * SG_NUM_T)));
         attrs = true;
     }
     H.degree = p.degree;

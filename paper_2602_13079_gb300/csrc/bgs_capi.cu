@@ -543,6 +543,26 @@ double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// BGS_TRACE=1: wall time of the phases of bgs_create (stream synchronised at each mark)
+struct CreateTrace {
+    bool on = getenv("BGS_TRACE") != nullptr;
+    cudaStream_t s;
+    double t;
+    explicit CreateTrace(cudaStream_t st) : s(st) {
+        if (on) {
+            cudaStreamSynchronize(s);
+            t = now_ms();
+        }
+    }
+    void mark(const char *what) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        const double n = now_ms();
+        fprintf(stderr, "bgs-trace create %-22s %8.3f ms\n", what, n - t);
+        t = n;
+    }
+};
+
 }  // namespace
 
 // ================================================================== C ABI
@@ -556,7 +576,7 @@ int bgs_default_options(bgs_options *o) {
     o->rtol = 1e-8;
     o->precision = 0;
     o->graph = 1;
-    o->autotune = 0;
+    o->autotune = 1;
     for (int k = 0; k < 8; k++) {
         o->cheb_degree[k] = 2;
         o->theta[k] = 0.0;
@@ -635,6 +655,7 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
             h->pos[order[k]] = k;
         }
         cudaStream_t s = h->s;
+        CreateTrace tr(s);
         h->sc.init(s);
         h->blk.resize((size_t)F * F);
         for (int r = 0; r < F; r++)
@@ -653,6 +674,7 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
                 int st = validate_csr(view(D), r == c, h->sc, s);
                 if (st) return st;
             }
+        tr.mark("copy+validate blocks");
         // full operator, field-blocked rows
         std::vector<DCsr> rowblocks((size_t)F);
         for (int r = 0; r < F; r++) {
@@ -668,9 +690,12 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
         }
         std::vector<DCsr *> rb;
         for (auto &x : rowblocks) rb.push_back(&x);
+        tr.mark("row blocks");
         vstack(rb, (int)tot, h->full, s);
         rowblocks.clear();
+        tr.mark("vstack");
         build_sell(h->full, kMaxPad, h->sc, s);
+        tr.mark("sell(full)");
         // lower couplings per field: blocks (k, j) with pos(j) < pos(k), global columns
         for (int k = 0; k < F; k++) {
             std::vector<CsrView> parts;
@@ -687,6 +712,7 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
             build_sell(h->lower[k], kMaxPad, h->sc, s);
         }
         CK(cudaStreamSynchronize(s));
+        tr.mark("couplings");
         *out = h.release();
         return BGS_OK;
     });
@@ -720,7 +746,11 @@ int bgs_setup(bgs_handle h) {
             amg_build(H, p, h->sc, s);
             if (H.status) return H.status;
             for (size_t l = 0; l + 1 < H.L.size(); l++)
-                for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R}) build_sell(*M, kMaxPad, h->sc, s);
+                for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R}) {
+                    build_sell(*M, kMaxPad, h->sc, s);
+                    if (h->opt.autotune) autotune_spmv(*M, h->sc, s);
+                }
+            if (h->opt.autotune && h->lower[k].nnz) autotune_spmv(h->lower[k], h->sc, s);
             for (size_t l = 0; l < H.L.size(); l++) {
                 Level &Lv = H.L[l];
                 if (mixed) {
@@ -744,6 +774,7 @@ int bgs_setup(bgs_handle h) {
                 sell_refresh(h->lower[k], s);
             }
         }
+        if (h->opt.autotune) autotune_spmv(h->full, h->sc, s);
         const int64_t n = total_n(h);
         const int m = h->opt.restart;
         h->V.alloc((size_t)basis_ld(n) * (m + 1), s);
@@ -936,6 +967,13 @@ int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int6
 }
 
 int64_t bgs_launch_count(void) { return (int64_t)launch_count(); }
+
+int bgs_release_cached_memory(void) {
+    return guarded([&]() -> int {
+        release_cached_memory();
+        return BGS_OK;
+    });
+}
 
 void bgs_destroy(bgs_handle h) {
     if (!h) return;

@@ -36,9 +36,12 @@ void count_launch();
 // ------------------------------------------------------------------------------------------
 // Device buffers: stream-ordered allocation, freed on the stream they were allocated on.
 // ------------------------------------------------------------------------------------------
-// Device allocations are stream-ordered (cudaMallocAsync from the device's default pool) unless
-// the environment sets BGS_PLAIN_ALLOC=1, which switches to cudaMalloc / cudaFree (synchronous).
+// Device allocations are stream-ordered, from a memory pool the library owns (one per device)
+// that keeps freed memory cached for the next allocation instead of returning it to the driver
+// at every synchronisation (bgs_release_cached_memory() trims it).  BGS_PLAIN_ALLOC=1 switches to
+// cudaMalloc / cudaFree (synchronous).
 bool plain_alloc();
+cudaMemPool_t device_pool();
 
 template <class T>
 struct DBuf {
@@ -65,7 +68,7 @@ struct DBuf {
         n = count;
         if (count) {
             if (plain_alloc()) CK(cudaMalloc((void **)&p, count * sizeof(T)));
-            else CK(cudaMallocAsync((void **)&p, count * sizeof(T), st));
+            else CK(cudaMallocFromPoolAsync((void **)&p, count * sizeof(T), device_pool(), st));
         }
     }
     void release() {

@@ -28,6 +28,7 @@ struct Scratch {
 
 // ---------------------------------------------------------------- util.cu
 long long launch_count();
+void release_cached_memory();
 // out[0..n] = exclusive scan of in[0..n-1] (out[n] = total); in and out may alias.
 // Returns the total (synchronises the stream).  Throws if the total exceeds INT32_MAX.
 int64_t scan_exclusive(const int *in, int *out, int64_t n, Scratch &sc, cudaStream_t s);
@@ -84,6 +85,9 @@ void dense_gemv(int n, const double *W, const XT *x, XT *y, cudaStream_t s);
 // sell_refresh re-gathers the FP32 / BF16 value copies after they are created.
 bool build_sell(DCsr &A, double max_pad, Scratch &sc, cudaStream_t s);
 void sell_refresh(DCsr &A, cudaStream_t s);
+// Times SELL-32 (if built) against CSR with 1..32 lanes per row and keeps the fastest for A
+// (cached per shape); returns 0 for SELL or the lane count.
+int autotune_spmv(DCsr &A, Scratch &sc, cudaStream_t s);
 
 // ---------------------------------------------------------------- krylov.cu
 // h[k] = V_k . w for k < cnt and h[cnt] = w . w (V column-major, leading dimension ld, even)

@@ -35,7 +35,7 @@ __device__ void block_reduce_to(const double (&acc)[NACC], int nvalid, double *o
 }
 
 // part layout: [chunk][block][KC + 1]; slot KC holds ||w||^2 (chunk 0 only)
-__global__ void __launch_bounds__(KT) k_mdot(const double *__restrict__ V, int64_t ld, int cnt,
+__global__ void __launch_bounds__(KT, 3) k_mdot(const double *__restrict__ V, int64_t ld, int cnt,
                                              const double *__restrict__ w, int64_t n, double *part) {
     const int k0 = blockIdx.y * KC;
     const int kc = min(KC, cnt - k0);
@@ -50,9 +50,11 @@ __global__ void __launch_bounds__(KT) k_mdot(const double *__restrict__ V, int64
         for (int k = 0; k < KC; k++)
             if (k < kc) {
                 const double2 v = reinterpret_cast<const double2 *>(V + (int64_t)(k0 + k) * ld)[p];
-                acc[k] += v.x * wi.x + v.y * wi.y;
+                acc[k] = fma(v.x, wi.x, acc[k]);   // two FMAs per pair: FP64 issue rate is the limit
+                acc[k] = fma(v.y, wi.y, acc[k]);
             }
-        acc[KC] += wi.x * wi.x + wi.y * wi.y;
+        acc[KC] = fma(wi.x, wi.x, acc[KC]);
+        acc[KC] = fma(wi.y, wi.y, acc[KC]);
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {   // odd tail row
         const int64_t i = n - 1;
@@ -100,7 +102,8 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double *__restrict__ V, in
             a.y -= v.y * hs[k];
         }
         wo2[p] = a;
-        nrm += a.x * a.x + a.y * a.y;
+        nrm = fma(a.x, a.x, nrm);
+        nrm = fma(a.y, a.y, nrm);
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         const int64_t i = n - 1;

@@ -7,6 +7,10 @@
 //    (residual, Chebyshev step, prolongation add, coupling subtraction) is fully coalesced.
 //  * CSR with L threads per row (coarse levels with long, irregular rows): rows are taken in
 //    warp-uniform strips of 32/L rows, the L lanes stride over the row and reduce by shuffles.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "internal.h"
 
 namespace bgs {
@@ -354,6 +358,83 @@ void sell_refresh(DCsr &A, cudaStream_t s) {
     if (!A.sell) return;
     if (A.vf.p) gather_into(A, A.vf.p, A.svf, s);
     if (A.vb.p) gather_into(A, A.vb.p, A.svb, s);
+}
+
+// ------------------------------------------------------------------------------------------ autotuner
+// Picks the SpMV kernel of one stored operator by timing y = A x (FP64) with every candidate:
+// SELL-32 (when built) and CSR with 1, 2, 4, 8, 16, 32 threads per row.  One warm-up and three
+// timed launches each, CUDA events on the stream.  The choice is cached for the process, keyed by
+// (rows, columns, stored entries, longest row, SELL slots), so repeated set-ups of operators
+// with the same shape reuse it without timing.
+__global__ void k_max_row(int n, const int *rp, int *out) {
+    int m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = max(m, rp[i + 1] - rp[i]);
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int64_t, int, int64_t>, int> g_tune;   // -> 0 SELL, else lanes
+
+int autotune_spmv(DCsr &A, Scratch &sc, cudaStream_t s) {
+    if (A.n <= 0 || A.nnz <= 0) return 0;
+    CK(cudaMemsetAsync(sc.flags.p + 9, 0, sizeof(int), s));
+    k_max_row<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp.p, sc.flags.p + 9);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(sc.h_flags + 9, sc.flags.p + 9, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const auto key = std::make_tuple(A.n, A.m, A.nnz, sc.h_flags[9], A.sell ? A.sell_nnz : (int64_t)0);
+    int choice = -1;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) choice = it->second;
+    }
+    if (choice < 0) {
+        DBuf<double> x((size_t)std::max(A.m, 1), s), y((size_t)A.n, s);
+        dev_fill_double(x.p, 1.0, A.m, s);
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float best = 1e30f;
+        const int cands[7] = {0, 1, 2, 4, 8, 16, 32};
+        for (int c : cands) {
+            if (c == 0 && !A.sell) continue;
+            const bool keep_sell = A.sell;
+            A.sell = (c == 0);
+            A.lanes = c;
+            float tot = 0.f;
+            for (int rep = 0; rep < 4; rep++) {
+                CK(cudaEventRecord(e0, s));
+                run<double, double>(A, x.p, EStore<double>{y.p}, s);
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep) tot += ms;
+            }
+            A.sell = keep_sell;
+            if (tot < best) {
+                best = tot;
+                choice = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[key] = choice;
+    }
+    if (choice == 0) {
+        A.lanes = 0;
+    } else {
+        A.lanes = choice;
+        if (A.sell) {   // CSR won: drop the SELL copy
+            A.sell = false;
+            A.sptr.release(); A.sci.release(); A.sperm.release(); A.sv.release(); A.svf.release(); A.svb.release();
+        }
+    }
+    return choice;
 }
 
 // explicit instantiations

@@ -2,12 +2,38 @@
 #include <atomic>
 #include <climits>
 #include <cstdlib>
+#include <mutex>
 
 #include "internal.h"
 
 namespace bgs {
 
 static std::atomic<long long> g_launches{0};
+cudaMemPool_t device_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[128] = {};
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        CK(cudaMemPoolCreate(&pools[dev], &props));
+        uint64_t keep = UINT64_MAX;
+        CK(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    return pools[dev];
+}
+
+void release_cached_memory() {
+    if (!plain_alloc()) {
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemPoolTrimTo(device_pool(), 0));
+    }
+}
+
 bool plain_alloc() {
     static const bool v = [] {
         const char *e = getenv("BGS_PLAIN_ALLOC");
