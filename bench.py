@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler")
     p.add_argument("--arms", default="both", choices=["both", "fp64", "mixed"])
     p.add_argument("--graph", type=int, default=None, help="override the library default (CUDA graph sweep)")
+    p.add_argument("--reorth-eta", type=float, default=None, help="override the re-orthogonalisation threshold")
     p.add_argument("--profile-case", default=None, choices=["vcycle", "arnoldi", "spmv"],
                    help="run one small kernel case for an ncu capture and exit")
     return p.parse_args()
@@ -221,6 +222,8 @@ def gpu_arm(args, rank, world):
     torch.cuda.synchronize()
 
     extra = {} if args.graph is None else {"graph": args.graph}
+    if args.reorth_eta is not None:
+        extra["reorth_eta"] = args.reorth_eta
 
     def step(precision, prof=False):
         s = bgs.Solver(blocks, sizes, order, precision=precision, **extra)
@@ -268,6 +271,7 @@ def gpu_arm(args, rank, world):
         rel = float(np.linalg.norm(system.b - system.matvec(xs)) / np.linalg.norm(system.b))
         return {"s_per_step": ms / 1e3, "setup_s": statistics.mean(k.t_setup_ms for k in infos) / 1e3,
                 "solve_s": statistics.mean(k.t_solve_ms for k in infos) / 1e3, "iters": i.iters,
+                "reorth_steps": i.reorth,
                 "converged": bool(i.converged), "rel_true_resid_host_check": rel}
 
     arm64 = summary(ms64, inf64, x64)

@@ -61,7 +61,7 @@ typedef struct {
                                timing at setup; choices cached per process by operator shape */
     int cheb_degree[8];     /* Chebyshev degree per field id (Sec. 2.2.1: 2; voltage blocks 4, Sec. 3.1.5) */
     double theta[8];        /* strength drop tolerance per field id (Sec. 3.1.4: 0.04 for phi_s) */
-    int max_coarse;         /* stop coarsening at this many rows (default 1000; the paper uses 5000 with
+    int max_coarse;         /* stop coarsening at this many rows (default 500; the paper uses 5000 with
                                a sparse direct solver, Sec. 2.2.1; here the coarsest solve is dense) */
     int max_levels;         /* at most this many levels (default 10) */
     double cheb_ratio;      /* lambda_min = lambda_max / ratio (default 30) */
@@ -69,6 +69,9 @@ typedef struct {
     int power_iters;        /* power iterations for the eigenvalue estimates (default 10) */
     int filter_diag;        /* smoothing diagonal of the filtered matrix: 1 absolute row sum
                                (Sec. 2.2.1), 0 its plain diagonal */
+    double reorth_eta;      /* Arnoldi: second Gram-Schmidt pass when ||w1|| < reorth_eta ||w|| (more than
+                               log10(1/eta) digits cancelled); default 0.01; 1 always (CGS2),
+                               1/sqrt(2) the DGKS test, 0 never */
 } bgs_options;
 
 typedef struct {
@@ -76,6 +79,7 @@ typedef struct {
     int converged;          /* 1 if the true relative residual reached rtol */
     int status;             /* same as the return value */
     int restarts;
+    int reorth;             /* Arnoldi steps that ran the second Gram-Schmidt pass */
     double rel_true_resid;  /* ||b - A x|| / ||b|| of the returned x, in FP64 */
     double rel_est_resid;   /* last Arnoldi residual estimate */
     double t_setup_ms;      /* bgs_setup wall time */

@@ -726,7 +726,7 @@ void or_default_options(or_options *o) {
     o->theta[0] = 0.04;        /* phi_s: the grid-searched drop tolerance (Sec. 3.1.4) */
     o->cheb_degree[0] = 4;     /* voltage blocks: degree 4 in the coupled solve (Sec. 3.1.5) */
     o->cheb_degree[1] = 4;
-    o->max_coarse = 1000;      /* the coarsest level is a dense LU; the paper's 5000 suits a sparse solver */
+    o->max_coarse = 500;       /* the coarsest level is a dense LU; the paper's 5000 suits a sparse solver */
     o->max_levels = 10;
     o->cheb_ratio = 30.0;
     o->cheb_boost = 1.1;

@@ -28,12 +28,12 @@ class bgs_options(C.Structure):
                 ("graph", C.c_int), ("autotune", C.c_int), ("cheb_degree", C.c_int * 8),
                 ("theta", C.c_double * 8), ("max_coarse", C.c_int), ("max_levels", C.c_int),
                 ("cheb_ratio", C.c_double), ("cheb_boost", C.c_double), ("power_iters", C.c_int),
-                ("filter_diag", C.c_int)]
+                ("filter_diag", C.c_int), ("reorth_eta", C.c_double)]
 
 
 class bgs_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("status", C.c_int), ("restarts", C.c_int),
-                ("rel_true_resid", C.c_double), ("rel_est_resid", C.c_double),
+                ("reorth", C.c_int), ("rel_true_resid", C.c_double), ("rel_est_resid", C.c_double),
                 ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double)]
 
     def as_dict(self):

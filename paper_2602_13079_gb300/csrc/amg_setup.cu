@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 
 #include "internal.h"
 
@@ -432,6 +433,7 @@ constexpr int SG_SYM_T = 2048;
 constexpr int SG_NUM_T = 1024;
 constexpr int SG_LOCAL = 48;       // thread-per-row path: at most this many distinct columns
 constexpr int SG_LOCAL_UB = 128;   // and at most this many products; other rows use the warp-hash path
+constexpr int SG_SMALL_T = 256;    // warp-hash tables up to this size run with small shared tables
 
 __device__ __forceinline__ unsigned nextpow2u(unsigned x) {
     x = x < 2 ? 2 : x;
@@ -519,11 +521,12 @@ __global__ void k_sg_ub(int n, const int *arp, const int *aci, const int *brp, i
 }
 
 // symbolic: distinct column count per row; rows that overflow the shared table get -1
+template <int TMAX>
 __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_sym(int n, const int *rows, const int *arp, const int *aci,
                                                           const int *brp, const int *bci, const int *ub, int *cnt) {
     extern __shared__ int sg_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int *keys = sg_smem + wib * SG_SYM_T;
+    int *keys = sg_smem + wib * TMAX;
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n; it += (gridDim.x * blockDim.x) >> 5) {
         const int row = rows ? rows[it] : it;
         const int u = ub[row];
@@ -531,12 +534,12 @@ __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_sym(int n, const int *rows
             if (lane == 0) cnt[row] = 0;
             continue;
         }
-        const unsigned T = min((unsigned)SG_SYM_T, nextpow2u(2u * (unsigned)u));
+        const unsigned T = min((unsigned)TMAX, nextpow2u(2u * (unsigned)u));
         for (unsigned t = lane; t < T; t += 32) keys[t] = -1;
         __syncwarp();
         bool over = false;
-        const int mine = sg_accumulate<false>(row, keys, nullptr, T, T == (unsigned)SG_SYM_T, nullptr, arp, aci,
-                                              nullptr, brp, bci, nullptr, over);
+        const int mine = sg_accumulate<false>(row, keys, nullptr, T, T == (unsigned)TMAX && u > (int)(TMAX / 2),
+                                              nullptr, arp, aci, nullptr, brp, bci, nullptr, over);
         const int total = __reduce_add_sync(0xffffffffu, mine);
         if (lane == 0) cnt[row] = over ? -1 : total;
         __syncwarp();
@@ -608,19 +611,20 @@ __device__ void sg_numeric_row(int row, int *keys, double *vals, unsigned T, dou
     __syncwarp();
 }
 
+template <int TMAX>
 __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *rows, const int *arp, const int *aci,
                                                           const double *av, const int *brp, const int *bci,
                                                           const double *bv, const int *crp, int *cci, double *cv,
                                                           int *err) {
     extern __shared__ double sg_nsm[];
     const int wib = threadIdx.x >> 5;
-    double *vals = sg_nsm + wib * SG_NUM_T;
-    double *sv = sg_nsm + SG_WARPS * SG_NUM_T + wib * 32;
-    int *keys = (int *)(sg_nsm + SG_WARPS * (SG_NUM_T + 32)) + wib * SG_NUM_T;
+    double *vals = sg_nsm + wib * TMAX;
+    double *sv = sg_nsm + SG_WARPS * TMAX + wib * 32;
+    int *keys = (int *)(sg_nsm + SG_WARPS * (TMAX + 32)) + wib * TMAX;
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n; it += (gridDim.x * blockDim.x) >> 5) {
         const int row = rows ? rows[it] : it;
         const int c = crp[row + 1] - crp[row];
-        if (c == 0 || c > SG_NUM_T / 2) continue;
+        if (c == 0 || c > TMAX / 2) continue;
         const unsigned T = nextpow2u(2u * (unsigned)c);
         sg_numeric_row(row, keys, vals, T, sv, arp, aci, av, brp, bci, bv, crp, cci, cv, err);
     }
@@ -667,6 +671,17 @@ __global__ void k_ll_excl_scan_small(long long *a, int n) {
     }
 }
 
+static int collect_flag(int n, const int *flag, DBuf<int> &rows, Scratch &sc, cudaStream_t s) {
+    DBuf<int> pos((size_t)n + 1, s);
+    int nb = (int)scan_exclusive(flag, pos.p, n, sc, s);
+    rows.alloc((size_t)std::max(nb, 1), s);
+    if (nb) {
+        k_big_list<<<grid_for(n, 256), 256, 0, s>>>(n, flag, pos.p, rows.p);
+        CK_LAUNCH();
+    }
+    return nb;
+}
+
 static int collect_big(int n, const int *cnt, int limit, DBuf<int> &rows, Scratch &sc, cudaStream_t s) {
     DBuf<int> flag((size_t)n + 1, s);
     k_big_mark<<<grid_for(n, 256), 256, 0, s>>>(n, cnt, limit, flag.p);
@@ -692,6 +707,25 @@ static long long big_tables(int nbig, const int *rows, const int *size, DBuf<lon
     CK(cudaMemcpyAsync(&total, toff.p + nbig, sizeof(long long), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return total;
+}
+
+// symbolic rows still open (cnt < 0) whose table for ub products fits in hi slots
+__global__ void k_sym_class(int n, const int *cnt, const int *ub, unsigned hi, int *flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned t = 2;
+        while (t < 2u * (unsigned)ub[i]) t <<= 1;
+        flag[i] = (cnt[i] < 0 && t <= hi) ? 1 : 0;
+    }
+}
+
+// flag rows whose needed table size nextpow2(2 * size[i]) lies in (lo, hi] (size[i] < 0: use ub)
+__global__ void k_table_class(int n, const int *size, const int *ub, unsigned lo, unsigned hi, int *flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int sz = size[i] < 0 ? ub[i] : size[i];
+        unsigned t = 2;
+        while (t < 2u * (unsigned)sz) t <<= 1;
+        flag[i] = (sz > 0 && t > lo && t <= hi) ? 1 : 0;
+    }
 }
 
 __global__ void k_hash_rows(int n, const int *cnt, const int *ub, int *out) {
@@ -780,13 +814,33 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
     const int gl = grid_for(n, 128, kSMs * 32);
     k_sg_local<false><<<gl, 128, 0, s>>>(n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, C.rp.p, nullptr, nullptr, nullptr);
     CK_LAUNCH();
-    const size_t sym_smem = sizeof(int) * SG_WARPS * SG_SYM_T;
     {
-        DBuf<int> rows;
-        const int nb1 = collect_big(n, C.rp.p, 1 << 30, rows, sc, s);
+        // rows with small tables, then rows with large tables, then rows past the shared table
+        DBuf<int> flag((size_t)n, s), rows;
+        k_sym_class<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp.p, ub.p, SG_SMALL_T, flag.p);
+        CK_LAUNCH();
+        const int nbA = collect_flag(n, flag.p, rows, sc, s);
+        if (nbA) {
+            k_sg_sym<SG_SMALL_T><<<grid_for((int64_t)nbA * 32, SG_WARPS * 32, kSMs * 32), SG_WARPS * 32,
+                                   sizeof(int) * SG_WARPS * SG_SMALL_T, s>>>(nbA, rows.p, A.rp, A.ci, B.rp, B.ci,
+                                                                             ub.p, C.rp.p);
+            CK_LAUNCH();
+        }
+        k_sym_class<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp.p, ub.p, 1024, flag.p);
+        CK_LAUNCH();
+        DBuf<int> rowsM;
+        const int nbM = collect_flag(n, flag.p, rowsM, sc, s);
+        if (nbM) {
+            k_sg_sym<1024><<<grid_for((int64_t)nbM * 32, SG_WARPS * 32, kSMs * 16), SG_WARPS * 32,
+                             sizeof(int) * SG_WARPS * 1024, s>>>(nbM, rowsM.p, A.rp, A.ci, B.rp, B.ci, ub.p, C.rp.p);
+            CK_LAUNCH();
+        }
+        DBuf<int> rows1;
+        const int nb1 = collect_big(n, C.rp.p, 1 << 30, rows1, sc, s);
         if (nb1) {
-            k_sg_sym<<<grid_for((int64_t)nb1 * 32, SG_WARPS * 32, kSMs * 8), SG_WARPS * 32, sym_smem, s>>>(
-                nb1, rows.p, A.rp, A.ci, B.rp, B.ci, ub.p, C.rp.p);
+            k_sg_sym<SG_SYM_T><<<grid_for((int64_t)nb1 * 32, SG_WARPS * 32, kSMs * 8), SG_WARPS * 32,
+                                 sizeof(int) * SG_WARPS * SG_SYM_T, s>>>(nb1, rows1.p, A.rp, A.ci, B.rp, B.ci, ub.p,
+                                                                         C.rp.p);
             CK_LAUNCH();
             DBuf<int> rows2;
             const int nb2 = collect_big(n, C.rp.p, 1 << 30, rows2, sc, s);
@@ -814,12 +868,29 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
         DBuf<int> hashcnt((size_t)n, s);   // row length for rows the hash path owns, else 0
         k_hash_rows<<<grid_for(n, 256), 256, 0, s>>>(n, cnt.p, ub.p, hashcnt.p);
         CK_LAUNCH();
-        const int nb1 = collect_big(n, hashcnt.p, 0, rows, sc, s);
-        if (nb1) {
-            const size_t num_smem = sizeof(double) * SG_WARPS * (SG_NUM_T + 32) + sizeof(int) * SG_WARPS * SG_NUM_T;
-            k_sg_num<<<grid_for((int64_t)nb1 * 32, SG_WARPS * 32, kSMs * 8), SG_WARPS * 32, num_smem, s>>>(
-                nb1, rows.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p, sc.flags.p + 8);
+        DBuf<int> flag((size_t)n, s);
+        const unsigned cls[3] = {0u, (unsigned)SG_SMALL_T, (unsigned)SG_NUM_T};
+        for (int c = 0; c < 2; c++) {
+            k_table_class<<<grid_for(n, 256), 256, 0, s>>>(n, hashcnt.p, ub.p, cls[c], cls[c + 1], flag.p);
             CK_LAUNCH();
+            DBuf<int> rl;
+            const int nb = collect_flag(n, flag.p, rl, sc, s);
+            if (!nb) continue;
+            if (c == 0) {
+                k_sg_num<SG_SMALL_T><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, kSMs * 32), SG_WARPS * 32,
+                                       sizeof(double) * SG_WARPS * (SG_SMALL_T + 32) +
+                                           sizeof(int) * SG_WARPS * SG_SMALL_T,
+                                       s>>>(nb, rl.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
+                                            sc.flags.p + 8);
+            } else {
+                k_sg_num<SG_NUM_T><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, kSMs * 8), SG_WARPS * 32,
+                                     sizeof(double) * SG_WARPS * (SG_NUM_T + 32) + sizeof(int) * SG_WARPS * SG_NUM_T,
+                                     s>>>(nb, rl.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
+                                          sc.flags.p + 8);
+            }
+            CK_LAUNCH();
+        }
+        {
             DBuf<int> rows2;
             const int nb2 = collect_big(n, cnt.p, SG_NUM_T / 2, rows2, sc, s);
             if (nb2) {
@@ -1085,14 +1156,13 @@ void Hier::build_inv_T(cudaStream_t s) {
 // Hierarchy construction
 // ==========================================================================================
 void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
-    static bool attrs = false;
-    if (!attrs) {
-        CK(cudaFuncSetAttribute(k_sg_sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static std::once_flag attrs;
+    std::call_once(attrs, [] {
+        CK(cudaFuncSetAttribute(k_sg_sym<SG_SYM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(int) * SG_WARPS * SG_SYM_T)));
-        CK(cudaFuncSetAttribute(k_sg_num, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CK(cudaFuncSetAttribute(k_sg_num<SG_NUM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(double) * SG_WARPS * (SG_NUM_T + 32) + sizeof(int) * SG_WARPS * SG_NUM_T)));
-        attrs = true;
-    }
+    });
     H.degree = p.degree;
     H.L.reserve(32);
     const double t2 = p.theta * p.theta;

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <cstdlib>
 #include <memory>
+#include <thread>
 #include <type_traits>
 
 #include "internal.h"
@@ -40,6 +41,10 @@ struct bgs_ctx {
     Hier H[8];
     bool setup_done = false, adjoint_ready = false;
     Scratch sc;
+    // per-block set-up streams and scratch (the hierarchies are built concurrently); the streams
+    // live as long as the handle because the hierarchy memory is released on them
+    cudaStream_t bs[8] = {};
+    Scratch bsc[8];
     DBuf<double> V, Z, w, r, x, bvec, hdev;
     double t_setup_ms = 0.0;
     int last_reorth = 0;
@@ -341,20 +346,37 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
             if (h->opt.graph && !h->prof) apply_prec_graph(h, vj, zj, adjoint);
             else apply_prec(h, vj, zj, adjoint);
             full_spmv(h, zj, w, adjoint);
-            // classical Gram-Schmidt applied twice (CGS2): with a good preconditioner w = A M^-1 v_j
-            // lies mostly in span(V), so the second pass is always needed
+            // classical Gram-Schmidt; the second pass runs when ||w1|| < eta ||w|| (eta = 1: always,
+            // i.e. CGS2; 1/sqrt(2): the Daniel-Gragg-Kaufman-Stewart test; 0: never)
             {
-                Prof pf(h, 2, 8.0 * n * (4.0 * (j + 1) + 6.0));
-                arnoldi_dots(V, ld, j + 1, w, n, hd, h->sc, s);                     // h1
-                arnoldi_update(V, ld, j + 1, hd, w, w, n, hd + 70, h->sc, s);      // w1
-                arnoldi_dots(V, ld, j + 1, w, n, hd + 80, h->sc, s);                // h2
-                arnoldi_update(V, ld, j + 1, hd + 80, w, w, n, hd + 150, h->sc, s); // w2, ||w2||^2
+                Prof pf(h, 2, 8.0 * n * (2.0 * (j + 1) + 3.0));
+                arnoldi_dots(V, ld, j + 1, w, n, hd, h->sc, s);                     // h1, ||w||^2
+                arnoldi_update(V, ld, j + 1, hd, w, w, n, hd + 70, h->sc, s);      // w1, ||w1||^2
+            }
+            const double eta = h->opt.reorth_eta;
+            if (eta >= 1.0) {   // always: queue the second pass before the single read-back
+                Prof pf(h, 2, 8.0 * n * (2.0 * (j + 1) + 3.0));
+                arnoldi_dots(V, ld, j + 1, w, n, hd + 80, h->sc, s);
+                arnoldi_update(V, ld, j + 1, hd + 80, w, w, n, hd + 150, h->sc, s);
             }
             CK(cudaMemcpyAsync(hh, hd, sizeof(double) * 152, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            for (int i = 0; i <= j; i++) Hm[(size_t)i * m + j] = hh[i] + hh[80 + i];
-            const double nw2 = hh[150];
-            reorth++;
+            for (int i = 0; i <= j; i++) Hm[(size_t)i * m + j] = hh[i];
+            double nw2 = hh[70];
+            if (eta >= 1.0) {
+                for (int i = 0; i <= j; i++) Hm[(size_t)i * m + j] += hh[80 + i];
+                nw2 = hh[150];
+                reorth++;
+            } else if (nw2 < eta * eta * hh[j + 1]) {
+                Prof pf(h, 2, 8.0 * n * (2.0 * (j + 1) + 3.0));
+                arnoldi_dots(V, ld, j + 1, w, n, hd + 80, h->sc, s);
+                arnoldi_update(V, ld, j + 1, hd + 80, w, w, n, hd + 150, h->sc, s);
+                CK(cudaMemcpyAsync(hh + 80, hd + 80, sizeof(double) * 72, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                for (int i = 0; i <= j; i++) Hm[(size_t)i * m + j] += hh[80 + i];
+                nw2 = hh[150];
+                reorth++;
+            }
             const double hn = std::sqrt(nw2);
             Hm[(size_t)(j + 1) * m + j] = hn;
             it++;
@@ -417,6 +439,7 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
     inf.converged = status == BGS_OK;
     inf.status = status;
     inf.restarts = restarts;
+    inf.reorth = reorth;
     h->last_reorth = reorth;
     inf.rel_true_resid = rel;
     inf.rel_est_resid = est;
@@ -584,12 +607,13 @@ int bgs_default_options(bgs_options *o) {
     o->theta[0] = 0.04;
     o->cheb_degree[0] = 4;
     o->cheb_degree[1] = 4;
-    o->max_coarse = 1000;       /* dense coarsest solve on the GPU; the paper's 5000 fits a sparse CPU solver */
+    o->max_coarse = 500;        /* dense coarsest solve on the GPU; the paper's 5000 fits a sparse CPU solver */
     o->max_levels = 10;
     o->cheb_ratio = 30.0;
     o->cheb_boost = 1.1;
     o->power_iters = 10;
     o->filter_diag = 1;
+    o->reorth_eta = 0.01;
     return BGS_OK;
 }
 
@@ -617,7 +641,8 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
     if (opt) o = *opt;
     else bgs_default_options(&o);
     if (o.restart < 1 || o.restart > 63 || o.maxit < 1 || !(o.rtol > 0) || o.max_coarse < 1 || o.max_levels < 1 ||
-        o.precision < 0 || o.precision > 1 || o.power_iters < 1 || !(o.cheb_ratio > 1.0) || !(o.cheb_boost > 0))
+        o.precision < 0 || o.precision > 1 || o.power_iters < 1 || !(o.cheb_ratio > 1.0) || !(o.cheb_boost > 0) ||
+        !(o.reorth_eta >= 0.0))
         return BGS_INVALID_ARG;
     // host-side shape checks
     int seen[8] = {};
@@ -718,63 +743,108 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
     });
 }
 
-int bgs_setup(bgs_handle h) {
+namespace {
+
+// Builds block k's hierarchy and its solve-side copies on stream sk (no timing-based tuning here).
+void build_block(bgs_ctx *h, int k, cudaStream_t sk, Scratch &sck) {
+    const bool mixed = h->opt.precision == 1;
+    Hier &H = h->H[k];
+    H = Hier();
+    H.L.reserve(32);
+    H.L.emplace_back();
+    DCsr &B = h->blk[(size_t)k * h->F + k];
+    DCsr &A0 = H.L[0].A;
+    A0.n = B.n;
+    A0.m = B.m;
+    A0.nnz = B.nnz;
+    A0.rp.alloc((size_t)B.n + 1, sk);
+    A0.ci.alloc((size_t)B.nnz, sk);
+    A0.v.alloc((size_t)B.nnz, sk);
+    CK(cudaMemcpyAsync(A0.rp.p, B.rp.p, sizeof(int) * ((size_t)B.n + 1), cudaMemcpyDeviceToDevice, sk));
+    CK(cudaMemcpyAsync(A0.ci.p, B.ci.p, sizeof(int) * B.nnz, cudaMemcpyDeviceToDevice, sk));
+    CK(cudaMemcpyAsync(A0.v.p, B.v.p, sizeof(double) * B.nnz, cudaMemcpyDeviceToDevice, sk));
+    AmgParams p{h->opt.theta[k], h->opt.cheb_degree[k], h->opt.max_coarse, h->opt.max_levels,
+                h->opt.power_iters, h->opt.filter_diag, h->opt.cheb_ratio, h->opt.cheb_boost};
+    amg_build(H, p, sck, sk);
+    if (H.status) throw Error(H.status, "coarsest-level factorisation");
+    for (size_t l = 0; l + 1 < H.L.size(); l++)
+        for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R}) build_sell(*M, kMaxPad, sck, sk);
+    for (size_t l = 0; l < H.L.size(); l++) {
+        Level &Lv = H.L[l];
+        if (mixed) {
+            Buf<float>::alloc(Lv, Lv.A.n, sk);
+            if (l + 1 < H.L.size()) {
+                for (DCsr *M : {&Lv.A, &Lv.P, &Lv.R}) {
+                    M->vf.alloc((size_t)M->nnz, sk);
+                    convert_d2f(M->v.p, M->vf.p, M->nnz, sk);
+                    sell_refresh(*M, sk);
+                }
+                Lv.dinvf.alloc((size_t)Lv.A.n, sk);
+                convert_d2f(Lv.dinv.p, Lv.dinvf.p, Lv.A.n, sk);
+            }
+        } else {
+            Buf<double>::alloc(Lv, Lv.A.n, sk);
+        }
+    }
+    CK(cudaStreamSynchronize(sk));
+}
+
+}  // namespace
+
+extern "C" int bgs_setup(bgs_handle h) {
     if (!h) return BGS_INVALID_ARG;
     return guarded([&]() -> int {
         cudaStream_t s = h->s;
         CK(cudaStreamSynchronize(s));
         const double t0 = now_ms();
         const bool mixed = h->opt.precision == 1;
-        for (int k = 0; k < h->F; k++) {
-            Hier &H = h->H[k];
-            H = Hier();
-            H.L.reserve(32);
-            H.L.emplace_back();
-            DCsr &B = h->blk[(size_t)k * h->F + k];
-            DCsr &A0 = H.L[0].A;
-            A0.n = B.n;
-            A0.m = B.m;
-            A0.nnz = B.nnz;
-            A0.rp.alloc((size_t)B.n + 1, s);
-            A0.ci.alloc((size_t)B.nnz, s);
-            A0.v.alloc((size_t)B.nnz, s);
-            CK(cudaMemcpyAsync(A0.rp.p, B.rp.p, sizeof(int) * ((size_t)B.n + 1), cudaMemcpyDeviceToDevice, s));
-            CK(cudaMemcpyAsync(A0.ci.p, B.ci.p, sizeof(int) * B.nnz, cudaMemcpyDeviceToDevice, s));
-            CK(cudaMemcpyAsync(A0.v.p, B.v.p, sizeof(double) * B.nnz, cudaMemcpyDeviceToDevice, s));
-            AmgParams p{h->opt.theta[k], h->opt.cheb_degree[k], h->opt.max_coarse, h->opt.max_levels,
-                        h->opt.power_iters, h->opt.filter_diag, h->opt.cheb_ratio, h->opt.cheb_boost};
-            amg_build(H, p, h->sc, s);
-            if (H.status) return H.status;
-            for (size_t l = 0; l + 1 < H.L.size(); l++)
-                for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R}) {
-                    build_sell(*M, kMaxPad, h->sc, s);
-                    if (h->opt.autotune) autotune_spmv(*M, h->sc, s);
-                }
-            if (h->opt.autotune && h->lower[k].nnz) autotune_spmv(h->lower[k], h->sc, s);
-            for (size_t l = 0; l < H.L.size(); l++) {
-                Level &Lv = H.L[l];
-                if (mixed) {
-                    Buf<float>::alloc(Lv, Lv.A.n, s);
-                    if (l + 1 < H.L.size()) {
-                        for (DCsr *M : {&Lv.A, &Lv.P, &Lv.R}) {
-                            M->vf.alloc((size_t)M->nnz, s);
-                            convert_d2f(M->v.p, M->vf.p, M->nnz, s);
-                            sell_refresh(*M, s);
-                        }
-                        Lv.dinvf.alloc((size_t)Lv.A.n, s);
-                        convert_d2f(Lv.dinv.p, Lv.dinvf.p, Lv.A.n, s);
-                    }
-                } else {
-                    Buf<double>::alloc(Lv, Lv.A.n, s);
-                }
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        for (int k = 0; k < h->F; k++)
+            if (!h->bs[k]) {
+                CK(cudaStreamCreateWithFlags(&h->bs[k], cudaStreamNonBlocking));
+                h->bsc[k].init(h->bs[k]);
             }
+        // the diagonal blocks' hierarchies are independent: one host thread and stream each
+        std::vector<int> st((size_t)h->F, BGS_OK);
+        auto work = [&](int k) {
+            try {
+                CK(cudaSetDevice(dev));
+                build_block(h, k, h->bs[k], h->bsc[k]);
+            } catch (const Error &e) {
+                if (getenv("BGS_VERBOSE")) fprintf(stderr, "libbgs: block %d: %s\n", k, e.what());
+                st[k] = e.status;
+            } catch (const std::bad_alloc &) {
+                st[k] = BGS_OOM;
+            } catch (...) {
+                st[k] = BGS_INTERNAL;
+            }
+        };
+        if (h->F > 1 && !getenv("BGS_SERIAL_SETUP")) {
+            std::vector<std::thread> th;
+            for (int k = 0; k < h->F; k++) th.emplace_back(work, k);
+            for (auto &t : th) t.join();
+        } else {
+            for (int k = 0; k < h->F; k++) work(k);
+        }
+        for (int k = 0; k < h->F; k++)
+            if (st[k]) return st[k];
+        // kernel choice by timing runs alone, after the concurrent build
+        if (h->opt.autotune) {
+            for (int k = 0; k < h->F; k++) {
+                Hier &H = h->H[k];
+                for (size_t l = 0; l + 1 < H.L.size(); l++)
+                    for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R}) autotune_spmv(*M, h->sc, s);
+                if (h->lower[k].nnz) autotune_spmv(h->lower[k], h->sc, s);
+            }
+            autotune_spmv(h->full, h->sc, s);
+        }
+        for (int k = 0; k < h->F; k++)
             if (mixed && h->lower[k].nnz) {
                 h->lower[k].vb.alloc((size_t)h->lower[k].nnz, s);
                 convert_d2bf(h->lower[k].v.p, h->lower[k].vb.p, h->lower[k].nnz, s);
                 sell_refresh(h->lower[k], s);
             }
-        }
-        if (h->opt.autotune) autotune_spmv(h->full, h->sc, s);
         const int64_t n = total_n(h);
         const int m = h->opt.restart;
         h->V.alloc((size_t)basis_ld(n) * (m + 1), s);
@@ -978,6 +1048,12 @@ int bgs_release_cached_memory(void) {
 void bgs_destroy(bgs_handle h) {
     if (!h) return;
     cudaStreamSynchronize(h->s);
+    for (int k = 0; k < 8; k++) {
+        if (!h->bs[k]) continue;
+        cudaStreamSynchronize(h->bs[k]);
+        h->H[k] = Hier();   // released on the block's stream
+        cudaStreamSynchronize(h->bs[k]);
+    }
     if (h->gs) cudaStreamSynchronize(h->gs);
     drop_graphs(h);
     for (auto &e : h->gev)
@@ -988,8 +1064,15 @@ void bgs_destroy(bgs_handle h) {
         cudaEventDestroy(e.b);
     }
     cudaStream_t s = h->s;
+    cudaStream_t bs[8];
+    for (int k = 0; k < 8; k++) bs[k] = h->bs[k];
     delete h;
     cudaStreamSynchronize(s);
+    for (int k = 0; k < 8; k++)
+        if (bs[k]) {
+            cudaStreamSynchronize(bs[k]);
+            cudaStreamDestroy(bs[k]);
+        }
 }
 
 }  // extern "C"

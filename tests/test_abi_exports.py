@@ -36,5 +36,5 @@ def test_options_struct_matches_header_defaults():
     assert o.restart == 50 and o.maxit == 1000 and o.rtol == 1e-8
     assert list(o.cheb_degree)[:5] == [4, 4, 2, 2, 2]
     assert abs(o.theta[0] - 0.04) < 1e-15 and o.theta[1] == 0.0
-    assert o.max_coarse == 1000 and o.max_levels == 10 and o.filter_diag == 1
+    assert o.max_coarse == 500 and o.max_levels == 10 and o.filter_diag == 1 and o.reorth_eta == 0.01
     assert bgs.status_string(3) == "no convergence within maxit"
