@@ -113,9 +113,23 @@ class Clocks:
 # --------------------------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline): bounded sample
 # --------------------------------------------------------------------------------------------
-def oracle_sample(seed):
-    """The FP64 oracle's setup+solve on the 3D 64^3 system (1.31M DOFs, 1/8 of the workload),
-    single-threaded; returns (seconds, scaled seconds for 10.5M DOFs, iterations)."""
+def workload_dofs(name):
+    from battery_system import spec
+    c = spec.CONFIGS[name]
+    return 5 * c["nx"] * c["ny"] * c["nz"]
+
+
+def workload_desc(name):
+    from battery_system import spec
+    c = spec.CONFIGS[name]
+    dims = f"{c['nx']}x{c['ny']}" + (f"x{c['nz']}" if c["dim"] == 3 else "")
+    kind = "layered pellet stack (20 repeats along z)" if c["stack"] else "layered system (thirds along x)"
+    return f"{name}: {c['dim']}D {dims} {kind}, 5 fields (phi_s, phi_e, p, c1, c2)"
+
+
+def oracle_sample(seed, target="C4"):
+    """The FP64 oracle's setup+solve on the 3D 64^3 system (1.31M DOFs), single-threaded; returns
+    (seconds, seconds scaled by DOFs to the target workload, iterations, converged)."""
     import battery_system as bs
     import oracle
     system = bs.assemble("C2", seed=seed)
@@ -123,7 +137,7 @@ def oracle_sample(seed):
     o = oracle.bgs_for_system(system)
     x, info = o.solve(system.b)
     dt = time.perf_counter() - t0
-    scale = (5 * 128 ** 3) / system.ndof
+    scale = workload_dofs(target) / system.ndof
     return dt, dt * scale, info.iters, bool(info.converged)
 
 
@@ -132,18 +146,19 @@ def reference_arm(args, rank, world):
         return
     times = []
     for _ in range(args.warmup):
-        oracle_sample(args.seed)
+        oracle_sample(args.seed, args.config)
     for _ in range(args.steps):
-        dt, scaled, iters, conv = oracle_sample(args.seed)
+        dt, scaled, iters, conv = oracle_sample(args.seed, args.config)
         times.append(scaled)
     v = statistics.mean(times)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded layered battery system)",
-            "config": {"workload": "C4: 3D 128^3, 5 fields, 10.5M DOFs (projected from the 64^3 sample)",
-                       "parallelism": "replicas"},
+            "config": {"workload": workload_desc(args.config) + f", {workload_dofs(args.config)} DOFs "
+                                   "(projected from the 64^3 sample)", "parallelism": "replicas"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": "oracle setup+solve on 3D 64^3 (1.31M DOFs, seed 1), x8 DOF scaling"},
+                             "sample": f"oracle setup+solve on 3D 64^3 (1.31M DOFs, seed {args.seed}), scaled by "
+                                       f"DOFs x{workload_dofs(args.config) / 1310720:.1f}"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -364,21 +379,22 @@ def gpu_arm(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, scaled, iters, conv = oracle_sample(args.seed)
+        dt, scaled, iters, conv = oracle_sample(args.seed, args.config)
         cpu = {"value": scaled, "unit": "s", "cores": 1, "kind": "oracle",
                "sample": f"oracle setup+solve on 3D 64^3 (1.31M DOFs, seed {args.seed}) took {dt:.1f} s "
-                         f"({iters} iterations), x8 DOF scaling to 10.5M"}
+                         f"({iters} iterations), scaled by DOFs x{workload_dofs(args.config) / 1310720:.1f}"}
 
     if rank == 0:
         v = ms64 / 1e3
         line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded layered battery system)",
-                "config": {"workload": "C4: 3D 128^3 layered system, 5 fields (phi_s, phi_e, p, c1, c2), "
-                                       f"{system.ndof} DOFs, {system.nnz} nnz, seed {args.seed}",
+                "config": {"workload": workload_desc(args.config) + f", {system.ndof} DOFs, {system.nnz} nnz, "
+                                                                  f"seed {args.seed}",
                            "order": "[phi_s, phi_e] -> p -> [c1, c2]", "rtol": 1e-8, "restart": 50,
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "l2": "inputs larger than L2 (matrix 1.4 GB)", "generation_s": t_gen,
+                           "l2": f"inputs larger than L2 (matrix {system.nnz * 12 / 1e9:.1f} GB)",
+                           "generation_s": t_gen,
                            "graph": int(bgs.bgs_default_options(**extra).graph)},
                 "fp64": arm64, "mixed": armmx,
                 "mixed_speedup_vs_fp64": (ms64 / msmx) if msmx else None,

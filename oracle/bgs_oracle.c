@@ -9,6 +9,8 @@
  *  - strength (Sec. 2.2.1 drop tolerance theta; Sec. 3.1.4 theta = 0.04): j is strong for
  *    i != j iff a_ij^2 > theta^2 |a_ii a_jj| or a_ji^2 > theta^2 |a_ii a_jj| (symmetric test;
  *    a missing entry counts as 0).
+ *  - coarsening that stalls (n_{l+1} > 0.9 n_l) while the level is above max_coarse is retried
+ *    once with theta = 0 (no dropping); if that stalls too, the hierarchy stops there.
  *  - aggregation (not stated in the paper): distance-2 maximal independent set over the
  *    strength graph by synchronous rounds with keys (fmix32(i ^ salt), i); aggregates are a
  *    root plus its strong neighbours, the rest join the neighbouring phase-1 aggregate with the
@@ -586,13 +588,21 @@ or_amg *or_amg_setup(const or_csr *A0, double theta, int degree, const or_option
         int n = A->n;
         if (n <= opt->max_coarse || l + 1 >= maxlev) break;
         unsigned char *strong = (unsigned char *)malloc((size_t)(A->nnz > 0 ? A->nnz : 1));
-        or_strength_flags(A, theta, strong);
-        or_csr *S = or_strength_graph(A, strong);
-        int *state = (int *)malloc(sizeof(int) * (size_t)n);
-        h->mis_rounds[l] = or_mis2(S, (uint32_t)l * 0x9E3779B9u, state);
+        or_csr *S = NULL;
         int *agg = (int *)malloc(sizeof(int) * (size_t)n);
-        int nagg = or_aggregate(S, state, agg);
-        free(state);
+        int nagg = -1;
+        /* coarsening that stalls above max_coarse is retried once without dropping (theta = 0) */
+        for (int attempt = 0; attempt < 2; attempt++) {
+            double th = attempt == 0 ? theta : 0.0;
+            if (attempt == 1 && (theta == 0.0 || nagg < 0 || (long long)nagg * 10 <= (long long)n * 9)) break;
+            or_csr_free(S);
+            or_strength_flags(A, th, strong);
+            S = or_strength_graph(A, strong);
+            int *state = (int *)malloc(sizeof(int) * (size_t)n);
+            h->mis_rounds[l] = or_mis2(S, (uint32_t)l * 0x9E3779B9u, state);
+            nagg = or_aggregate(S, state, agg);
+            free(state);
+        }
         if (nagg < 0) {
             h->status = ST_INVALID;
             free(agg);

@@ -1176,24 +1176,32 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
         DBuf<double> diag((size_t)n, s);
         extract_diag(view(A), diag.p, s);
         DBuf<uint8_t> strong((size_t)std::max<int64_t>(A.nnz, 1), s);
-        CK(cudaMemsetAsync(sc.flags.p + 7, 0, sizeof(int), s));
-        k_strength<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, diag.p, t2, strong.p, sc.flags.p + 7);
-        CK_LAUNCH();
-        CK(cudaMemcpyAsync(sc.h_flags + 7, sc.flags.p + 7, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        const int sflags = sc.h_flags[7];
-        if (sflags & 2) throw Error(BGS_ZERO_PIVOT, "zero diagonal entry in a level operator");
         DCsr S;
-        strength_graph(view(A), strong.p, (sflags & 1) != 0, S, sc, s);
-        tr.mark("strength", l, n);
-        DBuf<int> state((size_t)n, s);
-        const uint32_t salt = (uint32_t)l * 0x9E3779B9u;
-        const int rounds = mis2(S, salt, state.p, sc, s);
-        tr.mark("mis2", l, rounds);
         DBuf<int> agg((size_t)n, s);
-        const int nagg = aggregate(S, state.p, agg.p, sc, s);
-        tr.mark("aggregate", l, nagg);
-        if (nagg < 0) throw Error(BGS_INTERNAL, "aggregation left a node unassigned");
+        int nagg = -1, rounds = 0;
+        // coarsening that stalls above max_coarse is retried once without dropping (theta = 0)
+        for (int attempt = 0; attempt < 2; attempt++) {
+            const double th2 = attempt == 0 ? t2 : 0.0;
+            if (attempt == 1 && (t2 == 0.0 || (long long)nagg * 10 <= (long long)n * 9)) break;
+            CK(cudaMemsetAsync(sc.flags.p + 7, 0, sizeof(int), s));
+            k_strength<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, diag.p, th2, strong.p,
+                                                         sc.flags.p + 7);
+            CK_LAUNCH();
+            CK(cudaMemcpyAsync(sc.h_flags + 7, sc.flags.p + 7, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const int sflags = sc.h_flags[7];
+            if (sflags & 2) throw Error(BGS_ZERO_PIVOT, "zero diagonal entry in a level operator");
+            S = DCsr();
+            strength_graph(view(A), strong.p, (sflags & 1) != 0, S, sc, s);
+            tr.mark("strength", l, n);
+            DBuf<int> state((size_t)n, s);
+            const uint32_t salt = (uint32_t)l * 0x9E3779B9u;
+            rounds = mis2(S, salt, state.p, sc, s);
+            tr.mark("mis2", l, rounds);
+            nagg = aggregate(S, state.p, agg.p, sc, s);
+            tr.mark("aggregate", l, nagg);
+            if (nagg < 0) throw Error(BGS_INTERNAL, "aggregation left a node unassigned");
+        }
         if ((long long)nagg * 10 > (long long)n * 9) break;   // coarsening stalled
         // filtered matrix and its smoothing diagonal
         DCsr AF;
@@ -1256,6 +1264,7 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
         tr.mark("power(cheb)", (int)k, n);
     }
     H.nc = H.L.back().A.n;
+    if (H.nc > 16384) throw Error(BGS_INTERNAL, "coarsest level too large for the dense direct solve");
     H.status = dense_inverse(H.L.back().A, H.inv, sc, s);
     tr.mark("dense LU+inverse", (int)H.L.size() - 1, H.nc);
 }

@@ -133,6 +133,29 @@ def test_hierarchy_parity(bgs, name, mk, kw):
             assert np.abs(v - ref.val).max() <= 1e-11 * np.abs(ref.val).max(), (k, l)
 
 
+def test_stalled_coarsening_retry_parity(bgs):
+    """A block whose couplings are all weak at theta = 0.04: both sides retry the aggregation without
+    dropping and must agree bit for bit."""
+    n = 16
+    g = bs.Grid(2, n, n, 1)
+    c = np.ones(g.ncells)
+    lap = bs._stencil_block(g, [c, c, c]).to_csr()
+    val = np.where(np.repeat(np.arange(lap.nrows), np.diff(lap.rowptr)) == lap.col, 4.0, 1e-3 * lap.val)
+    blk = bs.CSR(lap.rowptr, lap.col, val, lap.nrows, lap.ncols)
+
+    class _O:
+        pass
+    o = _O()
+    o.rowptr, o.col, o.val = blk.rowptr, blk.col, blk.val
+    solver = bgs.Solver([[o]], [blk.nrows], [0], max_coarse=10, theta=[0.04])
+    solver.setup()
+    ref = oracle.AMG(oracle.CSR(blk.rowptr, blk.col, blk.val, blk.nrows, blk.ncols), theta=0.04, degree=4,
+                     opts=oracle.default_options(max_coarse=10))
+    assert solver.bgs_num_levels(0) == ref.nlevels >= 2
+    for l in range(ref.nlevels - 1):
+        assert np.array_equal(solver.bgs_level_aggregates(0, l), ref.aggregates(l))
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_vcycle_and_sweep_parity(bgs, precision):
     system = bs.assemble(grid=bs.Grid(3, 17, 13, 11), seed=2)

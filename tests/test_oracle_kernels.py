@@ -358,3 +358,24 @@ def test_vcycle_convergence_factor_poisson():
     assert abs(r2a - r2b) < 0.05         # independent of h
     r3, _ = _vcycle_factor(3, 16, 4)
     assert r3 < 0.3
+
+
+def weak_laplacian(n, eps=1e-3):
+    """2D 5-point pattern whose off-diagonals are all weak at theta = 0.04 (diagonally dominant)."""
+    A = laplacian_2d(n)
+    d = A.to_dense()
+    off = d - np.diag(np.diag(d))
+    d = eps * off + np.diag(np.full(n * n, 4.0))
+    return dense_to_csr(d)
+
+
+def test_stalled_coarsening_is_retried_without_dropping():
+    A = weak_laplacian(12)
+    # theta = 0.04: every node isolated -> singleton aggregates, coarsening stalls
+    s = oracle.strength_flags(A, 0.04)
+    assert s.sum() == 0
+    amg = oracle.AMG(A, theta=0.04, degree=2, opts=oracle.default_options(max_coarse=10))
+    assert amg.nlevels >= 2
+    assert amg.nagg(0) < 0.5 * A.nrows                  # aggregated as with theta = 0
+    ref = oracle.AMG(A, theta=0.0, degree=2, opts=oracle.default_options(max_coarse=10))
+    assert np.array_equal(amg.aggregates(0), ref.aggregates(0))
