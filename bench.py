@@ -111,6 +111,33 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------------------------
+# ranks: replicas only (no data-path collective); barrier + MAX of the per-rank step time
+# --------------------------------------------------------------------------------------------
+def rank_barrier(dist):
+    if dist is not None and dist.is_initialized():
+        dist.barrier()
+
+
+def rank_max(value, dist, device="cpu"):
+    """MAX over ranks of a per-rank scalar (the slowest replica sets the time)."""
+    if dist is None or not dist.is_initialized():
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_sum(value, dist, device="cpu"):
+    if dist is None or not dist.is_initialized():
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline): bounded sample
 # --------------------------------------------------------------------------------------------
 def workload_dofs(name):
@@ -215,15 +242,10 @@ def gpu_arm(args, rank, world):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        rank_barrier(dist)
 
     def allmax(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(v, dist, "cuda")
 
     tg = time.perf_counter()
     system = bs.assemble(args.config, seed=args.seed)
@@ -401,6 +423,7 @@ def gpu_arm(args, rank, world):
                 "spmv_full_fp64": {"GBps": spmv_gbs, "ms": statistics.median(spmv_ms), "bytes": spmv_bytes,
                                    "frac_of_measured_peak": spmv_gbs / peak,
                                    "csr_ms": spmv_csr_ms, "sell32_ms": spmv_sell_ms},
+                "solves_per_s": world / (ms64 / 1e3),
                 "gpu_launches": int(launches64 // max(args.steps, 1)) * args.steps,
                 "gpu_launches_per_step": int(launches64 // max(args.steps, 1)),
                 "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}
