@@ -29,8 +29,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "setup+solve sec to rtol 1e-8 at 10.5M DOFs, mixed vs FP64 on same GB300; SpMV HBM GB/s"
 # DRAM bytes (read + write) of one finest-level FP64 Chebyshev-step launch on the 128^3 phi_s block,
-# from the ncu capture in profiles/k_sell_cheb_phi_s_128cubed.md; None once that kernel changes
-CHEB_FINE_TRAFFIC_BYTES = 264.757248e6
+# per SpMV variant the autotuner can pick for it (0 = SELL-32, k = CSR with k threads per row), from
+# the ncu captures named beside each; a variant without a capture reports null
+CHEB_FINE_TRAFFIC = {
+    0: (264.757248e6, "profiles/k_sell_cheb_phi_s_128cubed.md"),
+}
+WORKLOAD = "C4"
 WORKLOAD = "C4"
 
 
@@ -269,6 +273,8 @@ def gpu_arm(args, rank, world):
             s.bgs_set_profiling(True)
         info = s.bgs_solve(b, x)
         stats = {k: s.bgs_kernel_stats(v) for k, v in bgs.KERNEL_CLASSES.items()} if prof else None
+        if prof:
+            stats["_fine_format"] = s.bgs_level_format(spec.PHI_S, 0, 0)
         s.close()
         return info, stats
 
@@ -380,21 +386,27 @@ def gpu_arm(args, rank, world):
     peak, peak_kind = measured_peaks()
     roof = None
     if prof:
-        # Dominant kernel: the fused Chebyshev step k_sell<ECheb> (top share of the ncu launch list,
-        # profiles/launch_list_c4_fp64_step.md); its HBM-bound launches are the finest-level ones.
+        # Dominant kernel: the fused Chebyshev step on the finest level (top share of the ncu launch
+        # list, profiles/launch_list_c4_fp64_step.md), in the SpMV variant the autotuner chose for the
+        # 128^3 diagonal blocks in this process
+        fmt = prof.pop("_fine_format")
+        kname = ("k_sell<double,double,double,ECheb>" if fmt == 0 else
+                 f"k_spmv<{fmt},double,double,double,ECheb>")
+        traffic, tsrc = CHEB_FINE_TRAFFIC.get(fmt, (None, "no ncu capture of this variant"))
         d = prof["chebyshev_fine"]
         ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-        roof = {"bound": "hbm", "kernel": "k_sell<double,double,double,ECheb> (Chebyshev step, finest level, FP64)",
+        roof = {"bound": "hbm", "kernel": kname + " (Chebyshev step, finest level, FP64)",
                 "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_kind": peak_kind,
-                "traffic": CHEB_FINE_TRAFFIC_BYTES, "traffic_source": "ncu --set full, one phi_s launch "
-                "(profiles/k_sell_cheb_phi_s_128cubed.md)",
+                "traffic": traffic, "traffic_source": tsrc,
                 "launches": d["launches"], "avg_launch_ms": d["ms"] / max(d["launches"], 1),
                 "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
-                "note": "FP64 pipe 81% busy vs DRAM 61% under ncu: co-bound by GB300's FP64 FMA rate",
                 "classes": {k: {"launches": v["launches"], "ms": v["ms"],
                                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                             for k, v in prof.items()}}
         if prof_mx:
+            fmx = prof_mx.pop("_fine_format")
+            roof["fine_kernel_mixed"] = ("k_sell<float,float,float,ECheb>" if fmx == 0 else
+                                         f"k_spmv<{fmx},float,float,float,ECheb>")
             roof["classes_mixed"] = {k: {"launches": v["launches"], "ms": v["ms"],
                                          "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                                      for k, v in prof_mx.items()}

@@ -58,12 +58,14 @@ typedef struct {
     int precision;          /* 0: FP64 hierarchy; 1: FP32 hierarchy + BF16 coupling values */
     int graph;              /* 1 (default): replay the preconditioner sweep as a captured CUDA graph */
     int autotune;           /* 1 (default): pick SELL-32 or CSR (1..32 lanes per row) per stored operator by
-                               timing at setup; choices cached per process by operator shape */
+                               timing at setup, in the precision the solve uses; choices are cached per
+                               process by operator shape, and in the text file named by the environment
+                               variable BGS_AUTOTUNE_CACHE when it is set */
     int cheb_degree[8];     /* Chebyshev degree per field id (Sec. 2.2.1: 2; voltage blocks 4, Sec. 3.1.5) */
     double theta[8];        /* strength drop tolerance per field id (Sec. 3.1.4: 0.04 for phi_s) */
     int max_coarse;         /* stop coarsening at this many rows (default 500; the paper uses 5000 with
                                a sparse direct solver, Sec. 2.2.1; here the coarsest solve is dense) */
-    int max_levels;         /* at most this many levels (default 10) */
+    int max_levels;         /* at most this many levels, 1..16 (default 10) */
     double cheb_ratio;      /* lambda_min = lambda_max / ratio (default 30) */
     double cheb_boost;      /* lambda_max = boost * power-iteration estimate (default 1.1) */
     int power_iters;        /* power iterations for the eigenvalue estimates (default 10) */
@@ -72,6 +74,9 @@ typedef struct {
     double reorth_eta;      /* Arnoldi: second Gram-Schmidt pass when ||w1|| < reorth_eta ||w|| (more than
                                log10(1/eta) digits cancelled); default 0.01; 1 always (CGS2),
                                1/sqrt(2) the DGKS test, 0 never */
+    int jacobi;             /* 0 (default): forward block Gauss-Seidel sweep; 1: block Jacobi, the
+                               couplings left out (the alternative Secs. 3.2 and 4 discuss): the
+                               per-block V-cycles are independent and run concurrently */
 } bgs_options;
 
 typedef struct {
@@ -82,7 +87,7 @@ typedef struct {
     int reorth;             /* Arnoldi steps that ran the second Gram-Schmidt pass */
     double rel_true_resid;  /* ||b - A x|| / ||b|| of the returned x, in FP64 */
     double rel_est_resid;   /* last Arnoldi residual estimate */
-    double t_setup_ms;      /* bgs_setup wall time */
+    double t_setup_ms;      /* wall time of the last bgs_setup or bgs_update_values */
     double t_solve_ms;      /* this solve's wall time */
 } bgs_info;
 
@@ -102,6 +107,20 @@ int bgs_create(bgs_handle *out, int nfields, const int64_t *field_sizes, const b
 /* Builds the SA-AMG hierarchy of every diagonal block (Sec. 2.2.1): strength filter, MIS-2
  * aggregation, smoothed prolongator, Galerkin coarse operators, Chebyshev bounds, coarsest LU. */
 int bgs_setup(bgs_handle h);
+
+/* Numeric re-set-up after the blocks' values changed on unchanged patterns, as in the nonlinear
+ * iterations of a simulation (Sec. 3.2 notes that the symbolic phase of a factorisation can be
+ * recycled across them while the numeric phase is redone).  values[r*F + c] points to the new
+ * nnz(r, c) values of block (r, c) in the order of its stored entries (host or device memory,
+ * read before the call returns; the caller keeps ownership); NULL keeps that block's values.
+ * Every level keeps the strength flags and aggregates of the last bgs_setup (so all patterns, SELL
+ * layouts and tuned kernels stay); the full operator, the couplings, the filtered matrices,
+ * omega, P, R, the Galerkin operators, the Chebyshev bounds and the coarsest inverse are
+ * recomputed from the new values.  The result equals a fresh bgs_setup on the new values whenever
+ * that would make the same strength and aggregation decisions.  Returns BGS_NOT_SETUP before the
+ * first bgs_setup, BGS_INVALID_ARG for values == NULL, BGS_ZERO_PIVOT if the new coarsest operator
+ * is singular.  Captured CUDA graphs are dropped (they are re-captured by the next solve). */
+int bgs_update_values(bgs_handle h, const double *const *values);
 
 /* Solves A x = b by FGMRES(m) with the block Gauss-Seidel preconditioner, x0 = 0.
  * b, x: host or device, length sum(field_sizes).  info may be NULL. */
@@ -134,6 +153,9 @@ int bgs_level_info(bgs_handle h, int field, int level, int64_t *rows, int64_t *n
 /* which: 0 level operator A_l, 1 prolongator P_l, 2 restriction R_l.  rowptr/col/val: host
  * arrays sized by bgs_level_info (rows+1 / nnz / nnz; P_l has rows(l) rows and nagg columns). */
 int bgs_level_copy(bgs_handle h, int field, int level, int which, int32_t *rowptr, int32_t *col, double *val);
+/* SpMV kernel used for A_l (which 0), P_l (1) or R_l (2): 0 = SELL-32, k > 0 = CSR with k threads
+ * per row (chosen by the autotuner when it is on). */
+int bgs_level_format(bgs_handle h, int field, int level, int which, int *format);
 /* Aggregate id of every node of level `level` (host array of rows(level) entries). */
 int bgs_level_aggregates(bgs_handle h, int field, int level, int32_t *agg);
 
@@ -163,7 +185,7 @@ int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int6
  * work inside a captured or frozen execution context, memory fully pre-reserved by the caller's
  * own pool, or hosts that forbid allocation after start-up.  Same arguments, results and limits
  * as bgs_arnoldi_dots (1 <= cnt <= 64, ld even and >= n; anything else returns BGS_INVALID_ARG).
- * The partial sums go to one fixed array of 330,752 bytes inside the library's device image,
+ * The partial sums go to one fixed array of 248,064 bytes inside the library's device image,
  * held by every GPU that loads the library until the process exits.  The first call on each
  * device looks up that array's address (cudaGetSymbolAddress with the device current), so make
  * the first call on a device before any stream capture.  All calls share the array: calls whose

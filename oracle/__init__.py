@@ -40,7 +40,7 @@ class Options(C.Structure):
                 ("cheb_degree", C.c_int * 8), ("theta", C.c_double * 8),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int),
                 ("cheb_ratio", C.c_double), ("cheb_boost", C.c_double),
-                ("power_iters", C.c_int), ("filter_diag", C.c_int)]
+                ("power_iters", C.c_int), ("filter_diag", C.c_int), ("jacobi", C.c_int)]
 
 
 class Info(C.Structure):
@@ -58,7 +58,8 @@ MAXL = 16
 
 class _AMG(C.Structure):
     _fields_ = [("nlevels", C.c_int), ("A", C.POINTER(_CSR) * MAXL), ("P", C.POINTER(_CSR) * MAXL),
-                ("R", C.POINTER(_CSR) * MAXL), ("agg", C.POINTER(C.c_int) * MAXL), ("nagg", C.c_int * MAXL),
+                ("R", C.POINTER(_CSR) * MAXL), ("agg", C.POINTER(C.c_int) * MAXL),
+                ("strong", C.POINTER(C.c_uint8) * MAXL), ("nagg", C.c_int * MAXL),
                 ("mis_rounds", C.c_int * MAXL), ("omega", C.c_double * MAXL),
                 ("dinv", C.POINTER(C.c_double) * MAXL), ("lmax", C.c_double * MAXL),
                 ("lmin", C.c_double * MAXL), ("degree", C.c_int), ("nc", C.c_int),
@@ -111,12 +112,16 @@ def lib():
             L.or_amg_setup.argtypes = [P, C.c_double, C.c_int, C.POINTER(Options)]
             L.or_amg_free.argtypes = [C.POINTER(_AMG)]
             L.or_vcycle.argtypes = [C.POINTER(_AMG), f64p, f64p]
+            L.or_amg_update.restype = C.c_int
+            L.or_amg_update.argtypes = [C.POINTER(_AMG), f64p, C.POINTER(Options)]
             L.or_default_options.argtypes = [C.POINTER(Options)]
             L.or_bgs_create.restype = C.POINTER(_BGS)
             L.or_bgs_create.argtypes = [C.c_int, i32p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                         C.POINTER(C.c_void_p), i32p, i32p, C.POINTER(Options)]
             L.or_bgs_setup.restype = C.c_int
             L.or_bgs_setup.argtypes = [C.POINTER(_BGS)]
+            L.or_bgs_update_values.restype = C.c_int
+            L.or_bgs_update_values.argtypes = [C.POINTER(_BGS), C.POINTER(C.c_void_p)]
             L.or_bgs_free.argtypes = [C.POINTER(_BGS)]
             L.or_bgs_apply.argtypes = [C.POINTER(_BGS), f64p, f64p]
             L.or_bgs_apply_adjoint.argtypes = [C.POINTER(_BGS), f64p, f64p]
@@ -306,8 +311,19 @@ class AMG:
             self.p, self._own, self._owner = _ptr, False, _owner
         else:
             self._A = _Handle(A)
-            self.p = lib().or_amg_setup(self._A.p, float(theta), int(degree), C.byref(opts or default_options()))
+            self._opts = opts or default_options()
+            self.p = lib().or_amg_setup(self._A.p, float(theta), int(degree), C.byref(self._opts))
             self._own = True
+
+    def update(self, values):
+        """Numeric re-set-up with new level-0 values on the same pattern."""
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        assert v.size == self.s.A[0].contents.nnz
+        return lib().or_amg_update(self.p, v, C.byref(getattr(self, "_opts", None) or default_options()))
+
+    def strong(self, l):
+        nnz = self.s.A[l].contents.nnz
+        return np.ctypeslib.as_array(self.s.strong[l], shape=(nnz,)).copy()
 
     def __del__(self):
         if getattr(self, "_own", False):
@@ -403,6 +419,21 @@ class BGS:
 
     def setup(self):
         return lib().or_bgs_setup(self.p)
+
+    def update_values(self, values):
+        """values: F x F nested list of new value arrays (same patterns); None keeps a block's values."""
+        F = self.F
+        vs = (C.c_void_p * (F * F))()
+        keep = []
+        for r in range(F):
+            for c in range(F):
+                v = values[r][c]
+                if v is None:
+                    continue
+                v = np.ascontiguousarray(v, dtype=np.float64)
+                keep.append(v)
+                vs[r * F + c] = v.ctypes.data
+        return lib().or_bgs_update_values(self.p, vs)
 
     def amg(self, field):
         return AMG(None, _ptr=self.p.contents.amg[field], _owner=self)

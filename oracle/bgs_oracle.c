@@ -577,6 +577,80 @@ static void lu_solve_transposed(int n, const double *lu, const int *piv, const d
 /* ------------------------------------------------------------------------------------ */
 /* SA-AMG hierarchy                                                                      */
 /* ------------------------------------------------------------------------------------ */
+/* Numeric part of one coarsening step, given the strength flags and aggregates of level l:
+ * filtered matrix A_F (diagonal + strong entries, dropped entries lumped), D_F, omega from the
+ * power iteration, P = P_tent - omega D_F^-1 A_F P_tent, R = P^T, A_{l+1} = R (A_l P).  The
+ * full set-up and the numeric re-set-up both go through here. */
+static void level_numeric(or_amg *h, int l, const unsigned char *strong, const or_options *opt) {
+    or_csr *A = h->A[l];
+    int n = A->n;
+    double *vF = (double *)malloc(sizeof(double) * (size_t)(A->nnz > 0 ? A->nnz : 1));
+    double *dF = (double *)malloc(sizeof(double) * (size_t)n);
+    or_filter(A, strong, opt->filter_diag, vF, dF);
+    /* A_F as its own matrix: the dropped entries leave the pattern (they would only add
+     * structural zeros to P and to the coarse operators) */
+    int nf = 0;
+    for (int i = 0; i < n; i++)
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) nf += (A->ci[e] == i) || strong[e];
+    or_csr *AF = or_csr_new(n, n, nf);
+    nf = 0;
+    for (int i = 0; i < n; i++) {
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++)
+            if (A->ci[e] == i || strong[e]) {
+                AF->ci[nf] = A->ci[e];
+                AF->v[nf] = vF[e];
+                nf++;
+            }
+        AF->rp[i + 1] = nf;
+    }
+    double *dinvF = (double *)malloc(sizeof(double) * (size_t)n);
+    /* a row whose filtered entries lump to zero (all its connections weak and a zero row sum)
+     * takes no part in the smoothing: D_F^-1 = 0 there, so its row of P stays the P_tent row */
+    for (int i = 0; i < n; i++) dinvF[i] = dF[i] != 0.0 ? 1.0 / dF[i] : 0.0;
+    double lam = or_power_lambda(AF, dinvF, opt->power_iters);
+    double omega = (4.0 / 3.0) / lam;
+    or_csr *P = or_smooth_prolongator(AF, dinvF, h->agg[l], h->nagg[l], omega);
+    or_csr_free(AF);
+    or_csr *R = or_transpose(P);
+    or_csr *AP = or_spgemm(A, P);
+    or_csr *Ac = or_spgemm(R, AP);
+    or_csr_free(AP);
+    free(vF);
+    free(dF);
+    free(dinvF);
+    or_csr_free(h->P[l]);
+    or_csr_free(h->R[l]);
+    or_csr_free(h->A[l + 1]);
+    h->omega[l] = omega;
+    h->P[l] = P;
+    h->R[l] = R;
+    h->A[l + 1] = Ac;
+}
+
+/* Smoother bounds on every level above the coarsest, and the dense LU of the coarsest. */
+static void smoothers_and_lu(or_amg *h, const or_options *opt) {
+    for (int k = 0; k + 1 < h->nlevels; k++) {
+        or_csr *A = h->A[k];
+        free(h->dinv[k]);
+        h->dinv[k] = (double *)malloc(sizeof(double) * (size_t)A->n);
+        for (int i = 0; i < A->n; i++) h->dinv[k][i] = 1.0 / diag_of(A, i);
+        double lam = or_power_lambda(A, h->dinv[k], opt->power_iters);
+        h->lmax[k] = opt->cheb_boost * lam;
+        h->lmin[k] = h->lmax[k] / opt->cheb_ratio;
+    }
+    or_csr *Ac = h->A[h->nlevels - 1];
+    int nc = Ac->n;
+    h->nc = nc;
+    free(h->lu);
+    free(h->piv);
+    h->lu = (double *)calloc((size_t)nc * nc, sizeof(double));
+    h->piv = (int *)malloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
+    for (int i = 0; i < nc; i++)
+        for (int e = Ac->rp[i]; e < Ac->rp[i + 1]; e++) h->lu[(size_t)i * nc + Ac->ci[e]] = Ac->v[e];
+    int st = or_lu_factor(nc, h->lu, h->piv);
+    if (st != ST_OK && h->status == ST_OK) h->status = st;
+}
+
 or_amg *or_amg_setup(const or_csr *A0, double theta, int degree, const or_options *opt) {
     or_amg *h = (or_amg *)calloc(1, sizeof(or_amg));
     h->degree = degree;
@@ -603,82 +677,40 @@ or_amg *or_amg_setup(const or_csr *A0, double theta, int degree, const or_option
             nagg = or_aggregate(S, state, agg);
             free(state);
         }
+        or_csr_free(S);
         if (nagg < 0) {
             h->status = ST_INVALID;
             free(agg);
             free(strong);
-            or_csr_free(S);
             break;
         }
         if ((long long)nagg * 10 > (long long)n * 9) { /* coarsening stalled: stop here */
             free(agg);
             free(strong);
-            or_csr_free(S);
             break;
         }
-        double *vF = (double *)malloc(sizeof(double) * (size_t)(A->nnz > 0 ? A->nnz : 1));
-        double *dF = (double *)malloc(sizeof(double) * (size_t)n);
-        or_filter(A, strong, opt->filter_diag, vF, dF);
-        /* A_F as its own matrix: the dropped entries leave the pattern (they would only add
-         * structural zeros to P and to the coarse operators) */
-        int nf = 0;
-        for (int i = 0; i < n; i++)
-            for (int e = A->rp[i]; e < A->rp[i + 1]; e++) nf += (A->ci[e] == i) || strong[e];
-        or_csr *AF = or_csr_new(n, n, nf);
-        nf = 0;
-        for (int i = 0; i < n; i++) {
-            for (int e = A->rp[i]; e < A->rp[i + 1]; e++)
-                if (A->ci[e] == i || strong[e]) {
-                    AF->ci[nf] = A->ci[e];
-                    AF->v[nf] = vF[e];
-                    nf++;
-                }
-            AF->rp[i + 1] = nf;
-        }
-        double *dinvF = (double *)malloc(sizeof(double) * (size_t)n);
-        for (int i = 0; i < n; i++) dinvF[i] = 1.0 / dF[i];
-        double lam = or_power_lambda(AF, dinvF, opt->power_iters);
-        double omega = (4.0 / 3.0) / lam;
-        or_csr *P = or_smooth_prolongator(AF, dinvF, agg, nagg, omega);
-        or_csr_free(AF);
-        or_csr *R = or_transpose(P);
-        or_csr *AP = or_spgemm(A, P);
-        or_csr *Ac = or_spgemm(R, AP);
-        or_csr_free(AP);
-        free(vF);
-        free(dF);
-        free(dinvF);
-        free(strong);
-        or_csr_free(S);
         h->agg[l] = agg;
         h->nagg[l] = nagg;
-        h->omega[l] = omega;
-        h->P[l] = P;
-        h->R[l] = R;
-        h->A[l + 1] = Ac;
+        h->strong[l] = strong;   /* kept for the numeric re-set-up */
+        level_numeric(h, l, strong, opt);
         l++;
     }
     h->nlevels = l + 1;
-    /* smoothers on every level above the coarsest */
-    for (int k = 0; k + 1 < h->nlevels; k++) {
-        or_csr *A = h->A[k];
-        h->dinv[k] = (double *)malloc(sizeof(double) * (size_t)A->n);
-        for (int i = 0; i < A->n; i++) h->dinv[k][i] = 1.0 / diag_of(A, i);
-        double lam = or_power_lambda(A, h->dinv[k], opt->power_iters);
-        h->lmax[k] = opt->cheb_boost * lam;
-        h->lmin[k] = h->lmax[k] / opt->cheb_ratio;
-    }
-    /* coarsest: dense LU */
-    or_csr *Ac = h->A[h->nlevels - 1];
-    int nc = Ac->n;
-    h->nc = nc;
-    h->lu = (double *)calloc((size_t)nc * nc, sizeof(double));
-    h->piv = (int *)malloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
-    for (int i = 0; i < nc; i++)
-        for (int e = Ac->rp[i]; e < Ac->rp[i + 1]; e++) h->lu[(size_t)i * nc + Ac->ci[e]] = Ac->v[e];
-    int st = or_lu_factor(nc, h->lu, h->piv);
-    if (st != ST_OK && h->status == ST_OK) h->status = st;
+    smoothers_and_lu(h, opt);
     return h;
+}
+
+/* Numeric re-set-up: Sec. 3.2 notes that the symbolic phase of a factorisation can be recycled
+ * across the linear solves of a simulation while the numeric phase is repeated every nonlinear
+ * iteration.  The same split is taken here for the hierarchy: the level-0 operator takes new
+ * values on its old pattern; every level keeps the strength flags and aggregates of the full
+ * set-up (so every pattern stays the same), and all numeric quantities are recomputed. */
+int or_amg_update(or_amg *h, const double *v0, const or_options *opt) {
+    memcpy(h->A[0]->v, v0, sizeof(double) * (size_t)h->A[0]->nnz);
+    h->status = ST_OK;
+    for (int l = 0; l + 1 < h->nlevels; l++) level_numeric(h, l, h->strong[l], opt);
+    smoothers_and_lu(h, opt);
+    return h->status;
 }
 
 void or_amg_free(or_amg *h) {
@@ -688,6 +720,7 @@ void or_amg_free(or_amg *h) {
         or_csr_free(h->P[l]);
         or_csr_free(h->R[l]);
         free(h->agg[l]);
+        free(h->strong[l]);
         free(h->dinv[l]);
     }
     free(h->lu);
@@ -795,6 +828,28 @@ int or_bgs_setup(or_bgs *h) {
     return h->status;
 }
 
+/* New values for the stored blocks (same patterns; NULL keeps a block's values): the full
+ * operator takes them, and every diagonal block's hierarchy is re-set-up numerically. */
+int or_bgs_update_values(or_bgs *h, const double *const *vs) {
+    int F = h->F;
+    for (int b = 0; b < F * F; b++)
+        if (h->blk[b] && vs[b]) memcpy(h->blk[b]->v, vs[b], sizeof(double) * (size_t)h->blk[b]->nnz);
+    int q = 0;   /* the full operator's entries in the order or_bgs_create laid them out */
+    for (int r = 0; r < F; r++)
+        for (int i = 0; i < h->sizes[r]; i++)
+            for (int c = 0; c < F; c++) {
+                or_csr *B = h->blk[r * F + c];
+                if (!B) continue;
+                for (int e = B->rp[i]; e < B->rp[i + 1]; e++) h->full->v[q++] = B->v[e];
+            }
+    h->status = ST_OK;
+    for (int k = 0; k < F; k++) {
+        int st = or_amg_update(h->amg[k], h->blk[k * F + k]->v, &h->opt);
+        if (st) h->status = st;
+    }
+    return h->status;
+}
+
 void or_bgs_free(or_bgs *h) {
     if (!h) return;
     for (int b = 0; b < 64; b++) or_csr_free(h->blk[b]);
@@ -805,7 +860,9 @@ void or_bgs_free(or_bgs *h) {
 
 void or_full_spmv(const or_bgs *h, const double *x, double *y) { or_spmv(h->full, x, y); }
 
-/* z = M^-1 v: for k in order, r_k = v_k - sum_{pos(j) < pos(k)} A_kj z_j, z_k = V-cycle_k(r_k). */
+/* z = M^-1 v: for k in order, r_k = v_k - sum_{pos(j) < pos(k)} A_kj z_j, z_k = V-cycle_k(r_k).
+ * With opt.jacobi the couplings are left out (block Jacobi, the alternative Secs. 3.2 and 4 discuss):
+ * z_k = V-cycle_k(v_k). */
 void or_bgs_apply(const or_bgs *h, const double *v, double *z) {
     int F = h->F;
     for (int p = 0; p < F; p++) {
@@ -814,7 +871,7 @@ void or_bgs_apply(const or_bgs *h, const double *v, double *z) {
         double *r = (double *)malloc(sizeof(double) * (size_t)nk);
         double *t = (double *)malloc(sizeof(double) * (size_t)nk);
         for (int i = 0; i < nk; i++) r[i] = v[h->offs[k] + i];
-        for (int q = 0; q < p; q++) {
+        for (int q = 0; q < p && !h->opt.jacobi; q++) {   /* block Jacobi: no couplings */
             int j = h->order[q];
             or_csr *B = h->blk[k * F + j];
             if (!B) continue;
@@ -836,7 +893,7 @@ void or_bgs_apply_adjoint(const or_bgs *h, const double *v, double *z) {
         int nk = h->sizes[k];
         double *r = (double *)malloc(sizeof(double) * (size_t)nk);
         for (int i = 0; i < nk; i++) r[i] = v[h->offs[k] + i];
-        for (int q = p + 1; q < F; q++) {
+        for (int q = p + 1; q < F && !h->opt.jacobi; q++) {
             int j = h->order[q];
             or_csr *B = h->blk[j * F + k]; /* A_jk, applied transposed: r_k -= A_jk^T z_j */
             if (!B) continue;

@@ -12,6 +12,7 @@
  *   block Gauss-Seidel sweep                                      - Sec. 2.2, Eqs. hierarchical-bgs,
  *                                                                   non-voltage-bgs, voltage-bgs
  *   flexible GMRES (right preconditioned, restarted)              - Sec. 2.2 (flexible GMRES)
+ *   numeric re-set-up with the aggregation kept                    - Sec. 3.2 (symbolic reuse)
  * The paper leaves the aggregation rule, the strength measure, eigenvalue estimation and
  * the filtered-diagonal form to the library it configures; the readings taken here are
  * spelled out next to each function in bgs_oracle.c.
@@ -40,6 +41,7 @@ typedef struct {
     double cheb_ratio, cheb_boost;
     int power_iters;
     int filter_diag;        /* 0: diag(A_F) ; 1: absolute row sum of A_F */
+    int jacobi;             /* 1: block Jacobi (couplings left out of the sweep) */
 } or_options;
 
 typedef struct {
@@ -56,6 +58,7 @@ typedef struct {
     or_csr *P[OR_MAX_LEVELS];       /* prolongator level l -> from level l+1 */
     or_csr *R[OR_MAX_LEVELS];       /* restriction = P^T */
     int *agg[OR_MAX_LEVELS];        /* aggregate id per node of level l */
+    unsigned char *strong[OR_MAX_LEVELS]; /* strength flag per stored entry of A_l (last attempt) */
     int nagg[OR_MAX_LEVELS];
     int mis_rounds[OR_MAX_LEVELS];
     double omega[OR_MAX_LEVELS];    /* prolongator damping */
@@ -105,6 +108,7 @@ void or_lu_solve(int n, const double *lu, const int *piv, const double *b, doubl
 
 or_amg *or_amg_setup(const or_csr *A, double theta, int degree, const or_options *opt);
 void or_amg_free(or_amg *h);
+int or_amg_update(or_amg *h, const double *v0, const or_options *opt);
 void or_vcycle(const or_amg *h, const double *b, double *x);
 
 /* Block Gauss-Seidel and FGMRES */
@@ -112,6 +116,7 @@ void or_default_options(or_options *o);
 or_bgs *or_bgs_create(int F, const int *sizes, const int *const *rps, const int *const *cis,
                       const double *const *vs, const int *nnzs, const int *order, const or_options *opt);
 int or_bgs_setup(or_bgs *h);
+int or_bgs_update_values(or_bgs *h, const double *const *vs);
 void or_bgs_free(or_bgs *h);
 void or_bgs_apply(const or_bgs *h, const double *v, double *z);
 void or_bgs_apply_adjoint(const or_bgs *h, const double *v, double *z);

@@ -28,7 +28,7 @@ class bgs_options(C.Structure):
                 ("graph", C.c_int), ("autotune", C.c_int), ("cheb_degree", C.c_int * 8),
                 ("theta", C.c_double * 8), ("max_coarse", C.c_int), ("max_levels", C.c_int),
                 ("cheb_ratio", C.c_double), ("cheb_boost", C.c_double), ("power_iters", C.c_int),
-                ("filter_diag", C.c_int), ("reorth_eta", C.c_double)]
+                ("filter_diag", C.c_int), ("reorth_eta", C.c_double), ("jacobi", C.c_int)]
 
 
 class bgs_info(C.Structure):
@@ -62,6 +62,7 @@ def lib():
             "bgs_create": (i32, [C.POINTER(vp), i32, C.POINTER(C.c_int64), C.POINTER(bgs_csr), C.POINTER(C.c_int),
                                  C.POINTER(bgs_options), vp]),
             "bgs_setup": (i32, [vp]),
+            "bgs_update_values": (i32, [vp, C.POINTER(vp)]),
             "bgs_solve": (i32, [vp, vp, vp, C.POINTER(bgs_info)]),
             "bgs_solve_adjoint": (i32, [vp, vp, vp, C.POINTER(bgs_info)]),
             "bgs_grad_values": (i32, [vp, i32, i32, vp, vp, vp]),
@@ -74,6 +75,7 @@ def lib():
                                      C.POINTER(dbl)]),
             "bgs_level_copy": (i32, [vp, i32, i32, i32, vp, vp, vp]),
             "bgs_level_aggregates": (i32, [vp, i32, i32, vp]),
+            "bgs_level_format": (i32, [vp, i32, i32, i32, C.POINTER(C.c_int)]),
             "bgs_set_profiling": (i32, [vp, i32]),
             "bgs_kernel_stats": (i32, [vp, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
             "bgs_csr_spmv": (i32, [i64, i64, vp, vp, vp, vp, vp, i32, vp]),
@@ -207,6 +209,24 @@ class Solver:
 
     setup = bgs_setup
 
+    def bgs_update_values(self, values):
+        """values: F x F nested list of new value arrays (numpy or torch, host or device, in the
+        order of each block's stored entries); None keeps a block's values."""
+        F = self.F
+        arr = (C.c_void_p * (F * F))()
+        keep = []
+        for r in range(F):
+            for c in range(F):
+                v = values[r][c]
+                if v is None:
+                    continue
+                if isinstance(v, np.ndarray):
+                    v = np.ascontiguousarray(v, dtype=np.float64)
+                keep.append(v)
+                arr[r * F + c] = _ptr(v)
+        _check(lib().bgs_update_values(self.h, arr), "bgs_update_values")
+        del keep
+
     def bgs_solve(self, b, x, check=True) -> bgs_info:
         info = bgs_info()
         st = lib().bgs_solve(self.h, _ptr(b), _ptr(x), C.byref(info))
@@ -270,6 +290,12 @@ class Solver:
         agg = np.zeros(info["rows"], dtype=np.int32)
         _check(lib().bgs_level_aggregates(self.h, int(field), int(level), _ptr(agg)), "bgs_level_aggregates")
         return agg
+
+    def bgs_level_format(self, field, level, which=0) -> int:
+        """0 = SELL-32, k > 0 = CSR with k threads per row."""
+        f = C.c_int()
+        _check(lib().bgs_level_format(self.h, int(field), int(level), int(which), C.byref(f)), "bgs_level_format")
+        return f.value
 
     def bgs_set_profiling(self, on=True):
         _check(lib().bgs_set_profiling(self.h, 1 if on else 0), "bgs_set_profiling")

@@ -17,6 +17,8 @@
 #include <cstdlib>
 #include <mutex>
 
+#include <climits>
+
 #include "internal.h"
 
 namespace bgs {
@@ -393,7 +395,8 @@ __global__ void k_filter_fill(int n, const int *rp, const int *ci, const double 
             for (int t = frp[i]; t < q; t++) sabs += fabs(fv[t]);
             dg = sabs;
         }
-        dinvF[i] = 1.0 / dg;
+        // a row whose lumped filtered entries are all zero takes no part in the smoothing
+        dinvF[i] = dg != 0.0 ? 1.0 / dg : 0.0;
     }
 }
 
@@ -936,200 +939,158 @@ __global__ void k_psmooth(int n, const int *rp, const int *ci, double *v, const 
 }
 
 // ==========================================================================================
-// Coarsest level: dense LU with partial pivoting (column-major), explicit inverse (row-major)
+// Coarsest level: explicit inverse by Gauss-Jordan elimination with partial (row) pivoting
 // ==========================================================================================
-__global__ void k_to_dense_cm(int n, const int *rp, const int *ci, const double *v, double *a) {
+// In-place Gauss-Jordan on the row-major n x n matrix: step k takes the pivot row p (largest
+// |a_ik| for i >= k, ties to the smaller row), moves it to row k, scales it by 1/a_pk and
+// eliminates column k from every other row, leaving column k of the running inverse in column k.
+// After the last step the columns are unscrambled by undoing the row interchanges in reverse.
+// GB300 issues about two FP64 FMAs per clock per SM, so every step spreads its n^2 updates over
+// the whole GPU: one launch per step, reading the state before the step (S) and writing the state
+// after it (D), so no block ever waits on another.  Each launch also leaves one (|value|, row)
+// pivot candidate per block for the next column; every block of the next launch reduces them in
+// the same fixed order and so all agree on the pivot.
+constexpr int GJ_T = 256;
+
+__global__ void k_to_dense_rm(int n, const int *rp, const int *ci, const double *v, double *a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        for (int e = rp[i]; e < rp[i + 1]; e++) a[(size_t)ci[e] * n + i] = v[e];
+        for (int e = rp[i]; e < rp[i + 1]; e++) a[(size_t)i * n + ci[e]] = v[e];
 }
 
-constexpr int LU_NB = 32;
-constexpr int LU_T = 1024;
+__device__ __forceinline__ bool gj_better(double v, int i, double bv, int bi) {
+    return v > bv || (v == bv && i < bi);
+}
 
-__global__ void __launch_bounds__(LU_T) k_lu_panel(double *a, int n, int k0, int nb, int *piv, int *status) {
-    __shared__ double sv[32];
-    __shared__ int si[32];
+// block-wide (|value|, row) maximum, written by thread 0 to cv[blockIdx.x], ci[blockIdx.x]
+__device__ void gj_block_best(double best, int bi, double *cv, int *cidx) {
+    __shared__ double sv[GJ_T / 32];
+    __shared__ int si[GJ_T / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (gj_better(ov, oi, best, bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { sv[w] = best; si[w] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < GJ_T / 32; q++)
+            if (gj_better(sv[q], si[q], best, bi)) { best = sv[q]; bi = si[q]; }
+        cv[blockIdx.x] = best;
+        cidx[blockIdx.x] = bi;
+    }
+}
+
+__global__ void __launch_bounds__(GJ_T) k_gj_first(int n, const double *a, double *cv, int *cidx) {
+    double best = -1.0;
+    int bi = INT_MAX;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double t = fabs(a[(size_t)i * n]);
+        if (gj_better(t, i, best, bi)) { best = t; bi = i; }
+    }
+    gj_block_best(best, bi, cv, cidx);
+}
+
+__global__ void __launch_bounds__(GJ_T) k_gj_step(int n, int k, const double *__restrict__ S, double *__restrict__ D,
+                                                  const double *cv_in, const int *ci_in, int g_in, double *cv_out,
+                                                  int *ci_out, int *perm, int *status) {
     __shared__ int sp;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int j = k0; j < k0 + nb; j++) {
-        double *colj = a + (size_t)j * n;
+    __shared__ double srp;
+    if (threadIdx.x < 32) {
         double best = -1.0;
-        int bi = n;
-        for (int i = j + tid; i < n; i += LU_T) {
-            double t = fabs(colj[i]);
-            if (t > best) { best = t; bi = i; }
-        }
+        int bi = INT_MAX;
+        for (int b = threadIdx.x; b < g_in; b += 32)
+            if (gj_better(cv_in[b], ci_in[b], best, bi)) { best = cv_in[b]; bi = ci_in[b]; }
         for (int o = 16; o > 0; o >>= 1) {
-            double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (gj_better(ov, oi, best, bi)) { best = ov; bi = oi; }
         }
-        if (lane == 0) { sv[w] = best; si[w] = bi; }
-        __syncthreads();
-        if (w == 0) {
-            best = sv[lane];
-            bi = si[lane];
-            for (int o = 16; o > 0; o >>= 1) {
-                double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        if (threadIdx.x == 0) {
+            if (!(best > 0.0) || bi >= n) {   // singular: continue on row k with a unit pivot
+                bi = k;
+                srp = 1.0;
+                if (blockIdx.x == 0) *status = 1;
+            } else {
+                srp = 1.0 / S[(size_t)bi * n + k];
             }
-            if (lane == 0) {
-                sp = bi;
-                piv[j] = bi;
-                if (!(best > 0.0)) *status = 1;
-            }
+            sp = bi;
+            if (blockIdx.x == 0) perm[k] = bi;
         }
-        __syncthreads();
-        const int p = sp;
-        if (p != j)
-            for (int c = k0 + tid; c < k0 + nb; c += LU_T) {
-                double t = a[(size_t)c * n + j];
-                a[(size_t)c * n + j] = a[(size_t)c * n + p];
-                a[(size_t)c * n + p] = t;
-            }
-        __syncthreads();
-        const double pivot = colj[j];
-        if (pivot != 0.0)
-            for (int i = j + 1 + tid; i < n; i += LU_T) colj[i] = colj[i] / pivot;
-        __syncthreads();
-        for (int i = j + 1 + tid; i < n; i += LU_T) {
-            const double l = colj[i];
-            for (int c = j + 1; c < k0 + nb; c++) a[(size_t)c * n + i] -= l * a[(size_t)c * n + j];
+    }
+    __syncthreads();
+    const int p = sp;
+    const double rpiv = srp;
+    const int kn = k + 1;
+    double best = -1.0;
+    int bi = INT_MAX;
+    const unsigned un = (unsigned)n;
+    const unsigned total = un * un;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int i = (int)(t / un), j = (int)(t - (unsigned)i * un);
+        const double pk = S[(size_t)p * n + j] * rpiv;   // entry j of the scaled pivot row
+        double out;
+        if (i == k) {
+            out = (j == k) ? rpiv : pk;
+        } else {
+            const size_t src = (size_t)(i == p ? k : i) * n;
+            const double f = S[src + k];
+            out = (j == k) ? -f * rpiv : S[src + j] - f * pk;
         }
-        __syncthreads();
+        D[t] = out;
+        if (j == kn && i >= kn && gj_better(fabs(out), i, best, bi)) { best = fabs(out); bi = i; }
+    }
+    gj_block_best(best, bi, cv_out, ci_out);
+}
+
+// tau = the column order that undoes the row interchanges (applied in reverse order)
+__global__ void k_gj_tau(int n, const int *perm, int *tau) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int c = 0; c < n; c++) tau[c] = c;
+    for (int k = n - 1; k >= 0; k--) {
+        const int p = perm[k];
+        const int t = tau[k];
+        tau[k] = tau[p];
+        tau[p] = t;
     }
 }
 
-__global__ void k_lu_swap(double *a, int n, int k0, int nb, const int *piv) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        if (c >= k0 && c < k0 + nb) continue;
-        double *col = a + (size_t)c * n;
-        for (int j = k0; j < k0 + nb; j++) {
-            int p = piv[j];
-            if (p != j) {
-                double t = col[j];
-                col[j] = col[p];
-                col[p] = t;
-            }
-        }
+__global__ void k_gj_unscramble(int n, const double *D, const int *tau, double *W) {
+    const unsigned un = (unsigned)n, total = un * un;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const unsigned i = t / un, c = t - i * un;
+        W[t] = D[(size_t)i * n + tau[c]];
     }
-}
-
-__global__ void k_lu_trsm(double *a, int n, int k0, int nb) {
-    __shared__ double L[LU_NB][LU_NB];
-    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-        int r = t % nb, c = t / nb;
-        L[r][c] = a[(size_t)(k0 + c) * n + (k0 + r)];
-    }
-    __syncthreads();
-    for (int c = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        double *col = a + (size_t)c * n + k0;
-        double x[LU_NB];
-        for (int r = 0; r < nb; r++) x[r] = col[r];
-        for (int r = 0; r < nb; r++) {
-            double s = x[r];
-            for (int t = 0; t < r; t++) s -= L[r][t] * x[t];
-            x[r] = s;
-        }
-        for (int r = 0; r < nb; r++) col[r] = x[r];
-    }
-}
-
-// A22 -= L21 U12: 64 x 64 output tiles, 256 threads each computing 4 x 4
-__global__ void __launch_bounds__(256) k_lu_gemm(double *a, int n, int k0, int nb) {
-    __shared__ double Ls[64][LU_NB + 1];
-    __shared__ double Us[LU_NB][64 + 1];
-    const int r0 = k0 + nb + blockIdx.x * 64, c0 = k0 + nb + blockIdx.y * 64;
-    for (int t = threadIdx.x; t < 64 * nb; t += 256) {
-        int r = t % 64, k = t / 64;
-        Ls[r][k] = (r0 + r < n) ? a[(size_t)(k0 + k) * n + r0 + r] : 0.0;
-    }
-    for (int t = threadIdx.x; t < 64 * nb; t += 256) {
-        int k = t % nb, c = t / nb;
-        Us[k][c] = (c0 + c < n) ? a[(size_t)(c0 + c) * n + k0 + k] : 0.0;
-    }
-    __syncthreads();
-    const int tr = (threadIdx.x % 16) * 4, tc = (threadIdx.x / 16) * 4;
-    double acc[4][4] = {};
-    for (int k = 0; k < nb; k++) {
-        double lv[4], uv[4];
-        for (int q = 0; q < 4; q++) { lv[q] = Ls[tr + q][k]; uv[q] = Us[k][tc + q]; }
-        for (int p = 0; p < 4; p++)
-            for (int q = 0; q < 4; q++) acc[p][q] += lv[p] * uv[q];
-    }
-    for (int q = 0; q < 4; q++) {
-        const int c = c0 + tc + q;
-        if (c >= n) continue;
-        for (int p = 0; p < 4; p++) {
-            const int r = r0 + tr + p;
-            if (r < n) a[(size_t)c * n + r] -= acc[p][q];
-        }
-    }
-}
-
-// one block per column c of the inverse: x = U^-1 L^-1 P e_c, written to row-major W[i][c]
-__global__ void k_lu_inverse(const double *a, const int *piv, int n, double *W) {
-    extern __shared__ double xs[];
-    const int c = blockIdx.x;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = (i == c) ? 1.0 : 0.0;
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int k = 0; k < n; k++) {
-            int p = piv[k];
-            if (p != k) {
-                double t = xs[k];
-                xs[k] = xs[p];
-                xs[p] = t;
-            }
-        }
-    __syncthreads();
-    for (int j = 0; j < n; j++) {
-        const double xj = xs[j];
-        const double *col = a + (size_t)j * n;
-        if (xj != 0.0)
-            for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) xs[i] -= col[i] * xj;
-        __syncthreads();
-    }
-    for (int j = n - 1; j >= 0; j--) {
-        const double *col = a + (size_t)j * n;
-        const double xj = xs[j] / col[j];
-        __syncthreads();
-        if (threadIdx.x == 0) xs[j] = xj;
-        if (xj != 0.0)
-            for (int i = threadIdx.x; i < j; i += blockDim.x) xs[i] -= col[i] * xj;
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) W[(size_t)i * n + c] = xs[i];
 }
 
 static int dense_inverse(const DCsr &Ac, DBuf<double> &W, Scratch &sc, cudaStream_t s) {
     const int n = Ac.n;
-    DBuf<double> a((size_t)n * n, s);
-    DBuf<int> piv((size_t)n, s);
+    W.alloc((size_t)n * n, s);
+    if (n == 0) return BGS_OK;
+    DBuf<double> a((size_t)n * n, s), b((size_t)n * n, s);
+    const int g = grid_for((int64_t)n * n, GJ_T, kSMs * 2);
+    DBuf<double> cv((size_t)2 * g, s);
+    DBuf<int> cidx((size_t)2 * g, s), perm((size_t)n, s), tau((size_t)n, s);
     CK(cudaMemsetAsync(a.p, 0, sizeof(double) * (size_t)n * n, s));
-    k_to_dense_cm<<<grid_for(n, 256), 256, 0, s>>>(n, Ac.rp.p, Ac.ci.p, Ac.v.p, a.p);
+    k_to_dense_rm<<<grid_for(n, 256), 256, 0, s>>>(n, Ac.rp.p, Ac.ci.p, Ac.v.p, a.p);
     CK_LAUNCH();
     CK(cudaMemsetAsync(sc.flags.p + 6, 0, sizeof(int), s));
-    for (int k0 = 0; k0 < n; k0 += LU_NB) {
-        const int nb = std::min(LU_NB, n - k0);
-        k_lu_panel<<<1, LU_T, 0, s>>>(a.p, n, k0, nb, piv.p, sc.flags.p + 6);
+    const int g0 = grid_for(n, GJ_T, kSMs);
+    k_gj_first<<<g0, GJ_T, 0, s>>>(n, a.p, cv.p, cidx.p);
+    CK_LAUNCH();
+    double *S = a.p, *D = b.p;
+    int gin = g0;
+    for (int k = 0; k < n; k++) {
+        const int in = k & 1, out = in ^ 1;
+        k_gj_step<<<g, GJ_T, 0, s>>>(n, k, S, D, cv.p + (size_t)in * g, cidx.p + (size_t)in * g, gin,
+                                     cv.p + (size_t)out * g, cidx.p + (size_t)out * g, perm.p, sc.flags.p + 6);
         CK_LAUNCH();
-        k_lu_swap<<<grid_for(n, 256), 256, 0, s>>>(a.p, n, k0, nb, piv.p);
-        CK_LAUNCH();
-        const int rest = n - k0 - nb;
-        if (rest > 0) {
-            k_lu_trsm<<<grid_for(rest, 128), 128, 0, s>>>(a.p, n, k0, nb);
-            CK_LAUNCH();
-            dim3 g((rest + 63) / 64, (rest + 63) / 64);
-            k_lu_gemm<<<g, 256, 0, s>>>(a.p, n, k0, nb);
-            CK_LAUNCH();
-        }
+        std::swap(S, D);
+        gin = g;
     }
-    W.alloc((size_t)n * n, s);
-    const size_t smem = sizeof(double) * (size_t)n;
-    if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_lu_inverse<<<n, 256, smem, s>>>(a.p, piv.p, n, W.p);
+    k_gj_tau<<<1, 1, 0, s>>>(n, perm.p, tau.p);
+    CK_LAUNCH();
+    k_gj_unscramble<<<g, GJ_T, 0, s>>>(n, S, tau.p, W.p);
     CK_LAUNCH();
     CK(cudaMemcpyAsync(sc.h_flags + 6, sc.flags.p + 6, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1155,7 +1116,7 @@ void Hier::build_inv_T(cudaStream_t s) {
 // ==========================================================================================
 // Hierarchy construction
 // ==========================================================================================
-void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
+static void set_attributes() {
     static std::once_flag attrs;
     std::call_once(attrs, [] {
         CK(cudaFuncSetAttribute(k_sg_sym<SG_SYM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1163,15 +1124,118 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
         CK(cudaFuncSetAttribute(k_sg_num<SG_NUM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(double) * SG_WARPS * (SG_NUM_T + 32) + sizeof(int) * SG_WARPS * SG_NUM_T)));
     });
+}
+
+__global__ void k_same_pattern(int n, int64_t nnz, const int *rp1, const int *ci1, const int *rp2, const int *ci2,
+                               int *flag) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= n || t < nnz;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t <= n && rp1[t] != rp2[t]) *flag = 1;
+        if (t < nnz && ci1[t] != ci2[t]) *flag = 1;
+    }
+}
+
+void take_values(DCsr &dst, const DCsr &src, Scratch &sc, cudaStream_t s) {
+    if (dst.n != src.n || dst.m != src.m || dst.nnz != src.nnz)
+        throw Error(BGS_INTERNAL, "numeric re-set-up produced a different operator shape");
+    k_same_pattern<<<grid_for(std::max<int64_t>(dst.nnz, dst.n + 1), 256), 256, 0, s>>>(
+        dst.n, dst.nnz, dst.rp.p, dst.ci.p, src.rp.p, src.ci.p, sc.flags.p + 10);
+    CK_LAUNCH();
+    if (dst.nnz)
+        CK(cudaMemcpyAsync(dst.v.p, src.v.p, sizeof(double) * (size_t)dst.nnz, cudaMemcpyDeviceToDevice, s));
+    refresh_values(dst, s);
+}
+
+// Numeric part of coarsening step l, given the level's strength flags and aggregates: the
+// filtered matrix A_F and D_F, omega from the power iteration, P = P_tent - omega D_F^-1 A_F P_tent,
+// R = P^T and A_{l+1} = R (A_l P).  With `update` the results replace the values of the stored
+// P_l, R_l and A_{l+1}, whose patterns come out the same because flags and aggregates are kept.
+static void level_numeric(Hier &H, int l, const AmgParams &p, Scratch &sc, cudaStream_t s, Trace &tr,
+                          bool update) {
+    Level &Lv = H.L[l];
+    DCsr &A = Lv.A;
+    const int n = A.n;
+    const int nagg = Lv.nagg;
+    DCsr AF;
+    AF.n = AF.m = n;
+    AF.rp.alloc((size_t)n + 1, s);
+    k_filter_count<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, Lv.strong.p, AF.rp.p);
+    CK_LAUNCH();
+    AF.nnz = scan_exclusive(AF.rp.p, AF.rp.p, n, sc, s);
+    AF.ci.alloc((size_t)AF.nnz, s);
+    AF.v.alloc((size_t)AF.nnz, s);
+    DBuf<double> dinvF((size_t)n, s);
+    k_filter_fill<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, Lv.strong.p, AF.rp.p, AF.ci.p, AF.v.p,
+                                                   dinvF.p, p.filter_diag);
+    CK_LAUNCH();
+    tr.mark("filter", l, AF.nnz);
+    build_sell(AF, kMaxPad, sc, s);
+    const double lamF = power_lambda(AF, dinvF.p, p.power_iters, sc, s);
+    const double omega = (4.0 / 3.0) / lamF;
+    tr.mark("power(omega)", l, n);
+    DCsr Pt;
+    Pt.n = n;
+    Pt.m = nagg;
+    Pt.nnz = n;
+    Pt.rp.alloc((size_t)n + 1, s);
+    Pt.ci.alloc((size_t)n, s);
+    Pt.v.alloc((size_t)n, s);
+    k_ptent<<<grid_for(n + 1, 256), 256, 0, s>>>(n, Lv.agg.p, Pt.rp.p, Pt.ci.p, Pt.v.p);
+    CK_LAUNCH();
+    DCsr P, R, AP, Ac;
+    spgemm(view(AF), view(Pt), P, sc, s);
+    k_psmooth<<<grid_for(n, 256), 256, 0, s>>>(n, P.rp.p, P.ci.p, P.v.p, Lv.agg.p, dinvF.p, omega);
+    CK_LAUNCH();
+    tr.mark("prolongator", l, P.nnz);
+    transpose_csr(view(P), R, sc, s);
+    tr.mark("transpose", l, R.nnz);
+    spgemm(view(A), view(P), AP, sc, s);
+    tr.mark("spgemm AP", l, AP.nnz);
+    spgemm(view(R), view(AP), Ac, sc, s);
+    tr.mark("spgemm R(AP)", l, Ac.nnz);
+    Lv.omega = omega;
+    if (update) {
+        take_values(Lv.P, P, sc, s);
+        take_values(Lv.R, R, sc, s);
+        take_values(H.L[l + 1].A, Ac, sc, s);
+    } else {
+        Lv.P = std::move(P);
+        Lv.R = std::move(R);
+        H.L[l + 1].A = std::move(Ac);
+    }
+}
+
+// Chebyshev bounds on every level above the coarsest and the coarsest dense inverse.
+static void smoothers_and_inverse(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s, Trace &tr) {
+    for (size_t k = 0; k + 1 < H.L.size(); k++) {
+        Level &Lv = H.L[k];
+        const int n = Lv.A.n;
+        DBuf<double> diag((size_t)n, s);
+        extract_diag(view(Lv.A), diag.p, s);
+        if (Lv.dinv.n != (size_t)n) Lv.dinv.alloc((size_t)n, s);
+        reciprocal(diag.p, Lv.dinv.p, n, s);
+        build_sell(Lv.A, kMaxPad, sc, s);
+        const double lam = power_lambda(Lv.A, Lv.dinv.p, p.power_iters, sc, s);
+        Lv.lmax = p.cheb_boost * lam;
+        Lv.lmin = Lv.lmax / p.cheb_ratio;
+        tr.mark("power(cheb)", (int)k, n);
+    }
+    H.nc = H.L.back().A.n;
+    if (H.nc > 16384) throw Error(BGS_INTERNAL, "coarsest level too large for the dense direct solve");
+    H.status = dense_inverse(H.L.back().A, H.inv, sc, s);
+    tr.mark("dense LU+inverse", (int)H.L.size() - 1, H.nc);
+}
+
+void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
+    set_attributes();
     H.degree = p.degree;
-    H.L.reserve(32);
+    H.L.reserve(kMaxLevels + 1);
     const double t2 = p.theta * p.theta;
     Trace tr(s);
     for (int l = 0;; l++) {
-        Level &Lv = H.L[l];
-        DCsr &A = Lv.A;
-        const int n = A.n;
-        if (n <= p.max_coarse || l + 1 >= p.max_levels) break;
+        const int n = H.L[l].A.n;
+        if (n <= p.max_coarse || l + 1 >= std::min(p.max_levels, kMaxLevels)) break;
+        DCsr &A = H.L[l].A;
         build_sell(A, kMaxPad, sc, s);
         DBuf<double> diag((size_t)n, s);
         extract_diag(view(A), diag.p, s);
@@ -1203,70 +1267,26 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
             if (nagg < 0) throw Error(BGS_INTERNAL, "aggregation left a node unassigned");
         }
         if ((long long)nagg * 10 > (long long)n * 9) break;   // coarsening stalled
-        // filtered matrix and its smoothing diagonal
-        DCsr AF;
-        AF.n = AF.m = n;
-        AF.rp.alloc((size_t)n + 1, s);
-        k_filter_count<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, strong.p, AF.rp.p);
-        CK_LAUNCH();
-        AF.nnz = scan_exclusive(AF.rp.p, AF.rp.p, n, sc, s);
-        AF.ci.alloc((size_t)AF.nnz, s);
-        AF.v.alloc((size_t)AF.nnz, s);
-        DBuf<double> dinvF((size_t)n, s);
-        k_filter_fill<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, strong.p, AF.rp.p, AF.ci.p, AF.v.p,
-                                                       dinvF.p, p.filter_diag);
-        CK_LAUNCH();
-        tr.mark("filter", l, AF.nnz);
-        build_sell(AF, kMaxPad, sc, s);
-        const double lamF = power_lambda(AF, dinvF.p, p.power_iters, sc, s);
-        const double omega = (4.0 / 3.0) / lamF;
-        tr.mark("power(omega)", l, n);
-        // P = P_tent - omega D_F^-1 A_F P_tent
-        DCsr Pt;
-        Pt.n = n;
-        Pt.m = nagg;
-        Pt.nnz = n;
-        Pt.rp.alloc((size_t)n + 1, s);
-        Pt.ci.alloc((size_t)n, s);
-        Pt.v.alloc((size_t)n, s);
-        k_ptent<<<grid_for(n + 1, 256), 256, 0, s>>>(n, agg.p, Pt.rp.p, Pt.ci.p, Pt.v.p);
-        CK_LAUNCH();
-        spgemm(view(AF), view(Pt), Lv.P, sc, s);
-        k_psmooth<<<grid_for(n, 256), 256, 0, s>>>(n, Lv.P.rp.p, Lv.P.ci.p, Lv.P.v.p, agg.p, dinvF.p, omega);
-        CK_LAUNCH();
-        tr.mark("prolongator", l, Lv.P.nnz);
-        transpose_csr(view(Lv.P), Lv.R, sc, s);
-        tr.mark("transpose", l, Lv.R.nnz);
-        DCsr AP;
-        spgemm(view(A), view(Lv.P), AP, sc, s);
-        tr.mark("spgemm AP", l, AP.nnz);
         H.L.emplace_back();
-        Level &Lv2 = H.L[l];
-        spgemm(view(Lv2.R), view(AP), H.L[l + 1].A, sc, s);
-        tr.mark("spgemm R(AP)", l, H.L[l + 1].A.nnz);
-        Lv2.agg = std::move(agg);
-        Lv2.nagg = nagg;
-        Lv2.mis_rounds = rounds;
-        Lv2.omega = omega;
+        Level &Lv = H.L[l];
+        Lv.strong = std::move(strong);   // kept for the numeric re-set-up
+        Lv.agg = std::move(agg);
+        Lv.nagg = nagg;
+        Lv.mis_rounds = rounds;
+        level_numeric(H, l, p, sc, s, tr, false);
     }
-    // Chebyshev bounds on every level above the coarsest
-    for (size_t k = 0; k + 1 < H.L.size(); k++) {
-        Level &Lv = H.L[k];
-        const int n = Lv.A.n;
-        DBuf<double> diag((size_t)n, s);
-        extract_diag(view(Lv.A), diag.p, s);
-        Lv.dinv.alloc((size_t)n, s);
-        reciprocal(diag.p, Lv.dinv.p, n, s);
-        build_sell(Lv.A, kMaxPad, sc, s);
-        const double lam = power_lambda(Lv.A, Lv.dinv.p, p.power_iters, sc, s);
-        Lv.lmax = p.cheb_boost * lam;
-        Lv.lmin = Lv.lmax / p.cheb_ratio;
-        tr.mark("power(cheb)", (int)k, n);
-    }
-    H.nc = H.L.back().A.n;
-    if (H.nc > 16384) throw Error(BGS_INTERNAL, "coarsest level too large for the dense direct solve");
-    H.status = dense_inverse(H.L.back().A, H.inv, sc, s);
-    tr.mark("dense LU+inverse", (int)H.L.size() - 1, H.nc);
+    smoothers_and_inverse(H, p, sc, s, tr);
+}
+
+void amg_update(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
+    set_attributes();
+    Trace tr(s);
+    CK(cudaMemsetAsync(sc.flags.p + 10, 0, sizeof(int), s));
+    for (int l = 0; l + 1 < (int)H.L.size(); l++) level_numeric(H, l, p, sc, s, tr, true);
+    smoothers_and_inverse(H, p, sc, s, tr);
+    CK(cudaMemcpyAsync(sc.h_flags + 10, sc.flags.p + 10, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (sc.h_flags[10]) throw Error(BGS_INTERNAL, "numeric re-set-up produced a different operator pattern");
 }
 
 }  // namespace bgs

@@ -45,6 +45,8 @@ struct bgs_ctx {
     // live as long as the handle because the hierarchy memory is released on them
     cudaStream_t bs[8] = {};
     Scratch bsc[8];
+    // block Jacobi: the V-cycles fork onto bs[k] from the solve stream and join back
+    cudaEvent_t fork_ev = nullptr, join_ev[8] = {};
     DBuf<double> V, Z, w, r, x, bvec, hdev;
     double t_setup_ms = 0.0;
     int last_reorth = 0;
@@ -209,8 +211,44 @@ template <>
 void copy_out<float>(const float *src, double *dst, int64_t n, cudaStream_t s) { copy_f2d(src, dst, n, s); }
 
 // ------------------------------------------------------------------ block Gauss-Seidel sweep
+// block Jacobi: z_k = V_k(v_k) for every k, each block's V-cycle on its own stream (forked from
+// and joined back into the solve stream, so a captured graph holds F parallel branches)
+template <class VT, class XT>
+void jacobi_sweep(bgs_ctx *h, const double *v, double *z, bool transposed) {
+    cudaStream_t s = h->s;
+    const bool fork = !h->prof;   // per-class event timing needs a single stream
+    if (fork && !h->fork_ev) {
+        CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+        for (int k = 0; k < h->F; k++) CK(cudaEventCreateWithFlags(&h->join_ev[k], cudaEventDisableTiming));
+    }
+    if (fork) CK(cudaEventRecord(h->fork_ev, s));
+    for (int k = 0; k < h->F; k++) {
+        cudaStream_t sk = fork ? h->bs[k] : s;
+        if (fork) CK(cudaStreamWaitEvent(sk, h->fork_ev, 0));
+        h->s = sk;
+        try {
+            Hier &H = h->H[k];
+            copy_in<XT>(v + h->offs[k], Buf<XT>::b(H.L[0]), h->sizes[k], sk);
+            XT *xk = vcycle<VT, XT>(h, H, 0, transposed);
+            copy_out<XT>(xk, z + h->offs[k], h->sizes[k], sk);
+        } catch (...) {
+            h->s = s;
+            throw;
+        }
+        h->s = s;
+        if (fork) {
+            CK(cudaEventRecord(h->join_ev[k], sk));
+            CK(cudaStreamWaitEvent(s, h->join_ev[k], 0));
+        }
+    }
+}
+
 template <class VT, class XT, class CVT>
 void sweep(bgs_ctx *h, const double *v, double *z, bool transposed) {
+    if (h->opt.jacobi) {
+        jacobi_sweep<VT, XT>(h, v, z, transposed);
+        return;
+    }
     cudaStream_t s = h->s;
     for (int p = 0; p < h->F; p++) {
         const int k = transposed ? h->order[h->F - 1 - p] : h->order[p];
@@ -498,9 +536,52 @@ void vstack(const std::vector<DCsr *> &parts, int ncols, DCsr &C, cudaStream_t s
     CK(cudaStreamSynchronize(s));
 }
 
+// The full operator (field-blocked rows: row i of field r is blocks (r, 0..F-1) with global
+// columns) and, per field k, the lower couplings {A_kj : pos(j) < pos(k)} with global columns,
+// from the stored blocks (Sec. 2.2, Eq. block-splitting).
+void assemble_operators(bgs_ctx *h, DCsr &full, DCsr *lower, cudaStream_t s) {
+    const int F = h->F;
+    const int64_t tot = total_n(h);
+    std::vector<DCsr> rowblocks((size_t)F);
+    for (int r = 0; r < F; r++) {
+        std::vector<CsrView> parts;
+        std::vector<int> offs;
+        for (int c = 0; c < F; c++) {
+            DCsr &B = h->blk[(size_t)r * F + c];
+            if (B.nnz == 0) continue;
+            parts.push_back(view(B));
+            offs.push_back((int)h->offs[c]);
+        }
+        concat_rows((int)h->sizes[r], (int)parts.size(), parts.data(), offs.data(), rowblocks[r], h->sc, s);
+    }
+    std::vector<DCsr *> rb;
+    for (auto &x : rowblocks) rb.push_back(&x);
+    vstack(rb, (int)tot, full, s);
+    rowblocks.clear();
+    for (int k = 0; k < F; k++) {
+        std::vector<CsrView> parts;
+        std::vector<int> offs;
+        for (int j = 0; j < F; j++) {
+            if (h->pos[j] >= h->pos[k]) continue;
+            DCsr &B = h->blk[(size_t)k * F + j];
+            if (B.nnz == 0) continue;
+            parts.push_back(view(B));
+            offs.push_back((int)h->offs[j]);
+        }
+        concat_rows((int)h->sizes[k], (int)parts.size(), parts.data(), offs.data(), lower[k], h->sc, s);
+        lower[k].m = (int)tot;
+    }
+}
+
 void build_adjoint(bgs_ctx *h) {
     if (h->adjoint_ready) return;
     cudaStream_t s = h->s;
+    // rebuilt from scratch: the targets may hold SELL copies of earlier values
+    h->fullT = DCsr();
+    for (int k = 0; k < h->F; k++) {
+        h->upperT[k] = DCsr();
+        for (auto &Lv : h->H[k].L) Lv.AT = DCsr();
+    }
     transpose_csr(view(h->full), h->fullT, h->sc, s);
     build_sell(h->fullT, kMaxPad, h->sc, s);
     for (int k = 0; k < h->F; k++) {
@@ -546,6 +627,48 @@ void build_adjoint(bgs_ctx *h) {
     }
     CK(cudaStreamSynchronize(s));
     h->adjoint_ready = true;
+}
+
+AmgParams params_for(const bgs_ctx *h, int k) {
+    return AmgParams{h->opt.theta[k], h->opt.cheb_degree[k], h->opt.max_coarse, h->opt.max_levels,
+                     h->opt.power_iters, h->opt.filter_diag, h->opt.cheb_ratio, h->opt.cheb_boost};
+}
+
+// Runs fn(k, stream, scratch) for every diagonal block: the hierarchies are independent, so
+// each gets a host thread and a stream of its own (BGS_SERIAL_SETUP=1 runs them one by one).
+template <class Fn>
+int run_per_block(bgs_ctx *h, Fn &&fn) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    for (int k = 0; k < h->F; k++)
+        if (!h->bs[k]) {
+            CK(cudaStreamCreateWithFlags(&h->bs[k], cudaStreamNonBlocking));
+            h->bsc[k].init(h->bs[k]);
+        }
+    std::vector<int> st((size_t)h->F, BGS_OK);
+    auto work = [&](int k) {
+        try {
+            CK(cudaSetDevice(dev));
+            fn(k, h->bs[k], h->bsc[k]);
+        } catch (const Error &e) {
+            if (getenv("BGS_VERBOSE")) fprintf(stderr, "libbgs: block %d: %s\n", k, e.what());
+            st[k] = e.status;
+        } catch (const std::bad_alloc &) {
+            st[k] = BGS_OOM;
+        } catch (...) {
+            st[k] = BGS_INTERNAL;
+        }
+    };
+    if (h->F > 1 && !getenv("BGS_SERIAL_SETUP")) {
+        std::vector<std::thread> th;
+        for (int k = 0; k < h->F; k++) th.emplace_back(work, k);
+        for (auto &t : th) t.join();
+    } else {
+        for (int k = 0; k < h->F; k++) work(k);
+    }
+    for (int k = 0; k < h->F; k++)
+        if (st[k]) return st[k];
+    return BGS_OK;
 }
 
 template <class F>
@@ -614,6 +737,7 @@ int bgs_default_options(bgs_options *o) {
     o->power_iters = 10;
     o->filter_diag = 1;
     o->reorth_eta = 0.01;
+    o->jacobi = 0;
     return BGS_OK;
 }
 
@@ -641,8 +765,9 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
     if (opt) o = *opt;
     else bgs_default_options(&o);
     if (o.restart < 1 || o.restart > 63 || o.maxit < 1 || !(o.rtol > 0) || o.max_coarse < 1 || o.max_levels < 1 ||
+        o.max_levels > kMaxLevels ||
         o.precision < 0 || o.precision > 1 || o.power_iters < 1 || !(o.cheb_ratio > 1.0) || !(o.cheb_boost > 0) ||
-        !(o.reorth_eta >= 0.0))
+        !(o.reorth_eta >= 0.0) || o.jacobi < 0 || o.jacobi > 1)
         return BGS_INVALID_ARG;
     // host-side shape checks
     int seen[8] = {};
@@ -700,44 +825,12 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
                 if (st) return st;
             }
         tr.mark("copy+validate blocks");
-        // full operator, field-blocked rows
-        std::vector<DCsr> rowblocks((size_t)F);
-        for (int r = 0; r < F; r++) {
-            std::vector<CsrView> parts;
-            std::vector<int> offs;
-            for (int c = 0; c < F; c++) {
-                DCsr &B = h->blk[(size_t)r * F + c];
-                if (B.nnz == 0) continue;
-                parts.push_back(view(B));
-                offs.push_back((int)h->offs[c]);
-            }
-            concat_rows((int)sizes[r], (int)parts.size(), parts.data(), offs.data(), rowblocks[r], h->sc, s);
-        }
-        std::vector<DCsr *> rb;
-        for (auto &x : rowblocks) rb.push_back(&x);
-        tr.mark("row blocks");
-        vstack(rb, (int)tot, h->full, s);
-        rowblocks.clear();
-        tr.mark("vstack");
+        assemble_operators(h.get(), h->full, h->lower, s);
+        tr.mark("full operator + couplings");
         build_sell(h->full, kMaxPad, h->sc, s);
-        tr.mark("sell(full)");
-        // lower couplings per field: blocks (k, j) with pos(j) < pos(k), global columns
-        for (int k = 0; k < F; k++) {
-            std::vector<CsrView> parts;
-            std::vector<int> offs;
-            for (int j = 0; j < F; j++) {
-                if (h->pos[j] >= h->pos[k]) continue;
-                DCsr &B = h->blk[(size_t)k * F + j];
-                if (B.nnz == 0) continue;
-                parts.push_back(view(B));
-                offs.push_back((int)h->offs[j]);
-            }
-            concat_rows((int)sizes[k], (int)parts.size(), parts.data(), offs.data(), h->lower[k], h->sc, s);
-            h->lower[k].m = (int)tot;
-            build_sell(h->lower[k], kMaxPad, h->sc, s);
-        }
+        for (int k = 0; k < F; k++) build_sell(h->lower[k], kMaxPad, h->sc, s);
         CK(cudaStreamSynchronize(s));
-        tr.mark("couplings");
+        tr.mark("sell");
         *out = h.release();
         return BGS_OK;
     });
@@ -763,9 +856,7 @@ void build_block(bgs_ctx *h, int k, cudaStream_t sk, Scratch &sck) {
     CK(cudaMemcpyAsync(A0.rp.p, B.rp.p, sizeof(int) * ((size_t)B.n + 1), cudaMemcpyDeviceToDevice, sk));
     CK(cudaMemcpyAsync(A0.ci.p, B.ci.p, sizeof(int) * B.nnz, cudaMemcpyDeviceToDevice, sk));
     CK(cudaMemcpyAsync(A0.v.p, B.v.p, sizeof(double) * B.nnz, cudaMemcpyDeviceToDevice, sk));
-    AmgParams p{h->opt.theta[k], h->opt.cheb_degree[k], h->opt.max_coarse, h->opt.max_levels,
-                h->opt.power_iters, h->opt.filter_diag, h->opt.cheb_ratio, h->opt.cheb_boost};
-    amg_build(H, p, sck, sk);
+    amg_build(H, params_for(h, k), sck, sk);
     if (H.status) throw Error(H.status, "coarsest-level factorisation");
     for (size_t l = 0; l + 1 < H.L.size(); l++)
         for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R}) build_sell(*M, kMaxPad, sck, sk);
@@ -798,53 +889,25 @@ extern "C" int bgs_setup(bgs_handle h) {
         CK(cudaStreamSynchronize(s));
         const double t0 = now_ms();
         const bool mixed = h->opt.precision == 1;
-        int dev = 0;
-        CK(cudaGetDevice(&dev));
-        for (int k = 0; k < h->F; k++)
-            if (!h->bs[k]) {
-                CK(cudaStreamCreateWithFlags(&h->bs[k], cudaStreamNonBlocking));
-                h->bsc[k].init(h->bs[k]);
-            }
-        // the diagonal blocks' hierarchies are independent: one host thread and stream each
-        std::vector<int> st((size_t)h->F, BGS_OK);
-        auto work = [&](int k) {
-            try {
-                CK(cudaSetDevice(dev));
-                build_block(h, k, h->bs[k], h->bsc[k]);
-            } catch (const Error &e) {
-                if (getenv("BGS_VERBOSE")) fprintf(stderr, "libbgs: block %d: %s\n", k, e.what());
-                st[k] = e.status;
-            } catch (const std::bad_alloc &) {
-                st[k] = BGS_OOM;
-            } catch (...) {
-                st[k] = BGS_INTERNAL;
-            }
-        };
-        if (h->F > 1 && !getenv("BGS_SERIAL_SETUP")) {
-            std::vector<std::thread> th;
-            for (int k = 0; k < h->F; k++) th.emplace_back(work, k);
-            for (auto &t : th) t.join();
-        } else {
-            for (int k = 0; k < h->F; k++) work(k);
-        }
-        for (int k = 0; k < h->F; k++)
-            if (st[k]) return st[k];
+        const int st = run_per_block(h, [&](int k, cudaStream_t sk, Scratch &sck) { build_block(h, k, sk, sck); });
+        if (st) return st;
         // kernel choice by timing runs alone, after the concurrent build
-        if (h->opt.autotune) {
-            for (int k = 0; k < h->F; k++) {
-                Hier &H = h->H[k];
-                for (size_t l = 0; l + 1 < H.L.size(); l++)
-                    for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R}) autotune_spmv(*M, h->sc, s);
-                if (h->lower[k].nnz) autotune_spmv(h->lower[k], h->sc, s);
-            }
-            autotune_spmv(h->full, h->sc, s);
-        }
         for (int k = 0; k < h->F; k++)
             if (mixed && h->lower[k].nnz) {
                 h->lower[k].vb.alloc((size_t)h->lower[k].nnz, s);
                 convert_d2bf(h->lower[k].v.p, h->lower[k].vb.p, h->lower[k].nnz, s);
                 sell_refresh(h->lower[k], s);
             }
+        if (h->opt.autotune) {
+            const int hb = mixed ? 4 : 8, cb = mixed ? 2 : 8;
+            for (int k = 0; k < h->F; k++) {
+                Hier &H = h->H[k];
+                for (size_t l = 0; l + 1 < H.L.size(); l++)
+                    for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R}) autotune_spmv(*M, hb, h->sc, s);
+                if (h->lower[k].nnz) autotune_spmv(h->lower[k], cb, h->sc, s);
+            }
+            autotune_spmv(h->full, 8, h->sc, s);
+        }
         const int64_t n = total_n(h);
         const int m = h->opt.restart;
         h->V.alloc((size_t)basis_ld(n) * (m + 1), s);
@@ -859,6 +922,54 @@ extern "C" int bgs_setup(bgs_handle h) {
         CK(cudaStreamSynchronize(s));
         h->t_setup_ms = now_ms() - t0;
         h->setup_done = true;
+        return BGS_OK;
+    });
+}
+
+extern "C" int bgs_update_values(bgs_handle h, const double *const *values) {
+    if (!h || !values) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    return guarded([&]() -> int {
+        cudaStream_t s = h->s;
+        CK(cudaStreamSynchronize(s));
+        const double t0 = now_ms();
+        const int F = h->F;
+        const bool mixed = h->opt.precision == 1;
+        for (int b = 0; b < F * F; b++)
+            if (values[b] && h->blk[b].nnz)
+                CK(cudaMemcpyAsync(h->blk[b].v.p, values[b], sizeof(double) * (size_t)h->blk[b].nnz,
+                                   cudaMemcpyDefault, s));
+        {
+            // the full operator and the couplings: re-assembled, then their values taken over so
+            // that their SELL layouts and tuned kernels stay
+            DCsr full2, lower2[8];
+            assemble_operators(h, full2, lower2, s);
+            CK(cudaMemsetAsync(h->sc.flags.p + 10, 0, sizeof(int), s));
+            take_values(h->full, full2, h->sc, s);
+            for (int k = 0; k < F; k++)
+                if (h->lower[k].nnz) take_values(h->lower[k], lower2[k], h->sc, s);
+            CK(cudaMemcpyAsync(h->sc.h_flags + 10, h->sc.flags.p + 10, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (h->sc.h_flags[10]) throw Error(BGS_INTERNAL, "re-assembled operator has a different pattern");
+        }
+        const int st = run_per_block(h, [&](int k, cudaStream_t sk, Scratch &sck) {
+            Hier &H = h->H[k];
+            const DCsr &B = h->blk[(size_t)k * F + k];
+            DCsr &A0 = H.L[0].A;
+            CK(cudaMemcpyAsync(A0.v.p, B.v.p, sizeof(double) * (size_t)B.nnz, cudaMemcpyDeviceToDevice, sk));
+            refresh_values(A0, sk);
+            amg_update(H, params_for(h, k), sck, sk);
+            if (H.status) throw Error(H.status, "coarsest-level factorisation");
+            if (mixed)
+                for (size_t l = 0; l + 1 < H.L.size(); l++)
+                    convert_d2f(H.L[l].dinv.p, H.L[l].dinvf.p, H.L[l].A.n, sk);
+            CK(cudaStreamSynchronize(sk));
+        });
+        if (st) return st;
+        h->adjoint_ready = false;
+        drop_graphs(h);
+        CK(cudaStreamSynchronize(s));
+        h->t_setup_ms = now_ms() - t0;
         return BGS_OK;
     });
 }
@@ -986,6 +1097,17 @@ int bgs_level_copy(bgs_handle h, int field, int level, int which, int32_t *rowpt
     });
 }
 
+int bgs_level_format(bgs_handle h, int field, int level, int which, int *format) {
+    if (!h || field < 0 || field >= h->F || which < 0 || which > 2 || !format) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    Hier &H = h->H[field];
+    if (level < 0 || level >= (int)H.L.size()) return BGS_INVALID_ARG;
+    if (which > 0 && level + 1 >= (int)H.L.size()) return BGS_INVALID_ARG;
+    const DCsr &M = which == 0 ? H.L[level].A : (which == 1 ? H.L[level].P : H.L[level].R);
+    *format = M.sell ? 0 : (M.lanes ? M.lanes : choose_lanes(M.n, M.nnz));
+    return BGS_OK;
+}
+
 int bgs_level_aggregates(bgs_handle h, int field, int level, int32_t *agg) {
     if (!h || field < 0 || field >= h->F || !agg) return BGS_INVALID_ARG;
     if (!h->setup_done) return BGS_NOT_SETUP;
@@ -1057,6 +1179,9 @@ void bgs_destroy(bgs_handle h) {
     if (h->gs) cudaStreamSynchronize(h->gs);
     drop_graphs(h);
     for (auto &e : h->gev)
+        if (e) cudaEventDestroy(e);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    for (auto &e : h->join_ev)
         if (e) cudaEventDestroy(e);
     if (h->gs) cudaStreamDestroy(h->gs);
     for (auto &e : h->ev) {

@@ -85,9 +85,13 @@ void dense_gemv(int n, const double *W, const XT *x, XT *y, cudaStream_t s);
 // sell_refresh re-gathers the FP32 / BF16 value copies after they are created.
 bool build_sell(DCsr &A, double max_pad, Scratch &sc, cudaStream_t s);
 void sell_refresh(DCsr &A, cudaStream_t s);
+// After A.v changed in place: re-derive the FP32 / BF16 copies that exist and re-gather every
+// SELL value copy (no allocation when the copies exist).
+void refresh_values(DCsr &A, cudaStream_t s);
 // Times SELL-32 (if built) against CSR with 1..32 lanes per row and keeps the fastest for A
 // (cached per shape); returns 0 for SELL or the lane count.
-int autotune_spmv(DCsr &A, Scratch &sc, cudaStream_t s);
+// value_bytes selects the precision timed (8 FP64, 4 FP32 hierarchy, 2 BF16 couplings).
+int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s);
 
 // ---------------------------------------------------------------- krylov.cu
 // h[k] = V_k . w for k < cnt and h[cnt] = w . w (V column-major, leading dimension ld, even)
@@ -112,6 +116,7 @@ void scale_by_inv_dev(const double *in, const double *dev_scalar, double *out, i
 struct Level {
     DCsr A, P, R, AT;
     DBuf<int> agg;
+    DBuf<uint8_t> strong;   // strength flag per stored entry of A (the attempt that was kept)
     int nagg = 0, mis_rounds = 0;
     double omega = 0.0;
     DBuf<double> dinv;
@@ -139,8 +144,16 @@ struct AmgParams {
     double cheb_ratio, cheb_boost;
 };
 
+constexpr int kMaxLevels = 16;
 // Builds the hierarchy on the level-0 operator already stored in H.L[0].A.
 void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s);
+// Numeric re-set-up: H.L[0].A holds new values on its old pattern (value copies refreshed); the
+// strength flags and aggregates of every level are kept and every numeric quantity is recomputed
+// in place (P_l, R_l, A_l+1 values, smoother bounds, coarsest inverse).
+void amg_update(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s);
+// dst takes src's values (same shape and pattern; a pattern difference sets device flag slot 10 of
+// sc, which the caller clears before and reads after) and refreshes its value copies.
+void take_values(DCsr &dst, const DCsr &src, Scratch &sc, cudaStream_t s);
 void transpose_csr(const CsrView &A, DCsr &T, Scratch &sc, cudaStream_t s);
 // SELL-32 is used for an operator when its padding adds at most this factor to the stored entries
 constexpr double kMaxPad = 2.0;

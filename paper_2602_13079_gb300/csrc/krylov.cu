@@ -12,7 +12,9 @@ namespace bgs {
 
 constexpr int KT = 256;          // threads per block
 constexpr int KC = 16;           // basis vectors per dot chunk
-constexpr int KG = kSMs * 4;     // blocks along x
+constexpr int KG = kSMs * 4;     // blocks along x (update)
+constexpr int KGD = kSMs * 3;    // blocks along x (dots): one wave at the 3 blocks per SM that
+                                 // k_mdot's registers allow, so no SM runs a lone fourth block
 
 // Sums each of the NACC per-thread accumulators over the block; thread k writes sum k to out[k].
 template <int NACC>
@@ -125,7 +127,7 @@ __global__ void k_sum_partials(const double *part, int g, double *out) {
 
 size_t arnoldi_dots_scratch(int cnt, int64_t n) {
     const int nchunk = (cnt + KC - 1) / KC;
-    const int g = grid_for(n / 2 + 1, KT, KG);
+    const int g = grid_for(n / 2 + 1, KT, KGD);
     return (size_t)nchunk * g * (KC + 1);
 }
 
@@ -134,7 +136,7 @@ void arnoldi_dots_into(const double *V, int64_t ld, int cnt, const double *w, in
     if (cnt < 1 || cnt > 64) throw Error(BGS_INVALID_ARG, "basis size outside 1..64");
     if (ld & 1) throw Error(BGS_INVALID_ARG, "basis leading dimension must be even");
     const int nchunk = (cnt + KC - 1) / KC;
-    const int g = grid_for(n / 2 + 1, KT, KG);
+    const int g = grid_for(n / 2 + 1, KT, KGD);
     if ((size_t)nchunk * g * (KC + 1) > partial_cap) throw Error(BGS_INTERNAL, "partial scratch too small");
     k_mdot<<<dim3(g, nchunk), KT, 0, s>>>(V, ld, cnt, w, n, partial);
     CK_LAUNCH();

@@ -13,9 +13,9 @@
 namespace {
 
 // Largest partial-sum buffer the dot kernel can need: 4 chunks of 16 vectors (cnt <= 64) times
-// at most 608 blocks times 17 sums = 41,344 doubles (330,752 bytes).  Every GPU that loads the
+// at most 456 blocks times 17 sums = 31,008 doubles (248,064 bytes).  Every GPU that loads the
 // library holds this array until the process exits.
-constexpr size_t kNoAllocPartials = 4 * 608 * 17;
+constexpr size_t kNoAllocPartials = 4 * 456 * 17;
 
 __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
 

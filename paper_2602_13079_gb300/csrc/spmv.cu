@@ -7,6 +7,8 @@
 //    (residual, Chebyshev step, prolongation add, coupling subtraction) is fully coalesced.
 //  * CSR with L threads per row (coarse levels with long, irregular rows): rows are taken in
 //    warp-uniform strips of 32/L rows, the L lanes stride over the row and reduce by shuffles.
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -67,20 +69,24 @@ __global__ void __launch_bounds__(256) k_sell(int n, const int *__restrict__ spt
     const VT *v = sv + s0 + lane;
     AT acc = (AT)0;
     int j = 0;
+    // padded slots hold column -1: they are skipped, so they read nothing from x (x may hold
+    // unwritten entries outside the columns the matrix references, e.g. the sweep output that a
+    // coupling block reads while later fields are still to be computed)
 #pragma unroll 1
     for (; j + 4 <= w; j += 4) {
         const int c0 = __ldg(c + 0 * 32), c1 = __ldg(c + 1 * 32), c2 = __ldg(c + 2 * 32), c3 = __ldg(c + 3 * 32);
         const AT a0 = Cvt<AT>::f(ldg(v + 0 * 32)), a1 = Cvt<AT>::f(ldg(v + 1 * 32));
         const AT a2 = Cvt<AT>::f(ldg(v + 2 * 32)), a3 = Cvt<AT>::f(ldg(v + 3 * 32));
-        acc += a0 * Cvt<AT>::f(ldg(x + c0));
-        acc += a1 * Cvt<AT>::f(ldg(x + c1));
-        acc += a2 * Cvt<AT>::f(ldg(x + c2));
-        acc += a3 * Cvt<AT>::f(ldg(x + c3));
+        if (c0 >= 0) acc += a0 * Cvt<AT>::f(ldg(x + c0));
+        if (c1 >= 0) acc += a1 * Cvt<AT>::f(ldg(x + c1));
+        if (c2 >= 0) acc += a2 * Cvt<AT>::f(ldg(x + c2));
+        if (c3 >= 0) acc += a3 * Cvt<AT>::f(ldg(x + c3));
         c += 4 * 32;
         v += 4 * 32;
     }
     for (; j < w; j++) {
-        acc += Cvt<AT>::f(ldg(v)) * Cvt<AT>::f(ldg(x + __ldg(c)));
+        const int cj = __ldg(c);
+        if (cj >= 0) acc += Cvt<AT>::f(ldg(v)) * Cvt<AT>::f(ldg(x + cj));
         c += 32;
         v += 32;
     }
@@ -311,7 +317,7 @@ __global__ void k_sell_fill(int n, const int *rp, const int *ci, const int *sptr
             sci[slot] = ci[b + j];
             sperm[slot] = b + j;
         } else {
-            sci[slot] = 0;
+            sci[slot] = -1;   // padding: skipped by the kernels
             sperm[slot] = -1;
         }
     }
@@ -327,7 +333,7 @@ __global__ void k_gather_vals(int64_t m, const int *perm, const T *src, T *dst) 
 
 template <class T>
 static void gather_into(const DCsr &A, const T *src, DBuf<T> &dst, cudaStream_t s) {
-    dst.alloc((size_t)A.sell_nnz, s);
+    if (dst.n != (size_t)A.sell_nnz || !dst.p) dst.alloc((size_t)A.sell_nnz, s);
     k_gather_vals<T><<<grid_for(A.sell_nnz, 256), 256, 0, s>>>(A.sell_nnz, A.sperm.p, src, dst.p);
     CK_LAUNCH();
 }
@@ -360,6 +366,15 @@ void sell_refresh(DCsr &A, cudaStream_t s) {
     if (A.vb.p) gather_into(A, A.vb.p, A.svb, s);
 }
 
+void refresh_values(DCsr &A, cudaStream_t s) {
+    if (A.nnz <= 0) return;
+    if (A.vf.p) convert_d2f(A.v.p, A.vf.p, A.nnz, s);
+    if (A.vb.p) convert_d2bf(A.v.p, A.vb.p, A.nnz, s);
+    if (!A.sell) return;
+    gather_into(A, A.v.p, A.sv, s);
+    sell_refresh(A, s);
+}
+
 // ------------------------------------------------------------------------------------------ autotuner
 // Picks the SpMV kernel of one stored operator by timing y = A x (FP64) with every candidate:
 // SELL-32 (when built) and CSR with 1, 2, 4, 8, 16, 32 threads per row.  One warm-up and three
@@ -375,55 +390,93 @@ __global__ void k_max_row(int n, const int *rp, int *out) {
 }
 
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int64_t, int, int64_t>, int> g_tune;   // -> 0 SELL, else lanes
+static std::map<std::tuple<int, int, int64_t, int, int64_t, int>, int> g_tune;   // -> 0 SELL, else lanes
+static bool g_tune_loaded = false;
 
-int autotune_spmv(DCsr &A, Scratch &sc, cudaStream_t s) {
+// BGS_AUTOTUNE_CACHE=<file>: choices are read from and appended to this text file, so another
+// process (or a profiled run) reuses them instead of timing again.
+static void tune_cache_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("BGS_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    int n, m, r, vb, c;
+    long long nnz, snnz;
+    while (fscanf(f, "%d %d %lld %d %lld %d %d", &n, &m, &nnz, &r, &snnz, &vb, &c) == 7)
+        g_tune[std::make_tuple(n, m, (int64_t)nnz, r, (int64_t)snnz, vb)] = c;
+    fclose(f);
+}
+
+static void tune_cache_append(const std::tuple<int, int, int64_t, int, int64_t, int> &k, int c) {
+    const char *path = getenv("BGS_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%d %d %lld %d %lld %d %d\n", std::get<0>(k), std::get<1>(k), (long long)std::get<2>(k),
+            std::get<3>(k), (long long)std::get<4>(k), std::get<5>(k), c);
+    fclose(f);
+}
+
+template <class VT, class XT>
+static float time_candidates(DCsr &A, int &choice, cudaStream_t s) {
+    DBuf<XT> x((size_t)std::max(A.m, 1), s), y((size_t)A.n, s);
+    CK(cudaMemsetAsync(x.p, 0, sizeof(XT) * (size_t)std::max(A.m, 1), s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    const int cands[7] = {0, 1, 2, 4, 8, 16, 32};
+    for (int c : cands) {
+        if (c == 0 && !A.sell) continue;
+        const bool keep_sell = A.sell;
+        A.sell = (c == 0);
+        A.lanes = c;
+        float tot = 0.f;
+        for (int rep = 0; rep < 4; rep++) {
+            CK(cudaEventRecord(e0, s));
+            run<VT, XT>(A, x.p, EStore<XT>{y.p}, s);
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep) tot += ms;
+        }
+        A.sell = keep_sell;
+        if (tot < best) {
+            best = tot;
+            choice = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s) {
     if (A.n <= 0 || A.nnz <= 0) return 0;
     CK(cudaMemsetAsync(sc.flags.p + 9, 0, sizeof(int), s));
     k_max_row<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp.p, sc.flags.p + 9);
     CK_LAUNCH();
     CK(cudaMemcpyAsync(sc.h_flags + 9, sc.flags.p + 9, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const auto key = std::make_tuple(A.n, A.m, A.nnz, sc.h_flags[9], A.sell ? A.sell_nnz : (int64_t)0);
+    const auto key = std::make_tuple(A.n, A.m, A.nnz, sc.h_flags[9], A.sell ? A.sell_nnz : (int64_t)0, value_bytes);
     int choice = -1;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_cache_load();
         auto it = g_tune.find(key);
         if (it != g_tune.end()) choice = it->second;
     }
     if (choice < 0) {
-        DBuf<double> x((size_t)std::max(A.m, 1), s), y((size_t)A.n, s);
-        dev_fill_double(x.p, 1.0, A.m, s);
-        cudaEvent_t e0, e1;
-        CK(cudaEventCreate(&e0));
-        CK(cudaEventCreate(&e1));
-        float best = 1e30f;
-        const int cands[7] = {0, 1, 2, 4, 8, 16, 32};
-        for (int c : cands) {
-            if (c == 0 && !A.sell) continue;
-            const bool keep_sell = A.sell;
-            A.sell = (c == 0);
-            A.lanes = c;
-            float tot = 0.f;
-            for (int rep = 0; rep < 4; rep++) {
-                CK(cudaEventRecord(e0, s));
-                run<double, double>(A, x.p, EStore<double>{y.p}, s);
-                CK(cudaEventRecord(e1, s));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (rep) tot += ms;
-            }
-            A.sell = keep_sell;
-            if (tot < best) {
-                best = tot;
-                choice = c;
-            }
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        // time the kernels in the precision the solve will use
+        if (value_bytes == 2 && A.vb.p) time_candidates<__nv_bfloat16, double>(A, choice, s);
+        else if (value_bytes == 4 && A.vf.p) time_candidates<float, float>(A, choice, s);
+        else time_candidates<double, double>(A, choice, s);
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune[key] = choice;
+        tune_cache_append(key, choice);
     }
     if (choice == 0) {
         A.lanes = 0;

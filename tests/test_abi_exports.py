@@ -37,4 +37,5 @@ def test_options_struct_matches_header_defaults():
     assert list(o.cheb_degree)[:5] == [4, 4, 2, 2, 2]
     assert abs(o.theta[0] - 0.04) < 1e-15 and o.theta[1] == 0.0
     assert o.max_coarse == 500 and o.max_levels == 10 and o.filter_diag == 1 and o.reorth_eta == 0.01
+    assert o.jacobi == 0
     assert bgs.status_string(3) == "no convergence within maxit"

@@ -1,0 +1,76 @@
+"""SpMV autotuner: the choice per stored operator is visible through bgs_level_format, is written to
+the file named by BGS_AUTOTUNE_CACHE, and a later process obeys that file (here rewritten so that
+every operator uses CSR with one thread per row) and still solves to the same answer."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import json, sys
+import numpy as np
+import battery_system as bs
+import paper_2602_13079_gb300 as bgs
+system = bs.assemble(grid=bs.Grid(3, 24, 20, 18), seed=11)
+out = {}
+for precision in (0, 1):
+    g = bgs.solver_for_system(system, device=False, precision=precision, max_coarse=40)
+    g.bgs_setup()
+    fmt = []
+    for k in range(5):
+        L = g.bgs_num_levels(k)
+        for l in range(L - 1):    # the coarsest level is solved through its dense inverse
+            fmt += [g.bgs_level_format(k, l, w) for w in (0, 1, 2)]
+    x = np.zeros(system.ndof)
+    info = g.bgs_solve(system.b, x)
+    out[precision] = {"fmt": fmt, "iters": info.iters, "converged": bool(info.converged), "x": x.tolist()}
+    g.close()
+json.dump(out, open(sys.argv[1], "w"))
+"""
+
+
+def _run(tmp_path, cache, tag):
+    res = tmp_path / f"{tag}.json"
+    env = dict(os.environ, BGS_AUTOTUNE_CACHE=str(cache), PYTHONPATH=ROOT)
+    subprocess.run([sys.executable, "-c", CHILD, str(res)], cwd=ROOT, env=env, check=True, timeout=600)
+    return json.loads(res.read_text())
+
+
+@pytest.fixture(scope="module")
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_13079_gb300 import _build
+    _build.build()
+
+
+def test_autotune_cache_written_and_obeyed(built, tmp_path):
+    cache = tmp_path / "tune.txt"
+    first = _run(tmp_path, cache, "first")
+    lines = [ln.split() for ln in cache.read_text().splitlines() if ln.strip()]
+    assert lines and all(len(f) == 7 for f in lines)
+    for p in ("0", "1"):
+        assert first[p]["converged"]
+        assert all(f >= 0 for f in first[p]["fmt"])
+    # a second process with the same file times nothing new and makes the same choices
+    again = _run(tmp_path, cache, "again")
+    assert len(cache.read_text().splitlines()) == len(lines)
+    for p in ("0", "1"):
+        assert again[p]["fmt"] == first[p]["fmt"]
+        assert again[p]["x"] == first[p]["x"]          # same kernels, same order: bit-identical
+    # force CSR with one thread per row everywhere
+    cache.write_text("".join(" ".join(f[:6] + ["1"]) + "\n" for f in lines))
+    forced = _run(tmp_path, cache, "forced")
+    for p in ("0", "1"):
+        assert forced[p]["converged"]
+        assert all(f == 1 for f in forced[p]["fmt"])
+        x0, x1 = np.array(first[p]["x"]), np.array(forced[p]["x"])
+        assert np.linalg.norm(x1 - x0) <= 1e-6 * np.linalg.norm(x0)

@@ -102,11 +102,11 @@ def test_degenerate_block_structures(bgs, fields):
         g = _solver(bgs, blocks, sizes, order, max_coarse=mc)
         g.setup()
         x = np.zeros(sum(sizes))
-        info = g.bgs_solve(b, x)
+        info = g.bgs_solve(b, x, check=False)
         o = oracle.BGS(blocks, sizes, order, oracle.default_options(max_coarse=mc))
         assert o.setup() == 0
         xr, ir = o.solve(b)
-        assert info.converged and ir.converged
+        assert info.converged and ir.converged, (mc, info.status, info.iters, ir.iters)
         assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr)
         if mc == 5000:
             assert all(g.bgs_num_levels(k) == 1 for k in range(len(fields)))

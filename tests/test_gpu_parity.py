@@ -101,6 +101,9 @@ SETUP_CASES = [
     ("3D-17x13x11", lambda: bs.assemble(grid=bs.Grid(3, 17, 13, 11), seed=2), dict(max_coarse=60)),
     ("3D-24", lambda: bs.assemble(grid=bs.Grid(3, 24, 24, 24), seed=1), dict()),
     ("stack-8x8x40", lambda: bs.assemble(grid=bs.Grid(3, 8, 8, 40), stack=True, seed=3), dict(max_coarse=80)),
+    # theta = 0.08 on phi_s: level-1 rows whose filtered entries lump to zero (D_F = 0)
+    ("3D-24-theta0.08", lambda: bs.assemble(grid=bs.Grid(3, 24, 24, 24), seed=1),
+     dict(max_coarse=100, theta=[0.08, 0, 0, 0, 0])),
 ]
 
 
@@ -179,6 +182,24 @@ def test_vcycle_and_sweep_parity(bgs, precision):
     assert err <= (1e-10 if precision == 0 else 5e-3), err
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sweep_ignores_unwritten_output_entries(bgs, precision):
+    """The coupling SpMVs of the sweep read the output z only in fields already computed in the same
+    sweep; the entries of later fields may hold anything (here NaN) without changing the result.
+    In the paper's order phi_s (column block 0) comes last, so no padded SELL slot may read a column
+    it does not store (SELL kept: autotuning off)."""
+    system = bs.assemble(grid=bs.Grid(3, 17, 13, 11), seed=2)
+    g = bgs.solver_for_system(system, order=list(spec.PAPER_ORDER), max_coarse=60, precision=precision,
+                              autotune=0)
+    g.setup()
+    v = dev(np.random.default_rng(11).standard_normal(system.ndof))
+    z0 = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+    g.bgs_apply_preconditioner(v, z0)
+    zn = torch.full((system.ndof,), float("nan"), dtype=torch.float64, device="cuda")
+    g.bgs_apply_preconditioner(v, zn)
+    assert bool(torch.isfinite(zn).all()) and torch.equal(z0, zn)
+
+
 # ------------------------------------------------------------------------------------- solve
 @pytest.mark.parametrize("order", [spec.WORKLOAD_ORDER, spec.PAPER_ORDER], ids=["workload", "paper"])
 @pytest.mark.parametrize("precision", [0, 1])
@@ -215,6 +236,43 @@ def test_graph_replay_is_bit_identical(bgs, precision):
         g.close()
     assert out[0][1] == out[1][1] and out[0][3] == out[1][3]
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_block_jacobi_parity(bgs, precision):
+    """Block Jacobi (couplings left out; the V-cycles run as concurrent branches): the
+    preconditioner against the oracle's, the solve and adjoint against the oracle, and the
+    concurrent graph replay bit-identical to the direct launches."""
+    system = bs.assemble(grid=bs.Grid(3, 17, 13, 11), seed=2)
+    o = oracle.bgs_for_system(system, order=list(spec.WORKLOAD_ORDER),
+                              opts=oracle.default_options(max_coarse=60, jacobi=1))
+    v = np.random.default_rng(7).standard_normal(system.ndof)
+    ref = o.apply(v)
+    xr, ir = o.solve(system.b)
+    lr, il = o.solve_adjoint(system.b)
+    out = []
+    for graph in (0, 1):
+        g = bgs.solver_for_system(system, order=list(spec.WORKLOAD_ORDER), max_coarse=60, precision=precision,
+                                  graph=graph, jacobi=1)
+        g.setup()
+        z = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+        g.bgs_apply_preconditioner(dev(v), z)
+        err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err <= (1e-10 if precision == 0 else 5e-3), err
+        x = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+        info = g.bgs_solve(dev(system.b), x)
+        lam = torch.zeros_like(x)
+        info_a = g.bgs_solve_adjoint(dev(system.b), lam)
+        assert info.converged and info_a.converged
+        xh, lh = x.cpu().numpy(), lam.cpu().numpy()
+        assert np.linalg.norm(xh - xr) <= 1e-6 * np.linalg.norm(xr)
+        assert np.linalg.norm(lh - lr) <= 1e-6 * np.linalg.norm(lr)
+        if precision == 0:
+            assert abs(info.iters - ir.iters) <= 2
+        out.append((xh, lh, info.iters))
+        g.close()
+    assert out[0][2] == out[1][2]
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
 def test_solve_3d_default_options_and_host_buffers(bgs):

@@ -1,0 +1,156 @@
+"""Numeric re-set-up (bgs_update_values) on the GPU against the oracle's numeric re-set-up on the same
+new values, and against a fresh GPU set-up when no strength or aggregation decision changes."""
+import numpy as np
+import pytest
+
+import battery_system as bs
+import oracle
+from battery_system import spec
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ORDER = list(spec.WORKLOAD_ORDER)
+
+
+@pytest.fixture(scope="module")
+def bgs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_13079_gb300 import _build
+    _build.build()
+    import paper_2602_13079_gb300 as m
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def new_values(system, rel, seed, rel_phi_s=None, phi_s_scale=None):
+    """Diagonal entries of every diagonal block grow by a random factor in [0, rel] (phi_s: up to
+    rel_phi_s when given, or the whole phi_s block times phi_s_scale); couplings scaled by 0.75;
+    off-diagonal entries of the diagonal blocks kept."""
+    u = bs.rng_uniform(seed, 9, np.arange(sum(B.nnz for B in system.blocks.values()), dtype=np.uint64))
+    out, q = {}, 0
+    for key in sorted(system.blocks):
+        B = system.blocks[key]
+        v = B.val.copy()
+        if phi_s_scale is not None and key == (spec.PHI_S, spec.PHI_S):
+            v = v * phi_s_scale
+        elif key[0] == key[1]:
+            rows = np.repeat(np.arange(B.nrows), np.diff(B.rowptr))
+            d = B.col == rows
+            g = rel_phi_s if (rel_phi_s is not None and key[0] == spec.PHI_S) else rel
+            v[d] = v[d] * (1.0 + g * u[q:q + B.nnz][d])
+        else:
+            v = v * 0.75
+        q += B.nnz
+        out[key] = v
+    return out
+
+
+def nested(vals, device=False):
+    out = [[None] * 5 for _ in range(5)]
+    for (r, c), v in vals.items():
+        out[r][c] = dev(v) if device else v
+    return out
+
+
+def with_values(system, vals):
+    blocks = {k: bs.CSR(B.rowptr, B.col, vals[k], B.nrows, B.ncols) for k, B in system.blocks.items()}
+    return bs.CoupledSystem(**{**system.__dict__, "blocks": blocks})
+
+
+def oracle_pair(system, **kw):
+    return oracle.bgs_for_system(system, order=ORDER, opts=oracle.default_options(**kw))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_update_matches_oracle_update(bgs, precision):
+    system = bs.assemble(grid=bs.Grid(3, 16, 13, 11), seed=4)
+    vals = new_values(system, 0.8, seed=31, rel_phi_s=100.0)     # decisions would change
+    g = bgs.solver_for_system(system, order=ORDER, precision=precision, max_coarse=60)
+    g.setup()
+    x0 = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+    assert g.bgs_solve(dev(system.b), x0).converged            # captures the sweep graph
+    agg_before = [[g.bgs_level_aggregates(k, l) for l in range(g.bgs_num_levels(k) - 1)] for k in range(5)]
+    g.bgs_update_values(nested(vals, device=True))
+    o = oracle_pair(system, max_coarse=60)
+    assert o.update_values(nested(vals)) == 0
+    for k in range(5):
+        oa = o.amg(k)
+        assert g.bgs_num_levels(k) == oa.nlevels
+        for l in range(oa.nlevels - 1):
+            ag = g.bgs_level_aggregates(k, l)
+            assert np.array_equal(ag, agg_before[k][l]) and np.array_equal(ag, oa.aggregates(l))
+            info = g.bgs_level_info(k, l)
+            assert abs(info["omega"] - oa.omega(l)) <= 1e-12 * abs(oa.omega(l))
+            lo, hi = oa.cheb_bounds(l)
+            assert abs(info["lmax"] - hi) <= 1e-10 * hi
+            for which, ref in ((0, oa.level_matrix(l)), (1, oa.prolongator(l)), (2, oa.restriction(l))):
+                rp, ci, v = g.bgs_level_copy(k, l, which)
+                assert np.array_equal(rp, ref.rowptr) and np.array_equal(ci, ref.col)
+                assert np.abs(v - ref.val).max() <= 1e-11 * max(1.0, np.abs(ref.val).max()), (k, l, which)
+        rp, ci, v = g.bgs_level_copy(k, oa.nlevels - 1, 0)
+        ref = oa.level_matrix(oa.nlevels - 1)
+        assert np.abs(v - ref.val).max() <= 1e-11 * np.abs(ref.val).max()
+    # the solve after the update: the new system's solution
+    x = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+    info = g.bgs_solve(dev(system.b), x)
+    xr, ir = o.solve(system.b)
+    assert info.converged and ir.converged
+    new_sys = with_values(system, vals)
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(system.b - new_sys.matvec(xs)) <= 1e-8 * np.linalg.norm(system.b)
+    assert np.linalg.norm(xs - xr) <= 1e-6 * np.linalg.norm(xr)
+    # the adjoint operators are rebuilt from the new values as well
+    lam = torch.zeros_like(x)
+    assert g.bgs_solve_adjoint(dev(system.b), lam).converged
+    lr, il = o.solve_adjoint(system.b)
+    assert np.linalg.norm(lam.cpu().numpy() - lr) <= 1e-6 * np.linalg.norm(lr)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_update_equals_fresh_setup(bgs, precision):
+    """No decision changes: phi_s (theta = 0.04) is scaled by exactly 2, which leaves every strength
+    test and phase-2 comparison as it was; the other blocks (theta = 0: every stored entry is strong)
+    get a small diagonal change, and their aggregates are checked against a fresh set-up.  Then the
+    updated handle and a fresh handle on the new values compute the same bits."""
+    system = bs.assemble(grid=bs.Grid(3, 14, 12, 10), seed=6)
+    vals = new_values(system, 1e-3, seed=5, phi_s_scale=2.0)
+    g = bgs.solver_for_system(system, order=ORDER, precision=precision, max_coarse=60)
+    g.setup()
+    g.bgs_update_values(nested(vals))                        # host arrays
+    fresh = bgs.solver_for_system(with_values(system, vals), order=ORDER, precision=precision, max_coarse=60)
+    fresh.setup()
+    for k in range(5):
+        assert g.bgs_num_levels(k) == fresh.bgs_num_levels(k)
+        for l in range(g.bgs_num_levels(k) - 1):
+            assert np.array_equal(g.bgs_level_aggregates(k, l), fresh.bgs_level_aggregates(k, l))
+            for which in (0, 1, 2):
+                a, b = g.bgs_level_copy(k, l, which), fresh.bgs_level_copy(k, l, which)
+                assert all(np.array_equal(p, q) for p, q in zip(a, b)), (k, l, which)
+    x1 = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+    x2 = torch.zeros_like(x1)
+    i1 = g.bgs_solve(dev(system.b), x1)
+    i2 = fresh.bgs_solve(dev(system.b), x2)
+    assert i1.converged and i1.iters == i2.iters
+    assert torch.equal(x1, x2)
+
+
+def test_update_errors(bgs):
+    system = bs.assemble(grid=bs.Grid(3, 8, 7, 6), seed=2)
+    g = bgs.solver_for_system(system, order=ORDER)
+    with pytest.raises(bgs.BGSError) as e:
+        g.bgs_update_values(nested({k: B.val for k, B in system.blocks.items()}))
+    assert e.value.status == bgs.NOT_SETUP
+    g.setup()
+    assert bgs.lib().bgs_update_values(g.h, None) == bgs.INVALID_ARG
+    # keeping every block (all None) reproduces the same solve
+    x1 = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+    g.bgs_solve(dev(system.b), x1)
+    g.bgs_update_values([[None] * 5 for _ in range(5)])
+    x2 = torch.zeros_like(x1)
+    g.bgs_solve(dev(system.b), x2)
+    assert torch.equal(x1, x2)

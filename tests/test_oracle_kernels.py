@@ -379,3 +379,34 @@ def test_stalled_coarsening_is_retried_without_dropping():
     assert amg.nagg(0) < 0.5 * A.nrows                  # aggregated as with theta = 0
     ref = oracle.AMG(A, theta=0.0, degree=2, opts=oracle.default_options(max_coarse=10))
     assert np.array_equal(amg.aggregates(0), ref.aggregates(0))
+
+
+def test_zero_filtered_rows_keep_the_tentative_prolongator():
+    """theta = 0.08 on the 24^3 phi_s block: some level-1 rows have every connection weak and a zero
+    row sum, so their lumped filtered row is zero (D_F = 0).  Such a row takes no part in the
+    smoothing: its row of P is its P_tent row, omega stays finite, and the solve converges."""
+    s = bs.assemble(grid=bs.Grid(3, 24, 24, 24), seed=1)
+    B = s.blocks[(0, 0)]
+    opts = oracle.default_options(max_coarse=100)
+    opts.theta[0] = 0.08
+    h = oracle.AMG(oracle.CSR(B.rowptr, B.col, B.val, B.nrows, B.ncols), theta=0.08, degree=4, opts=opts)
+    assert h.status == 0 and h.nlevels >= 3
+    zero_rows = 0
+    for l in range(h.nlevels - 1):
+        assert np.isfinite(h.omega(l))
+        A = h.level_matrix(l)
+        strong = h.strong(l)
+        vF, dF = oracle.filter_matrix(A, strong, 1)
+        P = h.prolongator(l)
+        agg = h.aggregates(l)
+        for i in np.flatnonzero(dF == 0.0):
+            zero_rows += 1
+            row = slice(P.rowptr[i], P.rowptr[i + 1])
+            assert list(P.col[row]) == [agg[i]] and list(P.val[row]) == [1.0]
+    assert zero_rows > 0
+    x = h.vcycle(s.b[:s.ncells])
+    assert np.isfinite(x).all()
+    o = oracle.BGS([[oracle.CSR(B.rowptr, B.col, B.val, B.nrows, B.ncols)]], [s.ncells], [0], opts)
+    assert o.setup() == 0
+    xs, info = o.solve(s.b[:s.ncells])
+    assert info.converged

@@ -36,6 +36,30 @@ def test_bgs_with_exact_block_solves_is_the_block_triangular_inverse(order):
     assert np.abs(z - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
+def test_block_jacobi_with_exact_block_solves_is_the_block_diagonal_inverse():
+    """Block Jacobi (couplings left out, Secs. 3.2 and 4): M^-1 = blockdiag(A_kk)^-1, in either
+    direction (the adjoint of a block-diagonal M is blockdiag(A_kk^T)^-1)."""
+    s = small_system(bs.Grid(3, 4, 4, 4))
+    opts = oracle.default_options(max_coarse=10_000, jacobi=1)
+    o = oracle.bgs_for_system(s, order=list(spec.WORKLOAD_ORDER), opts=opts)
+    n = s.ncells
+    D = np.zeros((s.ndof, s.ndof))
+    for k in range(5):
+        D[k * n:(k + 1) * n, k * n:(k + 1) * n] = s.blocks[(k, k)].to_dense()
+    v = np.random.default_rng(4).standard_normal(s.ndof)
+    ref = np.linalg.solve(D, v)
+    assert np.abs(o.apply(v) - ref).max() <= 1e-10 * np.abs(ref).max()
+    refT = np.linalg.solve(D.T, v)
+    assert np.abs(o.apply_adjoint(v) - refT).max() <= 1e-10 * np.abs(refT).max()
+    # with AMG blocks the Jacobi-preconditioned FGMRES still solves, in more iterations than GS
+    gs = oracle.bgs_for_system(s, opts=oracle.default_options(max_coarse=20))
+    jac = oracle.bgs_for_system(s, opts=oracle.default_options(max_coarse=20, jacobi=1))
+    xg, ig = gs.solve(s.b)
+    xj, ij = jac.solve(s.b)
+    assert ig.converged and ij.converged and ij.iters >= ig.iters
+    assert np.linalg.norm(xj - xg) <= 1e-6 * np.linalg.norm(xg)
+
+
 def test_fgmres_converges_in_one_iteration_without_upper_blocks():
     s = small_system(bs.Grid(3, 4, 4, 4))
     order = list(spec.WORKLOAD_ORDER)
