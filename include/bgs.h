@@ -77,6 +77,12 @@ typedef struct {
     int jacobi;             /* 0 (default): forward block Gauss-Seidel sweep; 1: block Jacobi, the
                                couplings left out (the alternative Secs. 3.2 and 4 discuss): the
                                per-block V-cycles are independent and run concurrently */
+    int subsolver[8];       /* per field id, the diagonal-block solver of the sweep: 0 (default) one
+                               SA-AMG V-cycle; 1 DD(0)-ILU(0), i.e. restricted additive Schwarz without
+                               overlap over subdomains of ilu_rows consecutive rows, one ILU(0) sweep
+                               per subdomain (Sec. 2.1, Eq. one-level-schwarz; the species solver of
+                               Sec. 3.1.1) */
+    int ilu_rows;           /* DD(0)-ILU(0) subdomain size in rows, 1..8192 (default 4096) */
 } bgs_options;
 
 typedef struct {
@@ -140,7 +146,8 @@ int bgs_grad_values(bgs_handle h, int row_field, int col_field, const double *la
 /* One application of the preconditioner z = M^-1 v (device pointers, full length). */
 int bgs_apply_preconditioner(bgs_handle h, const double *v, double *z);
 
-/* One V-cycle of field k's hierarchy from x = 0: x = V_k(b) (device pointers, field length). */
+/* The block solver of field k applied to b: one V-cycle of its hierarchy from x = 0, x = V_k(b),
+ * or the DD(0)-ILU(0) sweep when subsolver[k] = 1 (device pointers, field length). */
 int bgs_apply_vcycle(bgs_handle h, int field, const double *b, double *x);
 
 /* y = A x with the assembled FP64 operator (device pointers, full length). */
@@ -153,6 +160,11 @@ int bgs_level_info(bgs_handle h, int field, int level, int64_t *rows, int64_t *n
 /* which: 0 level operator A_l, 1 prolongator P_l, 2 restriction R_l.  rowptr/col/val: host
  * arrays sized by bgs_level_info (rows+1 / nnz / nnz; P_l has rows(l) rows and nagg columns). */
 int bgs_level_copy(bgs_handle h, int field, int level, int which, int32_t *rowptr, int32_t *col, double *val);
+/* DD(0)-ILU(0) factors of a field whose subsolver is 1: the subdomain-restricted pattern of A_kk with
+ * L (unit diagonal, strictly lower, not stored) and U in place.  *nnz receives the entry count; rowptr
+ * (rows + 1), col and val (nnz each) are filled when not NULL (host or device).  BGS_INVALID_ARG for
+ * a field on the V-cycle. */
+int bgs_ilu_factors(bgs_handle h, int field, int64_t *nnz, int32_t *rowptr, int32_t *col, double *val);
 /* SpMV kernel used for A_l (which 0), P_l (1) or R_l (2): 0 = SELL-32, k > 0 = CSR with k threads
  * per row (chosen by the autotuner when it is on). */
 int bgs_level_format(bgs_handle h, int field, int level, int which, int *format);
@@ -162,7 +174,7 @@ int bgs_level_aggregates(bgs_handle h, int field, int level, int32_t *agg);
 /* Per-kernel-class timing of the last solve when enabled (bgs_set_profiling(h, 1)): launches,
  * summed CUDA-event milliseconds and algorithmic bytes.  kernel_class: 0 full SpMV, 1 Chebyshev
  * step on the finest level, 2 Arnoldi orthogonalisation, 3 coupling SpMV, 4 Chebyshev steps on
- * the coarser levels.  Algorithmic bytes: matrix values + column indices + row pointers + each
+ * the coarser levels, 5 DD(0)-ILU(0) sweeps (factors read twice).  Algorithmic bytes: matrix values + column indices + row pointers + each
  * vector read or written once. */
 int bgs_set_profiling(bgs_handle h, int on);
 int bgs_kernel_stats(bgs_handle h, int kernel_class, int64_t *launches, double *ms, double *bytes);

@@ -40,7 +40,8 @@ class Options(C.Structure):
                 ("cheb_degree", C.c_int * 8), ("theta", C.c_double * 8),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int),
                 ("cheb_ratio", C.c_double), ("cheb_boost", C.c_double),
-                ("power_iters", C.c_int), ("filter_diag", C.c_int), ("jacobi", C.c_int)]
+                ("power_iters", C.c_int), ("filter_diag", C.c_int), ("jacobi", C.c_int),
+                ("subsolver", C.c_int * 8), ("ilu_rows", C.c_int)]
 
 
 class Info(C.Structure):
@@ -66,10 +67,15 @@ class _AMG(C.Structure):
                 ("lu", C.POINTER(C.c_double)), ("piv", C.POINTER(C.c_int)), ("status", C.c_int)]
 
 
+class _ILU(C.Structure):
+    _fields_ = [("rows", C.c_int), ("F", C.POINTER(_CSR)), ("status", C.c_int)]
+
+
 class _BGS(C.Structure):
     _fields_ = [("F", C.c_int), ("sizes", C.c_int * 8), ("offs", C.c_int * 9), ("order", C.c_int * 8),
                 ("pos", C.c_int * 8), ("blk", C.POINTER(_CSR) * 64), ("full", C.POINTER(_CSR)),
-                ("amg", C.POINTER(_AMG) * 8), ("opt", Options), ("status", C.c_int)]
+                ("amg", C.POINTER(_AMG) * 8), ("ilu", C.POINTER(_ILU) * 8), ("opt", Options),
+                ("status", C.c_int)]
 
 
 APPLY_FN = C.CFUNCTYPE(None, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double))
@@ -115,6 +121,11 @@ def lib():
             L.or_amg_update.restype = C.c_int
             L.or_amg_update.argtypes = [C.POINTER(_AMG), f64p, C.POINTER(Options)]
             L.or_default_options.argtypes = [C.POINTER(Options)]
+            L.or_ilu_setup.restype = C.POINTER(_ILU)
+            L.or_ilu_setup.argtypes = [P, C.c_int]
+            L.or_ilu_free.argtypes = [C.POINTER(_ILU)]
+            L.or_ilu_apply.argtypes = [C.POINTER(_ILU), f64p, f64p]
+            L.or_ilu_apply_transposed.argtypes = [C.POINTER(_ILU), f64p, f64p]
             L.or_bgs_create.restype = C.POINTER(_BGS)
             L.or_bgs_create.argtypes = [C.c_int, i32p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                         C.POINTER(C.c_void_p), i32p, i32p, C.POINTER(Options)]
@@ -294,13 +305,50 @@ def default_options(**kw) -> Options:
     o = Options()
     lib().or_default_options(C.byref(o))
     for k, v in kw.items():
-        if k in ("cheb_degree", "theta"):
+        if k in ("cheb_degree", "theta", "subsolver"):
             arr = getattr(o, k)
             for i, x in enumerate(v):
                 arr[i] = x
         else:
             setattr(o, k, v)
     return o
+
+
+class ILU:
+    """DD(0)-ILU(0) on a square CSR matrix: subdomains of `rows` consecutive rows."""
+
+    def __init__(self, A, rows, _ptr=None):
+        if _ptr is not None:
+            self.p, self._own = _ptr, False
+        else:
+            self._A = _Handle(A)
+            self.p = lib().or_ilu_setup(self._A.p, int(rows))
+            self._own = True
+
+    def __del__(self):
+        if getattr(self, "_own", False):
+            try:
+                lib().or_ilu_free(self.p)
+            except Exception:
+                pass
+
+    @property
+    def status(self):
+        return self.p.contents.status
+
+    def factors(self):
+        """The subdomain-restricted pattern with L (unit, strictly lower) and U in place."""
+        return _from_c(self.p.contents.F, free=False)
+
+    def apply(self, r):
+        z = np.zeros(self.p.contents.F.contents.n)
+        lib().or_ilu_apply(self.p, np.ascontiguousarray(r, dtype=np.float64), z)
+        return z
+
+    def apply_transposed(self, r):
+        z = np.zeros(self.p.contents.F.contents.n)
+        lib().or_ilu_apply_transposed(self.p, np.ascontiguousarray(r, dtype=np.float64), z)
+        return z
 
 
 class AMG:
@@ -437,6 +485,9 @@ class BGS:
 
     def amg(self, field):
         return AMG(None, _ptr=self.p.contents.amg[field], _owner=self)
+
+    def ilu(self, field):
+        return ILU(None, None, _ptr=self.p.contents.ilu[field])
 
     def apply(self, v):
         z = np.zeros(self.n)

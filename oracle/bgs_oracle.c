@@ -399,6 +399,15 @@ void or_filter(const or_csr *A, const unsigned char *strong, int filter_diag, do
             }
         }
         if (dpos >= 0) vF[dpos] = A->v[dpos] + lump;
+        /* a row left with its lumped diagonal only, which is zero up to rounding (a zero row sum:
+         * below 1e-12 of the row's absolute sum), is an exact zero row */
+        int nstrong = 0;
+        double rabs = 0.0;
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) {
+            rabs += fabs(A->v[e]);
+            nstrong += A->ci[e] != i && strong[e];
+        }
+        if (dpos >= 0 && nstrong == 0 && fabs(vF[dpos]) <= 1e-12 * rabs) vF[dpos] = 0.0;
         if (filter_diag) {
             double s = 0.0;
             for (int e = A->rp[i]; e < A->rp[i + 1]; e++)
@@ -755,6 +764,128 @@ static void vcycle_level(const or_amg *h, int l, const double *b, double *x, int
 void or_vcycle(const or_amg *h, const double *b, double *x) { vcycle_level(h, 0, b, x, 0, NULL); }
 
 /* ------------------------------------------------------------------------------------ */
+/* DD(0)-ILU(0) subblock solver                                                          */
+/* ------------------------------------------------------------------------------------ */
+/* One-level restricted additive Schwarz without overlap (Sec. 2.1, Eq. one-level-schwarz with
+ * D_i = I) over subdomains of `rows` consecutive rows, each subdomain matrix A_i = R_i A R_i^T
+ * approximated by one ILU(0) factorisation (the species solver of Sec. 3.1.1).  F holds A_i for
+ * every subdomain (entries coupling two subdomains dropped), then L (unit, strictly lower) and U
+ * (upper, with the diagonal) in its pattern. */
+or_ilu *or_ilu_setup(const or_csr *A, int rows) {
+    or_ilu *m = (or_ilu *)calloc(1, sizeof(or_ilu));
+    int n = A->n;
+    m->rows = rows > 0 ? rows : n;
+    int nf = 0;
+    for (int i = 0; i < n; i++)
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) nf += A->ci[e] / m->rows == i / m->rows;
+    or_csr *F = or_csr_new(n, n, nf);
+    nf = 0;
+    for (int i = 0; i < n; i++) {
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++)
+            if (A->ci[e] / m->rows == i / m->rows) {
+                F->ci[nf] = A->ci[e];
+                F->v[nf] = A->v[e];
+                nf++;
+            }
+        F->rp[i + 1] = nf;
+    }
+    m->F = F;
+    m->status = or_ilu_factor(m);
+    return m;
+}
+
+/* ILU(0) in place, row by row (IKJ): for each k < i stored in row i, l_ik = a_ik / u_kk, then
+ * a_ij -= l_ik u_kj for every j > k stored in both row i and row k. */
+int or_ilu_factor(or_ilu *m) {
+    or_csr *F = m->F;
+    int st = ST_OK;
+    for (int i = 0; i < F->n; i++) {
+        for (int e = F->rp[i]; e < F->rp[i + 1] && F->ci[e] < i; e++) {
+            int k = F->ci[e];
+            int dk = -1;
+            for (int f = F->rp[k]; f < F->rp[k + 1]; f++)
+                if (F->ci[f] == k) dk = f;
+            if (dk < 0 || F->v[dk] == 0.0) {
+                st = ST_ZEROPIV;
+                continue;
+            }
+            double l = F->v[e] / F->v[dk];
+            F->v[e] = l;
+            /* merge the rest of row i with the upper part of row k */
+            int f = dk + 1;
+            for (int g = e + 1; g < F->rp[i + 1]; g++) {
+                while (f < F->rp[k + 1] && F->ci[f] < F->ci[g]) f++;
+                if (f < F->rp[k + 1] && F->ci[f] == F->ci[g]) F->v[g] = F->v[g] - l * F->v[f];
+            }
+        }
+    }
+    for (int i = 0; i < F->n; i++) {
+        int has = 0;
+        for (int e = F->rp[i]; e < F->rp[i + 1]; e++)
+            if (F->ci[e] == i) has = F->v[e] != 0.0;
+        if (!has) st = ST_ZEROPIV;
+    }
+    return st;
+}
+
+/* z = (L U)^-1 r, subdomain by subdomain: L y = r forward, U z = y backward (CSR order sums). */
+void or_ilu_apply(const or_ilu *m, const double *r, double *z) {
+    const or_csr *F = m->F;
+    for (int i = 0; i < F->n; i++) {
+        double t = r[i];
+        for (int e = F->rp[i]; e < F->rp[i + 1] && F->ci[e] < i; e++) t = t - F->v[e] * z[F->ci[e]];
+        z[i] = t;
+    }
+    for (int i = F->n - 1; i >= 0; i--) {
+        double t = z[i], d = 0.0;
+        for (int e = F->rp[i]; e < F->rp[i + 1]; e++) {
+            if (F->ci[e] == i) d = F->v[e];
+            else if (F->ci[e] > i) t = t - F->v[e] * z[F->ci[e]];
+        }
+        z[i] = t / d;
+    }
+}
+
+/* z = (L U)^-T r: U^T w = r (forward, column sweeps of U), then L^T z = w (backward). */
+void or_ilu_apply_transposed(const or_ilu *m, const double *r, double *z) {
+    const or_csr *F = m->F;
+    int n = F->n;
+    double *t = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    memcpy(t, r, sizeof(double) * (size_t)n);
+    for (int i = 0; i < n; i++) {
+        double d = 0.0;
+        for (int e = F->rp[i]; e < F->rp[i + 1]; e++)
+            if (F->ci[e] == i) d = F->v[e];
+        double w = t[i] / d;
+        z[i] = w;
+        for (int e = F->rp[i]; e < F->rp[i + 1]; e++)
+            if (F->ci[e] > i) t[F->ci[e]] -= F->v[e] * w;
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        double w = z[i];
+        for (int e = F->rp[i]; e < F->rp[i + 1] && F->ci[e] < i; e++) z[F->ci[e]] -= F->v[e] * w;
+    }
+    free(t);
+}
+
+/* numeric refactorisation after the values of A changed on the same pattern */
+int or_ilu_update(or_ilu *m, const or_csr *A) {
+    or_csr *F = m->F;
+    int q = 0;
+    for (int i = 0; i < A->n; i++)
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++)
+            if (A->ci[e] / m->rows == i / m->rows) F->v[q++] = A->v[e];
+    m->status = or_ilu_factor(m);
+    return m->status;
+}
+
+void or_ilu_free(or_ilu *m) {
+    if (!m) return;
+    or_csr_free(m->F);
+    free(m);
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Block Gauss-Seidel                                                                    */
 /* ------------------------------------------------------------------------------------ */
 void or_default_options(or_options *o) {
@@ -775,6 +906,7 @@ void or_default_options(or_options *o) {
     o->cheb_boost = 1.1;
     o->power_iters = 10;
     o->filter_diag = 1;
+    o->ilu_rows = 4096;
 }
 
 or_bgs *or_bgs_create(int F, const int *sizes, const int *const *rps, const int *const *cis,
@@ -822,6 +954,11 @@ or_bgs *or_bgs_create(int F, const int *sizes, const int *const *rps, const int 
 int or_bgs_setup(or_bgs *h) {
     for (int k = 0; k < h->F; k++) {
         or_csr *Akk = h->blk[k * h->F + k];
+        if (h->opt.subsolver[k] == 1) {   /* DD(0)-ILU(0) */
+            h->ilu[k] = or_ilu_setup(Akk, h->opt.ilu_rows);
+            if (h->ilu[k]->status) h->status = h->ilu[k]->status;
+            continue;
+        }
         h->amg[k] = or_amg_setup(Akk, h->opt.theta[k], h->opt.cheb_degree[k], &h->opt);
         if (h->amg[k]->status) h->status = h->amg[k]->status;
     }
@@ -844,7 +981,8 @@ int or_bgs_update_values(or_bgs *h, const double *const *vs) {
             }
     h->status = ST_OK;
     for (int k = 0; k < F; k++) {
-        int st = or_amg_update(h->amg[k], h->blk[k * F + k]->v, &h->opt);
+        int st = h->ilu[k] ? or_ilu_update(h->ilu[k], h->blk[k * F + k])
+                           : or_amg_update(h->amg[k], h->blk[k * F + k]->v, &h->opt);
         if (st) h->status = st;
     }
     return h->status;
@@ -854,7 +992,10 @@ void or_bgs_free(or_bgs *h) {
     if (!h) return;
     for (int b = 0; b < 64; b++) or_csr_free(h->blk[b]);
     or_csr_free(h->full);
-    for (int k = 0; k < 8; k++) or_amg_free(h->amg[k]);
+    for (int k = 0; k < 8; k++) {
+        or_amg_free(h->amg[k]);
+        or_ilu_free(h->ilu[k]);
+    }
     free(h);
 }
 
@@ -878,7 +1019,8 @@ void or_bgs_apply(const or_bgs *h, const double *v, double *z) {
             or_spmv(B, z + h->offs[j], t);
             for (int i = 0; i < nk; i++) r[i] -= t[i];
         }
-        or_vcycle(h->amg[k], r, z + h->offs[k]);
+        if (h->ilu[k]) or_ilu_apply(h->ilu[k], r, z + h->offs[k]);
+        else or_vcycle(h->amg[k], r, z + h->offs[k]);
         free(r);
         free(t);
     }
@@ -899,6 +1041,11 @@ void or_bgs_apply_adjoint(const or_bgs *h, const double *v, double *z) {
             if (!B) continue;
             for (int i = 0; i < B->n; i++)
                 for (int e = B->rp[i]; e < B->rp[i + 1]; e++) r[B->ci[e]] -= B->v[e] * z[h->offs[j] + i];
+        }
+        if (h->ilu[k]) {
+            or_ilu_apply_transposed(h->ilu[k], r, z + h->offs[k]);
+            free(r);
+            continue;
         }
         const or_amg *g = h->amg[k];
         or_csr *AT[OR_MAX_LEVELS] = {0};

@@ -13,6 +13,8 @@
  *                                                                   non-voltage-bgs, voltage-bgs
  *   flexible GMRES (right preconditioned, restarted)              - Sec. 2.2 (flexible GMRES)
  *   numeric re-set-up with the aggregation kept                    - Sec. 3.2 (symbolic reuse)
+ *   DD(0)-ILU(0) subblock solver                                  - Sec. 2.1, Eq. one-level-schwarz;
+ *                                                                   Sec. 3.1.1
  * The paper leaves the aggregation rule, the strength measure, eigenvalue estimation and
  * the filtered-diagonal form to the library it configures; the readings taken here are
  * spelled out next to each function in bgs_oracle.c.
@@ -42,6 +44,8 @@ typedef struct {
     int power_iters;
     int filter_diag;        /* 0: diag(A_F) ; 1: absolute row sum of A_F */
     int jacobi;             /* 1: block Jacobi (couplings left out of the sweep) */
+    int subsolver[8];       /* per field id: 0 SA-AMG V-cycle, 1 DD(0)-ILU(0) */
+    int ilu_rows;           /* DD(0)-ILU(0) subdomain size in rows */
 } or_options;
 
 typedef struct {
@@ -72,12 +76,19 @@ typedef struct {
 } or_amg;
 
 typedef struct {
+    int rows;          /* subdomain size: rows [s*rows, (s+1)*rows) */
+    or_csr *F;         /* subdomain-restricted pattern; L (unit, strictly lower) and U in place */
+    int status;
+} or_ilu;
+
+typedef struct {
     int F;
     int sizes[8], offs[9];
     int order[8], pos[8];
     or_csr *blk[64];        /* F*F, NULL = zero */
     or_csr *full;           /* assembled full operator, field-blocked */
     or_amg *amg[8];
+    or_ilu *ilu[8];         /* DD(0)-ILU(0) fields (amg[k] NULL there) */
     or_options opt;
     int status;
 } or_bgs;
@@ -110,6 +121,14 @@ or_amg *or_amg_setup(const or_csr *A, double theta, int degree, const or_options
 void or_amg_free(or_amg *h);
 int or_amg_update(or_amg *h, const double *v0, const or_options *opt);
 void or_vcycle(const or_amg *h, const double *b, double *x);
+
+/* DD(0)-ILU(0) */
+or_ilu *or_ilu_setup(const or_csr *A, int rows);
+int or_ilu_factor(or_ilu *m);
+int or_ilu_update(or_ilu *m, const or_csr *A);
+void or_ilu_apply(const or_ilu *m, const double *r, double *z);
+void or_ilu_apply_transposed(const or_ilu *m, const double *r, double *z);
+void or_ilu_free(or_ilu *m);
 
 /* Block Gauss-Seidel and FGMRES */
 void or_default_options(or_options *o);

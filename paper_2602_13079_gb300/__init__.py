@@ -28,7 +28,8 @@ class bgs_options(C.Structure):
                 ("graph", C.c_int), ("autotune", C.c_int), ("cheb_degree", C.c_int * 8),
                 ("theta", C.c_double * 8), ("max_coarse", C.c_int), ("max_levels", C.c_int),
                 ("cheb_ratio", C.c_double), ("cheb_boost", C.c_double), ("power_iters", C.c_int),
-                ("filter_diag", C.c_int), ("reorth_eta", C.c_double), ("jacobi", C.c_int)]
+                ("filter_diag", C.c_int), ("reorth_eta", C.c_double), ("jacobi", C.c_int),
+                ("subsolver", C.c_int * 8), ("ilu_rows", C.c_int)]
 
 
 class bgs_info(C.Structure):
@@ -76,6 +77,7 @@ def lib():
             "bgs_level_copy": (i32, [vp, i32, i32, i32, vp, vp, vp]),
             "bgs_level_aggregates": (i32, [vp, i32, i32, vp]),
             "bgs_level_format": (i32, [vp, i32, i32, i32, C.POINTER(C.c_int)]),
+            "bgs_ilu_factors": (i32, [vp, i32, C.POINTER(C.c_int64), vp, vp, vp]),
             "bgs_set_profiling": (i32, [vp, i32]),
             "bgs_kernel_stats": (i32, [vp, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
             "bgs_csr_spmv": (i32, [i64, i64, vp, vp, vp, vp, vp, i32, vp]),
@@ -126,7 +128,7 @@ def bgs_default_options(**overrides) -> bgs_options:
     o = bgs_options()
     _check(lib().bgs_default_options(C.byref(o)), "bgs_default_options")
     for k, v in overrides.items():
-        if k in ("cheb_degree", "theta"):
+        if k in ("cheb_degree", "theta", "subsolver"):
             arr = getattr(o, k)
             for i, x in enumerate(v):
                 arr[i] = x
@@ -291,6 +293,17 @@ class Solver:
         _check(lib().bgs_level_aggregates(self.h, int(field), int(level), _ptr(agg)), "bgs_level_aggregates")
         return agg
 
+    def bgs_ilu_factors(self, field):
+        """DD(0)-ILU(0) factors of a field on subsolver 1: (rowptr, col, val) host arrays."""
+        nnz = C.c_int64()
+        _check(lib().bgs_ilu_factors(self.h, int(field), C.byref(nnz), None, None, None), "bgs_ilu_factors")
+        rp = np.zeros(self.field_sizes[field] + 1, dtype=np.int32)
+        ci = np.zeros(max(nnz.value, 1), dtype=np.int32)
+        v = np.zeros(max(nnz.value, 1))
+        _check(lib().bgs_ilu_factors(self.h, int(field), C.byref(nnz), _ptr(rp), _ptr(ci), _ptr(v)),
+               "bgs_ilu_factors")
+        return rp, ci[:nnz.value], v[:nnz.value]
+
     def bgs_level_format(self, field, level, which=0) -> int:
         """0 = SELL-32, k > 0 = CSR with k threads per row."""
         f = C.c_int()
@@ -307,7 +320,8 @@ class Solver:
         return dict(launches=n.value, ms=ms.value, bytes=by.value)
 
 
-KERNEL_CLASSES = {"full_spmv": 0, "chebyshev_fine": 1, "arnoldi": 2, "coupling": 3, "chebyshev_coarse": 4}
+KERNEL_CLASSES = {"full_spmv": 0, "chebyshev_fine": 1, "arnoldi": 2, "coupling": 3, "chebyshev_coarse": 4,
+                  "dd_ilu": 5}
 
 
 def solver_for_system(system, order=None, device=True, **opts):

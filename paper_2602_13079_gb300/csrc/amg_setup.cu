@@ -373,15 +373,22 @@ __global__ void k_filter_count(int n, const int *rp, const int *ci, const uint8_
 __global__ void k_filter_fill(int n, const int *rp, const int *ci, const double *v, const uint8_t *strong,
                               const int *frp, int *fci, double *fv, double *dinvF, int filter_diag) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double lump = 0.0;
-        for (int e = rp[i]; e < rp[i + 1]; e++)
+        double lump = 0.0, rabs = 0.0;
+        int nstrong = 0;
+        for (int e = rp[i]; e < rp[i + 1]; e++) {
             if (ci[e] != i && !strong[e]) lump += v[e];
+            rabs += fabs(v[e]);
+            nstrong += ci[e] != i && strong[e];
+        }
         int q = frp[i];
         double dg = 0.0;
         for (int e = rp[i]; e < rp[i + 1]; e++) {
             if (ci[e] == i) {
                 fci[q] = i;
                 fv[q] = v[e] + lump;
+                // only the lumped diagonal left and zero up to rounding (a zero row sum, below
+                // 1e-12 of the row's absolute sum): an exact zero row
+                if (nstrong == 0 && fabs(fv[q]) <= 1e-12 * rabs) fv[q] = 0.0;
                 dg = fv[q];
                 q++;
             } else if (strong[e]) {

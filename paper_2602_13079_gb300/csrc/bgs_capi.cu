@@ -61,7 +61,7 @@ struct bgs_ctx {
     bool prof = false;
     std::vector<EventPair> ev;
     size_t ev_used = 0;
-    KStats stats[5];
+    KStats stats[6];
 };
 
 namespace {
@@ -193,6 +193,20 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     return cur;
 }
 
+// The block solve of one diagonal block on L[0].b: one V-cycle, or the DD(0)-ILU(0) sweep.
+template <class VT, class XT>
+XT *block_solve(bgs_ctx *h, Hier &H, bool transposed) {
+    if (H.solver == 1) {
+        Level &L0 = H.L[0];
+        const IluFactors &M = transposed ? H.iluT : H.ilu;
+        const int vb = sizeof(XT) == 8 ? 8 : 4;
+        Prof pf(h, 5, 2.0 * ((double)M.F.nnz * (vb + 4) + 4.0 * (M.F.n + 1)) + 2.0 * sizeof(XT) * M.F.n);
+        ilu_apply<XT>(M, transposed, Buf<XT>::b(L0), Buf<XT>::x0(L0), h->s);
+        return Buf<XT>::x0(L0);
+    }
+    return vcycle<VT, XT>(h, H, 0, transposed);
+}
+
 template <class XT>
 void copy_in(const double *src, XT *dst, int64_t n, cudaStream_t s);
 template <>
@@ -229,7 +243,7 @@ void jacobi_sweep(bgs_ctx *h, const double *v, double *z, bool transposed) {
         try {
             Hier &H = h->H[k];
             copy_in<XT>(v + h->offs[k], Buf<XT>::b(H.L[0]), h->sizes[k], sk);
-            XT *xk = vcycle<VT, XT>(h, H, 0, transposed);
+            XT *xk = block_solve<VT, XT>(h, H, transposed);
             copy_out<XT>(xk, z + h->offs[k], h->sizes[k], sk);
         } catch (...) {
             h->s = s;
@@ -263,7 +277,7 @@ void sweep(bgs_ctx *h, const double *v, double *z, bool transposed) {
         } else {
             copy_in<XT>(v + h->offs[k], b0, nk, s);
         }
-        XT *xk = vcycle<VT, XT>(h, H, 0, transposed);
+        XT *xk = block_solve<VT, XT>(h, H, transposed);
         copy_out<XT>(xk, z + h->offs[k], nk, s);
     }
 }
@@ -614,6 +628,10 @@ void build_adjoint(bgs_ctx *h) {
             sell_refresh(h->upperT[k], s);
         }
         Hier &H = h->H[k];
+        if (H.solver == 1) {
+            ilu_build_transposed(H.ilu, H.iluT, h->sc, s);
+            continue;
+        }
         for (size_t l = 0; l + 1 < H.L.size(); l++) {
             transpose_csr(view(H.L[l].A), H.L[l].AT, h->sc, s);
             build_sell(H.L[l].AT, kMaxPad, h->sc, s);
@@ -738,6 +756,8 @@ int bgs_default_options(bgs_options *o) {
     o->filter_diag = 1;
     o->reorth_eta = 0.01;
     o->jacobi = 0;
+    for (int k = 0; k < 8; k++) o->subsolver[k] = 0;
+    o->ilu_rows = 4096;
     return BGS_OK;
 }
 
@@ -767,7 +787,7 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
     if (o.restart < 1 || o.restart > 63 || o.maxit < 1 || !(o.rtol > 0) || o.max_coarse < 1 || o.max_levels < 1 ||
         o.max_levels > kMaxLevels ||
         o.precision < 0 || o.precision > 1 || o.power_iters < 1 || !(o.cheb_ratio > 1.0) || !(o.cheb_boost > 0) ||
-        !(o.reorth_eta >= 0.0) || o.jacobi < 0 || o.jacobi > 1)
+        !(o.reorth_eta >= 0.0) || o.jacobi < 0 || o.jacobi > 1 || o.ilu_rows < 1 || o.ilu_rows > kIluMaxRows)
         return BGS_INVALID_ARG;
     // host-side shape checks
     int seen[8] = {};
@@ -779,7 +799,8 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
     for (int k = 0; k < F; k++) {
         if (sizes[k] < 1 || sizes[k] >= INT32_MAX) return BGS_INVALID_ARG;
         tot += sizes[k];
-        if (o.cheb_degree[k] < 1 || o.theta[k] < 0) return BGS_INVALID_ARG;
+        if (o.cheb_degree[k] < 1 || o.theta[k] < 0 || o.subsolver[k] < 0 || o.subsolver[k] > 1)
+            return BGS_INVALID_ARG;
     }
     if (tot >= INT32_MAX) return BGS_INVALID_ARG;
     for (int r = 0; r < F; r++)
@@ -856,6 +877,14 @@ void build_block(bgs_ctx *h, int k, cudaStream_t sk, Scratch &sck) {
     CK(cudaMemcpyAsync(A0.rp.p, B.rp.p, sizeof(int) * ((size_t)B.n + 1), cudaMemcpyDeviceToDevice, sk));
     CK(cudaMemcpyAsync(A0.ci.p, B.ci.p, sizeof(int) * B.nnz, cudaMemcpyDeviceToDevice, sk));
     CK(cudaMemcpyAsync(A0.v.p, B.v.p, sizeof(double) * B.nnz, cudaMemcpyDeviceToDevice, sk));
+    if (h->opt.subsolver[k] == 1) {   // DD(0)-ILU(0): factors of level 0 only
+        H.solver = 1;
+        ilu_setup(H.ilu, A0, h->opt.ilu_rows, mixed, sck, sk);
+        if (mixed) Buf<float>::alloc(H.L[0], A0.n, sk);
+        else Buf<double>::alloc(H.L[0], A0.n, sk);
+        CK(cudaStreamSynchronize(sk));
+        return;
+    }
     amg_build(H, params_for(h, k), sck, sk);
     if (H.status) throw Error(H.status, "coarsest-level factorisation");
     for (size_t l = 0; l + 1 < H.L.size(); l++)
@@ -958,6 +987,11 @@ extern "C" int bgs_update_values(bgs_handle h, const double *const *values) {
             DCsr &A0 = H.L[0].A;
             CK(cudaMemcpyAsync(A0.v.p, B.v.p, sizeof(double) * (size_t)B.nnz, cudaMemcpyDeviceToDevice, sk));
             refresh_values(A0, sk);
+            if (H.solver == 1) {
+                ilu_update(H.ilu, A0, sck, sk);
+                CK(cudaStreamSynchronize(sk));
+                return;
+            }
             amg_update(H, params_for(h, k), sck, sk);
             if (H.status) throw Error(H.status, "coarsest-level factorisation");
             if (mixed)
@@ -1033,11 +1067,11 @@ int bgs_apply_vcycle(bgs_handle h, int field, const double *b, double *x) {
         const int64_t n = h->sizes[field];
         if (h->opt.precision == 1) {
             copy_in<float>(b, Buf<float>::b(H.L[0]), n, h->s);
-            float *r = vcycle<float, float>(h, H, 0, false);
+            float *r = block_solve<float, float>(h, H, false);
             copy_out<float>(r, x, n, h->s);
         } else {
             copy_in<double>(b, Buf<double>::b(H.L[0]), n, h->s);
-            double *r = vcycle<double, double>(h, H, 0, false);
+            double *r = block_solve<double, double>(h, H, false);
             copy_out<double>(r, x, n, h->s);
         }
         CK(cudaStreamSynchronize(h->s));
@@ -1097,6 +1131,22 @@ int bgs_level_copy(bgs_handle h, int field, int level, int which, int32_t *rowpt
     });
 }
 
+int bgs_ilu_factors(bgs_handle h, int field, int64_t *nnz, int32_t *rowptr, int32_t *col, double *val) {
+    if (!h || field < 0 || field >= h->F || !nnz) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    const Hier &H = h->H[field];
+    if (H.solver != 1) return BGS_INVALID_ARG;
+    return guarded([&]() -> int {
+        const DCsr &F = H.ilu.F;
+        *nnz = F.nnz;
+        if (rowptr) CK(cudaMemcpyAsync(rowptr, F.rp.p, sizeof(int) * ((size_t)F.n + 1), cudaMemcpyDefault, h->s));
+        if (col && F.nnz) CK(cudaMemcpyAsync(col, F.ci.p, sizeof(int) * (size_t)F.nnz, cudaMemcpyDefault, h->s));
+        if (val && F.nnz) CK(cudaMemcpyAsync(val, F.v.p, sizeof(double) * (size_t)F.nnz, cudaMemcpyDefault, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        return BGS_OK;
+    });
+}
+
 int bgs_level_format(bgs_handle h, int field, int level, int which, int *format) {
     if (!h || field < 0 || field >= h->F || which < 0 || which > 2 || !format) return BGS_INVALID_ARG;
     if (!h->setup_done) return BGS_NOT_SETUP;
@@ -1128,7 +1178,7 @@ int bgs_set_profiling(bgs_handle h, int on) {
 }
 
 int bgs_kernel_stats(bgs_handle h, int cls, int64_t *launches, double *ms, double *bytes) {
-    if (!h || cls < 0 || cls > 4) return BGS_INVALID_ARG;
+    if (!h || cls < 0 || cls > 5) return BGS_INVALID_ARG;
     if (launches) *launches = h->stats[cls].launches;
     if (ms) *ms = h->stats[cls].ms;
     if (bytes) *bytes = h->stats[cls].bytes;

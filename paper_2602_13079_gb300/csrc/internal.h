@@ -75,7 +75,8 @@ template <class VT, class XT>
 void coupling_sub(const DCsr &L, const double *v, const double *z, XT *r, cudaStream_t s);
 // w_i = dinv_i * (A v)_i (FP64, power iteration)
 void spmv_scaled(const CsrView &A, const double *dinv, const double *v, double *w, cudaStream_t s);
-// w_i = dinv_i * (A v)_i / sqrt(*nrm2)  (power iteration step on a normalised v; SELL when built)
+// w_i = dinv_i * (A v)_i / sqrt(*nrm2)  (power iteration step on a normalised v; CSR with a lane
+// count fixed by the shape, whatever format the operator is stored in)
 void spmv_scaled_norm(const DCsr &A, const double *dinv, const double *v, const double *nrm2, double *w,
                       cudaStream_t s);
 // y = W x, W dense row-major n x n in FP64
@@ -127,8 +128,20 @@ struct Level {
     DBuf<float> fb, fx0, fx1, fd, fr;
 };
 
+// DD(0)-ILU(0) factors of one diagonal block: the subdomain-restricted pattern with L (unit,
+// strictly lower) and U in place, and per subdomain of R rows the level schedules of the forward
+// and backward sweeps (R + 1 level slots per subdomain).
+constexpr int kIluMaxRows = 8192;
+struct IluFactors {
+    DCsr F;
+    int R = 0, nsub = 0;
+    DBuf<int> fptr, bptr, fsched, bsched, nlf, nlb;
+};
+
 struct Hier {
     std::vector<Level> L;
+    int solver = 0;         // 0 SA-AMG V-cycle, 1 DD(0)-ILU(0) (then L holds level 0 only)
+    IluFactors ilu, iluT;   // the DD(0)-ILU(0) factors and their transpose (adjoint, built on use)
     int degree = 2;
     int nc = 0;
     DBuf<double> inv;      // dense inverse of the coarsest operator, row-major nc x nc
@@ -145,6 +158,14 @@ struct AmgParams {
 };
 
 constexpr int kMaxLevels = 16;
+// ---------------------------------------------------------------- ilu.cu
+void ilu_setup(IluFactors &M, const DCsr &A, int R, bool mixed, Scratch &sc, cudaStream_t s);
+void ilu_update(IluFactors &M, const DCsr &A, Scratch &sc, cudaStream_t s);
+void ilu_build_transposed(const IluFactors &M, IluFactors &T, Scratch &sc, cudaStream_t s);
+// z = (L U)^-1 r per subdomain (transposed: the transposed factors T, (U^T)^-1 then (L^T)^-1)
+template <class XT>
+void ilu_apply(const IluFactors &M, bool transposed, const XT *r, XT *z, cudaStream_t s);
+
 // Builds the hierarchy on the level-0 operator already stored in H.L[0].A.
 void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s);
 // Numeric re-set-up: H.L[0].A holds new values on its old pattern (value copies refreshed); the

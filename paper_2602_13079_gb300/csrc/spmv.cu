@@ -230,7 +230,11 @@ void spmv_scaled(const CsrView &A, const double *dinv, const double *v, double *
 
 void spmv_scaled_norm(const DCsr &A, const double *dinv, const double *v, const double *nrm2, double *w,
                       cudaStream_t s) {
-    run<double, double>(A, v, EScaleNorm{dinv, nrm2, w}, s);
+    // a kernel fixed by the shape alone (not by the autotuned format), so that a set-up and a later
+    // numeric re-set-up sum in the same order: one thread per row for short rows, else L lanes
+    const double avg = A.n > 0 ? (double)A.nnz / (double)A.n : 0.0;
+    const int lanes = avg <= 12.0 ? 1 : choose_lanes(A.n, A.nnz);
+    launch_csr<double, double, double>(lanes, A.n, A.rp.p, A.ci.p, A.v.p, v, EScaleNorm{dinv, nrm2, w}, s);
 }
 
 template <class VT, class XT>

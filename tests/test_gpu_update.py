@@ -131,6 +131,8 @@ def test_update_equals_fresh_setup(bgs, precision):
             for which in (0, 1, 2):
                 a, b = g.bgs_level_copy(k, l, which), fresh.bgs_level_copy(k, l, which)
                 assert all(np.array_equal(p, q) for p, q in zip(a, b)), (k, l, which)
+            ia, ib = g.bgs_level_info(k, l), fresh.bgs_level_info(k, l)
+            assert (ia["omega"], ia["lmin"], ia["lmax"]) == (ib["omega"], ib["lmin"], ib["lmax"]), (k, l)
     x1 = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
     x2 = torch.zeros_like(x1)
     i1 = g.bgs_solve(dev(system.b), x1)
