@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-profile", action="store_true")
     p.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler")
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the block-Jacobi, DD(0)-ILU(0) species and numeric re-setup measurements")
     p.add_argument("--arms", default="both", choices=["both", "fp64", "mixed"])
     p.add_argument("--graph", type=int, default=None, help="override the library default (CUDA graph sweep)")
     p.add_argument("--reorth-eta", type=float, default=None, help="override the re-orthogonalisation threshold")
@@ -322,6 +324,55 @@ def gpu_arm(args, rank, world):
     if armmx is not None:
         armmx["rel_diff_vs_fp64"] = float(np.linalg.norm(xmx - x64) / np.linalg.norm(x64))
 
+    # the other sweeps and block solvers, and the numeric re-setup, on the same system (FP64;
+    # one warm-up and `steps` timed steps each, CUDA events on the same stream)
+    variants = None
+    if not args.no_variants:
+        def timed_variant(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = [fn() for _ in range(args.steps)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / args.steps, res[-1]
+
+        def step_opts(**kw):
+            def fn():
+                g = bgs.Solver(blocks, sizes, order, precision=0, **kw)
+                g.setup()
+                info = g.bgs_solve(b, x)
+                g.close()
+                return info
+            return fn
+
+        variants = {}
+        for name, kw in (("jacobi", dict(jacobi=1)),
+                         ("dd_ilu_species", dict(subsolver=[0, 0, 0, 1, 1]))):
+            ms, info = timed_variant(step_opts(**kw))
+            rel = float(np.linalg.norm(system.b - system.matvec(x.cpu().numpy())) / np.linalg.norm(system.b))
+            variants[name] = {"s_per_step": ms / 1e3, "setup_s": info.t_setup_ms / 1e3,
+                              "solve_s": info.t_solve_ms / 1e3, "iters": info.iters,
+                              "converged": bool(info.converged), "rel_true_resid_host_check": rel}
+        # numeric re-setup: same handle, new values (every value x (1 + 1e-3 u)), then a solve
+        g = bgs.Solver(blocks, sizes, order, precision=0)
+        g.setup()
+        rng = np.random.default_rng(5)
+        newvals = [[None if B is None else B.val * torch.from_numpy(
+            1.0 + 1e-3 * rng.uniform(0, 1, int(B.val.numel()))).cuda() for B in row] for row in blocks]
+
+        def upd():
+            g.bgs_update_values(newvals)
+            return g.bgs_solve(b, x)
+        ms, info = timed_variant(upd)
+        variants["update_values"] = {"s_per_step": ms / 1e3, "update_s": info.t_setup_ms / 1e3,
+                                     "solve_s": info.t_solve_ms / 1e3, "iters": info.iters,
+                                     "converged": bool(info.converged),
+                                     "note": "bgs_update_values + solve on one handle (aggregation kept)"}
+        g.close()
+        del newvals
+
     # per-kernel-class timing inside a solve (CUDA events on the library stream)
     prof = prof_mx = None
     if not args.no_profile:
@@ -430,7 +481,7 @@ def gpu_arm(args, rank, world):
                            "l2": f"inputs larger than L2 (matrix {system.nnz * 12 / 1e9:.1f} GB)",
                            "generation_s": t_gen,
                            "graph": int(bgs.bgs_default_options(**extra).graph)},
-                "fp64": arm64, "mixed": armmx,
+                "fp64": arm64, "mixed": armmx, "variants": variants,
                 "mixed_speedup_vs_fp64": (ms64 / msmx) if msmx else None,
                 "spmv_full_fp64": {"GBps": spmv_gbs, "ms": statistics.median(spmv_ms), "bytes": spmv_bytes,
                                    "frac_of_measured_peak": spmv_gbs / peak,

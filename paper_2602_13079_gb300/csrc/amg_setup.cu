@@ -1176,7 +1176,6 @@ static void level_numeric(Hier &H, int l, const AmgParams &p, Scratch &sc, cudaS
                                                    dinvF.p, p.filter_diag);
     CK_LAUNCH();
     tr.mark("filter", l, AF.nnz);
-    build_sell(AF, kMaxPad, sc, s);
     const double lamF = power_lambda(AF, dinvF.p, p.power_iters, sc, s);
     const double omega = (4.0 / 3.0) / lamF;
     tr.mark("power(omega)", l, n);
@@ -1221,7 +1220,6 @@ static void smoothers_and_inverse(Hier &H, const AmgParams &p, Scratch &sc, cuda
         extract_diag(view(Lv.A), diag.p, s);
         if (Lv.dinv.n != (size_t)n) Lv.dinv.alloc((size_t)n, s);
         reciprocal(diag.p, Lv.dinv.p, n, s);
-        build_sell(Lv.A, kMaxPad, sc, s);
         const double lam = power_lambda(Lv.A, Lv.dinv.p, p.power_iters, sc, s);
         Lv.lmax = p.cheb_boost * lam;
         Lv.lmin = Lv.lmax / p.cheb_ratio;
@@ -1243,7 +1241,6 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
         const int n = H.L[l].A.n;
         if (n <= p.max_coarse || l + 1 >= std::min(p.max_levels, kMaxLevels)) break;
         DCsr &A = H.L[l].A;
-        build_sell(A, kMaxPad, sc, s);
         DBuf<double> diag((size_t)n, s);
         extract_diag(view(A), diag.p, s);
         DBuf<uint8_t> strong((size_t)std::max<int64_t>(A.nnz, 1), s);
