@@ -33,6 +33,7 @@ METRIC = "setup+solve sec to rtol 1e-8 at 10.5M DOFs, mixed vs FP64 on same GB30
 # the ncu captures named beside each; a variant without a capture reports null
 CHEB_FINE_TRAFFIC = {
     0: (264.757248e6, "profiles/k_sell_cheb_phi_s_128cubed.md"),
+    1: (275.506944e6, "profiles/k_spmv1_cheb_phi_s_128cubed.md"),
 }
 WORKLOAD = "C4"
 WORKLOAD = "C4"
@@ -55,6 +56,11 @@ def parse():
     p.add_argument("--arms", default="both", choices=["both", "fp64", "mixed"])
     p.add_argument("--graph", type=int, default=None, help="override the library default (CUDA graph sweep)")
     p.add_argument("--reorth-eta", type=float, default=None, help="override the re-orthogonalisation threshold")
+    p.add_argument("--theta-grid", default=None,
+                   help="comma-separated drop tolerances: solve the phi_s block alone by FGMRES(30) with one "
+                        "V-cycle per iteration for each, print one JSON line per value and exit")
+    p.add_argument("--sigma-means", default=None,
+                   help="anode,separator,cathode conductivity means for --theta-grid (default: the workload's)")
     p.add_argument("--profile-case", default=None, choices=["vcycle", "arnoldi", "spmv"],
                    help="run one small kernel case for an ncu capture and exit")
     return p.parse_args()
@@ -542,10 +548,55 @@ def profile_case(args):
         print("spmv case done", float(ys.norm()))
 
 
+def theta_grid(args):
+    """The drop-tolerance grid search of Sec. 3.1.4 on the phi_s block of the workload: for each
+    theta, set-up and FGMRES(30) solve to 1e-8 with one V-cycle per iteration (CUDA events), the
+    level sizes and the iteration count."""
+    import torch
+    import battery_system as bs
+    import paper_2602_13079_gb300 as bgs
+    from paper_2602_13079_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    sig = tuple(float(v) for v in args.sigma_means.split(",")) if args.sigma_means else None
+    system = bs.assemble(args.config, seed=args.seed, sigma_means=sig)
+    B = system.blocks[(0, 0)]
+
+    class _B:
+        pass
+    o = _B()
+    o.rowptr, o.col, o.val = B.rowptr, B.col, B.val
+    b = torch.from_numpy(system.b[:B.nrows].copy()).cuda()
+    for th in (float(t) for t in args.theta_grid.split(",")):
+        line = {"theta": th, "workload": workload_desc(args.config) + " phi_s block", "rows": B.nrows,
+                "sigma_means": list(sig) if sig else "workload"}
+        try:
+            times = []
+            for rep in range(3):
+                x = torch.zeros_like(b)
+                g = bgs.Solver([[o]], [B.nrows], [0], restart=30, theta=[th])
+                t0 = time.perf_counter()
+                g.setup()
+                info = g.bgs_solve(b, x, check=False)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+                levels = [g.bgs_level_info(0, l)["rows"] for l in range(g.bgs_num_levels(0))]
+                g.close()
+            line.update({"iters": info.iters, "converged": bool(info.converged), "setup_s": info.t_setup_ms / 1e3,
+                         "solve_s": info.t_solve_ms / 1e3, "setup_plus_solve_s": min(times[1:]),
+                         "levels": levels})
+        except bgs.BGSError as e:
+            line.update({"error": str(e)})
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.profile_case:
         profile_case(args)
+        return
+    if args.theta_grid:
+        theta_grid(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

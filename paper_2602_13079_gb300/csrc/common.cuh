@@ -99,7 +99,8 @@ struct DCsr {
     DBuf<float> vf;
     DBuf<__nv_bfloat16> vb;
     int lanes = 0;          // CSR SpMV threads per row chosen for this matrix
-    // SELL-32 copy (sell == true when built): slice offsets, columns (-1 pad), CSR index of each slot (-1 pad)
+    // SELL-32 copy (sell == true when built): slice offsets, columns (a padded slot repeats
+    // its slice's first stored column, with value 0), CSR index of each slot (-1 pad)
     bool sell = false;
     int64_t sell_nnz = 0;
     DBuf<int> sptr, sci, sperm;

@@ -69,24 +69,20 @@ __global__ void __launch_bounds__(256) k_sell(int n, const int *__restrict__ spt
     const VT *v = sv + s0 + lane;
     AT acc = (AT)0;
     int j = 0;
-    // padded slots hold column -1: they are skipped, so they read nothing from x (x may hold
-    // unwritten entries outside the columns the matrix references, e.g. the sweep output that a
-    // coupling block reads while later fields are still to be computed)
 #pragma unroll 1
     for (; j + 4 <= w; j += 4) {
         const int c0 = __ldg(c + 0 * 32), c1 = __ldg(c + 1 * 32), c2 = __ldg(c + 2 * 32), c3 = __ldg(c + 3 * 32);
         const AT a0 = Cvt<AT>::f(ldg(v + 0 * 32)), a1 = Cvt<AT>::f(ldg(v + 1 * 32));
         const AT a2 = Cvt<AT>::f(ldg(v + 2 * 32)), a3 = Cvt<AT>::f(ldg(v + 3 * 32));
-        if (c0 >= 0) acc += a0 * Cvt<AT>::f(ldg(x + c0));
-        if (c1 >= 0) acc += a1 * Cvt<AT>::f(ldg(x + c1));
-        if (c2 >= 0) acc += a2 * Cvt<AT>::f(ldg(x + c2));
-        if (c3 >= 0) acc += a3 * Cvt<AT>::f(ldg(x + c3));
+        acc += a0 * Cvt<AT>::f(ldg(x + c0));
+        acc += a1 * Cvt<AT>::f(ldg(x + c1));
+        acc += a2 * Cvt<AT>::f(ldg(x + c2));
+        acc += a3 * Cvt<AT>::f(ldg(x + c3));
         c += 4 * 32;
         v += 4 * 32;
     }
     for (; j < w; j++) {
-        const int cj = __ldg(c);
-        if (cj >= 0) acc += Cvt<AT>::f(ldg(v)) * Cvt<AT>::f(ldg(x + cj));
+        acc += Cvt<AT>::f(ldg(v)) * Cvt<AT>::f(ldg(x + __ldg(c)));
         c += 32;
         v += 32;
     }
@@ -307,6 +303,10 @@ __global__ void k_sell_width(int n, const int *rp, int *wslot) {
     if ((row & 31) == 0) wslot[slice] = w * 32;
 }
 
+// Padded slots get value 0 and the first stored column of their slice: a column the slice reads
+// anyway, so the padding never touches an entry of x outside the columns the matrix references
+// (x may hold unwritten entries there, e.g. the sweep output while later fields are still to be
+// computed, and 0 times such an entry need not be 0).
 __global__ void k_sell_fill(int n, const int *rp, const int *ci, const int *sptr, int *sci, int *sperm) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     const int slice = row >> 5;
@@ -315,13 +315,17 @@ __global__ void k_sell_fill(int n, const int *rp, const int *ci, const int *sptr
     const int s0 = sptr[slice];
     const int w = (sptr[slice + 1] - s0) >> 5;
     const int b = row < n ? rp[row] : 0, len = row < n ? rp[row + 1] - b : 0;
+    // the slice's first stored column (w > 0 means some row of the slice stores an entry)
+    const unsigned has = __ballot_sync(0xffffffffu, len > 0);
+    const int src = has ? __ffs(has) - 1 : 0;
+    const int pad = __shfl_sync(0xffffffffu, len > 0 ? ci[b] : 0, src);
     for (int j = 0; j < w; j++) {
         const int slot = s0 + j * 32 + lane;
         if (j < len) {
             sci[slot] = ci[b + j];
             sperm[slot] = b + j;
         } else {
-            sci[slot] = -1;   // padding: skipped by the kernels
+            sci[slot] = pad;
             sperm[slot] = -1;
         }
     }

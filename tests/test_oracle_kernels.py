@@ -410,3 +410,25 @@ def test_zero_filtered_rows_keep_the_tentative_prolongator():
     assert o.setup() == 0
     xs, info = o.solve(s.b[:s.ncells])
     assert info.converged
+
+
+def test_theta_grid_phi_s_always_solves():
+    """The drop-tolerance grid of Sec. 3.1.4 (theta = 0 ... 0.64, doubling) on a phi_s block: every
+    set-up succeeds with finite smoothing weights and FGMRES(30) with one V-cycle converges.  Large
+    theta drops every coupling on some levels; the stall retry and the zero-row rule keep the
+    hierarchy usable."""
+    s = bs.assemble(grid=bs.Grid(3, 14, 13, 12), seed=1)
+    B = s.blocks[(0, 0)]
+    A = oracle.CSR(B.rowptr, B.col, B.val, B.nrows, B.ncols)
+    iters = {}
+    for th in (0.0, 0.01, 0.02, 0.04, 0.08, 0.16, 0.32, 0.64):
+        opts = oracle.default_options(restart=30, max_coarse=60)
+        opts.theta[0] = th
+        o = oracle.BGS([[A]], [s.ncells], [0], opts)
+        assert o.setup() == 0, th
+        h = o.amg(0)
+        assert all(np.isfinite(h.omega(l)) for l in range(h.nlevels - 1)), th
+        x, info = o.solve(s.b[:s.ncells])
+        assert info.converged, th
+        iters[th] = info.iters
+    assert max(iters.values()) <= 3 * min(iters.values())
