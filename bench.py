@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--theta-grid", default=None,
                    help="comma-separated drop tolerances: solve the phi_s block alone by FGMRES(30) with one "
                         "V-cycle per iteration for each, print one JSON line per value and exit")
+    p.add_argument("--rtol", type=float, default=1e-8, help="relative tolerance for --theta-grid")
     p.add_argument("--sigma-means", default=None,
                    help="anode,separator,cathode conductivity means for --theta-grid (default: the workload's)")
     p.add_argument("--profile-case", default=None, choices=["vcycle", "arnoldi", "spmv"],
@@ -574,7 +575,7 @@ def theta_grid(args):
             times = []
             for rep in range(3):
                 x = torch.zeros_like(b)
-                g = bgs.Solver([[o]], [B.nrows], [0], restart=30, theta=[th])
+                g = bgs.Solver([[o]], [B.nrows], [0], restart=30, theta=[th], rtol=args.rtol)
                 t0 = time.perf_counter()
                 g.setup()
                 info = g.bgs_solve(b, x, check=False)
@@ -582,7 +583,8 @@ def theta_grid(args):
                 times.append(time.perf_counter() - t0)
                 levels = [g.bgs_level_info(0, l)["rows"] for l in range(g.bgs_num_levels(0))]
                 g.close()
-            line.update({"iters": info.iters, "converged": bool(info.converged), "setup_s": info.t_setup_ms / 1e3,
+            line.update({"rtol": args.rtol, "iters": info.iters, "converged": bool(info.converged),
+                         "rel_true_resid": info.rel_true_resid, "setup_s": info.t_setup_ms / 1e3,
                          "solve_s": info.t_solve_ms / 1e3, "setup_plus_solve_s": min(times[1:]),
                          "levels": levels})
         except bgs.BGSError as e:

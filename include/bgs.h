@@ -83,6 +83,19 @@ typedef struct {
                                per subdomain (Sec. 2.1, Eq. one-level-schwarz; the species solver of
                                Sec. 3.1.1) */
     int ilu_rows;           /* DD(0)-ILU(0) subdomain size in rows, 1..8192 (default 4096) */
+    int ngroups;            /* 0 (default): one flat sweep over the fields.  > 0: the nested variant
+                               (Sec. 2.2, Eq. hierarchical-bgs over groups of fields): group g is the
+                               order positions [group_end[g-1], group_end[g]) (group_end[ngroups-1] =
+                               nfields; a group's field ids must be consecutive); the preconditioner
+                               sweeps over the groups and solves each group's diagonal block by an inner
+                               FGMRES(inner_restart), preconditioned by the group's own sweep, to a
+                               relative residual inner_rtol or inner_maxit iterations.  The outer FGMRES
+                               uses restart (the paper's nested solver: restart 5, inner FGMRES(30) to
+                               1e-6, groups [phi_s, phi_e] and [p, c1, c2]).  No CUDA graph. */
+    int group_end[8];
+    int inner_restart;      /* 1..63 (default 30) */
+    int inner_maxit;        /* default 30 */
+    double inner_rtol;      /* default 1e-6 */
 } bgs_options;
 
 typedef struct {

@@ -41,7 +41,9 @@ class Options(C.Structure):
                 ("max_coarse", C.c_int), ("max_levels", C.c_int),
                 ("cheb_ratio", C.c_double), ("cheb_boost", C.c_double),
                 ("power_iters", C.c_int), ("filter_diag", C.c_int), ("jacobi", C.c_int),
-                ("subsolver", C.c_int * 8), ("ilu_rows", C.c_int)]
+                ("subsolver", C.c_int * 8), ("ilu_rows", C.c_int), ("ngroups", C.c_int),
+                ("group_end", C.c_int * 8), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
+                ("inner_rtol", C.c_double)]
 
 
 class Info(C.Structure):
@@ -305,7 +307,7 @@ def default_options(**kw) -> Options:
     o = Options()
     lib().or_default_options(C.byref(o))
     for k, v in kw.items():
-        if k in ("cheb_degree", "theta", "subsolver"):
+        if k in ("cheb_degree", "theta", "subsolver", "group_end"):
             arr = getattr(o, k)
             for i, x in enumerate(v):
                 arr[i] = x

@@ -907,6 +907,10 @@ void or_default_options(or_options *o) {
     o->power_iters = 10;
     o->filter_diag = 1;
     o->ilu_rows = 4096;
+    o->ngroups = 0;
+    o->inner_restart = 30;
+    o->inner_maxit = 30;
+    o->inner_rtol = 1e-6;
 }
 
 or_bgs *or_bgs_create(int F, const int *sizes, const int *const *rps, const int *const *cis,
@@ -1001,59 +1005,143 @@ void or_bgs_free(or_bgs *h) {
 
 void or_full_spmv(const or_bgs *h, const double *x, double *y) { or_spmv(h->full, x, y); }
 
-/* z = M^-1 v: for k in order, r_k = v_k - sum_{pos(j) < pos(k)} A_kj z_j, z_k = V-cycle_k(r_k).
- * With opt.jacobi the couplings are left out (block Jacobi, the alternative Secs. 3.2 and 4 discuss):
- * z_k = V-cycle_k(v_k). */
-void or_bgs_apply(const or_bgs *h, const double *v, double *z) {
+/* The solver of diagonal block k applied to r (z = V_k(r) or the DD(0)-ILU(0) sweep), or its
+ * transpose for the adjoint (V-cycle on the transposed level operators, same transfers, LU solved
+ * transposed; the transposed ILU sweep). */
+static void block_solve(const or_bgs *h, int k, const double *r, double *z, int transposed) {
+    if (h->ilu[k]) {
+        if (transposed) or_ilu_apply_transposed(h->ilu[k], r, z);
+        else or_ilu_apply(h->ilu[k], r, z);
+        return;
+    }
+    if (!transposed) {
+        or_vcycle(h->amg[k], r, z);
+        return;
+    }
+    const or_amg *g = h->amg[k];
+    or_csr *AT[OR_MAX_LEVELS] = {0};
+    for (int l = 0; l + 1 < g->nlevels; l++) AT[l] = or_transpose(g->A[l]);
+    vcycle_level(g, 0, r, z, 1, AT);
+    for (int l = 0; l + 1 < g->nlevels; l++) or_csr_free(AT[l]);
+}
+
+/* r_k -= A_kj z_j (or, transposed, r_k -= A_jk^T z_j); r and z indexed from the field starts */
+static void sub_coupling(const or_bgs *h, int k, int j, const double *zj, double *rk, int transposed) {
     int F = h->F;
-    for (int p = 0; p < F; p++) {
+    if (!transposed) {
+        or_csr *B = h->blk[k * F + j];
+        if (!B) return;
+        for (int i = 0; i < B->n; i++) {
+            double t = 0.0;
+            for (int e = B->rp[i]; e < B->rp[i + 1]; e++) t += B->v[e] * zj[B->ci[e]];
+            rk[i] -= t;
+        }
+    } else {
+        or_csr *B = h->blk[j * F + k]; /* A_jk, applied transposed */
+        if (!B) return;
+        for (int i = 0; i < B->n; i++)
+            for (int e = B->rp[i]; e < B->rp[i + 1]; e++) rk[B->ci[e]] -= B->v[e] * zj[i];
+    }
+}
+
+/* One sweep over the order positions [p0, p1) on vectors indexed from offset `base`: forward,
+ * r_k = v_k - sum over earlier positions of A_kj z_j, z_k = block solve (block Jacobi: no
+ * couplings); transposed, the reverse order with the transposed couplings of later positions. */
+static void sweep_range(const or_bgs *h, int p0, int p1, int base, const double *v, double *z, int transposed) {
+    for (int t = p0; t < p1; t++) {
+        int p = transposed ? p1 - 1 - (t - p0) : t;
         int k = h->order[p];
         int nk = h->sizes[k];
         double *r = (double *)malloc(sizeof(double) * (size_t)nk);
-        double *t = (double *)malloc(sizeof(double) * (size_t)nk);
-        for (int i = 0; i < nk; i++) r[i] = v[h->offs[k] + i];
-        for (int q = 0; q < p && !h->opt.jacobi; q++) {   /* block Jacobi: no couplings */
-            int j = h->order[q];
-            or_csr *B = h->blk[k * F + j];
-            if (!B) continue;
-            or_spmv(B, z + h->offs[j], t);
-            for (int i = 0; i < nk; i++) r[i] -= t[i];
+        for (int i = 0; i < nk; i++) r[i] = v[h->offs[k] - base + i];
+        if (!h->opt.jacobi) {
+            if (!transposed)
+                for (int q = p0; q < p; q++) sub_coupling(h, k, h->order[q], z + h->offs[h->order[q]] - base, r, 0);
+            else
+                for (int q = p + 1; q < p1; q++) sub_coupling(h, k, h->order[q], z + h->offs[h->order[q]] - base, r, 1);
         }
-        if (h->ilu[k]) or_ilu_apply(h->ilu[k], r, z + h->offs[k]);
-        else or_vcycle(h->amg[k], r, z + h->offs[k]);
+        block_solve(h, k, r, z + h->offs[k] - base, transposed);
         free(r);
-        free(t);
     }
+}
+
+/* Nested variant (Sec. 2.2: the block-triangular preconditioner over the groups of Eq.
+ * hierarchical-bgs, each group's diagonal block solved by an inner FGMRES, preconditioned by the
+ * group's own sweep, Eqs. non-voltage-bgs and voltage-bgs; Sec. 3.2 runs the outer FGMRES(5)).
+ * Group g is the order positions [group_end[g-1], group_end[g]); its fields have consecutive ids,
+ * so its vector is one contiguous slice. */
+typedef struct {
+    const or_bgs *h;
+    int p0, p1, base, n, transposed;
+} grp_ctx;
+
+static void amul_group(void *ctx, const double *in, double *out) {
+    const grp_ctx *c = (const grp_ctx *)ctx;
+    const or_bgs *h = c->h;
+    for (int i = 0; i < c->n; i++) out[i] = 0.0;
+    for (int p = c->p0; p < c->p1; p++) {
+        int k = h->order[p];
+        for (int q = c->p0; q < c->p1; q++) {
+            int j = h->order[q];
+            /* out_k += A_kj in_j  (transposed: out_k += A_jk^T in_j) */
+            double *ok = out + h->offs[k] - c->base;
+            const double *ij = in + h->offs[j] - c->base;
+            int nk = h->sizes[k];
+            double *t = (double *)calloc((size_t)nk, sizeof(double));
+            sub_coupling(h, k, j, ij, t, c->transposed);
+            for (int i = 0; i < nk; i++) ok[i] -= t[i];
+            free(t);
+        }
+    }
+}
+
+static void prec_group(void *ctx, const double *in, double *out) {
+    const grp_ctx *c = (const grp_ctx *)ctx;
+    sweep_range(c->h, c->p0, c->p1, c->base, in, out, c->transposed);
+}
+
+static void apply_nested(const or_bgs *h, const double *v, double *z, int transposed) {
+    int G = h->opt.ngroups, F = h->F;
+    for (int t = 0; t < G; t++) {
+        int g = transposed ? G - 1 - t : t;
+        int p0 = g ? h->opt.group_end[g - 1] : 0, p1 = h->opt.group_end[g];
+        int base = h->offs[h->order[p0]], n = 0;
+        for (int p = p0; p < p1; p++) {
+            if (h->offs[h->order[p]] < base) base = h->offs[h->order[p]];
+            n += h->sizes[h->order[p]];
+        }
+        double *r = (double *)malloc(sizeof(double) * (size_t)n);
+        for (int i = 0; i < n; i++) r[i] = v[base + i];
+        /* couplings to the groups already solved in this sweep */
+        for (int p = p0; p < p1; p++) {
+            int k = h->order[p];
+            double *rk = r + h->offs[k] - base;
+            if (!transposed)
+                for (int q = 0; q < p0; q++) sub_coupling(h, k, h->order[q], z + h->offs[h->order[q]], rk, 0);
+            else
+                for (int q = p1; q < F; q++) sub_coupling(h, k, h->order[q], z + h->offs[h->order[q]], rk, 1);
+        }
+        grp_ctx c = {h, p0, p1, base, n, transposed};
+        or_info info;
+        or_fgmres(n, amul_group, &c, prec_group, &c, r, z + base, h->opt.inner_restart, h->opt.inner_maxit,
+                  h->opt.inner_rtol, &info);
+        free(r);
+    }
+}
+
+/* z = M^-1 v: for k in order, r_k = v_k - sum_{pos(j) < pos(k)} A_kj z_j, z_k = V-cycle_k(r_k).
+ * With opt.jacobi the couplings are left out (block Jacobi, the alternative Secs. 3.2 and 4
+ * discuss): z_k = V-cycle_k(v_k).  With opt.ngroups > 0: the nested variant above. */
+void or_bgs_apply(const or_bgs *h, const double *v, double *z) {
+    if (h->opt.ngroups > 0) apply_nested(h, v, z, 0);
+    else sweep_range(h, 0, h->F, 0, v, z, 0);
 }
 
 /* Transposed preconditioner for A^T: reverse order, upper couplings transposed,
  * V-cycle on A_kk^T (level operators transposed, same transfers, LU solved transposed). */
 void or_bgs_apply_adjoint(const or_bgs *h, const double *v, double *z) {
-    int F = h->F;
-    for (int p = F - 1; p >= 0; p--) {
-        int k = h->order[p];
-        int nk = h->sizes[k];
-        double *r = (double *)malloc(sizeof(double) * (size_t)nk);
-        for (int i = 0; i < nk; i++) r[i] = v[h->offs[k] + i];
-        for (int q = p + 1; q < F && !h->opt.jacobi; q++) {
-            int j = h->order[q];
-            or_csr *B = h->blk[j * F + k]; /* A_jk, applied transposed: r_k -= A_jk^T z_j */
-            if (!B) continue;
-            for (int i = 0; i < B->n; i++)
-                for (int e = B->rp[i]; e < B->rp[i + 1]; e++) r[B->ci[e]] -= B->v[e] * z[h->offs[j] + i];
-        }
-        if (h->ilu[k]) {
-            or_ilu_apply_transposed(h->ilu[k], r, z + h->offs[k]);
-            free(r);
-            continue;
-        }
-        const or_amg *g = h->amg[k];
-        or_csr *AT[OR_MAX_LEVELS] = {0};
-        for (int l = 0; l + 1 < g->nlevels; l++) AT[l] = or_transpose(g->A[l]);
-        vcycle_level(g, 0, r, z + h->offs[k], 1, AT);
-        for (int l = 0; l + 1 < g->nlevels; l++) or_csr_free(AT[l]);
-        free(r);
-    }
+    if (h->opt.ngroups > 0) apply_nested(h, v, z, 1);
+    else sweep_range(h, 0, h->F, 0, v, z, 1);
 }
 
 /* ------------------------------------------------------------------------------------ */

@@ -46,6 +46,10 @@ typedef struct {
     int jacobi;             /* 1: block Jacobi (couplings left out of the sweep) */
     int subsolver[8];       /* per field id: 0 SA-AMG V-cycle, 1 DD(0)-ILU(0) */
     int ilu_rows;           /* DD(0)-ILU(0) subdomain size in rows */
+    int ngroups;            /* > 0: nested variant with groups [group_end[g-1], group_end[g]) of order positions */
+    int group_end[8];
+    int inner_restart, inner_maxit;
+    double inner_rtol;      /* inner FGMRES relative tolerance per group solve */
 } or_options;
 
 typedef struct {

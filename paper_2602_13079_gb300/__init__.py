@@ -29,7 +29,9 @@ class bgs_options(C.Structure):
                 ("theta", C.c_double * 8), ("max_coarse", C.c_int), ("max_levels", C.c_int),
                 ("cheb_ratio", C.c_double), ("cheb_boost", C.c_double), ("power_iters", C.c_int),
                 ("filter_diag", C.c_int), ("reorth_eta", C.c_double), ("jacobi", C.c_int),
-                ("subsolver", C.c_int * 8), ("ilu_rows", C.c_int)]
+                ("subsolver", C.c_int * 8), ("ilu_rows", C.c_int), ("ngroups", C.c_int),
+                ("group_end", C.c_int * 8), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
+                ("inner_rtol", C.c_double)]
 
 
 class bgs_info(C.Structure):
@@ -128,7 +130,7 @@ def bgs_default_options(**overrides) -> bgs_options:
     o = bgs_options()
     _check(lib().bgs_default_options(C.byref(o)), "bgs_default_options")
     for k, v in overrides.items():
-        if k in ("cheb_degree", "theta", "subsolver"):
+        if k in ("cheb_degree", "theta", "subsolver", "group_end"):
             arr = getattr(o, k)
             for i, x in enumerate(v):
                 arr[i] = x

@@ -1070,19 +1070,22 @@ __global__ void k_gj_unscramble(int n, const double *D, const int *tau, double *
     }
 }
 
-static int dense_inverse(const DCsr &Ac, DBuf<double> &W, Scratch &sc, cudaStream_t s) {
+// Enqueues the inverse of Ac into W (allocated by the caller) on stream s without waiting; a zero
+// pivot sets device flag slot 6 of sc (cleared here).
+static void dense_inverse_async(const DCsr &Ac, double *W, Scratch &sc, cudaStream_t s) {
     const int n = Ac.n;
-    W.alloc((size_t)n * n, s);
-    if (n == 0) return BGS_OK;
+    CK(cudaMemsetAsync(sc.flags.p + 6, 0, sizeof(int), s));
+    if (n == 0) return;
     DBuf<double> a((size_t)n * n, s), b((size_t)n * n, s);
-    const int g = grid_for((int64_t)n * n, GJ_T, kSMs * 2);
+    // about eight matrix entries per thread in each step: fewer blocks keep the pivot reduction
+    // at the start of every step short
+    const int g = grid_for((int64_t)n * n, GJ_T * 8, kSMs);
     DBuf<double> cv((size_t)2 * g, s);
     DBuf<int> cidx((size_t)2 * g, s), perm((size_t)n, s), tau((size_t)n, s);
     CK(cudaMemsetAsync(a.p, 0, sizeof(double) * (size_t)n * n, s));
     k_to_dense_rm<<<grid_for(n, 256), 256, 0, s>>>(n, Ac.rp.p, Ac.ci.p, Ac.v.p, a.p);
     CK_LAUNCH();
-    CK(cudaMemsetAsync(sc.flags.p + 6, 0, sizeof(int), s));
-    const int g0 = grid_for(n, GJ_T, kSMs);
+    const int g0 = std::min(g, grid_for(n, GJ_T, kSMs));
     k_gj_first<<<g0, GJ_T, 0, s>>>(n, a.p, cv.p, cidx.p);
     CK_LAUNCH();
     double *S = a.p, *D = b.p;
@@ -1097,11 +1100,9 @@ static int dense_inverse(const DCsr &Ac, DBuf<double> &W, Scratch &sc, cudaStrea
     }
     k_gj_tau<<<1, 1, 0, s>>>(n, perm.p, tau.p);
     CK_LAUNCH();
-    k_gj_unscramble<<<g, GJ_T, 0, s>>>(n, S, tau.p, W.p);
+    k_gj_unscramble<<<g, GJ_T, 0, s>>>(n, S, tau.p, W);
     CK_LAUNCH();
     CK(cudaMemcpyAsync(sc.h_flags + 6, sc.flags.p + 6, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    return sc.h_flags[6] ? BGS_ZERO_PIVOT : BGS_OK;
 }
 
 __global__ void k_dense_transpose(int n, const double *in, double *out) {
@@ -1211,8 +1212,16 @@ static void level_numeric(Hier &H, int l, const AmgParams &p, Scratch &sc, cudaS
     }
 }
 
-// Chebyshev bounds on every level above the coarsest and the coarsest dense inverse.
+// Chebyshev bounds on every level above the coarsest and the coarsest dense inverse; the inverse
+// runs on the scratch's side stream while the power iterations run on s.
 static void smoothers_and_inverse(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s, Trace &tr) {
+    H.nc = H.L.back().A.n;
+    if (H.nc > 16384) throw Error(BGS_INTERNAL, "coarsest level too large for the dense direct solve");
+    H.inv.alloc((size_t)H.nc * H.nc, s);
+    sc.ensure_side();
+    CK(cudaEventRecord(sc.fork, s));
+    CK(cudaStreamWaitEvent(sc.side, sc.fork, 0));
+    dense_inverse_async(H.L.back().A, H.inv.p, sc, sc.side);
     for (size_t k = 0; k + 1 < H.L.size(); k++) {
         Level &Lv = H.L[k];
         const int n = Lv.A.n;
@@ -1225,9 +1234,11 @@ static void smoothers_and_inverse(Hier &H, const AmgParams &p, Scratch &sc, cuda
         Lv.lmin = Lv.lmax / p.cheb_ratio;
         tr.mark("power(cheb)", (int)k, n);
     }
-    H.nc = H.L.back().A.n;
-    if (H.nc > 16384) throw Error(BGS_INTERNAL, "coarsest level too large for the dense direct solve");
-    H.status = dense_inverse(H.L.back().A, H.inv, sc, s);
+    CK(cudaStreamSynchronize(sc.side));
+    // the inverse is used on s from here on
+    CK(cudaEventRecord(sc.fork, sc.side));
+    CK(cudaStreamWaitEvent(s, sc.fork, 0));
+    H.status = sc.h_flags[6] ? BGS_ZERO_PIVOT : BGS_OK;
     tr.mark("dense LU+inverse", (int)H.L.size() - 1, H.nc);
 }
 

@@ -29,6 +29,34 @@ struct EventPair {
 
 }  // namespace
 
+// Workspace of one FGMRES instance: the outer solve, or one group's inner solve (nested variant).
+struct Krylov {
+    int64_t n = 0, ld = 0;   // vector length, basis leading dimension (n rounded up to 64 entries)
+    int m = 0;               // restart length
+    DBuf<double> V, Z, w, r, x, b, hdev;
+    void alloc(int64_t n_, int m_, cudaStream_t s) {
+        n = n_;
+        m = m_;
+        ld = (n + 63) / 64 * 64;
+        V.alloc((size_t)ld * (m + 1), s);
+        Z.alloc((size_t)ld * m, s);
+        w.alloc((size_t)n, s);
+        r.alloc((size_t)n, s);
+        x.alloc((size_t)n, s);
+        b.alloc((size_t)n, s);
+        hdev.alloc(256, s);
+    }
+};
+
+// One group of the nested variant: order positions [p0, p1), fields with consecutive ids, so the
+// group's vector is the slice [base, base + n) of a global vector.
+struct Group {
+    int p0 = 0, p1 = 0;
+    int64_t base = 0, n = 0;
+    DCsr A, AT;              // the group's diagonal block and its transpose, local columns
+    Krylov K;                // inner FGMRES workspace
+};
+
 struct bgs_ctx {
     cudaStream_t s = nullptr;
     int F = 0;
@@ -47,7 +75,12 @@ struct bgs_ctx {
     Scratch bsc[8];
     // block Jacobi: the V-cycles fork onto bs[k] from the solve stream and join back
     cudaEvent_t fork_ev = nullptr, join_ev[8] = {};
-    DBuf<double> V, Z, w, r, x, bvec, hdev;
+    Krylov K;                       // outer FGMRES workspace
+    // nested variant: groups, and per field the couplings of the outer sweep over groups (rows of
+    // field k, global columns of the earlier groups; adjoint: transposed couplings of the later
+    // groups) and of the inner sweep inside its group (local columns of the group)
+    std::vector<Group> groups;
+    DCsr go_lower[8], go_upperT[8], gi_lower[8], gi_upperT[8];
     double t_setup_ms = 0.0;
     int last_reorth = 0;
     // profiling
@@ -67,8 +100,6 @@ struct bgs_ctx {
 namespace {
 
 int64_t total_n(const bgs_ctx *h) { return h->offs[h->F]; }
-// leading dimension of the Krylov bases: n rounded up to 64 entries (512 bytes)
-int64_t basis_ld(int64_t n) { return (n + 63) / 64 * 64; }
 
 
 // ------------------------------------------------------------------ profiling helpers
@@ -287,11 +318,6 @@ void apply_prec(bgs_ctx *h, const double *v, double *z, bool transposed) {
     else sweep<double, double, double>(h, v, z, transposed);
 }
 
-void full_spmv(bgs_ctx *h, const double *x, double *y, bool transposed) {
-    const DCsr &A = transposed ? h->fullT : h->full;
-    Prof pf(h, 0, spmv_bytes(A, 8, 8, 0));
-    spmv_store<double, double>(A, x, y, h->s);
-}
 
 void drop_graphs(bgs_ctx *h) {
     for (int a = 0; a < 2; a++)
@@ -359,14 +385,16 @@ double host_dot(bgs_ctx *h, const double *a, const double *b, int64_t n) {
 }
 
 // ------------------------------------------------------------------ FGMRES(m)
-int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
+// Restarted right-preconditioned flexible GMRES on the workspace K: solves A x = K.b from x = 0
+// into K.x.  prec(v, z) applies z = M^-1 v; A is the FP64 operator (w = A z and the true residual
+// at every restart).  Gram-Schmidt as described at the selective re-orthogonalisation below.
+template <class Prec>
+int fgmres_run(bgs_ctx *h, Krylov &K, const DCsr &A, int m, int maxit, double rtol, Prec &&prec, bgs_info *info) {
     cudaStream_t s = h->s;
-    const int64_t n = total_n(h);
-    const int64_t ld = basis_ld(n);
-    const int m = h->opt.restart;
-    const double rtol = h->opt.rtol;
-    const int maxit = h->opt.maxit;
-    double *V = h->V.p, *Z = h->Z.p, *w = h->w.p, *r = h->r.p, *x = h->x.p, *b = h->bvec.p;
+    const int64_t n = K.n;
+    const int64_t ld = K.ld;
+    if (m > K.m) throw Error(BGS_INTERNAL, "restart longer than the Krylov workspace");
+    double *V = K.V.p, *Z = K.Z.p, *w = K.w.p, *r = K.r.p, *x = K.x.p, *b = K.b.p;
     bgs_info inf{};
     CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     const double bn2 = host_dot(h, b, b, n);
@@ -386,7 +414,7 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
     CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     double beta = bnorm, rel = 1.0, est = 1.0;
     int it = 0, status = BGS_NO_CONVERGENCE, restarts = 0, reorth = 0;
-    double *hd = h->hdev.p, *hh = h->sc.h_scal;
+    double *hd = K.hdev.p, *hh = h->sc.h_scal;
     for (;;) {
         scale_copy(r, 1.0 / beta, V, n, s);
         std::fill(g.begin(), g.end(), 0.0);
@@ -395,9 +423,11 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
         bool breakdown = false, nan = false;
         for (int j = 0; j < m; j++) {
             double *vj = V + (size_t)j * ld, *zj = Z + (size_t)j * ld;
-            if (h->opt.graph && !h->prof) apply_prec_graph(h, vj, zj, adjoint);
-            else apply_prec(h, vj, zj, adjoint);
-            full_spmv(h, zj, w, adjoint);
+            prec((const double *)vj, zj);
+            {
+                Prof pf(h, 0, spmv_bytes(A, 8, 8, 0));
+                spmv_store<double, double>(A, zj, w, s);
+            }
             // classical Gram-Schmidt; the second pass runs when ||w1|| < eta ||w|| (eta = 1: always,
             // i.e. CGS2; 1/sqrt(2): the Daniel-Gragg-Kaufman-Stewart test; 0: never)
             {
@@ -465,7 +495,6 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
             y[i] = t / Hm[(size_t)i * m + i];
         }
         multi_axpy(Z, ld, jend, y.data(), x, n, s);
-        const DCsr &A = adjoint ? h->fullT : h->full;
         spmv_resid<double, double>(A, b, x, r, s);
         beta = std::sqrt(host_dot(h, r, r, n));
         rel = beta / bnorm;
@@ -492,11 +521,175 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
     inf.status = status;
     inf.restarts = restarts;
     inf.reorth = reorth;
-    h->last_reorth = reorth;
+
     inf.rel_true_resid = rel;
     inf.rel_est_resid = est;
     if (info) *info = inf;
     return status;
+}
+
+void vstack(const std::vector<DCsr *> &parts, int ncols, DCsr &C, cudaStream_t s);
+
+// ------------------------------------------------------------------ nested variant
+// Sweep inside group G on group-local vectors (the inner FGMRES preconditioner): forward over the
+// group's positions with the couplings inside the group, or the transposed sweep in reverse.
+template <class VT, class XT, class CVT>
+void group_sweep(bgs_ctx *h, const Group &G, const double *v, double *z, bool transposed) {
+    cudaStream_t s = h->s;
+    for (int t = G.p0; t < G.p1; t++) {
+        const int p = transposed ? G.p1 - 1 - (t - G.p0) : t;
+        const int k = h->order[p];
+        Hier &H = h->H[k];
+        const int64_t nk = h->sizes[k], off = h->offs[k] - G.base;
+        XT *b0 = Buf<XT>::b(H.L[0]);
+        const DCsr &C = transposed ? h->gi_upperT[k] : h->gi_lower[k];
+        if (C.nnz > 0 && !h->opt.jacobi) {
+            Prof pf(h, 3, spmv_bytes(C, sizeof(CVT), 8, 1));
+            coupling_sub<CVT, XT>(C, v + off, z, b0, s);
+        } else {
+            copy_in<XT>(v + off, b0, nk, s);
+        }
+        XT *xk = block_solve<VT, XT>(h, H, transposed);
+        copy_out<XT>(xk, z + off, nk, s);
+    }
+}
+
+// Nested preconditioner (Sec. 2.2, Eq. hierarchical-bgs over the groups): for each group in order,
+// r_g = v_g minus the couplings to the groups already solved, then A_gg z_g = r_g by an inner
+// FGMRES(inner_restart) to inner_rtol (at most inner_maxit iterations) preconditioned by the
+// group's own sweep.  The adjoint runs the groups in reverse with transposed operators.
+void apply_nested(bgs_ctx *h, const double *v, double *z, bool adjoint) {
+    cudaStream_t s = h->s;
+    const int G = (int)h->groups.size();
+    const bool mixed = h->opt.precision == 1;
+    for (int t = 0; t < G; t++) {
+        Group &g = h->groups[adjoint ? G - 1 - t : t];
+        for (int p = g.p0; p < g.p1; p++) {
+            const int k = h->order[p];
+            double *rk = g.K.b.p + (h->offs[k] - g.base);
+            const DCsr &C = adjoint ? h->go_upperT[k] : h->go_lower[k];
+            if (C.nnz > 0 && !h->opt.jacobi) {
+                Prof pf(h, 3, spmv_bytes(C, 8, 8, 1));
+                coupling_sub<double, double>(C, v + h->offs[k], z, rk, s);
+            } else {
+                CK(cudaMemcpyAsync(rk, v + h->offs[k], sizeof(double) * (size_t)h->sizes[k],
+                                   cudaMemcpyDeviceToDevice, s));
+            }
+        }
+        fgmres_run(h, g.K, adjoint ? g.AT : g.A, h->opt.inner_restart, h->opt.inner_maxit, h->opt.inner_rtol,
+                   [&](const double *vi, double *zi) {
+                       if (mixed) group_sweep<float, float, __nv_bfloat16>(h, g, vi, zi, adjoint);
+                       else group_sweep<double, double, double>(h, g, vi, zi, adjoint);
+                   },
+                   nullptr);
+        CK(cudaMemcpyAsync(z + g.base, g.K.x.p, sizeof(double) * (size_t)g.n, cudaMemcpyDeviceToDevice, s));
+    }
+}
+
+// Rows of field k: the blocks (k, j) for the listed j, columns shifted by col_off(j); transposed:
+// the blocks (j, k) transposed.
+template <class Keep, class Off>
+void coupling_rows(bgs_ctx *h, int k, bool transposed, Keep &&keep, Off &&col_off, DCsr &out, bool bf16) {
+    cudaStream_t s = h->s;
+    std::vector<DCsr> tr;
+    tr.reserve(h->F);
+    std::vector<CsrView> parts;
+    std::vector<int> offs;
+    for (int j = 0; j < h->F; j++) {
+        if (!keep(j)) continue;
+        const DCsr &B = transposed ? h->blk[(size_t)j * h->F + k] : h->blk[(size_t)k * h->F + j];
+        if (B.nnz == 0) continue;
+        if (transposed) {
+            tr.emplace_back();
+            transpose_csr(view(B), tr.back(), h->sc, s);
+            parts.push_back(view(tr.back()));
+        } else {
+            parts.push_back(view(B));
+        }
+        offs.push_back((int)col_off(j));
+    }
+    out = DCsr();
+    concat_rows((int)h->sizes[k], (int)parts.size(), parts.data(), offs.data(), out, h->sc, s);
+    build_sell(out, kMaxPad, h->sc, s);
+    if (bf16 && out.nnz) {
+        out.vb.alloc((size_t)out.nnz, s);
+        convert_d2bf(out.v.p, out.vb.p, out.nnz, s);
+        sell_refresh(out, s);
+    }
+    CK(cudaStreamSynchronize(s));
+}
+
+void build_groups(bgs_ctx *h) {
+    h->groups.clear();
+    const int G = h->opt.ngroups;
+    if (G <= 0) return;
+    cudaStream_t s = h->s;
+    const bool mixed = h->opt.precision == 1;
+    std::vector<int> grp((size_t)h->F);
+    h->groups.resize((size_t)G);
+    for (int g = 0; g < G; g++) {
+        Group &gr = h->groups[g];
+        gr.p0 = g ? h->opt.group_end[g - 1] : 0;
+        gr.p1 = h->opt.group_end[g];
+        gr.base = INT64_MAX;
+        gr.n = 0;
+        for (int p = gr.p0; p < gr.p1; p++) {
+            const int k = h->order[p];
+            grp[k] = g;
+            gr.base = std::min(gr.base, h->offs[k]);
+            gr.n += h->sizes[k];
+        }
+    }
+    for (int g = 0; g < G; g++) {
+        Group &gr = h->groups[g];
+        // the group's diagonal block: its fields' rows in field-id (memory) order, local columns
+        std::vector<DCsr> rows((size_t)h->F);
+        std::vector<DCsr *> rb;
+        for (int k = 0; k < h->F; k++) {
+            if (grp[k] != g) continue;
+            coupling_rows(h, k, false, [&](int j) { return grp[j] == g; },
+                          [&](int j) { return h->offs[j] - gr.base; }, rows[k], false);
+            rb.push_back(&rows[k]);
+        }
+        vstack(rb, (int)gr.n, gr.A, s);
+        gr.A.m = (int)gr.n;
+        build_sell(gr.A, kMaxPad, h->sc, s);
+        transpose_csr(view(gr.A), gr.AT, h->sc, s);
+        build_sell(gr.AT, kMaxPad, h->sc, s);
+        gr.K.alloc(gr.n, h->opt.inner_restart, s);
+    }
+    for (int k = 0; k < h->F; k++) {
+        const int g = grp[k];
+        const Group &gr = h->groups[g];
+        const int pk = h->pos[k];
+        coupling_rows(h, k, false, [&](int j) { return grp[j] < g; }, [&](int j) { return h->offs[j]; },
+                      h->go_lower[k], false);
+        h->go_lower[k].m = (int)total_n(h);
+        coupling_rows(h, k, true, [&](int j) { return grp[j] > g; }, [&](int j) { return h->offs[j]; },
+                      h->go_upperT[k], false);
+        h->go_upperT[k].m = (int)total_n(h);
+        coupling_rows(h, k, false, [&](int j) { return grp[j] == g && h->pos[j] < pk; },
+                      [&](int j) { return h->offs[j] - gr.base; }, h->gi_lower[k], mixed);
+        h->gi_lower[k].m = (int)gr.n;
+        coupling_rows(h, k, true, [&](int j) { return grp[j] == g && h->pos[j] > pk; },
+                      [&](int j) { return h->offs[j] - gr.base; }, h->gi_upperT[k], mixed);
+        h->gi_upperT[k].m = (int)gr.n;
+    }
+    CK(cudaStreamSynchronize(s));
+}
+
+int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
+    const DCsr &A = adjoint ? h->fullT : h->full;
+    const bool nested = !h->groups.empty();
+    const int st = fgmres_run(h, h->K, A, h->opt.restart, h->opt.maxit, h->opt.rtol,
+                              [&](const double *v, double *z) {
+                                  if (nested) apply_nested(h, v, z, adjoint);
+                                  else if (h->opt.graph && !h->prof) apply_prec_graph(h, v, z, adjoint);
+                                  else apply_prec(h, v, z, adjoint);
+                              },
+                              info);
+    if (info) h->last_reorth = info->reorth;
+    return st;
 }
 
 // ------------------------------------------------------------------ helpers for create/setup
@@ -758,6 +951,11 @@ int bgs_default_options(bgs_options *o) {
     o->jacobi = 0;
     for (int k = 0; k < 8; k++) o->subsolver[k] = 0;
     o->ilu_rows = 4096;
+    o->ngroups = 0;
+    for (int k = 0; k < 8; k++) o->group_end[k] = 0;
+    o->inner_restart = 30;
+    o->inner_maxit = 30;
+    o->inner_rtol = 1e-6;
     return BGS_OK;
 }
 
@@ -803,6 +1001,24 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
             return BGS_INVALID_ARG;
     }
     if (tot >= INT32_MAX) return BGS_INVALID_ARG;
+    if (o.ngroups < 0 || o.ngroups > F) return BGS_INVALID_ARG;
+    if (o.ngroups > 0) {
+        if (o.inner_restart < 1 || o.inner_restart > 63 || o.inner_maxit < 1 || !(o.inner_rtol > 0))
+            return BGS_INVALID_ARG;
+        int prev = 0;
+        for (int g = 0; g < o.ngroups; g++) {
+            const int e = o.group_end[g];
+            if (e <= prev || e > F) return BGS_INVALID_ARG;
+            int lo = F, hi = -1;   // the group's field ids must be consecutive
+            for (int p = prev; p < e; p++) {
+                lo = std::min(lo, order[p]);
+                hi = std::max(hi, order[p]);
+            }
+            if (hi - lo + 1 != e - prev) return BGS_INVALID_ARG;
+            prev = e;
+        }
+        if (prev != F) return BGS_INVALID_ARG;
+    }
     for (int r = 0; r < F; r++)
         for (int c = 0; c < F; c++) {
             const bgs_csr &B = blocks[r * F + c];
@@ -937,15 +1153,8 @@ extern "C" int bgs_setup(bgs_handle h) {
             }
             autotune_spmv(h->full, 8, h->sc, s);
         }
-        const int64_t n = total_n(h);
-        const int m = h->opt.restart;
-        h->V.alloc((size_t)basis_ld(n) * (m + 1), s);
-        h->Z.alloc((size_t)basis_ld(n) * m, s);
-        h->w.alloc((size_t)n, s);
-        h->r.alloc((size_t)n, s);
-        h->x.alloc((size_t)n, s);
-        h->bvec.alloc((size_t)n, s);
-        h->hdev.alloc(256, s);
+        h->K.alloc(total_n(h), h->opt.restart, s);
+        build_groups(h);
         h->adjoint_ready = false;
         drop_graphs(h);
         CK(cudaStreamSynchronize(s));
@@ -1000,6 +1209,7 @@ extern "C" int bgs_update_values(bgs_handle h, const double *const *values) {
             CK(cudaStreamSynchronize(sk));
         });
         if (st) return st;
+        build_groups(h);
         h->adjoint_ready = false;
         drop_graphs(h);
         CK(cudaStreamSynchronize(s));
@@ -1018,10 +1228,10 @@ static int solve_common(bgs_handle h, const double *b, double *x, bgs_info *info
         CK(cudaStreamSynchronize(s));
         const double t0 = now_ms();
         for (auto &k : h->stats) k = KStats();
-        CK(cudaMemcpyAsync(h->bvec.p, b, sizeof(double) * n, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(h->K.b.p, b, sizeof(double) * n, cudaMemcpyDefault, s));
         bgs_info inf{};
         int st = fgmres(h, adjoint, &inf);
-        CK(cudaMemcpyAsync(x, h->x.p, sizeof(double) * n, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(x, h->K.x.p, sizeof(double) * n, cudaMemcpyDefault, s));
         CK(cudaStreamSynchronize(s));
         inf.t_solve_ms = now_ms() - t0;
         inf.t_setup_ms = h->t_setup_ms;

@@ -53,7 +53,18 @@ void Scratch::init(cudaStream_t s) {
     CK(cudaMallocHost((void **)&h_flags, 64 * sizeof(int)));
 }
 
+void Scratch::ensure_side() {
+    if (side) return;
+    CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+}
+
 Scratch::~Scratch() {
+    if (side) {
+        cudaStreamSynchronize(side);
+        cudaStreamDestroy(side);
+        cudaEventDestroy(fork);
+    }
     if (h_scal) cudaFreeHost(h_scal);
     if (h_flags) cudaFreeHost(h_flags);
 }

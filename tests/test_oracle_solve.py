@@ -178,3 +178,69 @@ def test_grad_values_is_minus_lambda_x_on_pattern():
         fd = (c @ np.linalg.solve(Ap, s.b) - c @ np.linalg.solve(Am, s.b)) / (2 * hstep)
         # relative 1e-5, plus the rounding floor of the dense solves (|L| eps / h)
         assert abs(fd - g[e]) <= 1e-5 * abs(fd) + 1e-13 * abs(c @ x) / hstep
+
+
+def group_lower_matrix(system, order, group_end):
+    """Dense matrix of the blocks the nested preconditioner inverts: whole diagonal groups and the
+    couplings from earlier groups to later ones."""
+    n = system.ncells
+    grp = {}
+    start = 0
+    for g, end in enumerate(group_end):
+        for p in range(start, end):
+            grp[order[p]] = g
+        start = end
+    M = np.zeros((system.ndof, system.ndof))
+    for (r, c), blk in system.blocks.items():
+        if grp[c] <= grp[r]:
+            M[r * n:(r + 1) * n, c * n:(c + 1) * n] = blk.to_dense()
+    return M
+
+
+@pytest.mark.parametrize("order,group_end", [(spec.WORKLOAD_ORDER, [2, 5]), (spec.PAPER_ORDER, [3, 5])],
+                         ids=["voltage-first", "paper-order"])
+def test_nested_with_exact_inner_solves_is_the_group_triangular_inverse(order, group_end):
+    """Nested variant (Sec. 2.2, Eq. hierarchical-bgs over the groups; inner FGMRES per group): with
+    the inner solves converged to 1e-13, M^-1 = (group-block lower triangle of A)^-1."""
+    s = small_system(bs.Grid(3, 5, 4, 4))
+    opts = oracle.default_options(max_coarse=20, ngroups=2, group_end=group_end, inner_rtol=1e-13,
+                                  inner_maxit=400, inner_restart=60)
+    o = oracle.bgs_for_system(s, order=list(order), opts=opts)
+    M = group_lower_matrix(s, list(order), group_end)
+    v = np.random.default_rng(6).standard_normal(s.ndof)
+    ref = np.linalg.solve(M, v)
+    assert np.linalg.norm(o.apply(v) - ref) <= 1e-9 * np.linalg.norm(ref)
+    refT = np.linalg.solve(M.T, v)
+    assert np.linalg.norm(o.apply_adjoint(v) - refT) <= 1e-9 * np.linalg.norm(refT)
+
+
+def test_nested_outer_converges_in_one_iteration_without_upper_group_couplings():
+    """The paper's observation for the nested solver (outer FGMRES in one iteration) holds exactly
+    when no coupling points from a later group to an earlier one and the inner solves are exact."""
+    s = small_system(bs.Grid(3, 4, 4, 4))
+    order = list(spec.WORKLOAD_ORDER)
+    grp = {0: 0, 1: 0, 2: 1, 3: 1, 4: 1}
+    blocks = [[s.blocks.get((r, c)) if grp[c] <= grp[r] else None for c in range(5)] for r in range(5)]
+    opts = oracle.default_options(max_coarse=10, ngroups=2, group_end=[2, 5], inner_rtol=1e-13,
+                                  inner_maxit=400, inner_restart=60, restart=5)
+    o = oracle.BGS(blocks, s.field_sizes, order, opts)
+    assert o.setup() == 0
+    x, info = o.solve(s.b)
+    assert info.converged and info.iters == 1
+
+
+def test_nested_solve_matches_flattened_solve():
+    s = small_system(bs.Grid(3, 8, 7, 6), seed=3)
+    order = list(spec.WORKLOAD_ORDER)
+    flat = oracle.bgs_for_system(s, order=order, opts=oracle.default_options(max_coarse=30))
+    nest = oracle.bgs_for_system(s, order=order, opts=oracle.default_options(
+        max_coarse=30, ngroups=2, group_end=[2, 5], restart=5))
+    xf, inf_ = flat.solve(s.b)
+    xn, inn = nest.solve(s.b)
+    assert inf_.converged and inn.converged
+    assert inn.iters < inf_.iters                     # each outer step holds inner solves
+    assert np.linalg.norm(xn - xf) <= 1e-6 * np.linalg.norm(xf)
+    assert np.linalg.norm(s.b - s.matvec(xn)) <= 1e-8 * np.linalg.norm(s.b)
+    lf, _ = flat.solve_adjoint(s.b)
+    ln, ia = nest.solve_adjoint(s.b)
+    assert ia.converged and np.linalg.norm(ln - lf) <= 1e-6 * np.linalg.norm(lf)
