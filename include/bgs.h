@@ -156,7 +156,8 @@ int bgs_solve_adjoint(bgs_handle h, const double *g, double *lambda, bgs_info *i
 int bgs_grad_values(bgs_handle h, int row_field, int col_field, const double *lambda, const double *x,
                     double *dvals);
 
-/* One application of the preconditioner z = M^-1 v (device pointers, full length). */
+/* One application of the preconditioner z = M^-1 v (device pointers, full length): the block sweep,
+ * or with ngroups > 0 the nested preconditioner (inner FGMRES solves per group). */
 int bgs_apply_preconditioner(bgs_handle h, const double *v, double *z);
 
 /* The block solver of field k applied to b: one V-cycle of its hierarchy from x = 0, x = V_k(b),

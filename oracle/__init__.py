@@ -43,7 +43,7 @@ class Options(C.Structure):
                 ("power_iters", C.c_int), ("filter_diag", C.c_int), ("jacobi", C.c_int),
                 ("subsolver", C.c_int * 8), ("ilu_rows", C.c_int), ("ngroups", C.c_int),
                 ("group_end", C.c_int * 8), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
-                ("inner_rtol", C.c_double)]
+                ("inner_rtol", C.c_double), ("cheb_ellipse", C.c_int)]
 
 
 class Info(C.Structure):
@@ -65,7 +65,7 @@ class _AMG(C.Structure):
                 ("strong", C.POINTER(C.c_uint8) * MAXL), ("nagg", C.c_int * MAXL),
                 ("mis_rounds", C.c_int * MAXL), ("omega", C.c_double * MAXL),
                 ("dinv", C.POINTER(C.c_double) * MAXL), ("lmax", C.c_double * MAXL),
-                ("lmin", C.c_double * MAXL), ("degree", C.c_int), ("nc", C.c_int),
+                ("lmin", C.c_double * MAXL), ("lim", C.c_double * MAXL), ("degree", C.c_int), ("nc", C.c_int),
                 ("lu", C.POINTER(C.c_double)), ("piv", C.POINTER(C.c_int)), ("status", C.c_int)]
 
 
@@ -113,6 +113,9 @@ def lib():
             L.or_smooth_prolongator.restype = P
             L.or_smooth_prolongator.argtypes = [P, f64p, i32p, C.c_int, C.c_double]
             L.or_chebyshev.argtypes = [P, f64p, C.c_double, C.c_double, C.c_int, f64p, f64p, C.c_int]
+            L.or_skew_radius.restype = C.c_double
+            L.or_skew_radius.argtypes = [P, C.c_int]
+            L.or_chebyshev_ellipse.argtypes = [P, f64p, C.c_double, C.c_double, C.c_int, f64p, f64p, C.c_int]
             L.or_lu_factor.restype = C.c_int
             L.or_lu_factor.argtypes = [C.c_int, f64p, i32p]
             L.or_lu_solve.argtypes = [C.c_int, f64p, i32p, f64p, f64p]
@@ -280,6 +283,19 @@ def chebyshev(A, dinv, lmin, lmax, deg, b, x0=None):
     return x
 
 
+def skew_radius(A, iters=10):
+    h = _Handle(A)                      # keep the C matrix alive across the call
+    return lib().or_skew_radius(h.p, int(iters))
+
+
+def chebyshev_ellipse(A, dinv, theta, c2, deg, b, x0=None):
+    h = _Handle(A)
+    x = np.zeros(A.nrows) if x0 is None else np.array(x0, dtype=np.float64)
+    lib().or_chebyshev_ellipse(h.p, np.ascontiguousarray(dinv, dtype=np.float64), float(theta), float(c2), int(deg),
+                               np.ascontiguousarray(b, dtype=np.float64), x, 1 if x0 is None else 0)
+    return x
+
+
 def lu_factor(a):
     n = a.shape[0]
     lu = np.ascontiguousarray(a, dtype=np.float64).copy()
@@ -422,6 +438,9 @@ class AMG:
 
     def cheb_bounds(self, l):
         return self.s.lmin[l], self.s.lmax[l]
+
+    def cheb_imag(self, l):
+        return self.s.lim[l]
 
     def sizes(self):
         return [self.s.A[l].contents.n for l in range(self.nlevels)]

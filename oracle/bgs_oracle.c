@@ -513,6 +513,105 @@ void or_chebyshev(const or_csr *A, const double *dinv, double lmin, double lmax,
 /* ------------------------------------------------------------------------------------ */
 /* Dense LU with partial pivoting (row-major, in place)                                  */
 /* ------------------------------------------------------------------------------------ */
+/* Radius of the skew-symmetric part of the diagonally scaled operator, rho(S) with
+ * S = (M - M^T)/2 and M = D^-1/2 A D^-1/2 (D = diag(A), all positive; else 0).  M is similar to
+ * D^-1 A, so by Bendixson's theorem every eigenvalue of D^-1 A has |Im| <= rho(S).  Power
+ * iteration on S^T S = -S S from the same hashed start as or_power_lambda; returns sqrt of the
+ * last estimate (0 for a symmetric A, where S = 0). */
+double or_skew_radius(const or_csr *A, int iters) {
+    int n = A->n;
+    double *sc = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; i++) {
+        double d = diag_of(A, i);
+        if (!(d > 0.0)) {
+            free(sc);
+            return 0.0;
+        }
+        sc[i] = 1.0 / sqrt(d);
+    }
+    or_csr *AT = or_transpose(A);
+    double *v = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *t = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *p = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *q = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *u = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double nv = 0.0;
+    for (int i = 0; i < n; i++) {
+        uint32_t h = or_fmix32((uint32_t)i ^ 0x7F4A7C15u) >> 8;
+        v[i] = ((double)h + 0.5) / 16777216.0;
+        nv += v[i] * v[i];
+    }
+    nv = sqrt(nv);
+    for (int i = 0; i < n; i++) v[i] = v[i] / nv;
+    double lam = 0.0;
+    for (int it = 0; it < iters; it++) {
+        /* u = S v, then w = -S u; S x = (s .* (A (s .* x)) - s .* (A^T (s .* x))) / 2 */
+        for (int pass = 0; pass < 2; pass++) {
+            const double *in = pass == 0 ? v : u;
+            for (int i = 0; i < n; i++) t[i] = sc[i] * in[i];
+            or_spmv(A, t, p);
+            or_spmv(AT, t, q);
+            double *out = pass == 0 ? u : t;
+            for (int i = 0; i < n; i++) out[i] = 0.5 * (sc[i] * p[i] - sc[i] * q[i]);
+        }
+        double s = 0.0;
+        for (int i = 0; i < n; i++) {
+            t[i] = -t[i];
+            s += t[i] * t[i];
+        }
+        lam = sqrt(s);
+        if (lam == 0.0) break;
+        for (int i = 0; i < n; i++) v[i] = t[i] / lam;
+    }
+    or_csr_free(AT);
+    free(sc);
+    free(v);
+    free(t);
+    free(p);
+    free(q);
+    free(u);
+    return sqrt(lam);
+}
+
+/* Chebyshev smoothing for a spectrum of D^-1 A inside the ellipse with centre theta on the real axis
+ * and focal parameter c2 = a^2 - b^2 (a real, b imaginary semi-axis; c2 < 0 when the ellipse is
+ * taller than wide), the nonsymmetric form of Sec. 2.2.1 (Manteuffel).  The iteration of
+ * or_chebyshev with tau_k = rho_k / delta, which keeps every coefficient real for any c2:
+ * tau_0 = 1/theta, d = tau_0 D^-1 r; tau_k = 1/(2 theta - c2 tau_{k-1}),
+ * d = c2 tau_k tau_{k-1} d + 2 tau_k D^-1 r, x += d.  The error is then multiplied by
+ * T_k((theta - z)/c)/T_k(theta/c) on each eigenvalue z. */
+void or_chebyshev_ellipse(const or_csr *A, const double *dinv, double theta, double c2, int deg,
+                          const double *b, double *x, int x_is_zero) {
+    int n = A->n;
+    if (deg <= 0) return;
+    double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *d = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double tau = 1.0 / theta;
+    if (x_is_zero) {
+        for (int i = 0; i < n; i++) r[i] = b[i];
+    } else {
+        or_spmv(A, x, r);
+        for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
+    }
+    for (int i = 0; i < n; i++) {
+        d[i] = tau * (dinv[i] * r[i]);
+        x[i] = (x_is_zero ? 0.0 : x[i]) + d[i];
+    }
+    for (int k = 1; k < deg; k++) {
+        double tau_new = 1.0 / (2.0 * theta - c2 * tau);
+        double c1 = c2 * tau_new * tau, cc = 2.0 * tau_new;
+        or_spmv(A, x, r);
+        for (int i = 0; i < n; i++) {
+            double ri = b[i] - r[i];
+            d[i] = c1 * d[i] + cc * (dinv[i] * ri);
+            x[i] = x[i] + d[i];
+        }
+        tau = tau_new;
+    }
+    free(r);
+    free(d);
+}
+
 int or_lu_factor(int n, double *a, int *piv) {
     for (int k = 0; k < n; k++) {
         int p = k;
@@ -646,6 +745,10 @@ static void smoothers_and_lu(or_amg *h, const or_options *opt) {
         double lam = or_power_lambda(A, h->dinv[k], opt->power_iters);
         h->lmax[k] = opt->cheb_boost * lam;
         h->lmin[k] = h->lmax[k] / opt->cheb_ratio;
+        h->lim[k] = opt->cheb_ellipse ? opt->cheb_boost * or_skew_radius(A, opt->power_iters) : 0.0;
+        /* below 1e-10 of lmax the skew part is rounding noise (e.g. a Galerkin product of a
+         * symmetric operator summed in two orders): keep the real interval */
+        if (h->lim[k] <= 1e-10 * h->lmax[k]) h->lim[k] = 0.0;
     }
     or_csr *Ac = h->A[h->nlevels - 1];
     int nc = Ac->n;
@@ -737,6 +840,17 @@ void or_amg_free(or_amg *h) {
     free(h);
 }
 
+/* the level's smoother: the real interval, or the ellipse when an imaginary extent was estimated
+ * (the transposed operator has the conjugate spectrum, so the same ellipse) */
+static void cheb_level(const or_amg *h, int l, const or_csr *A, const double *b, double *x, int x_is_zero) {
+    if (h->lim[l] > 0.0) {
+        double theta = (h->lmax[l] + h->lmin[l]) / 2.0, a = (h->lmax[l] - h->lmin[l]) / 2.0;
+        or_chebyshev_ellipse(A, h->dinv[l], theta, a * a - h->lim[l] * h->lim[l], h->degree, b, x, x_is_zero);
+    } else {
+        or_chebyshev(A, h->dinv[l], h->lmin[l], h->lmax[l], h->degree, b, x, x_is_zero);
+    }
+}
+
 static void vcycle_level(const or_amg *h, int l, const double *b, double *x, int transposed, or_csr **AT) {
     if (l == h->nlevels - 1) {
         if (transposed) lu_solve_transposed(h->nc, h->lu, h->piv, b, x);
@@ -745,7 +859,7 @@ static void vcycle_level(const or_amg *h, int l, const double *b, double *x, int
     }
     const or_csr *A = transposed ? AT[l] : h->A[l];
     int n = A->n, nc = h->A[l + 1]->n;
-    or_chebyshev(A, h->dinv[l], h->lmin[l], h->lmax[l], h->degree, b, x, 1);
+    cheb_level(h, l, A, b, x, 1);
     double *r = (double *)malloc(sizeof(double) * (size_t)n);
     or_spmv(A, x, r);
     for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
@@ -755,7 +869,7 @@ static void vcycle_level(const or_amg *h, int l, const double *b, double *x, int
     vcycle_level(h, l + 1, bc, xc, transposed, AT);
     or_spmv(h->P[l], xc, r);
     for (int i = 0; i < n; i++) x[i] += r[i];
-    or_chebyshev(A, h->dinv[l], h->lmin[l], h->lmax[l], h->degree, b, x, 0);
+    cheb_level(h, l, A, b, x, 0);
     free(r);
     free(bc);
     free(xc);

@@ -50,6 +50,7 @@ typedef struct {
     int group_end[8];
     int inner_restart, inner_maxit;
     double inner_rtol;      /* inner FGMRES relative tolerance per group solve */
+    int cheb_ellipse;       /* 1: Chebyshev on an ellipse with a Bendixson imaginary extent */
 } or_options;
 
 typedef struct {
@@ -72,6 +73,7 @@ typedef struct {
     double omega[OR_MAX_LEVELS];    /* prolongator damping */
     double *dinv[OR_MAX_LEVELS];    /* 1/diag(A_l) */
     double lmax[OR_MAX_LEVELS], lmin[OR_MAX_LEVELS];
+    double lim[OR_MAX_LEVELS];       /* imaginary semi-axis of the smoother's ellipse (0: interval) */
     int degree;
     int nc;                          /* coarsest size */
     double *lu;                      /* dense LU of the coarsest, row-major */
@@ -118,6 +120,9 @@ double or_power_lambda(const or_csr *A, const double *dinv, int iters);
 or_csr *or_smooth_prolongator(const or_csr *AF, const double *dinvF, const int *agg, int nagg, double omega);
 void or_chebyshev(const or_csr *A, const double *dinv, double lmin, double lmax, int deg,
                   const double *b, double *x, int x_is_zero);
+double or_skew_radius(const or_csr *A, int iters);
+void or_chebyshev_ellipse(const or_csr *A, const double *dinv, double theta, double c2, int deg,
+                          const double *b, double *x, int x_is_zero);
 int or_lu_factor(int n, double *a, int *piv);
 void or_lu_solve(int n, const double *lu, const int *piv, const double *b, double *x);
 

@@ -1263,7 +1263,8 @@ int bgs_apply_preconditioner(bgs_handle h, const double *v, double *z) {
     if (!h || !v || !z) return BGS_INVALID_ARG;
     if (!h->setup_done) return BGS_NOT_SETUP;
     return guarded([&]() -> int {
-        apply_prec(h, v, z, false);
+        if (!h->groups.empty()) apply_nested(h, v, z, false);
+        else apply_prec(h, v, z, false);
         CK(cudaStreamSynchronize(h->s));
         return BGS_OK;
     });

@@ -9,6 +9,7 @@ import pytest
 
 import battery_system as bs
 import oracle
+from battery_system import spec
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hash_vectors.txt")
 
@@ -432,3 +433,74 @@ def test_theta_grid_phi_s_always_solves():
         assert info.converged, th
         iters[th] = info.iters
     assert max(iters.values()) <= 3 * min(iters.values())
+
+
+def _cheb_T(k, w):
+    t0, t1 = np.ones_like(w), w
+    if k == 0:
+        return t0
+    for _ in range(k - 1):
+        t0, t1 = t1, 2 * w * t1 - t0
+    return t1
+
+
+def test_skew_radius_and_ellipse_chebyshev_closed_form():
+    """Nonsymmetric Chebyshev on an ellipse (Sec. 2.2.1, Manteuffel): on a normal matrix made of
+    2x2 rotation-scaling blocks [[a, -g], [g, a]] (eigenvalues of D^-1 A: 1 +- i g/a) the Bendixson
+    radius is max g/a exactly, and one smoother application from x = 0 multiplies each block's error
+    by |T_k((theta - z)/c) / T_k(theta/c)|, z = 1 + i g/a, for theta and c^2 = A^2 - B^2 of either
+    sign (an ellipse wider or taller than its real extent)."""
+    rng = np.random.default_rng(9)
+    m = 40
+    a = rng.uniform(1.0, 3.0, m)
+    t = np.sort(rng.uniform(0.05, 0.6, m))
+    t[-1] = 0.8                               # a separated largest rate: the power iteration converges
+    g = a * t
+    rp, ci, vals = [0], [], []
+    for j in range(m):
+        for r, row in ((0, [(0, a[j]), (1, -g[j])]), (1, [(0, g[j]), (1, a[j])])):
+            for c, v in row:
+                ci.append(2 * j + c)
+                vals.append(v)
+            rp.append(len(ci))
+    n = 2 * m
+    A = oracle.CSR(np.array(rp), np.array(ci), np.array(vals), n, n)
+    rad = oracle.skew_radius(A, 60)
+    assert abs(rad - t.max()) <= 1e-12 * t.max()
+    dinv = np.repeat(1.0 / a, 2)
+    xs = rng.standard_normal(n)
+    b = oracle.spmv(A, xs)
+    for theta, c2, deg in ((1.0, 0.3 ** 2 - 0.5 ** 2, 4), (1.1, 0.6 ** 2 - 0.2 ** 2, 3), (0.9, -0.04, 2)):
+        x = oracle.chebyshev_ellipse(A, dinv, theta, c2, deg, b)
+        e = (xs - x).reshape(m, 2)
+        c = np.sqrt(complex(c2))
+        z = 1.0 + 1j * t
+        fac = np.abs(_cheb_T(deg, (theta - z) / c) / _cheb_T(deg, theta / c + 0j))
+        assert np.allclose(np.linalg.norm(e, axis=1), fac * np.linalg.norm(xs.reshape(m, 2), axis=1),
+                           rtol=1e-10, atol=1e-14)
+    # a symmetric block: no imaginary extent, and the ellipse option leaves the hierarchy as it was
+    s = bs.assemble(grid=bs.Grid(3, 8, 7, 6), seed=2)
+    B = s.blocks[(spec.PRESS, spec.PRESS)]
+    Ap = oracle.CSR(B.rowptr, B.col, B.val, B.nrows, B.ncols)
+    assert np.array_equal(Ap.to_dense(), Ap.to_dense().T)
+    assert oracle.skew_radius(Ap) == 0.0
+
+
+def test_ellipse_smoother_on_advective_species_blocks():
+    """With the ellipse option the species blocks (upwind advection) get an imaginary extent on their
+    levels, the symmetric blocks keep theirs at 0, and the block sweep still solves."""
+    s = bs.assemble(grid=bs.Grid(3, 10, 9, 8), seed=4)
+    base = oracle.bgs_for_system(s, order=list(spec.WORKLOAD_ORDER), opts=oracle.default_options(max_coarse=40))
+    ell = oracle.bgs_for_system(s, order=list(spec.WORKLOAD_ORDER),
+                                opts=oracle.default_options(max_coarse=40, cheb_ellipse=1))
+    for k in (spec.C1, spec.C2):
+        h = ell.amg(k)
+        assert all(h.cheb_imag(l) > 0.0 for l in range(h.nlevels - 1))
+    h = ell.amg(spec.PRESS)
+    assert all(h.cheb_imag(l) == 0.0 for l in range(h.nlevels - 1))
+    v = np.random.default_rng(1).standard_normal(s.ncells)
+    assert np.array_equal(ell.amg(spec.PRESS).vcycle(v), base.amg(spec.PRESS).vcycle(v))
+    x, info = ell.solve(s.b)
+    assert info.converged and np.linalg.norm(s.b - s.matvec(x)) <= 1e-8 * np.linalg.norm(s.b)
+    lam, ia = ell.solve_adjoint(s.b)
+    assert ia.converged
