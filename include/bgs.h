@@ -96,6 +96,10 @@ typedef struct {
     int inner_restart;      /* 1..63 (default 30) */
     int inner_maxit;        /* default 30 */
     double inner_rtol;      /* default 1e-6 */
+    int cheb_ellipse;       /* 1: Chebyshev smoothing on an ellipse (the nonsymmetric form Sec. 2.2.1 cites):
+                               per level the real extent of the interval and an imaginary semi-axis
+                               boost * rho(S), S the skew part of D^-1/2 A D^-1/2 (Bendixson); a level
+                               whose radius is below 1e-10 lambda_max keeps the interval.  Default 0 */
 } bgs_options;
 
 typedef struct {
@@ -174,6 +178,8 @@ int bgs_level_info(bgs_handle h, int field, int level, int64_t *rows, int64_t *n
 /* which: 0 level operator A_l, 1 prolongator P_l, 2 restriction R_l.  rowptr/col/val: host
  * arrays sized by bgs_level_info (rows+1 / nnz / nnz; P_l has rows(l) rows and nagg columns). */
 int bgs_level_copy(bgs_handle h, int field, int level, int which, int32_t *rowptr, int32_t *col, double *val);
+/* Imaginary semi-axis of the smoother's ellipse on a level (0: the real interval). */
+int bgs_level_ellipse(bgs_handle h, int field, int level, double *imag);
 /* DD(0)-ILU(0) factors of a field whose subsolver is 1: the subdomain-restricted pattern of A_kk with
  * L (unit diagonal, strictly lower, not stored) and U in place.  *nnz receives the entry count; rowptr
  * (rows + 1), col and val (nnz each) are filled when not NULL (host or device).  BGS_INVALID_ARG for

@@ -31,7 +31,7 @@ class bgs_options(C.Structure):
                 ("filter_diag", C.c_int), ("reorth_eta", C.c_double), ("jacobi", C.c_int),
                 ("subsolver", C.c_int * 8), ("ilu_rows", C.c_int), ("ngroups", C.c_int),
                 ("group_end", C.c_int * 8), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
-                ("inner_rtol", C.c_double)]
+                ("inner_rtol", C.c_double), ("cheb_ellipse", C.c_int)]
 
 
 class bgs_info(C.Structure):
@@ -80,6 +80,7 @@ def lib():
             "bgs_level_aggregates": (i32, [vp, i32, i32, vp]),
             "bgs_level_format": (i32, [vp, i32, i32, i32, C.POINTER(C.c_int)]),
             "bgs_ilu_factors": (i32, [vp, i32, C.POINTER(C.c_int64), vp, vp, vp]),
+            "bgs_level_ellipse": (i32, [vp, i32, i32, C.POINTER(C.c_double)]),
             "bgs_set_profiling": (i32, [vp, i32]),
             "bgs_kernel_stats": (i32, [vp, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
             "bgs_csr_spmv": (i32, [i64, i64, vp, vp, vp, vp, vp, i32, vp]),
@@ -294,6 +295,11 @@ class Solver:
         agg = np.zeros(info["rows"], dtype=np.int32)
         _check(lib().bgs_level_aggregates(self.h, int(field), int(level), _ptr(agg)), "bgs_level_aggregates")
         return agg
+
+    def bgs_level_ellipse(self, field, level) -> float:
+        im = C.c_double()
+        _check(lib().bgs_level_ellipse(self.h, int(field), int(level), C.byref(im)), "bgs_level_ellipse")
+        return im.value
 
     def bgs_ilu_factors(self, field):
         """DD(0)-ILU(0) factors of a field on subsolver 1: (rowptr, col, val) host arrays."""

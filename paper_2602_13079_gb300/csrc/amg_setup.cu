@@ -1070,6 +1070,69 @@ __global__ void k_gj_unscramble(int n, const double *D, const int *tau, double *
     }
 }
 
+// Radius of the skew-symmetric part S = (M - M^T)/2 of M = D^-1/2 A D^-1/2 (D = diag(A), all
+// positive, else 0): a Bendixson bound on |Im| of the eigenvalues of D^-1 A.  Power iteration on
+// S^T S = -S S from the hashed start, CSR kernels fixed by the shape, no host round trip until the
+// end (a zero vector stays zero and gives 0, as for a symmetric A).
+__global__ void k_skew_scale(int n, const double *diag, double *sc, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double d = diag[i];
+        if (!(d > 0.0)) *bad = 1;
+        sc[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+    }
+}
+__global__ void k_vmul(int n, const double *a, const double *b, double *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a[i] * b[i];
+}
+__global__ void k_skew_out(int n, const double *sc, const double *p, const double *q, double *out, double sgn) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = sgn * (0.5 * (sc[i] * p[i] - sc[i] * q[i]));
+}
+__global__ void k_normalise_safe(int n, const double *in, const double *nrm2, double *out) {
+    const double d = sqrt(*nrm2);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = d > 0.0 ? in[i] / d : 0.0;
+}
+
+static double skew_radius(const DCsr &A, int iters, Scratch &sc, cudaStream_t s) {
+    const int n = A.n;
+    if (n <= 0) return 0.0;
+    const int g = grid_for(n, 256);
+    DBuf<double> diag((size_t)n, s), scl((size_t)n, s), v((size_t)n, s), u((size_t)n, s), t((size_t)n, s),
+        p((size_t)n, s), q((size_t)n, s);
+    extract_diag(view(A), diag.p, s);
+    CK(cudaMemsetAsync(sc.flags.p + 12, 0, sizeof(int), s));
+    k_skew_scale<<<g, 256, 0, s>>>(n, diag.p, scl.p, sc.flags.p + 12);
+    CK_LAUNCH();
+    DCsr AT;
+    transpose_csr(view(A), AT, sc, s);
+    const int la = choose_lanes(A.n, A.nnz);
+    double *nr = sc.scal.p + 18;
+    k_power_start<<<g, 256, 0, s>>>(n, v.p);
+    CK_LAUNCH();
+    dev_dot(v.p, v.p, n, nr, sc, s);
+    k_normalise_safe<<<g, 256, 0, s>>>(n, v.p, nr, v.p);
+    CK_LAUNCH();
+    for (int it = 0; it < iters; it++) {
+        for (int pass = 0; pass < 2; pass++) {
+            k_vmul<<<g, 256, 0, s>>>(n, scl.p, pass == 0 ? v.p : u.p, t.p);
+            CK_LAUNCH();
+            spmv_f64(view(A), la, t.p, p.p, s);
+            spmv_f64(view(AT), la, t.p, q.p, s);
+            k_skew_out<<<g, 256, 0, s>>>(n, scl.p, p.p, q.p, pass == 0 ? u.p : t.p, pass == 0 ? 1.0 : -1.0);
+            CK_LAUNCH();
+        }
+        dev_dot(t.p, t.p, n, nr, sc, s);
+        k_normalise_safe<<<g, 256, 0, s>>>(n, t.p, nr, v.p);
+        CK_LAUNCH();
+    }
+    CK(cudaMemcpyAsync(sc.h_scal + 2, nr, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(sc.h_flags + 12, sc.flags.p + 12, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (sc.h_flags[12]) return 0.0;
+    return std::sqrt(std::sqrt(sc.h_scal[2]));
+}
+
 // Enqueues the inverse of Ac into W (allocated by the caller) on stream s without waiting; a zero
 // pivot sets device flag slot 6 of sc (cleared here).
 static void dense_inverse_async(const DCsr &Ac, double *W, Scratch &sc, cudaStream_t s) {
@@ -1232,6 +1295,10 @@ static void smoothers_and_inverse(Hier &H, const AmgParams &p, Scratch &sc, cuda
         const double lam = power_lambda(Lv.A, Lv.dinv.p, p.power_iters, sc, s);
         Lv.lmax = p.cheb_boost * lam;
         Lv.lmin = Lv.lmax / p.cheb_ratio;
+        Lv.lim = p.cheb_ellipse ? p.cheb_boost * skew_radius(Lv.A, p.power_iters, sc, s) : 0.0;
+        // below 1e-10 of lmax the skew part is rounding noise (e.g. a Galerkin product of a
+        // symmetric operator summed in two orders): keep the real interval
+        if (Lv.lim <= 1e-10 * Lv.lmax) Lv.lim = 0.0;
         tr.mark("power(cheb)", (int)k, n);
     }
     CK(cudaStreamSynchronize(sc.side));

@@ -186,6 +186,24 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     const XT *dinv = Buf<XT>::dinv(Lv);
     const double theta = (Lv.lmax + Lv.lmin) / 2.0, delta = (Lv.lmax - Lv.lmin) / 2.0;
     const double sigma = theta / delta, inv_theta = 1.0 / theta;
+    // Chebyshev coefficients: the real interval (Saad's form), or the ellipse with imaginary
+    // semi-axis lim through its focal parameter c2 = delta^2 - lim^2 (tau_k = rho_k / delta form)
+    const bool ell = Lv.lim > 0.0;
+    const double c2e = delta * delta - Lv.lim * Lv.lim;
+    auto next = [&](double &st, double &c1, double &c2) {
+        if (ell) {
+            const double tn = 1.0 / (2.0 * theta - c2e * st);
+            c1 = c2e * tn * st;
+            c2 = 2.0 * tn;
+            st = tn;
+        } else {
+            const double rn = 1.0 / (2.0 * sigma - st);
+            c1 = rn * st;
+            c2 = 2.0 * rn / delta;
+            st = rn;
+        }
+    };
+    const double st0 = ell ? inv_theta : 1.0 / sigma;
     const int deg = H.degree;
     const int vb = sizeof(VT), xb = sizeof(XT);
     const double cbytes = spmv_bytes(A, vb, xb, 4);
@@ -193,13 +211,12 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     // pre-smoothing from x = 0
     cheb_first<XT>(n, b, dinv, inv_theta, x0, d, s);
     XT *cur = x0, *oth = x1;
-    double rho = 1.0 / sigma;
+    double st = st0, c1 = 0.0, c2 = 0.0;
     for (int k = 1; k < deg; k++) {
-        const double rn = 1.0 / (2.0 * sigma - rho);
+        next(st, c1, c2);
         Prof pf(h, ccls, cbytes);
-        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, rn * rho, 2.0 * rn / delta, false, s);
+        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, c1, c2, false, s);
         std::swap(cur, oth);
-        rho = rn;
     }
     // residual, restriction, coarse correction, prolongation
     spmv_resid<VT, XT>(A, b, cur, r, s);
@@ -208,18 +225,17 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     XT *xc = vcycle<VT, XT>(h, H, l + 1, transposed);
     spmv_addto<VT, XT>(Lv.P, xc, cur, s);
     // post-smoothing
-    rho = 1.0 / sigma;
+    st = st0;
     {
         Prof pf(h, ccls, cbytes);
         cheb_step<VT, XT>(A, b, dinv, cur, oth, d, 0.0, inv_theta, true, s);
     }
     std::swap(cur, oth);
     for (int k = 1; k < deg; k++) {
-        const double rn = 1.0 / (2.0 * sigma - rho);
+        next(st, c1, c2);
         Prof pf(h, ccls, cbytes);
-        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, rn * rho, 2.0 * rn / delta, false, s);
+        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, c1, c2, false, s);
         std::swap(cur, oth);
-        rho = rn;
     }
     return cur;
 }
@@ -842,7 +858,8 @@ void build_adjoint(bgs_ctx *h) {
 
 AmgParams params_for(const bgs_ctx *h, int k) {
     return AmgParams{h->opt.theta[k], h->opt.cheb_degree[k], h->opt.max_coarse, h->opt.max_levels,
-                     h->opt.power_iters, h->opt.filter_diag, h->opt.cheb_ratio, h->opt.cheb_boost};
+                     h->opt.power_iters, h->opt.filter_diag, h->opt.cheb_ratio, h->opt.cheb_boost,
+                     h->opt.cheb_ellipse};
 }
 
 // Runs fn(k, stream, scratch) for every diagonal block: the hierarchies are independent, so
@@ -956,6 +973,7 @@ int bgs_default_options(bgs_options *o) {
     o->inner_restart = 30;
     o->inner_maxit = 30;
     o->inner_rtol = 1e-6;
+    o->cheb_ellipse = 0;
     return BGS_OK;
 }
 
@@ -985,7 +1003,8 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
     if (o.restart < 1 || o.restart > 63 || o.maxit < 1 || !(o.rtol > 0) || o.max_coarse < 1 || o.max_levels < 1 ||
         o.max_levels > kMaxLevels ||
         o.precision < 0 || o.precision > 1 || o.power_iters < 1 || !(o.cheb_ratio > 1.0) || !(o.cheb_boost > 0) ||
-        !(o.reorth_eta >= 0.0) || o.jacobi < 0 || o.jacobi > 1 || o.ilu_rows < 1 || o.ilu_rows > kIluMaxRows)
+        !(o.reorth_eta >= 0.0) || o.jacobi < 0 || o.jacobi > 1 || o.ilu_rows < 1 || o.ilu_rows > kIluMaxRows ||
+        o.cheb_ellipse < 0 || o.cheb_ellipse > 1)
         return BGS_INVALID_ARG;
     // host-side shape checks
     int seen[8] = {};
@@ -1340,6 +1359,15 @@ int bgs_level_copy(bgs_handle h, int field, int level, int which, int32_t *rowpt
         CK(cudaStreamSynchronize(s));
         return BGS_OK;
     });
+}
+
+int bgs_level_ellipse(bgs_handle h, int field, int level, double *imag) {
+    if (!h || field < 0 || field >= h->F || !imag) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    const Hier &H = h->H[field];
+    if (level < 0 || level >= (int)H.L.size()) return BGS_INVALID_ARG;
+    *imag = H.L[level].lim;
+    return BGS_OK;
 }
 
 int bgs_ilu_factors(bgs_handle h, int field, int64_t *nnz, int32_t *rowptr, int32_t *col, double *val) {

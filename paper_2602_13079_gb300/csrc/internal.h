@@ -127,6 +127,7 @@ struct Level {
     DBuf<double> dinv;
     DBuf<float> dinvf;
     double lmin = 0.0, lmax = 0.0;
+    double lim = 0.0;       // imaginary semi-axis of the smoother's ellipse (0: the real interval)
     // V-cycle work vectors (FP64 or FP32 by precision)
     DBuf<double> b, x0, x1, d, r;
     DBuf<float> fb, fx0, fx1, fd, fr;
@@ -159,6 +160,7 @@ struct AmgParams {
     double theta;
     int degree, max_coarse, max_levels, power_iters, filter_diag;
     double cheb_ratio, cheb_boost;
+    int cheb_ellipse;
 };
 
 constexpr int kMaxLevels = 16;

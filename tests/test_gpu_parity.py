@@ -200,6 +200,32 @@ def test_sweep_ignores_unwritten_output_entries(bgs, precision):
     assert bool(torch.isfinite(zn).all()) and torch.equal(z0, zn)
 
 
+def test_ellipse_smoother_parity(bgs):
+    """Chebyshev on an ellipse (cheb_ellipse = 1): the imaginary semi-axis of every level against the
+    oracle's Bendixson estimate, the V-cycles of all blocks, and the solve."""
+    system = bs.assemble(grid=bs.Grid(3, 17, 13, 11), seed=2)
+    g, o = make_pair(bgs, system, max_coarse=60, cheb_ellipse=1)
+    rng = np.random.default_rng(12)
+    for k in range(5):
+        oa = o.amg(k)
+        for l in range(oa.nlevels - 1):
+            ref = oa.cheb_imag(l)
+            got = g.bgs_level_ellipse(k, l)
+            assert (ref == 0.0) == (got == 0.0), (k, l, ref, got)
+            assert abs(got - ref) <= 1e-10 * max(ref, 1e-300), (k, l, ref, got)
+        b = rng.standard_normal(system.ncells)
+        x = torch.zeros(system.ncells, dtype=torch.float64, device="cuda")
+        g.bgs_apply_vcycle(k, dev(b), x)
+        ref = oa.vcycle(b)
+        assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref), k
+    assert any(o.amg(k).cheb_imag(0) > 0 for k in (spec.C1, spec.C2))
+    xr, ir = o.solve(system.b)
+    x = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+    info = g.bgs_solve(dev(system.b), x)
+    assert info.converged and ir.converged
+    assert np.linalg.norm(x.cpu().numpy() - xr) <= 1e-6 * np.linalg.norm(xr)
+
+
 # ------------------------------------------------------------------------------------- solve
 @pytest.mark.parametrize("order", [spec.WORKLOAD_ORDER, spec.PAPER_ORDER], ids=["workload", "paper"])
 @pytest.mark.parametrize("precision", [0, 1])
