@@ -422,11 +422,11 @@ static double power_lambda(const DCsr &A, const double *dinv, int iters, Scratch
     DBuf<double> v((size_t)n, s), w((size_t)n, s);
     k_power_start<<<grid_for(n, 256), 256, 0, s>>>(n, v.p);
     CK_LAUNCH();
-    double *nv = sc.scal.p + 16, *nw = sc.scal.p + 17;
-    dev_dot(v.p, v.p, n, nv, sc, s);
+    double *nv = sc.scal.p + 20, *nw = sc.scal.p + 22;   // (||.||^2, 1/||.||) pairs
+    dev_dot_rsqrt(v.p, v.p, n, nv, sc, s);
     for (int it = 0; it < iters; it++) {
-        spmv_scaled_norm(A, dinv, v.p, nv, w.p, s);   // w = D^-1 A (v / ||v||)
-        dev_dot(w.p, w.p, n, nw, sc, s);
+        spmv_scaled_norm(A, dinv, v.p, nv + 1, w.p, s);   // w = D^-1 A (v / ||v||)
+        dev_dot_rsqrt(w.p, w.p, n, nw, sc, s);
         std::swap(v.p, w.p);
         std::swap(nv, nw);
     }

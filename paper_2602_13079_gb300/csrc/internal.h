@@ -38,6 +38,8 @@ void release_cached_memory();
 int64_t scan_exclusive(const int *in, int *out, int64_t n, Scratch &sc, cudaStream_t s);
 // sum of squares / dot products into a device scalar (deterministic two-pass reduction).
 void dev_dot(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s);
+// the same, and out[1] = 1/sqrt(out[0]) (0 when out[0] is 0)
+void dev_dot_rsqrt(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s);
 void dev_fill_int(int *p, int value, int64_t n, cudaStream_t s);
 void dev_fill_double(double *p, double value, int64_t n, cudaStream_t s);
 // Validation of one CSR (device arrays); returns 0 or BGS_INVALID_ARG.  Checks monotone rowptr,
@@ -79,9 +81,9 @@ template <class VT, class XT>
 void coupling_sub(const DCsr &L, const double *v, const double *z, XT *r, cudaStream_t s);
 // w_i = dinv_i * (A v)_i (FP64, power iteration)
 void spmv_scaled(const CsrView &A, const double *dinv, const double *v, double *w, cudaStream_t s);
-// w_i = dinv_i * (A v)_i / sqrt(*nrm2)  (power iteration step on a normalised v; CSR with a lane
-// count fixed by the shape, whatever format the operator is stored in)
-void spmv_scaled_norm(const DCsr &A, const double *dinv, const double *v, const double *nrm2, double *w,
+// w_i = dinv_i * (A v)_i * (*rnorm), rnorm = 1/||v|| on the device (power iteration step on a
+// normalised v; CSR with a lane count fixed by the shape, whatever format the operator is stored in)
+void spmv_scaled_norm(const DCsr &A, const double *dinv, const double *v, const double *rnorm, double *w,
                       cudaStream_t s);
 // y = W x, W dense row-major n x n in FP64
 template <class XT>

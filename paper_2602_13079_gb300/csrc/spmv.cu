@@ -121,11 +121,11 @@ struct EScale {
     double *w;
     __device__ void operator()(int i, double s) const { w[i] = dinv[i] * s; }
 };
-struct EScaleNorm {   // w = dinv (A v) / ||v||, ||v||^2 read from device memory
+struct EScaleNorm {   // w = dinv (A v) / ||v||, 1/||v|| read from device memory
     const double *dinv;
-    const double *nrm2;
+    const double *rnorm;
     double *w;
-    __device__ void operator()(int i, double s) const { w[i] = dinv[i] * (s / sqrt(*nrm2)); }
+    __device__ void operator()(int i, double s) const { w[i] = dinv[i] * (s * *rnorm); }
 };
 template <class XT, class CT>
 struct ECheb {   // r = b - A x_in ; d = c1 d + c2 (dinv r) ; x_out = x_in + d
@@ -224,13 +224,13 @@ void spmv_scaled(const CsrView &A, const double *dinv, const double *v, double *
     launch_csr<double, double, double>(choose_lanes(A.n, A.nnz), A.n, A.rp, A.ci, A.v, v, EScale{dinv, w}, s);
 }
 
-void spmv_scaled_norm(const DCsr &A, const double *dinv, const double *v, const double *nrm2, double *w,
+void spmv_scaled_norm(const DCsr &A, const double *dinv, const double *v, const double *rnorm, double *w,
                       cudaStream_t s) {
     // a kernel fixed by the shape alone (not by the autotuned format), so that a set-up and a later
     // numeric re-set-up sum in the same order: one thread per row for short rows, else L lanes
     const double avg = A.n > 0 ? (double)A.nnz / (double)A.n : 0.0;
-    const int lanes = avg <= 12.0 ? 1 : choose_lanes(A.n, A.nnz);
-    launch_csr<double, double, double>(lanes, A.n, A.rp.p, A.ci.p, A.v.p, v, EScaleNorm{dinv, nrm2, w}, s);
+    const int lanes = avg <= 12.0 ? 1 : (avg <= 64.0 ? 4 : 8);
+    launch_csr<double, double, double>(lanes, A.n, A.rp.p, A.ci.p, A.v.p, v, EScaleNorm{dinv, rnorm, w}, s);
 }
 
 template <class VT, class XT>

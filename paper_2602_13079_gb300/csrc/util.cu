@@ -217,6 +217,24 @@ __global__ void k_reduce_final(const double *part, int g, double *out) {
     if (threadIdx.x == 0) *out = t;
 }
 
+__global__ void k_reduce_final_rsqrt(const double *part, int g, double *out) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < g; i += blockDim.x) acc += part[i];
+    double t = block_sum(acc);
+    if (threadIdx.x == 0) {
+        out[0] = t;
+        out[1] = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+    }
+}
+
+void dev_dot_rsqrt(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s) {
+    int g = grid_for(n, 256, kSMs * 4);
+    k_dot_partial<<<g, 256, 0, s>>>(a, b, n, sc.partial.p);
+    CK_LAUNCH();
+    k_reduce_final_rsqrt<<<1, 256, 0, s>>>(sc.partial.p, g, out);
+    CK_LAUNCH();
+}
+
 void dev_dot(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s) {
     int g = grid_for(n, 256, kSMs * 4);
     k_dot_partial<<<g, 256, 0, s>>>(a, b, n, sc.partial.p);
