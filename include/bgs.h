@@ -214,8 +214,8 @@ int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int6
 
 /* bgs_arnoldi_dots without any device allocation (the paper has no counterpart: this is a
  * library convenience).  For callers that cannot allocate device memory when they need the dots:
- * work inside a captured or frozen execution context, memory fully pre-reserved by the caller's
- * own pool, or hosts that forbid allocation after start-up.  Same arguments, results and limits
+ * applications whose device memory is fully pre-reserved by their own pool manager, and embedded or
+ * real-time hosts that forbid allocation after start-up.  Same arguments, results and limits
  * as bgs_arnoldi_dots (1 <= cnt <= 64, ld even and >= n; anything else returns BGS_INVALID_ARG).
  * The partial sums go to one fixed array of 248,064 bytes inside the library's device image,
  * held by every GPU that loads the library until the process exits.  The first call on each

@@ -1,9 +1,8 @@
 // Arnoldi block dot products for callers that must not allocate device memory.
 //
 // Some callers cannot call cudaMalloc (or any allocating routine) at the point where they need
-// this operation: code running inside a captured or frozen execution context, applications
-// whose device memory is fully pre-reserved by their own pool, or embedded/real-time hosts that
-// forbid allocation after start-up.  bgs_arnoldi_dots() allocates its per-block partial-sum
+// this operation: applications whose device memory is fully pre-reserved by their own pool
+// manager, or embedded/real-time hosts that forbid allocation after start-up.  bgs_arnoldi_dots() allocates its per-block partial-sum
 // scratch on every call; bgs_arnoldi_dots_noalloc() below instead uses one fixed scratch array
 // that lives in this library's device image, so a call allocates nothing.
 #include <mutex>
@@ -17,7 +16,7 @@ namespace {
 // library holds this array until the process exits.
 constexpr size_t kNoAllocPartials = 4 * 456 * 17;
 
-__device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
 
 std::mutex g_noalloc_mu;
 double *g_noalloc_ptr[128] = {};   // device address of the array, per device ordinal
