@@ -81,7 +81,9 @@ typedef struct {
                                SA-AMG V-cycle; 1 DD(0)-ILU(0), i.e. restricted additive Schwarz without
                                overlap over subdomains of ilu_rows consecutive rows, one ILU(0) sweep
                                per subdomain (Sec. 2.1, Eq. one-level-schwarz; the species solver of
-                               Sec. 3.1.1) */
+                               Sec. 3.1.1); 2 the diagonal solve z = diag(A_kk)^-1 r, exact for a
+                               diagonal block such as the solid species A_s that Sec. 2.2 inverts
+                               directly (one Jacobi step for any other block) */
     int ilu_rows;           /* DD(0)-ILU(0) subdomain size in rows, 1..8192 (default 4096) */
     int ngroups;            /* 0 (default): one flat sweep over the fields.  > 0: the nested variant
                                (Sec. 2.2, Eq. hierarchical-bgs over groups of fields): group g is the

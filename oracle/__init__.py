@@ -76,7 +76,8 @@ class _ILU(C.Structure):
 class _BGS(C.Structure):
     _fields_ = [("F", C.c_int), ("sizes", C.c_int * 8), ("offs", C.c_int * 9), ("order", C.c_int * 8),
                 ("pos", C.c_int * 8), ("blk", C.POINTER(_CSR) * 64), ("full", C.POINTER(_CSR)),
-                ("amg", C.POINTER(_AMG) * 8), ("ilu", C.POINTER(_ILU) * 8), ("opt", Options),
+                ("amg", C.POINTER(_AMG) * 8), ("ilu", C.POINTER(_ILU) * 8),
+                ("dgs", C.POINTER(C.c_double) * 8), ("opt", Options),
                 ("status", C.c_int)]
 
 

@@ -1072,6 +1072,16 @@ or_bgs *or_bgs_create(int F, const int *sizes, const int *const *rps, const int 
 int or_bgs_setup(or_bgs *h) {
     for (int k = 0; k < h->F; k++) {
         or_csr *Akk = h->blk[k * h->F + k];
+        if (h->opt.subsolver[k] == 2) {   /* the block's diagonal: exact for a diagonal block */
+            int nk = h->sizes[k];
+            h->dgs[k] = (double *)malloc(sizeof(double) * (size_t)(nk > 0 ? nk : 1));
+            for (int i = 0; i < nk; i++) {
+                double d = diag_of(Akk, i);
+                if (d == 0.0) h->status = ST_ZEROPIV;
+                h->dgs[k][i] = 1.0 / d;
+            }
+            continue;
+        }
         if (h->opt.subsolver[k] == 1) {   /* DD(0)-ILU(0) */
             h->ilu[k] = or_ilu_setup(Akk, h->opt.ilu_rows);
             if (h->ilu[k]->status) h->status = h->ilu[k]->status;
@@ -1099,8 +1109,17 @@ int or_bgs_update_values(or_bgs *h, const double *const *vs) {
             }
     h->status = ST_OK;
     for (int k = 0; k < F; k++) {
-        int st = h->ilu[k] ? or_ilu_update(h->ilu[k], h->blk[k * F + k])
+        int st = ST_OK;
+        if (h->dgs[k]) {
+            for (int i = 0; i < h->sizes[k]; i++) {
+                double d = diag_of(h->blk[k * F + k], i);
+                if (d == 0.0) st = ST_ZEROPIV;
+                h->dgs[k][i] = 1.0 / d;
+            }
+        } else {
+            st = h->ilu[k] ? or_ilu_update(h->ilu[k], h->blk[k * F + k])
                            : or_amg_update(h->amg[k], h->blk[k * F + k]->v, &h->opt);
+        }
         if (st) h->status = st;
     }
     return h->status;
@@ -1113,6 +1132,7 @@ void or_bgs_free(or_bgs *h) {
     for (int k = 0; k < 8; k++) {
         or_amg_free(h->amg[k]);
         or_ilu_free(h->ilu[k]);
+        free(h->dgs[k]);
     }
     free(h);
 }
@@ -1123,6 +1143,10 @@ void or_full_spmv(const or_bgs *h, const double *x, double *y) { or_spmv(h->full
  * transpose for the adjoint (V-cycle on the transposed level operators, same transfers, LU solved
  * transposed; the transposed ILU sweep). */
 static void block_solve(const or_bgs *h, int k, const double *r, double *z, int transposed) {
+    if (h->dgs[k]) {   /* diagonal solve (its own transpose) */
+        for (int i = 0; i < h->sizes[k]; i++) z[i] = h->dgs[k][i] * r[i];
+        return;
+    }
     if (h->ilu[k]) {
         if (transposed) or_ilu_apply_transposed(h->ilu[k], r, z);
         else or_ilu_apply(h->ilu[k], r, z);

@@ -44,7 +44,7 @@ typedef struct {
     int power_iters;
     int filter_diag;        /* 0: diag(A_F) ; 1: absolute row sum of A_F */
     int jacobi;             /* 1: block Jacobi (couplings left out of the sweep) */
-    int subsolver[8];       /* per field id: 0 SA-AMG V-cycle, 1 DD(0)-ILU(0) */
+    int subsolver[8];       /* per field id: 0 SA-AMG V-cycle, 1 DD(0)-ILU(0), 2 diagonal solve */
     int ilu_rows;           /* DD(0)-ILU(0) subdomain size in rows */
     int ngroups;            /* > 0: nested variant with groups [group_end[g-1], group_end[g]) of order positions */
     int group_end[8];
@@ -95,6 +95,7 @@ typedef struct {
     or_csr *full;           /* assembled full operator, field-blocked */
     or_amg *amg[8];
     or_ilu *ilu[8];         /* DD(0)-ILU(0) fields (amg[k] NULL there) */
+    double *dgs[8];         /* diagonal-solve fields: 1 / diag(A_kk) (amg[k] NULL there) */
     or_options opt;
     int status;
 } or_bgs;

@@ -240,9 +240,15 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     return cur;
 }
 
-// The block solve of one diagonal block on L[0].b: one V-cycle, or the DD(0)-ILU(0) sweep.
+// The block solve of one diagonal block on L[0].b: one V-cycle, the DD(0)-ILU(0) sweep, or the
+// diagonal solve x = D^-1 b (its own transpose).
 template <class VT, class XT>
 XT *block_solve(bgs_ctx *h, Hier &H, bool transposed) {
+    if (H.solver == 2) {
+        Level &L0 = H.L[0];
+        cheb_first<XT>(L0.A.n, Buf<XT>::b(L0), Buf<XT>::dinv(L0), 1.0, Buf<XT>::x0(L0), Buf<XT>::d(L0), h->s);
+        return Buf<XT>::x0(L0);
+    }
     if (H.solver == 1) {
         Level &L0 = H.L[0];
         const IluFactors &M = transposed ? H.iluT : H.ilu;
@@ -841,6 +847,7 @@ void build_adjoint(bgs_ctx *h) {
             ilu_build_transposed(H.ilu, H.iluT, h->sc, s);
             continue;
         }
+        if (H.solver == 2) continue;   // a diagonal solve is its own transpose
         for (size_t l = 0; l + 1 < H.L.size(); l++) {
             transpose_csr(view(H.L[l].A), H.L[l].AT, h->sc, s);
             build_sell(H.L[l].AT, kMaxPad, h->sc, s);
@@ -1016,7 +1023,7 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
     for (int k = 0; k < F; k++) {
         if (sizes[k] < 1 || sizes[k] >= INT32_MAX) return BGS_INVALID_ARG;
         tot += sizes[k];
-        if (o.cheb_degree[k] < 1 || o.theta[k] < 0 || o.subsolver[k] < 0 || o.subsolver[k] > 1)
+        if (o.cheb_degree[k] < 1 || o.theta[k] < 0 || o.subsolver[k] < 0 || o.subsolver[k] > 2)
             return BGS_INVALID_ARG;
     }
     if (tot >= INT32_MAX) return BGS_INVALID_ARG;
@@ -1094,6 +1101,35 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
 
 namespace {
 
+__global__ void k_diag_recip(int n, const int *rp, const int *ci, const double *v, double *dinv, int *zero) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; e++)
+            if (ci[e] == i) d = v[e];
+        if (d == 0.0) *zero = 1;
+        dinv[i] = 1.0 / d;
+    }
+}
+
+// Lv.dinv = 1 / diag(Lv.A) (and its FP32 copy in mixed precision); a zero diagonal entry is a zero
+// pivot of the diagonal solve.
+void diag_reciprocal(Level &Lv, bool mixed, Scratch &sc, cudaStream_t s) {
+    const int n = Lv.A.n;
+    if (Lv.dinv.n != (size_t)n) Lv.dinv.alloc((size_t)n, s);
+    CK(cudaMemsetAsync(sc.flags.p + 13, 0, sizeof(int), s));
+    if (n > 0) {
+        k_diag_recip<<<grid_for(n, 256), 256, 0, s>>>(n, Lv.A.rp.p, Lv.A.ci.p, Lv.A.v.p, Lv.dinv.p, sc.flags.p + 13);
+        CK_LAUNCH();
+    }
+    if (mixed) {
+        if (Lv.dinvf.n != (size_t)n) Lv.dinvf.alloc((size_t)n, s);
+        convert_d2f(Lv.dinv.p, Lv.dinvf.p, n, s);
+    }
+    CK(cudaMemcpyAsync(sc.h_flags + 13, sc.flags.p + 13, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (sc.h_flags[13]) throw Error(BGS_ZERO_PIVOT, "zero diagonal entry in a block on the diagonal solve");
+}
+
 // Builds block k's hierarchy and its solve-side copies on stream sk (no timing-based tuning here).
 void build_block(bgs_ctx *h, int k, cudaStream_t sk, Scratch &sck) {
     const bool mixed = h->opt.precision == 1;
@@ -1112,6 +1148,14 @@ void build_block(bgs_ctx *h, int k, cudaStream_t sk, Scratch &sck) {
     CK(cudaMemcpyAsync(A0.rp.p, B.rp.p, sizeof(int) * ((size_t)B.n + 1), cudaMemcpyDeviceToDevice, sk));
     CK(cudaMemcpyAsync(A0.ci.p, B.ci.p, sizeof(int) * B.nnz, cudaMemcpyDeviceToDevice, sk));
     CK(cudaMemcpyAsync(A0.v.p, B.v.p, sizeof(double) * B.nnz, cudaMemcpyDeviceToDevice, sk));
+    if (h->opt.subsolver[k] == 2) {   // diagonal solve: 1 / diag(A_kk) on level 0 only
+        H.solver = 2;
+        diag_reciprocal(H.L[0], mixed, sck, sk);
+        if (mixed) Buf<float>::alloc(H.L[0], A0.n, sk);
+        else Buf<double>::alloc(H.L[0], A0.n, sk);
+        CK(cudaStreamSynchronize(sk));
+        return;
+    }
     if (h->opt.subsolver[k] == 1) {   // DD(0)-ILU(0): factors of level 0 only
         H.solver = 1;
         ilu_setup(H.ilu, A0, h->opt.ilu_rows, mixed, sck, sk);
@@ -1215,6 +1259,11 @@ extern "C" int bgs_update_values(bgs_handle h, const double *const *values) {
             DCsr &A0 = H.L[0].A;
             CK(cudaMemcpyAsync(A0.v.p, B.v.p, sizeof(double) * (size_t)B.nnz, cudaMemcpyDeviceToDevice, sk));
             refresh_values(A0, sk);
+            if (H.solver == 2) {
+                diag_reciprocal(H.L[0], mixed, sck, sk);
+                CK(cudaStreamSynchronize(sk));
+                return;
+            }
             if (H.solver == 1) {
                 ilu_update(H.ilu, A0, sck, sk);
                 CK(cudaStreamSynchronize(sk));
