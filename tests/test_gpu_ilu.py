@@ -105,7 +105,7 @@ def test_update_refactors_dd_ilu(bgs):
 def test_ilu_option_errors(bgs):
     system = bs.assemble(grid=bs.Grid(3, 6, 5, 4), seed=1)
     with pytest.raises(bgs.BGSError):
-        bgs.solver_for_system(system, subsolver=[0, 0, 0, 2, 0])
+        bgs.solver_for_system(system, subsolver=[0, 0, 0, 3, 0])
     with pytest.raises(bgs.BGSError):
         bgs.solver_for_system(system, subsolver=SUB, ilu_rows=9000)
     g = bgs.solver_for_system(system, order=ORDER)
