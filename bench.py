@@ -32,10 +32,9 @@ METRIC = "setup+solve sec to rtol 1e-8 at 10.5M DOFs, mixed vs FP64 on same GB30
 # per SpMV variant the autotuner can pick for it (0 = SELL-32, k = CSR with k threads per row), from
 # the ncu captures named beside each; a variant without a capture reports null
 CHEB_FINE_TRAFFIC = {
-    0: (265.932032e6, "profiles/k_sell_cheb_phi_s_128cubed.md"),
-    1: (275.506944e6, "profiles/k_spmv1_cheb_phi_s_128cubed.md"),
+    0: (264.967168e6, "profiles/k_sell_cheb_phi_s_128cubed.md"),
+    1: (275.055616e6, "profiles/k_spmv1_cheb_phi_s_128cubed.md"),
 }
-WORKLOAD = "C4"
 WORKLOAD = "C4"
 
 

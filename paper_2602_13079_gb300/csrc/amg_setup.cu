@@ -747,25 +747,18 @@ __global__ void k_row_lengths(int n, const int *rp, int *len) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) len[i] = rp[i + 1] - rp[i];
 }
 
-// Short rows: one thread per row keeps the distinct output columns of its row in an
-// insertion-sorted list (at most SG_LOCAL entries), visiting the products in the order of the
-// left operand's row, so every output entry is summed in that order.  Rows with more distinct
-// columns report -1 and go to the warp-hash kernels.
-
-template <bool NUM>
-__global__ void __launch_bounds__(128) k_sg_local(int n, const int *__restrict__ arp, const int *__restrict__ aci,
-                                                  const double *__restrict__ av, const int *__restrict__ brp,
-                                                  const int *__restrict__ bci, const double *__restrict__ bv,
-                                                  const int *__restrict__ ub, int *cnt, const int *__restrict__ crp,
-                                                  int *cci, double *cv) {
+// Short rows (at most SG_LOCAL_UB products), one thread per row.  Symbolic: the distinct output
+// columns of the row in an insertion-sorted local list (at most SG_LOCAL entries), written to the
+// row's SG_LOCAL slots of cols; rows with more distinct columns report -1 and go to the warp-hash
+// kernels.  Numeric: the row's sorted columns are copied into C, its values start at 0, and every
+// product, in the order of the left operand's row, is added in place at its column (binary search
+// in the row), so each output entry is summed in that order.
+__global__ void __launch_bounds__(128) k_sg_local_sym(int n, const int *__restrict__ arp, const int *__restrict__ aci,
+                                                      const int *__restrict__ brp, const int *__restrict__ bci,
+                                                      const int *__restrict__ ub, int *cnt, int *cols) {
     int lc[SG_LOCAL];
-    double lv[SG_LOCAL];
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
-        const bool local = ub[row] <= SG_LOCAL_UB;
-        if (NUM) {
-            const int want = crp[row + 1] - crp[row];
-            if (!local || want > SG_LOCAL) continue;         // handled by the hash path
-        } else if (!local) {
+        if (ub[row] > SG_LOCAL_UB) {
             cnt[row] = -1;
             continue;
         }
@@ -773,35 +766,59 @@ __global__ void __launch_bounds__(128) k_sg_local(int n, const int *__restrict__
         bool over = false;
         for (int e = arp[row]; e < arp[row + 1] && !over; e++) {
             const int k = aci[e];
-            const double a = NUM ? av[e] : 0.0;
             for (int f = brp[k]; f < brp[k + 1]; f++) {
                 const int j = bci[f];
                 int p = c - 1;
                 while (p >= 0 && lc[p] > j) p--;
-                if (p >= 0 && lc[p] == j) {
-                    if (NUM) lv[p] = __dadd_rn(lv[p], __dmul_rn(a, bv[f]));
-                    continue;
-                }
+                if (p >= 0 && lc[p] == j) continue;
                 if (c == SG_LOCAL) {
                     over = true;
                     break;
                 }
-                for (int q = c; q > p + 1; q--) {
-                    lc[q] = lc[q - 1];
-                    if (NUM) lv[q] = lv[q - 1];
-                }
+                for (int q = c; q > p + 1; q--) lc[q] = lc[q - 1];
                 lc[p + 1] = j;
-                if (NUM) lv[p + 1] = __dadd_rn(0.0, __dmul_rn(a, bv[f]));
                 c++;
             }
         }
-        if (!NUM) {
-            cnt[row] = over ? -1 : c;
-        } else {
-            const int o = crp[row];
-            for (int q = 0; q < c; q++) {
-                cci[o + q] = lc[q];
-                cv[o + q] = lv[q];
+        cnt[row] = over ? -1 : c;
+        if (!over) {
+            int *out = cols + (size_t)row * SG_LOCAL;
+            for (int q = 0; q < c; q++) out[q] = lc[q];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_sg_local_num(int n, const int *__restrict__ arp, const int *__restrict__ aci,
+                                                      const double *__restrict__ av, const int *__restrict__ brp,
+                                                      const int *__restrict__ bci, const double *__restrict__ bv,
+                                                      const int *__restrict__ ub, const int *__restrict__ cols,
+                                                      const int *__restrict__ crp, int *cci, double *cv, int *err) {
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+        const int o = crp[row], c = crp[row + 1] - o;
+        if (ub[row] > SG_LOCAL_UB || c > SG_LOCAL) continue;   // handled by the hash path
+        const int *in = cols + (size_t)row * SG_LOCAL;
+        int *rc = cci + o;
+        double *rv = cv + o;
+        for (int q = 0; q < c; q++) {
+            rc[q] = in[q];
+            rv[q] = 0.0;
+        }
+        for (int e = arp[row]; e < arp[row + 1]; e++) {
+            const int k = aci[e];
+            const double a = av[e];
+            for (int f = brp[k]; f < brp[k + 1]; f++) {
+                const int j = bci[f];
+                int lo = 0, hi = c;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (rc[mid] < j) lo = mid + 1;
+                    else hi = mid;
+                }
+                if (lo >= c || rc[lo] != j) {   // not in the symbolic pattern: never write outside it
+                    atomicOr(err, 1);
+                    continue;
+                }
+                rv[lo] = __dadd_rn(rv[lo], __dmul_rn(a, bv[f]));
             }
         }
     }
@@ -822,7 +839,8 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
     CK_LAUNCH();
     // symbolic: short rows per thread, the rest per warp (shared table), then global tables
     const int gl = grid_for(n, 128, kSMs * 32);
-    k_sg_local<false><<<gl, 128, 0, s>>>(n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, C.rp.p, nullptr, nullptr, nullptr);
+    DBuf<int> lcols((size_t)n * SG_LOCAL, s);   // sorted columns of the short rows
+    k_sg_local_sym<<<gl, 128, 0, s>>>(n, A.rp, A.ci, B.rp, B.ci, ub.p, C.rp.p, lcols.p);
     CK_LAUNCH();
     {
         // rows with small tables, then rows with large tables, then rows past the shared table
@@ -869,8 +887,10 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
     C.v.alloc((size_t)C.nnz, s);
     // numeric
     CK(cudaMemsetAsync(sc.flags.p + 8, 0, sizeof(int), s));
-    k_sg_local<true><<<gl, 128, 0, s>>>(n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, nullptr, C.rp.p, C.ci.p, C.v.p);
+    k_sg_local_num<<<gl, 128, 0, s>>>(n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, lcols.p, C.rp.p, C.ci.p, C.v.p,
+                                      sc.flags.p + 8);
     CK_LAUNCH();
+    lcols.release();
     {
         DBuf<int> cnt((size_t)n, s), rows;
         k_row_lengths<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp.p, cnt.p);

@@ -208,14 +208,15 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     const int vb = sizeof(VT), xb = sizeof(XT);
     const double cbytes = spmv_bytes(A, vb, xb, 4);
     const int ccls = l == 0 ? 1 : 4;   // fine-level vs coarse-level Chebyshev steps
-    // pre-smoothing from x = 0
+    // pre-smoothing from x = 0; the steps carry e = d / c2 (see ECheb): sc is the c2 of the last step
     cheb_first<XT>(n, b, dinv, inv_theta, x0, d, s);
     XT *cur = x0, *oth = x1;
-    double st = st0, c1 = 0.0, c2 = 0.0;
+    double st = st0, c1 = 0.0, c2 = 0.0, sc = inv_theta;
     for (int k = 1; k < deg; k++) {
         next(st, c1, c2);
         Prof pf(h, ccls, cbytes);
-        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, c1, c2, false, s);
+        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, c1 * sc / c2, c2, false, s);
+        sc = c2;
         std::swap(cur, oth);
     }
     // residual, restriction, coarse correction, prolongation
@@ -226,6 +227,7 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     spmv_addto<VT, XT>(Lv.P, xc, cur, s);
     // post-smoothing
     st = st0;
+    sc = inv_theta;
     {
         Prof pf(h, ccls, cbytes);
         cheb_step<VT, XT>(A, b, dinv, cur, oth, d, 0.0, inv_theta, true, s);
@@ -234,7 +236,8 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     for (int k = 1; k < deg; k++) {
         next(st, c1, c2);
         Prof pf(h, ccls, cbytes);
-        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, c1, c2, false, s);
+        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, c1 * sc / c2, c2, false, s);
+        sc = c2;
         std::swap(cur, oth);
     }
     return cur;

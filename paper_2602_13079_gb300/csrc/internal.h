@@ -72,10 +72,10 @@ void spmv_resid(const DCsr &A, const XT *b, const XT *x, XT *r, cudaStream_t s);
 template <class VT, class XT>
 void spmv_addto(const DCsr &A, const XT *x, XT *y, cudaStream_t s);
 template <class VT, class XT>
-void cheb_step(const DCsr &A, const XT *b, const XT *dinv, const XT *xin, XT *xout, XT *d, double c1, double c2,
-               bool first, cudaStream_t s);
+void cheb_step(const DCsr &A, const XT *b, const XT *dinv, const XT *xin, XT *xout, XT *e, double alpha,
+               double scale, bool first, cudaStream_t s);
 template <class XT>
-void cheb_first(int n, const XT *b, const XT *dinv, double inv_theta, XT *x, XT *d, cudaStream_t s);
+void cheb_first(int n, const XT *b, const XT *dinv, double inv_theta, XT *x, XT *e, cudaStream_t s);
 // r = v - L z (L with global columns into z), v/z FP64, output typed
 template <class VT, class XT>
 void coupling_sub(const DCsr &L, const double *v, const double *z, XT *r, cudaStream_t s);
