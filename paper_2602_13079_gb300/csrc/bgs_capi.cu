@@ -171,6 +171,37 @@ struct Buf<float> {
 };
 
 // ------------------------------------------------------------------ V-cycle (Sec. 2.2.1)
+// Chebyshev coefficients of one smoothing pass on a level (deg steps), in the scaled form of the
+// step kernels (e = d / c2): step 0 is cheb_first (from x = 0) or a step with alpha = 0 and scale
+// 1/theta; step k = 1..deg-1 has alpha[k-1] = c1 c2_prev / c2 and scale[k-1] = c2.  The real
+// interval (Saad's form) or the ellipse with imaginary semi-axis lim through its focal parameter
+// c2 = delta^2 - lim^2 (tau_k = rho_k / delta form).
+void cheb_coefs(const Level &Lv, int deg, double &inv_theta, double *alpha, double *scale) {
+    const double theta = (Lv.lmax + Lv.lmin) / 2.0, delta = (Lv.lmax - Lv.lmin) / 2.0;
+    const double sigma = theta / delta;
+    inv_theta = 1.0 / theta;
+    const bool ell = Lv.lim > 0.0;
+    const double c2e = delta * delta - Lv.lim * Lv.lim;
+    double st = ell ? inv_theta : 1.0 / sigma, sc = inv_theta;
+    for (int k = 1; k < deg; k++) {
+        double c1, c2;
+        if (ell) {
+            const double tn = 1.0 / (2.0 * theta - c2e * st);
+            c1 = c2e * tn * st;
+            c2 = 2.0 * tn;
+            st = tn;
+        } else {
+            const double rn = 1.0 / (2.0 * sigma - st);
+            c1 = rn * st;
+            c2 = 2.0 * rn / delta;
+            st = rn;
+        }
+        alpha[k - 1] = c1 * sc / c2;
+        scale[k - 1] = c2;
+        sc = c2;
+    }
+}
+
 template <class VT, class XT>
 XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     cudaStream_t s = h->s;
@@ -184,39 +215,19 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     }
     const DCsr &A = transposed ? Lv.AT : Lv.A;
     const XT *dinv = Buf<XT>::dinv(Lv);
-    const double theta = (Lv.lmax + Lv.lmin) / 2.0, delta = (Lv.lmax - Lv.lmin) / 2.0;
-    const double sigma = theta / delta, inv_theta = 1.0 / theta;
-    // Chebyshev coefficients: the real interval (Saad's form), or the ellipse with imaginary
-    // semi-axis lim through its focal parameter c2 = delta^2 - lim^2 (tau_k = rho_k / delta form)
-    const bool ell = Lv.lim > 0.0;
-    const double c2e = delta * delta - Lv.lim * Lv.lim;
-    auto next = [&](double &st, double &c1, double &c2) {
-        if (ell) {
-            const double tn = 1.0 / (2.0 * theta - c2e * st);
-            c1 = c2e * tn * st;
-            c2 = 2.0 * tn;
-            st = tn;
-        } else {
-            const double rn = 1.0 / (2.0 * sigma - st);
-            c1 = rn * st;
-            c2 = 2.0 * rn / delta;
-            st = rn;
-        }
-    };
-    const double st0 = ell ? inv_theta : 1.0 / sigma;
     const int deg = H.degree;
+    double inv_theta;
+    std::vector<double> alpha((size_t)deg), scale((size_t)deg);
+    cheb_coefs(Lv, deg, inv_theta, alpha.data(), scale.data());
     const int vb = sizeof(VT), xb = sizeof(XT);
     const double cbytes = spmv_bytes(A, vb, xb, 4);
     const int ccls = l == 0 ? 1 : 4;   // fine-level vs coarse-level Chebyshev steps
-    // pre-smoothing from x = 0; the steps carry e = d / c2 (see ECheb): sc is the c2 of the last step
+    // pre-smoothing from x = 0
     cheb_first<XT>(n, b, dinv, inv_theta, x0, d, s);
     XT *cur = x0, *oth = x1;
-    double st = st0, c1 = 0.0, c2 = 0.0, sc = inv_theta;
     for (int k = 1; k < deg; k++) {
-        next(st, c1, c2);
         Prof pf(h, ccls, cbytes);
-        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, c1 * sc / c2, c2, false, s);
-        sc = c2;
+        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, alpha[k - 1], scale[k - 1], false, s);
         std::swap(cur, oth);
     }
     // residual, restriction, coarse correction, prolongation
@@ -226,18 +237,14 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     XT *xc = vcycle<VT, XT>(h, H, l + 1, transposed);
     spmv_addto<VT, XT>(Lv.P, xc, cur, s);
     // post-smoothing
-    st = st0;
-    sc = inv_theta;
     {
         Prof pf(h, ccls, cbytes);
         cheb_step<VT, XT>(A, b, dinv, cur, oth, d, 0.0, inv_theta, true, s);
     }
     std::swap(cur, oth);
     for (int k = 1; k < deg; k++) {
-        next(st, c1, c2);
         Prof pf(h, ccls, cbytes);
-        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, c1 * sc / c2, c2, false, s);
-        sc = c2;
+        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, alpha[k - 1], scale[k - 1], false, s);
         std::swap(cur, oth);
     }
     return cur;
