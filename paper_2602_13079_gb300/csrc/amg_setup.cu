@@ -494,12 +494,16 @@ __device__ int sg_accumulate(int row, int *keys, double *vals, unsigned T, bool 
             const int j = act ? bci[bs + q] : -1;
             const unsigned grp = __match_any_sync(0xffffffffu, j);
             const int leader = __ffs(grp) - 1;
-            if (NUM) sv[lane] = act ? __dmul_rn(a, bv[bs + q]) : 0.0;
+            if (NUM && act) sv[lane] = __dmul_rn(a, bv[bs + q]);
             __syncwarp();
             if (act && lane == leader) {
+                // the group's products in lane order, starting from the leader's own (the leader
+                // is the group's lowest lane): one add per further member, none for a singleton
                 double sum = 0.0;
-                if (NUM)
-                    for (unsigned g = grp; g; g &= g - 1) sum = __dadd_rn(sum, sv[__ffs(g) - 1]);
+                if (NUM) {
+                    sum = sv[lane];
+                    for (unsigned g = grp & (grp - 1); g; g &= g - 1) sum = __dadd_rn(sum, sv[__ffs(g) - 1]);
+                }
                 bool ins;
                 const int sl = tbl_insert(keys, mask, j, ins);
                 if (sl < 0) over = true;
@@ -843,9 +847,11 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
     k_sg_local_sym<<<gl, 128, 0, s>>>(n, A.rp, A.ci, B.rp, B.ci, ub.p, C.rp.p, lcols.p);
     CK_LAUNCH();
     {
-        // rows with small tables, then rows with large tables, then rows past the shared table
+        // every open row first tries a small table (capped: a row with more than SG_SMALL_T / 2
+        // distinct columns gives up and stays open, whatever its product count), then the rows
+        // still open with large tables, then rows past the shared table
         DBuf<int> flag((size_t)n, s), rows;
-        k_sym_class<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp.p, ub.p, SG_SMALL_T, flag.p);
+        k_sym_class<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp.p, ub.p, 0xffffffffu, flag.p);
         CK_LAUNCH();
         const int nbA = collect_flag(n, flag.p, rows, sc, s);
         if (nbA) {
