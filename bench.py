@@ -422,13 +422,24 @@ def gpu_arm(args, rank, world):
         bh = torch.from_numpy(system.b).pin_memory()
         xh = torch.zeros_like(bh).pin_memory()
 
+        phases = []
+
         def hstep():
+            # each library call returns after its stream work (create, setup and solve synchronise),
+            # so the host clock between them splits the step without adding synchronisation
+            t = [time.perf_counter()]
             s = bgs.Solver(hblocks, sizes, order, precision=0, **extra)
+            t.append(time.perf_counter())
             s.setup()
+            t.append(time.perf_counter())
             s.bgs_solve(bh, xh)
+            t.append(time.perf_counter())
             s.close()
+            t.append(time.perf_counter())
+            phases.append([b - a for a, b in zip(t, t[1:])])
 
         hstep()
+        phases.clear()
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -437,8 +448,10 @@ def gpu_arm(args, rank, world):
         torch.cuda.synchronize()
         barrier()
         e2e_s = allmax((time.perf_counter() - t0) / args.steps)
+        split = [statistics.median(p[k] for p in phases) * 1e3 for k in range(4)]
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(hbytes + bh.numel() * 8),
-               "d2h_bytes_per_step": int(xh.numel() * 8), "precision": "fp64"}
+               "d2h_bytes_per_step": int(xh.numel() * 8), "precision": "fp64",
+               "median_ms": dict(zip(("create", "setup", "solve", "close"), (round(v, 2) for v in split)))}
 
     peak, peak_kind = measured_peaks()
     roof = None
