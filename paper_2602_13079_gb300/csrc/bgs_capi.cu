@@ -725,17 +725,88 @@ int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
 }
 
 // ------------------------------------------------------------------ helpers for create/setup
-void copy_block(const bgs_csr &in, int64_t nr, int64_t nc, DCsr &out, cudaStream_t s) {
+void alloc_block(const bgs_csr &in, int64_t nr, int64_t nc, DCsr &out, cudaStream_t s) {
     out.n = (int)nr;
     out.m = (int)nc;
     out.nnz = in.nnz;
     out.rp.alloc((size_t)nr + 1, s);
     out.ci.alloc((size_t)in.nnz, s);
     out.v.alloc((size_t)in.nnz, s);
-    CK(cudaMemcpyAsync(out.rp.p, in.rowptr, sizeof(int) * ((size_t)nr + 1), cudaMemcpyDefault, s));
+}
+
+void copy_block_data(const bgs_csr &in, DCsr &out, cudaStream_t s) {
+    CK(cudaMemcpyAsync(out.rp.p, in.rowptr, sizeof(int) * ((size_t)out.n + 1), cudaMemcpyDefault, s));
     if (in.nnz) {
         CK(cudaMemcpyAsync(out.ci.p, in.col, sizeof(int) * (size_t)in.nnz, cudaMemcpyDefault, s));
         CK(cudaMemcpyAsync(out.v.p, in.val, sizeof(double) * (size_t)in.nnz, cudaMemcpyDefault, s));
+    }
+}
+
+// The stored blocks' copies on two side streams (host buffers: more host-to-device bandwidth than
+// one stream; each block's validation on s overlaps the copies of the blocks after it), the
+// validation error bits one slot per block, read back once.
+int copy_and_validate(bgs_ctx *h, const int64_t *sizes, const bgs_csr *blocks, cudaStream_t s) {
+    const int F = h->F;
+    std::vector<int> todo;   // r * F + c of the stored blocks, largest first
+    for (int r = 0; r < F; r++)
+        for (int c = 0; c < F; c++) {
+            const bgs_csr &B = blocks[r * F + c];
+            DCsr &D = h->blk[(size_t)r * F + c];
+            if (B.nrows == 0 && B.nnz == 0) {
+                D.n = (int)sizes[r];
+                D.m = (int)sizes[c];
+                D.nnz = 0;
+                D.rp.alloc((size_t)sizes[r] + 1, s);
+                CK(cudaMemsetAsync(D.rp.p, 0, sizeof(int) * ((size_t)sizes[r] + 1), s));
+                continue;
+            }
+            alloc_block(B, sizes[r], sizes[c], D, s);
+            todo.push_back(r * F + c);
+        }
+    std::stable_sort(todo.begin(), todo.end(), [&](int a, int b) { return blocks[a].nnz > blocks[b].nnz; });
+    DBuf<int> flags(std::max<size_t>(todo.size(), 1), s);
+    cudaStream_t cs[2] = {nullptr, nullptr};
+    cudaEvent_t ready = nullptr;
+    std::vector<cudaEvent_t> done(todo.size(), nullptr);
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : done)
+            if (e) cudaEventDestroy(e);
+        if (ready) cudaEventDestroy(ready);
+        for (cudaStream_t q : cs)
+            if (q) cudaStreamDestroy(q);
+    };
+    try {
+        CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        CK(cudaEventRecord(ready, s));   // the allocations above are ordered before the copies
+        for (cudaStream_t &q : cs) {
+            CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+            CK(cudaStreamWaitEvent(q, ready, 0));
+        }
+        int64_t load[2] = {0, 0};
+        for (size_t i = 0; i < todo.size(); i++) {
+            const int b = todo[i];
+            const int q = load[0] <= load[1] ? 0 : 1;
+            load[q] += blocks[b].nnz * 12 + blocks[b].nrows * 4;
+            copy_block_data(blocks[b], h->blk[(size_t)b], cs[q]);
+            CK(cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming));
+            CK(cudaEventRecord(done[i], cs[q]));
+            CK(cudaStreamWaitEvent(s, done[i], 0));
+            validate_csr_launch(view(h->blk[(size_t)b]), b / F == b % F, flags.p + i, s);
+        }
+        std::vector<int> hf(todo.size(), 0);
+        if (!todo.empty())
+            CK(cudaMemcpyAsync(hf.data(), flags.p, sizeof(int) * todo.size(), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));   // s waited for every copy, so the side streams are idle
+        cleanup();
+        for (int f : hf)
+            if (int st = validate_status(f)) return st;
+        return BGS_OK;
+    } catch (...) {
+        cudaStreamSynchronize(s);
+        for (cudaStream_t q : cs)
+            if (q) cudaStreamSynchronize(q);
+        cleanup();
+        throw;
     }
 }
 
@@ -1081,22 +1152,7 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
         CreateTrace tr(s);
         h->sc.init(s);
         h->blk.resize((size_t)F * F);
-        for (int r = 0; r < F; r++)
-            for (int c = 0; c < F; c++) {
-                const bgs_csr &B = blocks[r * F + c];
-                DCsr &D = h->blk[(size_t)r * F + c];
-                if (B.nrows == 0 && B.nnz == 0) {
-                    D.n = (int)sizes[r];
-                    D.m = (int)sizes[c];
-                    D.nnz = 0;
-                    D.rp.alloc((size_t)sizes[r] + 1, s);
-                    CK(cudaMemsetAsync(D.rp.p, 0, sizeof(int) * ((size_t)sizes[r] + 1), s));
-                    continue;
-                }
-                copy_block(B, sizes[r], sizes[c], D, s);
-                int st = validate_csr(view(D), r == c, h->sc, s);
-                if (st) return st;
-            }
+        if (int st = copy_and_validate(h.get(), sizes, blocks, s)) return st;
         tr.mark("copy+validate blocks");
         assemble_operators(h.get(), h->full, h->lower, s);
         tr.mark("full operator + couplings");

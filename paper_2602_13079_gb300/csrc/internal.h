@@ -46,6 +46,9 @@ void dev_fill_double(double *p, double value, int64_t n, cudaStream_t s);
 // rowptr[0] = 0, rowptr[n] = nnz, columns in range and strictly increasing, and (need_diag) that
 // every row stores its diagonal.
 int validate_csr(const CsrView &A, bool need_diag, Scratch &sc, cudaStream_t s);
+// the validation kernel alone, its error bits in *flag (cleared first); validate_status maps them
+void validate_csr_launch(const CsrView &A, bool need_diag, int *flag, cudaStream_t s);
+int validate_status(int flag);
 // C = row-wise concatenation of blocks: row i of C = row i of parts[0] (columns + offs[0]), then
 // row i of parts[1] ... (all parts have n rows; columns stay sorted if offsets increase).
 void concat_rows(int n, int nparts, const CsrView *parts, const int *col_offs, DCsr &C, Scratch &sc,

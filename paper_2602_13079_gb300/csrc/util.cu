@@ -354,18 +354,24 @@ __global__ void k_validate(int n, int m, int64_t nnz, const int *rp, const int *
     }
 }
 
-int validate_csr(const CsrView &A, bool need_diag, Scratch &sc, cudaStream_t s) {
-    CK(cudaMemsetAsync(sc.flags.p, 0, sizeof(int), s));
+void validate_csr_launch(const CsrView &A, bool need_diag, int *flag, cudaStream_t s) {
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
     if (A.n > 0) {
-        k_validate<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.m, A.nnz, A.rp, A.ci, A.v, need_diag ? 1 : 0,
-                                                       sc.flags.p);
+        k_validate<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.m, A.nnz, A.rp, A.ci, A.v, need_diag ? 1 : 0, flag);
         CK_LAUNCH();
     }
+}
+
+int validate_status(int flag) {
+    if (flag & 16) return BGS_NAN_INF;
+    return flag ? BGS_INVALID_ARG : BGS_OK;
+}
+
+int validate_csr(const CsrView &A, bool need_diag, Scratch &sc, cudaStream_t s) {
+    validate_csr_launch(A, need_diag, sc.flags.p, s);
     CK(cudaMemcpyAsync(sc.h_flags, sc.flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    int f = sc.h_flags[0];
-    if (f & 16) return BGS_NAN_INF;
-    return f ? BGS_INVALID_ARG : BGS_OK;
+    return validate_status(sc.h_flags[0]);
 }
 
 // ------------------------------------------------------------------------------------------
