@@ -417,22 +417,32 @@ __global__ void k_power_start(int n, double *v) {
     }
 }
 
+// The iterates u_k = (D^-1 A)^k u_0 are left unnormalised and the estimate is ||u_k|| / ||u_k-1||
+// from the last two, which equals ||D^-1 A v|| for the normalised v = u_k-1 / ||u_k-1|| of the
+// textbook iteration.  Every 8 steps (never on the last) the iterate is rescaled to unit norm, so
+// its size stays far from FP64's range limits however many steps are asked for.
 static double power_lambda(const DCsr &A, const double *dinv, int iters, Scratch &sc, cudaStream_t s) {
     const int n = A.n;
     DBuf<double> v((size_t)n, s), w((size_t)n, s);
     k_power_start<<<grid_for(n, 256), 256, 0, s>>>(n, v.p);
     CK_LAUNCH();
-    double *nv = sc.scal.p + 20, *nw = sc.scal.p + 22;   // (||.||^2, 1/||.||) pairs
-    dev_dot_rsqrt(v.p, v.p, n, nv, sc, s);
+    double *nv = sc.scal.p + 20, *nw = sc.scal.p + 22;
     for (int it = 0; it < iters; it++) {
-        spmv_scaled_norm(A, dinv, v.p, nv + 1, w.p, s);   // w = D^-1 A (v / ||v||)
-        dev_dot_rsqrt(w.p, w.p, n, nw, sc, s);
+        if (it > 0 && it % 8 == 0 && it < iters - 1) {
+            dev_dot_rsqrt(v.p, v.p, n, nv, sc, s);           // (||v||^2, 1/||v||)
+            spmv_scaled_norm(A, dinv, v.p, nv + 1, w.p, s);  // w = D^-1 A (v / ||v||)
+        } else {
+            spmv_scaled_norm(A, dinv, v.p, nullptr, w.p, s); // w = D^-1 A v
+        }
         std::swap(v.p, w.p);
-        std::swap(nv, nw);
     }
+    dev_dot(v.p, v.p, n, nv, sc, s);   // ||u_k||^2
+    dev_dot(w.p, w.p, n, nw, sc, s);   // ||u_k-1||^2
     CK(cudaMemcpyAsync(sc.h_scal + 1, nv, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(sc.h_scal + 2, nw, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return std::sqrt(sc.h_scal[1]);
+    const double a = sc.h_scal[1], b = sc.h_scal[2];
+    return b > 0.0 ? std::sqrt(a / b) : 0.0;
 }
 
 // ==========================================================================================

@@ -75,14 +75,14 @@ struct EScale {   // w = D^-1 A v
     __device__ AT start(int) const { return (AT)0; }
     __device__ void operator()(int i, double s) const { w[i] = dinv[i] * s; }
 };
-struct EScaleNorm {   // w = dinv (A v) / ||v||, 1/||v|| read from device memory
+struct EScaleNorm {   // w = dinv (A v) / ||v||, 1/||v|| read from device memory (w = dinv (A v) without it)
     const double *dinv;
     const double *rnorm;
     double *w;
     static constexpr bool kSub = false;
     template <class AT>
     __device__ AT start(int) const { return (AT)0; }
-    __device__ void operator()(int i, double s) const { w[i] = dinv[i] * (s * *rnorm); }
+    __device__ void operator()(int i, double s) const { w[i] = rnorm ? dinv[i] * (s * *rnorm) : dinv[i] * s; }
 };
 // One Chebyshev step in scaled form.  The recurrence d' = c1 d + c2 D^-1 r, x' = x + d' is carried
 // as e = d / c2 (the step's own c2): e' = alpha e + D^-1 r with alpha = c1 c2_prev / c2, and
