@@ -453,7 +453,8 @@ def gpu_arm(args, rank, world):
         split = [statistics.median(p[k] for p in phases) * 1e3 for k in range(4)]
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(hbytes + bh.numel() * 8),
                "d2h_bytes_per_step": int(xh.numel() * 8), "precision": "fp64",
-               "median_ms": dict(zip(("create", "setup", "solve", "close"), (round(v, 2) for v in split)))}
+               "median_ms": dict(zip(("create", "setup", "solve", "close"), (round(v, 2) for v in split))),
+               "steps_ms": [[round(v * 1e3, 2) for v in p] for p in phases]}
 
     peak, peak_kind = measured_peaks()
     roof = None
