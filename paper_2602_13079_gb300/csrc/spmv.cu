@@ -38,6 +38,27 @@ __global__ void __launch_bounds__(256) k_sell(int n, const int *__restrict__ spt
     const VT *v = sv + s0 + lane;
     constexpr bool S = Epi::kSub;
     AT acc = row < n ? epi.template start<AT>(row) : (AT)0;
+    if constexpr (sizeof(AT) == 4 && sizeof(VT) == 4) {
+        // FP32 values and sums: batches of eight slots, the slot index clamped to the slice width
+        // and a slot past it taken as 0 (as in the one-thread-per-row CSR form)
+#pragma unroll 1
+        for (int j = 0; j < w; j += 8) {
+            int cc[8];
+            AT a[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int jj = min(j + u, w - 1) - j;
+                cc[u] = __ldg(c + jj * 32);
+                a[u] = j + u < w ? Cvt<AT>::f(ldg(v + jj * 32)) : (AT)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) acc = mac<S>(acc, a[u], Cvt<AT>::f(ldg(x + cc[u])));
+            c += 8 * 32;
+            v += 8 * 32;
+        }
+        if (row < n) epi(row, acc);
+        return;
+    }
     int j = 0;
 #pragma unroll 1
     for (; j + 4 <= w; j += 4) {
