@@ -479,10 +479,12 @@ __device__ __forceinline__ int tbl_insert(int *keys, unsigned mask, int col, boo
 
 // Accumulate the products of one row into a hash table, one warp: lanes take 32 entries of the
 // left operand's row at a time and walk their right-operand rows in step.  Lanes of one step that
-// hit the same column are grouped (__match_any_sync); the group leader adds the group's values
-// in lane order (= left-operand order) and updates the table once, so no two lanes race on a
-// slot and the sums are reproducible.  Returns this lane's count of new columns; sets over if
-// the table's limit is passed (symbolic pass with a capped shared table).
+// hit the same column are grouped (__match_any_sync); the group leader owns the column's slot
+// and adds the group's products to it in lane order (= left-operand order), each as one fused
+// multiply-add, so no two lanes race on a slot and the sums are reproducible.  sv holds 64
+// doubles per warp: the lanes' left values (per chunk) and right values (per step).  Returns
+// this lane's count of new columns; sets over if the table's limit is passed (symbolic pass with
+// a capped shared table).
 template <bool NUM>
 __device__ int sg_accumulate(int row, int *keys, double *vals, unsigned T, bool capped, double *sv, const int *arp,
                              const int *aci, const double *av, const int *brp, const int *bci, const double *bv,
@@ -499,26 +501,27 @@ __device__ int sg_accumulate(int row, int *keys, double *vals, unsigned T, bool 
         const int bs = has ? brp[k] : 0;
         const int len = has ? brp[k + 1] - bs : 0;
         const int maxlen = __reduce_max_sync(0xffffffffu, len);
+        if (NUM) sv[lane] = a;   // read by the leaders after the first step's __syncwarp
         for (int q = 0; q < maxlen; q++) {
             const bool act = q < len;
             const int j = act ? bci[bs + q] : -1;
             const unsigned grp = __match_any_sync(0xffffffffu, j);
             const int leader = __ffs(grp) - 1;
-            if (NUM && act) sv[lane] = __dmul_rn(a, bv[bs + q]);
+            if (NUM && act) sv[32 + lane] = bv[bs + q];
             __syncwarp();
             if (act && lane == leader) {
-                // the group's products in lane order, starting from the leader's own (the leader
-                // is the group's lowest lane): one add per further member, none for a singleton
-                double sum = 0.0;
-                if (NUM) {
-                    sum = sv[lane];
-                    for (unsigned g = grp & (grp - 1); g; g &= g - 1) sum = __dadd_rn(sum, sv[__ffs(g) - 1]);
-                }
                 bool ins;
                 const int sl = tbl_insert(keys, mask, j, ins);
                 if (sl < 0) over = true;
                 else {
-                    if (NUM) vals[sl] = __dadd_rn(vals[sl], sum);
+                    if (NUM) {
+                        double v = vals[sl];
+                        for (unsigned g = grp; g; g &= g - 1) {
+                            const int m = __ffs(g) - 1;
+                            v = fma(sv[m], sv[32 + m], v);
+                        }
+                        vals[sl] = v;
+                    }
                     mine += ins;
                 }
             }
@@ -643,8 +646,8 @@ __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *rows
     extern __shared__ double sg_nsm[];
     const int wib = threadIdx.x >> 5;
     double *vals = sg_nsm + wib * TMAX;
-    double *sv = sg_nsm + SG_WARPS * TMAX + wib * 32;
-    int *keys = (int *)(sg_nsm + SG_WARPS * (TMAX + 32)) + wib * TMAX;
+    double *sv = sg_nsm + SG_WARPS * TMAX + wib * 64;
+    int *keys = (int *)(sg_nsm + SG_WARPS * (TMAX + 64)) + wib * TMAX;
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n; it += (gridDim.x * blockDim.x) >> 5) {
         const int row = rows ? rows[it] : it;
         const int c = crp[row + 1] - crp[row];
@@ -657,7 +660,7 @@ __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *rows
 __global__ void k_sg_num_big(int nbig, const int *rows, const long long *toff, int *gkeys, double *gvals,
                              const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
                              const double *bv, const int *crp, int *cci, double *cv, int *err) {
-    __shared__ double svb[8][32];
+    __shared__ double svb[8][64];
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbig; b += (gridDim.x * blockDim.x) >> 5) {
         const unsigned T = (unsigned)(toff[b + 1] - toff[b]);
         sg_numeric_row(rows[b], gkeys + toff[b], gvals + toff[b], T, svb[(threadIdx.x >> 5) & 7], arp, aci, av, brp,
@@ -924,13 +927,13 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
             if (!nb) continue;
             if (c == 0) {
                 k_sg_num<SG_SMALL_T><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, kSMs * 32), SG_WARPS * 32,
-                                       sizeof(double) * SG_WARPS * (SG_SMALL_T + 32) +
+                                       sizeof(double) * SG_WARPS * (SG_SMALL_T + 64) +
                                            sizeof(int) * SG_WARPS * SG_SMALL_T,
                                        s>>>(nb, rl.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
                                             sc.flags.p + 8);
             } else {
                 k_sg_num<SG_NUM_T><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, kSMs * 8), SG_WARPS * 32,
-                                     sizeof(double) * SG_WARPS * (SG_NUM_T + 32) + sizeof(int) * SG_WARPS * SG_NUM_T,
+                                     sizeof(double) * SG_WARPS * (SG_NUM_T + 64) + sizeof(int) * SG_WARPS * SG_NUM_T,
                                      s>>>(nb, rl.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
                                           sc.flags.p + 8);
             }
@@ -1229,7 +1232,7 @@ static void set_attributes() {
         CK(cudaFuncSetAttribute(k_sg_sym<SG_SYM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(int) * SG_WARPS * SG_SYM_T)));
         CK(cudaFuncSetAttribute(k_sg_num<SG_NUM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(double) * SG_WARPS * (SG_NUM_T + 32) + sizeof(int) * SG_WARPS * SG_NUM_T)));
+                                (int)(sizeof(double) * SG_WARPS * (SG_NUM_T + 64) + sizeof(int) * SG_WARPS * SG_NUM_T)));
     });
 }
 
