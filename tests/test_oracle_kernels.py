@@ -568,3 +568,47 @@ def test_scaled_chebyshev_recurrence_equals_the_oracle(deg, start):
         ref = oracle.chebyshev_ellipse(A, dinv, theta, c2e, deg, b, x0)
         got = _scaled_chebyshev(D, dinv, *_scaled_coefs(theta, delta, c2e, deg, True), b, x0)
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def _fmix32_np(h):
+    h = np.uint32(h)
+    h ^= h >> np.uint32(16)
+    h = np.uint32((int(h) * 0x85EBCA6B) & 0xFFFFFFFF)
+    h ^= h >> np.uint32(13)
+    h = np.uint32((int(h) * 0xC2B2AE35) & 0xFFFFFFFF)
+    h ^= h >> np.uint32(16)
+    return int(h)
+
+
+def _power_unnormalised(D, dinv, iters):
+    """The CUDA form of the power iteration: unnormalised iterates u_k = D^-1 A u_k-1 from the
+    hashed start, rescaled to unit norm before every 8th step except the last, estimate
+    ||u_k|| / ||u_k-1||."""
+    n = D.shape[0]
+    u = np.array([((_fmix32_np(i ^ 0x7F4A7C15) >> 8) + 0.5) / 16777216.0 for i in range(n)])
+    prev = u
+    for it in range(iters):
+        if it > 0 and it % 8 == 0 and it < iters - 1:
+            nu = np.linalg.norm(u)
+            u = u / nu if nu > 0 else 0.0 * u   # a zero norm scales by 0, as the kernel's rsqrt does
+        prev, u = u, dinv * (D @ u)
+    b = prev @ prev
+    return float(np.sqrt((u @ u) / b)) if b > 0 else 0.0
+
+
+@pytest.mark.parametrize("iters", [1, 2, 8, 9, 10, 17, 40])
+def test_unnormalised_power_iteration_equals_the_oracle(iters):
+    """||u_k|| / ||u_k-1|| on the unnormalised iterates (what the kernels compute, with a rescale
+    every 8 steps) equals the oracle's normalised estimate ||D^-1 A v||, v = u_k-1 / ||u_k-1||."""
+    assert _fmix32_np(0) == oracle.fmix32(0) and _fmix32_np(12345) == oracle.fmix32(12345)
+    Lp = laplacian_2d(7, shift=0.3)
+    D = Lp.to_dense()
+    D[3, 10] -= 0.2                                   # nonsymmetric
+    A = dense_to_csr(D)
+    dinv = 1.0 / np.diag(D)
+    ref = oracle.power_lambda(A, dinv, iters)
+    got = _power_unnormalised(D, dinv, iters)
+    assert abs(got - ref) <= 1e-13 * ref
+    zero = dense_to_csr(np.zeros((6, 6)) + np.diag(np.zeros(6)))
+    assert oracle.power_lambda(zero, np.ones(6), iters) == 0.0
+    assert _power_unnormalised(np.zeros((6, 6)), np.ones(6), iters) == 0.0
