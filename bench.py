@@ -63,6 +63,8 @@ def parse():
                    help="anode,separator,cathode conductivity means for --theta-grid (default: the workload's)")
     p.add_argument("--profile-case", default=None, choices=["vcycle", "arnoldi", "spmv"],
                    help="run one small kernel case for an ncu capture and exit")
+    p.add_argument("--profile-precision", type=int, default=0, choices=[0, 1],
+                   help="hierarchy precision of --profile-case vcycle (0 FP64, 1 FP32)")
     return p.parse_args()
 
 
@@ -545,7 +547,7 @@ def profile_case(args):
             pass
         o = _B()
         o.rowptr, o.col, o.val = B.rowptr, B.col, B.val
-        s = bgs.Solver([[o]], [B.nrows], [0])
+        s = bgs.Solver([[o]], [B.nrows], [0], precision=args.profile_precision)
         s.setup()
         b = torch.from_numpy(system.b[:B.nrows].copy()).cuda()
         x = torch.zeros_like(b)
