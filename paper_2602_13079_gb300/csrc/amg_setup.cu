@@ -918,14 +918,22 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
         k_hash_rows<<<grid_for(n, 256), 256, 0, s>>>(n, cnt.p, ub.p, hashcnt.p);
         CK_LAUNCH();
         DBuf<int> flag((size_t)n, s);
-        const unsigned cls[3] = {0u, (unsigned)SG_SMALL_T, (unsigned)SG_NUM_T};
-        for (int c = 0; c < 2; c++) {
+        // rows by table size: up to 128 slots (8 blocks of 8 warps per SM fit the shared memory),
+        // up to SG_SMALL_T, up to SG_NUM_T; a row's table size follows from its own count, so the
+        // class only sets the shared memory reserved per warp
+        const unsigned cls[4] = {0u, 128u, (unsigned)SG_SMALL_T, (unsigned)SG_NUM_T};
+        for (int c = 0; c < 3; c++) {
             k_table_class<<<grid_for(n, 256), 256, 0, s>>>(n, hashcnt.p, ub.p, cls[c], cls[c + 1], flag.p);
             CK_LAUNCH();
             DBuf<int> rl;
             const int nb = collect_flag(n, flag.p, rl, sc, s);
             if (!nb) continue;
             if (c == 0) {
+                k_sg_num<128><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, kSMs * 32), SG_WARPS * 32,
+                                sizeof(double) * SG_WARPS * (128 + 64) + sizeof(int) * SG_WARPS * 128,
+                                s>>>(nb, rl.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
+                                     sc.flags.p + 8);
+            } else if (c == 1) {
                 k_sg_num<SG_SMALL_T><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, kSMs * 32), SG_WARPS * 32,
                                        sizeof(double) * SG_WARPS * (SG_SMALL_T + 64) +
                                            sizeof(int) * SG_WARPS * SG_SMALL_T,
