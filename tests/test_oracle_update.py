@@ -8,7 +8,6 @@ nonlinear iterations):
     operator equal the smoothing formula and a dense R A P built from the new values;
   * the updated solver still solves the new system."""
 import numpy as np
-import pytest
 
 import battery_system as bs
 import oracle
