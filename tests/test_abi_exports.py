@@ -38,4 +38,10 @@ def test_options_struct_matches_header_defaults():
     assert abs(o.theta[0] - 0.04) < 1e-15 and o.theta[1] == 0.0
     assert o.max_coarse == 500 and o.max_levels == 10 and o.filter_diag == 1 and o.reorth_eta == 0.01
     assert o.jacobi == 0
+    # the later options, as include/bgs.h documents their defaults
+    assert o.precision == 0 and o.graph == 1 and o.autotune == 1
+    assert o.cheb_ratio == 30.0 and abs(o.cheb_boost - 1.1) < 1e-15 and o.power_iters == 10
+    assert list(o.subsolver) == [0] * 8 and o.ilu_rows == 4096
+    assert o.ngroups == 0 and o.inner_restart == 30 and o.inner_maxit == 30 and o.inner_rtol == 1e-6
+    assert o.cheb_ellipse == 0
     assert bgs.status_string(3) == "no convergence within maxit"
