@@ -29,8 +29,8 @@ def build(force: bool = False) -> str:
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", _SRC,
-                               "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -99,6 +99,10 @@ def lib():
             L.or_transpose.argtypes = [P]
             L.or_spgemm.restype = P
             L.or_spgemm.argtypes = [P, P]
+            L.or_set_threads.restype = C.c_int
+            L.or_set_threads.argtypes = [C.c_int]
+            L.or_sum_prod.restype = C.c_double
+            L.or_sum_prod.argtypes = [C.c_int, f64p, f64p]
             L.or_fmix32.restype = C.c_uint32
             L.or_fmix32.argtypes = [C.c_uint32]
             L.or_strength_flags.argtypes = [P, C.c_double, u8p]
@@ -218,6 +222,20 @@ def transpose(A):
 def spgemm(A, B):
     ha, hb = _Handle(A), _Handle(B)
     return _from_c(lib().or_spgemm(ha.p, hb.p))
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads for the oracle's row loops (0 keeps the current count); returns the count in use.
+    Results do not depend on it."""
+    return int(lib().or_set_threads(int(n)))
+
+
+def sum_prod(a, b) -> float:
+    """sum_i a_i b_i in the oracle's fixed block order (blocks of 4096 terms left to right, then the
+    block sums left to right)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    return float(lib().or_sum_prod(int(a.size), a, b))
 
 
 def fmix32(x: int) -> int:

@@ -4,6 +4,9 @@
  * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the benchmark's
  * CPU-baseline leg, never by the library.  It shares no code with the CUDA path.
  * Compiled with -ffp-contract=off so that every product and sum is rounded on its own.
+ * Independent row loops run on the host's threads (OpenMP) without changing any row's
+ * arithmetic; whole-vector sums use the fixed block order of sum_prod below, so results do not
+ * depend on the number of threads.
  *
  * Readings of the paper (it configures a library and does not spell these out):
  *  - strength (Sec. 2.2.1 drop tolerance theta; Sec. 3.1.4 theta = 0.04): j is strong for
@@ -37,6 +40,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ST_OK 0
 #define ST_INVALID 1
@@ -44,6 +50,52 @@
 #define ST_BREAKDOWN 4
 #define ST_NANINF 5
 #define ST_ZEROPIV 6
+
+/* ------------------------------------------------------------------------------------ */
+/* Host threads and whole-vector sums                                                    */
+/* ------------------------------------------------------------------------------------ */
+/* Loops whose iterations are independent rows (each row's arithmetic written once, in stored
+ * order) may run on several host threads; a row's result is the same on any thread, so nothing
+ * depends on the thread count.  A sum over a whole vector is the one place where the order of
+ * the additions is a choice (the method states inner products and norms, not their summation
+ * order): it is taken in consecutive blocks of OR_SUM_BLOCK terms, each block added left to
+ * right, then the block sums left to right.  That order is fixed by n alone; for n up to
+ * OR_SUM_BLOCK it is the plain left-to-right sum. */
+#define OR_SUM_BLOCK 4096
+
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* sum_i a_i b_i in the fixed block order above */
+static double sum_prod(int n, const double *a, const double *b) {
+    int nb = (n + OR_SUM_BLOCK - 1) / OR_SUM_BLOCK;
+    if (nb <= 1) {
+        double s = 0.0;
+        for (int i = 0; i < n; i++) s += a[i] * b[i];
+        return s;
+    }
+    double *part = (double *)malloc(sizeof(double) * (size_t)nb);
+#pragma omp parallel for schedule(static)
+    for (int q = 0; q < nb; q++) {
+        int lo = q * OR_SUM_BLOCK, hi = lo + OR_SUM_BLOCK < n ? lo + OR_SUM_BLOCK : n;
+        double s = 0.0;
+        for (int i = lo; i < hi; i++) s += a[i] * b[i];
+        part[q] = s;
+    }
+    double s = 0.0;
+    for (int q = 0; q < nb; q++) s += part[q];
+    free(part);
+    return s;
+}
+
+double or_sum_prod(int n, const double *a, const double *b) { return sum_prod(n, a, b); }
 
 /* ------------------------------------------------------------------------------------ */
 /* CSR helpers                                                                           */
@@ -90,6 +142,7 @@ void or_csr_copy(const or_csr *A, int *rp, int *ci, double *v) {
 
 /* y = A x, each row summed in stored order */
 void or_spmv(const or_csr *A, const double *x, double *y) {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < A->n; i++) {
         double s = 0.0;
         for (int e = A->rp[i]; e < A->rp[i + 1]; e++) s += A->v[e] * x[A->ci[e]];
@@ -118,65 +171,76 @@ or_csr *or_transpose(const or_csr *A) {
  * acc[j] += a_ik * b_kj.  Every structural entry is kept; columns sorted. */
 or_csr *or_spgemm(const or_csr *A, const or_csr *B) {
     int n = A->n, m = B->m;
-    int *mark = (int *)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
-    double *acc = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
-    int *cols = (int *)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
-    for (int j = 0; j < m; j++) mark[j] = -1;
-    /* pass 1: count */
+    size_t mm = (size_t)(m > 0 ? m : 1);
+    /* pass 1: count (each thread marks the columns of its own rows) */
     int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
-    for (int i = 0; i < n; i++) {
-        int c = 0;
-        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) {
-            int k = A->ci[e];
-            for (int f = B->rp[k]; f < B->rp[k + 1]; f++) {
-                int j = B->ci[f];
-                if (mark[j] != i) {
-                    mark[j] = i;
-                    c++;
+#pragma omp parallel
+    {
+        int *mark = (int *)malloc(sizeof(int) * mm);
+        for (int j = 0; j < m; j++) mark[j] = -1;
+#pragma omp for schedule(dynamic, 256)
+        for (int i = 0; i < n; i++) {
+            int c = 0;
+            for (int e = A->rp[i]; e < A->rp[i + 1]; e++) {
+                int k = A->ci[e];
+                for (int f = B->rp[k]; f < B->rp[k + 1]; f++) {
+                    int j = B->ci[f];
+                    if (mark[j] != i) {
+                        mark[j] = i;
+                        c++;
+                    }
                 }
             }
+            cnt[i + 1] = c;
         }
-        cnt[i + 1] = c;
+        free(mark);
     }
     for (int i = 0; i < n; i++) cnt[i + 1] += cnt[i];
     or_csr *C = or_csr_new(n, m, cnt[n]);
     memcpy(C->rp, cnt, sizeof(int) * ((size_t)n + 1));
     free(cnt);
-    for (int j = 0; j < m; j++) mark[j] = -1;
     /* pass 2: accumulate in order, then emit sorted */
-    for (int i = 0; i < n; i++) {
-        int c = 0;
-        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) {
-            int k = A->ci[e];
-            double a = A->v[e];
-            for (int f = B->rp[k]; f < B->rp[k + 1]; f++) {
-                int j = B->ci[f];
-                if (mark[j] != i) {
-                    mark[j] = i;
-                    acc[j] = 0.0;
-                    cols[c++] = j;
+#pragma omp parallel
+    {
+        int *mark = (int *)malloc(sizeof(int) * mm);
+        double *acc = (double *)malloc(sizeof(double) * mm);
+        int *cols = (int *)malloc(sizeof(int) * mm);
+        for (int j = 0; j < m; j++) mark[j] = -1;
+#pragma omp for schedule(dynamic, 256)
+        for (int i = 0; i < n; i++) {
+            int c = 0;
+            for (int e = A->rp[i]; e < A->rp[i + 1]; e++) {
+                int k = A->ci[e];
+                double a = A->v[e];
+                for (int f = B->rp[k]; f < B->rp[k + 1]; f++) {
+                    int j = B->ci[f];
+                    if (mark[j] != i) {
+                        mark[j] = i;
+                        acc[j] = 0.0;
+                        cols[c++] = j;
+                    }
+                    acc[j] += a * B->v[f];
                 }
-                acc[j] += a * B->v[f];
+            }
+            /* insertion sort of the (short) column list */
+            for (int p = 1; p < c; p++) {
+                int key = cols[p], q = p - 1;
+                while (q >= 0 && cols[q] > key) {
+                    cols[q + 1] = cols[q];
+                    q--;
+                }
+                cols[q + 1] = key;
+            }
+            int base = C->rp[i];
+            for (int p = 0; p < c; p++) {
+                C->ci[base + p] = cols[p];
+                C->v[base + p] = acc[cols[p]];
             }
         }
-        /* insertion sort of the (short) column list */
-        for (int p = 1; p < c; p++) {
-            int key = cols[p], q = p - 1;
-            while (q >= 0 && cols[q] > key) {
-                cols[q + 1] = cols[q];
-                q--;
-            }
-            cols[q + 1] = key;
-        }
-        int base = C->rp[i];
-        for (int p = 0; p < c; p++) {
-            C->ci[base + p] = cols[p];
-            C->v[base + p] = acc[cols[p]];
-        }
+        free(mark);
+        free(acc);
+        free(cols);
     }
-    free(mark);
-    free(acc);
-    free(cols);
     return C;
 }
 
@@ -204,6 +268,7 @@ uint32_t or_fmix32(uint32_t h) {
 /* strong[e] for each stored entry e of A: off-diagonal and passes the symmetric test */
 void or_strength_flags(const or_csr *A, double theta, unsigned char *strong) {
     double t2 = theta * theta;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < A->n; i++) {
         double aii = diag_of(A, i);
         for (int e = A->rp[i]; e < A->rp[i + 1]; e++) {
@@ -227,19 +292,27 @@ or_csr *or_strength_graph(const or_csr *A, const unsigned char *strong) {
     int ns = 0;
     for (int e = 0; e < A->nnz; e++) ns += strong[e];
     or_csr *SA = or_csr_new(n, n, ns);
-    int p = 0;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) {
+        int c = 0;
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) c += strong[e];
+        SA->rp[i + 1] = c;
+    }
+    for (int i = 0; i < n; i++) SA->rp[i + 1] += SA->rp[i];
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; i++) {
+        int p = SA->rp[i];
         for (int e = A->rp[i]; e < A->rp[i + 1]; e++)
             if (strong[e]) {
                 SA->ci[p] = A->ci[e];
                 SA->v[p] = A->v[e];
                 p++;
             }
-        SA->rp[i + 1] = p;
     }
     or_csr *ST = or_transpose(SA);
     /* union of row i of S_A and row i of S_A^T */
     int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) {
         int a = SA->rp[i], ae = SA->rp[i + 1], b = ST->rp[i], be = ST->rp[i + 1], c = 0;
         while (a < ae || b < be) {
@@ -254,6 +327,7 @@ or_csr *or_strength_graph(const or_csr *A, const unsigned char *strong) {
     or_csr *S = or_csr_new(n, n, cnt[n]);
     memcpy(S->rp, cnt, sizeof(int) * ((size_t)n + 1));
     free(cnt);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) {
         int a = SA->rp[i], ae = SA->rp[i + 1], b = ST->rp[i], be = ST->rp[i + 1], q = S->rp[i];
         while (a < ae || b < be) {
@@ -297,6 +371,7 @@ int or_mis2(const or_csr *S, uint32_t salt, int *state) {
     while (undecided > 0) {
         rounds++;
         /* (i) by definition: scan the distance-2 ball of each undecided node */
+#pragma omp parallel for schedule(static)
         for (int v = 0; v < n; v++) {
             newin[v] = 0;
             if (state[v] != 0) continue;
@@ -312,9 +387,11 @@ int or_mis2(const or_csr *S, uint32_t salt, int *state) {
             }
             newin[v] = ok;
         }
+#pragma omp parallel for schedule(static)
         for (int v = 0; v < n; v++)
             if (newin[v]) state[v] = 1;
         /* (ii) undecided nodes within distance 2 of a root leave */
+#pragma omp parallel for schedule(static)
         for (int v = 0; v < n; v++) {
             if (state[v] != 0) continue;
             int near = 0;
@@ -327,6 +404,7 @@ int or_mis2(const or_csr *S, uint32_t salt, int *state) {
             newin[v] = near;
         }
         undecided = 0;
+#pragma omp parallel for schedule(static) reduction(+ : undecided)
         for (int v = 0; v < n; v++) {
             if (state[v] == 0 && newin[v]) state[v] = 2;
             if (state[v] == 0) undecided++;
@@ -345,6 +423,7 @@ int or_aggregate(const or_csr *S, const int *state, int *agg) {
     int nagg = 0;
     for (int i = 0; i < n; i++) rootid[i] = (state[i] == 1) ? nagg++ : -1;
     int *ph1 = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) {
         ph1[i] = -1;
         if (state[i] == 1) {
@@ -357,6 +436,7 @@ int or_aggregate(const or_csr *S, const int *state, int *agg) {
         }
     }
     int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
     for (int i = 0; i < n; i++) {
         if (ph1[i] >= 0) {
             agg[i] = ph1[i];
@@ -383,6 +463,7 @@ int or_aggregate(const or_csr *S, const int *state, int *agg) {
 
 /* Filtered matrix values vF (pattern of A) and its smoothing diagonal dF. */
 void or_filter(const or_csr *A, const unsigned char *strong, int filter_diag, double *vF, double *dF) {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < A->n; i++) {
         double lump = 0.0;
         int dpos = -1;
@@ -426,24 +507,22 @@ double or_power_lambda(const or_csr *A, const double *dinv, int iters) {
     int n = A->n;
     double *v = (double *)malloc(sizeof(double) * (size_t)n);
     double *w = (double *)malloc(sizeof(double) * (size_t)n);
-    double nv = 0.0;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) {
         uint32_t u = or_fmix32((uint32_t)i ^ 0x7F4A7C15u) >> 8;
         v[i] = ((double)u + 0.5) / 16777216.0;
-        nv += v[i] * v[i];
     }
-    nv = sqrt(nv);
+    double nv = sqrt(sum_prod(n, v, v));
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) v[i] = v[i] / nv;
     double lam = 0.0;
     for (int it = 0; it < iters; it++) {
         or_spmv(A, v, w);
-        double s = 0.0;
-        for (int i = 0; i < n; i++) {
-            w[i] = dinv[i] * w[i];
-            s += w[i] * w[i];
-        }
-        lam = sqrt(s);
+#pragma omp parallel for schedule(static)
+        for (int i = 0; i < n; i++) w[i] = dinv[i] * w[i];
+        lam = sqrt(sum_prod(n, w, w));
         if (lam == 0.0) break;
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; i++) v[i] = w[i] / lam;
     }
     free(v);
@@ -462,6 +541,7 @@ or_csr *or_smooth_prolongator(const or_csr *AF, const double *dinvF, const int *
         Pt->v[i] = 1.0;
     }
     or_csr *S = or_spgemm(AF, Pt);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) {
         double c = omega * dinvF[i];
         for (int e = S->rp[i]; e < S->rp[i + 1]; e++) {
@@ -486,11 +566,14 @@ void or_chebyshev(const or_csr *A, const double *dinv, double lmin, double lmax,
     double *d = (double *)malloc(sizeof(double) * (size_t)n);
     double inv_theta = 1.0 / theta;
     if (x_is_zero) {
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; i++) r[i] = b[i];
     } else {
         or_spmv(A, x, r);
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
     }
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) {
         d[i] = inv_theta * (dinv[i] * r[i]);
         x[i] = (x_is_zero ? 0.0 : x[i]) + d[i];
@@ -499,6 +582,7 @@ void or_chebyshev(const or_csr *A, const double *dinv, double lmin, double lmax,
         double rho_new = 1.0 / (2.0 * sigma - rho);
         double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
         or_spmv(A, x, r);
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; i++) {
             double ri = b[i] - r[i];
             d[i] = c1 * d[i] + c2 * (dinv[i] * ri);
@@ -535,32 +619,32 @@ double or_skew_radius(const or_csr *A, int iters) {
     double *p = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *q = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *u = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    double nv = 0.0;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) {
         uint32_t h = or_fmix32((uint32_t)i ^ 0x7F4A7C15u) >> 8;
         v[i] = ((double)h + 0.5) / 16777216.0;
-        nv += v[i] * v[i];
     }
-    nv = sqrt(nv);
+    double nv = sqrt(sum_prod(n, v, v));
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) v[i] = v[i] / nv;
     double lam = 0.0;
     for (int it = 0; it < iters; it++) {
         /* u = S v, then w = -S u; S x = (s .* (A (s .* x)) - s .* (A^T (s .* x))) / 2 */
         for (int pass = 0; pass < 2; pass++) {
             const double *in = pass == 0 ? v : u;
+#pragma omp parallel for schedule(static)
             for (int i = 0; i < n; i++) t[i] = sc[i] * in[i];
             or_spmv(A, t, p);
             or_spmv(AT, t, q);
             double *out = pass == 0 ? u : t;
+#pragma omp parallel for schedule(static)
             for (int i = 0; i < n; i++) out[i] = 0.5 * (sc[i] * p[i] - sc[i] * q[i]);
         }
-        double s = 0.0;
-        for (int i = 0; i < n; i++) {
-            t[i] = -t[i];
-            s += t[i] * t[i];
-        }
-        lam = sqrt(s);
+#pragma omp parallel for schedule(static)
+        for (int i = 0; i < n; i++) t[i] = -t[i];
+        lam = sqrt(sum_prod(n, t, t));
         if (lam == 0.0) break;
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; i++) v[i] = t[i] / lam;
     }
     or_csr_free(AT);
@@ -588,11 +672,14 @@ void or_chebyshev_ellipse(const or_csr *A, const double *dinv, double theta, dou
     double *d = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double tau = 1.0 / theta;
     if (x_is_zero) {
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; i++) r[i] = b[i];
     } else {
         or_spmv(A, x, r);
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
     }
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) {
         d[i] = tau * (dinv[i] * r[i]);
         x[i] = (x_is_zero ? 0.0 : x[i]) + d[i];
@@ -601,6 +688,7 @@ void or_chebyshev_ellipse(const or_csr *A, const double *dinv, double theta, dou
         double tau_new = 1.0 / (2.0 * theta - c2 * tau);
         double c1 = c2 * tau_new * tau, cc = 2.0 * tau_new;
         or_spmv(A, x, r);
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; i++) {
             double ri = b[i] - r[i];
             d[i] = c1 * d[i] + cc * (dinv[i] * ri);
@@ -697,19 +785,26 @@ static void level_numeric(or_amg *h, int l, const unsigned char *strong, const o
     or_filter(A, strong, opt->filter_diag, vF, dF);
     /* A_F as its own matrix: the dropped entries leave the pattern (they would only add
      * structural zeros to P and to the coarse operators) */
-    int nf = 0;
-    for (int i = 0; i < n; i++)
-        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) nf += (A->ci[e] == i) || strong[e];
-    or_csr *AF = or_csr_new(n, n, nf);
-    nf = 0;
+    int *len = (int *)calloc((size_t)n + 1, sizeof(int));
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) {
+        int c = 0;
+        for (int e = A->rp[i]; e < A->rp[i + 1]; e++) c += (A->ci[e] == i) || strong[e];
+        len[i + 1] = c;
+    }
+    for (int i = 0; i < n; i++) len[i + 1] += len[i];
+    or_csr *AF = or_csr_new(n, n, len[n]);
+    memcpy(AF->rp, len, sizeof(int) * ((size_t)n + 1));
+    free(len);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; i++) {
+        int q = AF->rp[i];
         for (int e = A->rp[i]; e < A->rp[i + 1]; e++)
             if (A->ci[e] == i || strong[e]) {
-                AF->ci[nf] = A->ci[e];
-                AF->v[nf] = vF[e];
-                nf++;
+                AF->ci[q] = A->ci[e];
+                AF->v[q] = vF[e];
+                q++;
             }
-        AF->rp[i + 1] = nf;
     }
     double *dinvF = (double *)malloc(sizeof(double) * (size_t)n);
     /* a row whose filtered entries lump to zero (all its connections weak and a zero row sum)
@@ -741,6 +836,7 @@ static void smoothers_and_lu(or_amg *h, const or_options *opt) {
         or_csr *A = h->A[k];
         free(h->dinv[k]);
         h->dinv[k] = (double *)malloc(sizeof(double) * (size_t)A->n);
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < A->n; i++) h->dinv[k][i] = 1.0 / diag_of(A, i);
         double lam = or_power_lambda(A, h->dinv[k], opt->power_iters);
         h->lmax[k] = opt->cheb_boost * lam;
@@ -862,12 +958,14 @@ static void vcycle_level(const or_amg *h, int l, const double *b, double *x, int
     cheb_level(h, l, A, b, x, 1);
     double *r = (double *)malloc(sizeof(double) * (size_t)n);
     or_spmv(A, x, r);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
     double *bc = (double *)malloc(sizeof(double) * (size_t)nc);
     double *xc = (double *)malloc(sizeof(double) * (size_t)nc);
     or_spmv(h->R[l], r, bc);
     vcycle_level(h, l + 1, bc, xc, transposed, AT);
     or_spmv(h->P[l], xc, r);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) x[i] += r[i];
     cheb_level(h, l, A, b, x, 0);
     free(r);
@@ -1051,9 +1149,23 @@ or_bgs *or_bgs_create(int F, const int *sizes, const int *const *rps, const int 
     for (int b = 0; b < F * F; b++)
         if (h->blk[b]) nnz += h->blk[b]->nnz;
     or_csr *A = or_csr_new(n, n, (int)nnz);
-    int q = 0;
-    for (int r = 0; r < F; r++)
+    /* row lengths, their running sum, then every row's entries (rows independent) */
+    for (int r = 0; r < F; r++) {
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < sizes[r]; i++) {
+            int len = 0;
+            for (int c = 0; c < F; c++) {
+                or_csr *B = h->blk[r * F + c];
+                if (B) len += B->rp[i + 1] - B->rp[i];
+            }
+            A->rp[h->offs[r] + i + 1] = len;
+        }
+    }
+    for (int i = 0; i < n; i++) A->rp[i + 1] += A->rp[i];
+    for (int r = 0; r < F; r++) {
+#pragma omp parallel for schedule(static)
+        for (int i = 0; i < sizes[r]; i++) {
+            int q = A->rp[h->offs[r] + i];
             for (int c = 0; c < F; c++) {
                 or_csr *B = h->blk[r * F + c];
                 if (!B) continue;
@@ -1063,33 +1175,45 @@ or_bgs *or_bgs_create(int F, const int *sizes, const int *const *rps, const int 
                     q++;
                 }
             }
-            A->rp[h->offs[r] + i + 1] = q;
         }
+    }
     h->full = A;
     return h;
 }
 
 int or_bgs_setup(or_bgs *h) {
+    int st[8] = {0};
+    /* the diagonal blocks are independent: each is set up on its own share of the host threads */
+#ifdef _OPENMP
+    int T = omp_get_max_threads(), outer = T < h->F ? T : h->F, inner = T / (outer > 0 ? outer : 1);
+    omp_set_max_active_levels(2);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(outer > 0 ? outer : 1)
+#endif
     for (int k = 0; k < h->F; k++) {
+#ifdef _OPENMP
+        omp_set_num_threads(inner > 0 ? inner : 1);
+#endif
         or_csr *Akk = h->blk[k * h->F + k];
         if (h->opt.subsolver[k] == 2) {   /* the block's diagonal: exact for a diagonal block */
             int nk = h->sizes[k];
             h->dgs[k] = (double *)malloc(sizeof(double) * (size_t)(nk > 0 ? nk : 1));
             for (int i = 0; i < nk; i++) {
                 double d = diag_of(Akk, i);
-                if (d == 0.0) h->status = ST_ZEROPIV;
+                if (d == 0.0) st[k] = ST_ZEROPIV;
                 h->dgs[k][i] = 1.0 / d;
             }
             continue;
         }
         if (h->opt.subsolver[k] == 1) {   /* DD(0)-ILU(0) */
             h->ilu[k] = or_ilu_setup(Akk, h->opt.ilu_rows);
-            if (h->ilu[k]->status) h->status = h->ilu[k]->status;
+            st[k] = h->ilu[k]->status;
             continue;
         }
         h->amg[k] = or_amg_setup(Akk, h->opt.theta[k], h->opt.cheb_degree[k], &h->opt);
-        if (h->amg[k]->status) h->status = h->amg[k]->status;
+        st[k] = h->amg[k]->status;
     }
+    for (int k = 0; k < h->F; k++)
+        if (st[k]) h->status = st[k];
     return h->status;
 }
 
@@ -1144,6 +1268,7 @@ void or_full_spmv(const or_bgs *h, const double *x, double *y) { or_spmv(h->full
  * transposed; the transposed ILU sweep). */
 static void block_solve(const or_bgs *h, int k, const double *r, double *z, int transposed) {
     if (h->dgs[k]) {   /* diagonal solve (its own transpose) */
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < h->sizes[k]; i++) z[i] = h->dgs[k][i] * r[i];
         return;
     }
@@ -1169,6 +1294,7 @@ static void sub_coupling(const or_bgs *h, int k, int j, const double *zj, double
     if (!transposed) {
         or_csr *B = h->blk[k * F + j];
         if (!B) return;
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < B->n; i++) {
             double t = 0.0;
             for (int e = B->rp[i]; e < B->rp[i + 1]; e++) t += B->v[e] * zj[B->ci[e]];
@@ -1191,6 +1317,7 @@ static void sweep_range(const or_bgs *h, int p0, int p1, int base, const double 
         int k = h->order[p];
         int nk = h->sizes[k];
         double *r = (double *)malloc(sizeof(double) * (size_t)nk);
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < nk; i++) r[i] = v[h->offs[k] - base + i];
         if (!h->opt.jacobi) {
             if (!transposed)
@@ -1285,15 +1412,12 @@ void or_bgs_apply_adjoint(const or_bgs *h, const double *v, double *z) {
 /* ------------------------------------------------------------------------------------ */
 /* Flexible GMRES(m), right preconditioned, modified Gram-Schmidt                        */
 /* ------------------------------------------------------------------------------------ */
-static double nrm2(int n, const double *x) {
-    double s = 0.0;
-    for (int i = 0; i < n; i++) s += x[i] * x[i];
-    return sqrt(s);
-}
+static double nrm2(int n, const double *x) { return sqrt(sum_prod(n, x, x)); }
 
 int or_fgmres(int n, or_apply_fn amul, void *actx, or_apply_fn prec, void *pctx, const double *b, double *x,
               int m, int maxit, double rtol, or_info *info) {
     memset(info, 0, sizeof(*info));
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) x[i] = 0.0;
     double bnorm = nrm2(n, b);
     if (bnorm == 0.0) {
@@ -1313,11 +1437,13 @@ int or_fgmres(int n, or_apply_fn amul, void *actx, or_apply_fn prec, void *pctx,
     double *sn = (double *)malloc(sizeof(double) * (size_t)m);
     double *g = (double *)malloc(sizeof(double) * (size_t)(m + 1));
     double *y = (double *)malloc(sizeof(double) * (size_t)m);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) r[i] = b[i];
     double beta = bnorm;
     int it = 0, status = ST_NOCONV;
     double rel = 1.0, est = 1.0;
     for (;;) {
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; i++) Vb[i] = r[i] / beta;
         for (int k = 0; k <= m; k++) g[k] = 0.0;
         g[0] = beta;
@@ -1328,17 +1454,19 @@ int or_fgmres(int n, or_apply_fn amul, void *actx, or_apply_fn prec, void *pctx,
             amul(actx, zj, w);
             for (int i = 0; i <= j; i++) {
                 double *vi = Vb + (size_t)i * n;
-                double hij = 0.0;
-                for (int t = 0; t < n; t++) hij += w[t] * vi[t];
+                double hij = sum_prod(n, w, vi);
                 H[(size_t)i * m + j] = hij;
+#pragma omp parallel for schedule(static)
                 for (int t = 0; t < n; t++) w[t] -= hij * vi[t];
             }
             double hn = nrm2(n, w);
             H[(size_t)(j + 1) * m + j] = hn;
             it++;
             if (hn == 0.0) breakdown = 1;
-            else
+            else {
+#pragma omp parallel for schedule(static)
                 for (int t = 0; t < n; t++) Vb[(size_t)(j + 1) * n + t] = w[t] / hn;
+            }
             for (int i = 0; i < j; i++) {
                 double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
                 H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
@@ -1369,9 +1497,12 @@ int or_fgmres(int n, or_apply_fn amul, void *actx, or_apply_fn prec, void *pctx,
             for (int k = i + 1; k < jend; k++) s -= H[(size_t)i * m + k] * y[k];
             y[i] = s / H[(size_t)i * m + i];
         }
-        for (int k = 0; k < jend; k++)
-            for (int t = 0; t < n; t++) x[t] += y[k] * Zb[(size_t)k * n + t];
+        /* x_t += y_k z_k,t for k = 0, 1, ... in that order for every entry t */
+#pragma omp parallel for schedule(static)
+        for (int t = 0; t < n; t++)
+            for (int k = 0; k < jend; k++) x[t] += y[k] * Zb[(size_t)k * n + t];
         amul(actx, x, r);
+#pragma omp parallel for schedule(static)
         for (int t = 0; t < n; t++) r[t] = b[t] - r[t];
         beta = nrm2(n, r);
         rel = beta / bnorm;
@@ -1435,6 +1566,7 @@ int or_bgs_solve_adjoint(const or_bgs *h, const double *g, double *lam, or_info 
 
 /* dL/da_ij = -lambda_i x_j on the pattern of block A (row offset roff, column offset coff) */
 void or_grad_values(const or_csr *A, int roff, int coff, const double *lam, const double *x, double *g) {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < A->n; i++)
         for (int e = A->rp[i]; e < A->rp[i + 1]; e++) g[e] = -(lam[roff + i] * x[coff + A->ci[e]]);
 }

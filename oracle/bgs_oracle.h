@@ -3,8 +3,11 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA library: only the
  * tests, the smoke check and the benchmark's CPU-baseline leg load it.  It shares no
- * header, helper or kernel with the CUDA path.  Everything is single-threaded,
- * unblocked and in the order the method states it (compiled with -ffp-contract=off).
+ * header, helper or kernel with the CUDA path.  Everything is unblocked and in the order
+ * the method states it (compiled with -ffp-contract=off).  Loops over independent rows may
+ * run on several host threads (each row's arithmetic is unchanged); sums over whole vectors
+ * (inner products, norms) are taken in consecutive blocks of 4096 terms, each block left to
+ * right, then the block sums left to right, so no result depends on the thread count.
  *
  * What each part follows (paper sections and equations):
  *   strength / filter / aggregation / prolongator / Galerkin RAP  - Sec. 2.2.1, Eq. galerkin
@@ -58,6 +61,11 @@ typedef struct {
     double rel_true_resid;
     double rel_est_resid;
 } or_info;
+
+/* host threads for the row loops (n <= 0: keep); returns the count in use */
+int or_set_threads(int n);
+/* sum_i a_i b_i in the fixed block order every whole-vector sum of the oracle uses */
+double or_sum_prod(int n, const double *a, const double *b);
 
 #define OR_MAX_LEVELS 16
 
