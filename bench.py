@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--config", default=WORKLOAD)
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-c5", action="store_true", help="skip the 160x160x400 (51.2M DOFs) measurement")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-profile", action="store_true")
     p.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler")
@@ -168,38 +169,53 @@ def workload_desc(name):
     return f"{name}: {c['dim']}D {dims} {kind}, 5 fields (phi_s, phi_e, p, c1, c2)"
 
 
-def oracle_sample(seed, target="C4"):
-    """The FP64 oracle's setup+solve on the 3D 64^3 system (1.31M DOFs), single-threaded; returns
-    (seconds, seconds scaled by DOFs to the target workload, iterations, converged)."""
-    import battery_system as bs
+def workload_line(name, system, seed):
+    return workload_desc(name) + f", {system.ndof} DOFs, {system.nnz} nnz, seed {seed}"
+
+
+def oracle_threads():
     import oracle
-    system = bs.assemble("C2", seed=seed)
+    return oracle.set_threads(0)
+
+
+def oracle_step(system):
+    """One complete FP64 oracle create + setup + solve of the system on the host's threads (the
+    oracle's row loops run in parallel; its results do not depend on the thread count).  Returns
+    (seconds, x, info)."""
+    import oracle
     t0 = time.perf_counter()
     o = oracle.bgs_for_system(system)
     x, info = o.solve(system.b)
     dt = time.perf_counter() - t0
-    scale = workload_dofs(target) / system.ndof
-    return dt, dt * scale, info.iters, bool(info.converged)
+    del o
+    return dt, x, info
 
 
 def reference_arm(args, rank, world):
+    """The oracle on the same workload, metric and unit as the GPU arm: every step (warm-up or
+    timed) is one complete create + setup + solve of the 128^3 system on the host's threads."""
     if rank != 0:
         return
-    times = []
+    import battery_system as bs
+    import oracle
+    oracle.build()
+    system = bs.assemble(args.config, seed=args.seed)
+    threads = oracle_threads()
     for _ in range(args.warmup):
-        oracle_sample(args.seed, args.config)
+        oracle_step(system)
+    times, iters = [], None
     for _ in range(args.steps):
-        dt, scaled, iters, conv = oracle_sample(args.seed, args.config)
-        times.append(scaled)
+        dt, x, info = oracle_step(system)
+        times.append(dt)
+        iters = info.iters
     v = statistics.mean(times)
+    sample = (f"one complete oracle create+setup+solve of the {args.config} system per step on {threads} host "
+              f"threads ({iters} iterations, rtol 1e-8); mean of {args.steps} steps")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded layered battery system)",
-            "config": {"workload": workload_desc(args.config) + f", {workload_dofs(args.config)} DOFs "
-                                   "(projected from the 64^3 sample)", "parallelism": "replicas"},
-            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": f"oracle setup+solve on 3D 64^3 (1.31M DOFs, seed {args.seed}), scaled by "
-                                       f"DOFs x{workload_dofs(args.config) / 1310720:.1f}"},
+            "config": {"workload": workload_line(args.config, system, args.seed), "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -458,6 +474,47 @@ def gpu_arm(args, rank, world):
                "median_ms": dict(zip(("create", "setup", "solve", "close"), (round(v, 2) for v in split))),
                "steps_ms": [[round(v * 1e3, 2) for v in p] for p in phases]}
 
+    # the largest workload (160x160x400 pellet stack, 51.2M DOFs): FP64 and mixed, one warm-up and
+    # two timed steps each (CUDA events), clocks sampled over its own timed region
+    c5 = None
+    if not args.no_c5 and args.config == WORKLOAD:
+        del blocks, b, x
+        if not args.no_e2e:
+            del hblocks, bh, xh
+        torch.cuda.synchronize()
+        sys5 = bs.assemble("C5", seed=args.seed)
+        blocks5, _ = device_blocks(sys5, torch)
+        b5 = torch.from_numpy(sys5.b).cuda()
+        x5 = torch.zeros_like(b5)
+        torch.cuda.synchronize()
+
+        def step5(precision):
+            g5 = bgs.Solver(blocks5, sys5.field_sizes, order, precision=precision, **extra)
+            g5.setup()
+            info = g5.bgs_solve(b5, x5)
+            g5.close()
+            return info
+
+        clk5 = None if args.no_clocks else Clocks(local)
+        c5 = {"workload": workload_line("C5", sys5, args.seed), "steps": 2, "warmup": 1}
+        for name, precision in (("fp64", 0), ("mixed", 1)):
+            step5(precision)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos = [step5(precision) for _ in range(2)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = allmax(e0.elapsed_time(e1) / 2)
+            xs5 = x5.cpu().numpy()
+            rel = float(np.linalg.norm(sys5.b - sys5.matvec(xs5)) / np.linalg.norm(sys5.b))
+            c5[name] = {"s_per_step": ms / 1e3, "setup_s": statistics.mean(k.t_setup_ms for k in infos) / 1e3,
+                        "solve_s": statistics.mean(k.t_solve_ms for k in infos) / 1e3, "iters": infos[-1].iters,
+                        "converged": bool(infos[-1].converged), "rel_true_resid_host_check": rel}
+        c5["mixed_speedup_vs_fp64"] = c5["fp64"]["s_per_step"] / c5["mixed"]["s_per_step"]
+        c5["clocks"] = clk5.stop() if clk5 else None
+        del blocks5, b5, x5, sys5
+
     peak, peak_kind = measured_peaks()
     roof = None
     if prof:
@@ -488,18 +545,25 @@ def gpu_arm(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, scaled, iters, conv = oracle_sample(args.seed, args.config)
-        cpu = {"value": scaled, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"oracle setup+solve on 3D 64^3 (1.31M DOFs, seed {args.seed}) took {dt:.1f} s "
-                         f"({iters} iterations), scaled by DOFs x{workload_dofs(args.config) / 1310720:.1f}"}
+        # one complete oracle run of the same system on the host's threads; its solution also gives
+        # the error of both GPU forms against the FP64 oracle
+        threads = oracle_threads()
+        dt, xo, io = oracle_step(system)
+        cpu = {"value": dt, "unit": "s", "cores": threads, "kind": "oracle",
+               "sample": f"one complete oracle create+setup+solve of the same {args.config} system "
+                         f"({io.iters} iterations) on {threads} host threads"}
+        on = np.linalg.norm(xo)
+        arm64["rel_err_vs_oracle"] = float(np.linalg.norm(x64 - xo) / on)
+        if armmx is not None:
+            armmx["rel_err_vs_oracle"] = float(np.linalg.norm(xmx - xo) / on)
+        del xo
 
     if rank == 0:
         v = ms64 / 1e3
         line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded layered battery system)",
-                "config": {"workload": workload_desc(args.config) + f", {system.ndof} DOFs, {system.nnz} nnz, "
-                                                                  f"seed {args.seed}",
+                "config": {"workload": workload_line(args.config, system, args.seed),
                            "order": "[phi_s, phi_e] -> p -> [c1, c2]", "rtol": 1e-8, "restart": 50,
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": f"inputs larger than L2 (matrix {system.nnz * 12 / 1e9:.1f} GB)",
@@ -513,7 +577,7 @@ def gpu_arm(args, rank, world):
                 "solves_per_s": world / (ms64 / 1e3),
                 "gpu_launches": int(launches64 // max(args.steps, 1)) * args.steps,
                 "gpu_launches_per_step": int(launches64 // max(args.steps, 1)),
-                "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}
+                "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "c5": c5}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -114,6 +114,8 @@ typedef struct {
     double rel_est_resid;   /* last Arnoldi residual estimate */
     double t_setup_ms;      /* wall time of the last bgs_setup or bgs_update_values */
     double t_solve_ms;      /* this solve's wall time */
+    int nlevels[8];         /* hierarchy levels per field id (1 for a field on DD(0)-ILU(0) or the diagonal
+                               solve); entries past nfields are 0 */
 } bgs_info;
 
 /* Fills *opt with the defaults listed above. */
@@ -162,6 +164,11 @@ int bgs_solve_adjoint(bgs_handle h, const double *g, double *lambda, bgs_info *i
 int bgs_grad_values(bgs_handle h, int row_field, int col_field, const double *lambda, const double *x,
                     double *dvals);
 
+/* The same gradient for every stored block at once: dvals[r*F + c] receives nnz(r, c) values for block
+ * (r, c) (device pointers; NULL skips that block, and zero blocks are skipped).  lambda, x: device,
+ * full length. */
+int bgs_grad_values_all(bgs_handle h, const double *lambda, const double *x, double *const *dvals);
+
 /* One application of the preconditioner z = M^-1 v (device pointers, full length): the block sweep,
  * or with ngroups > 0 the nested preconditioner (inner FGMRES solves per group). */
 int bgs_apply_preconditioner(bgs_handle h, const double *v, double *z);
@@ -192,6 +199,10 @@ int bgs_ilu_factors(bgs_handle h, int field, int64_t *nnz, int32_t *rowptr, int3
 int bgs_level_format(bgs_handle h, int field, int level, int which, int *format);
 /* Aggregate id of every node of level `level` (host array of rows(level) entries). */
 int bgs_level_aggregates(bgs_handle h, int field, int level, int32_t *agg);
+/* Strength decision of every stored entry of A_l (Sec. 2.2.1 drop tolerance: 1 strong, 0 weak or the
+ * diagonal), in CSR order, from the aggregation attempt that was kept (host array of nnz(A_l) bytes;
+ * levels below the coarsest). */
+int bgs_level_strength(bgs_handle h, int field, int level, uint8_t *strong);
 
 /* Per-kernel-class timing of the last solve when enabled (bgs_set_profiling(h, 1)): launches,
  * summed CUDA-event milliseconds and algorithmic bytes.  kernel_class: 0 full SpMV, 1 Chebyshev
@@ -208,7 +219,9 @@ int bgs_csr_spmv(int64_t nrows, int64_t nnz, const int32_t *rowptr, const int32_
 
 /* Block dot products of one Arnoldi step (K14, Sec. 2.2 flexible GMRES orthogonalisation):
  * h[k] = V_k . w for k < cnt and h[cnt] = w . w.  V: device, column-major, vector k at V + k*ld,
- * ld even and >= n; w: device, n entries; h: device, cnt + 1 entries; 1 <= cnt <= 64.  Per-block
+ * ld even and >= n; w: device, n entries; V and w 16-byte aligned (the kernel reads pairs of doubles;
+ * anything else returns BGS_INVALID_ARG before any GPU work); h: device, cnt + 1 entries;
+ * 1 <= cnt <= 64.  Per-block
  * partial sums go through device scratch that the call allocates and frees on the stream
  * (stream-ordered).  The sums are taken in a fixed order (run-to-run reproducible). */
 int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h,
@@ -218,13 +231,17 @@ int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int6
  * library convenience).  For callers that cannot allocate device memory when they need the dots:
  * applications whose device memory is fully pre-reserved by their own pool manager, and embedded or
  * real-time hosts that forbid allocation after start-up.  Same arguments, results and limits
- * as bgs_arnoldi_dots (1 <= cnt <= 64, ld even and >= n; anything else returns BGS_INVALID_ARG).
- * The partial sums go to one fixed array of 248,064 bytes inside the library's device image,
- * held by every GPU that loads the library until the process exits.  The first call on each
- * device looks up that array's address (cudaGetSymbolAddress with the device current), so make
- * the first call on a device before any stream capture.  All calls share the array: calls whose
- * GPU work overlaps (different streams, threads or processes sharing the context) race and give
- * wrong results; serialise them. */
+ * as bgs_arnoldi_dots (1 <= cnt <= 64, ld even and >= n, V and w 16-byte aligned; anything else
+ * returns BGS_INVALID_ARG before any GPU work).  The partial sums go to one fixed array of 248,064
+ * bytes inside the library's device image, held by every GPU that loads the library until the
+ * process exits; on a GPU with more multiprocessors the kernel uses fewer blocks, never more
+ * scratch.  The first call on each device looks up that array's address (cudaGetSymbolAddress with
+ * the device current); with lazy module loading (the CUDA default) that first lookup is also when
+ * the driver loads this part of the library and sets the array aside, so make the first call on
+ * each device at start-up, before any stream capture.  Later calls allocate nothing.  The address is
+ * kept for the life of the process: after cudaDeviceReset on a device, do not call this entry point
+ * again on that device.  All calls share the array: calls whose GPU work overlaps (different
+ * streams, threads or processes sharing the context) race and give wrong results; serialise them. */
 int bgs_arnoldi_dots_noalloc(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h,
                              void *cuda_stream);
 

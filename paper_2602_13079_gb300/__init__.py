@@ -37,10 +37,12 @@ class bgs_options(C.Structure):
 class bgs_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("status", C.c_int), ("restarts", C.c_int),
                 ("reorth", C.c_int), ("rel_true_resid", C.c_double), ("rel_est_resid", C.c_double),
-                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double)]
+                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double), ("nlevels", C.c_int * 8)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["nlevels"] = list(self.nlevels)
+        return d
 
 
 class BGSError(RuntimeError):
@@ -69,6 +71,7 @@ def lib():
             "bgs_solve": (i32, [vp, vp, vp, C.POINTER(bgs_info)]),
             "bgs_solve_adjoint": (i32, [vp, vp, vp, C.POINTER(bgs_info)]),
             "bgs_grad_values": (i32, [vp, i32, i32, vp, vp, vp]),
+            "bgs_grad_values_all": (i32, [vp, vp, vp, C.POINTER(vp)]),
             "bgs_apply_preconditioner": (i32, [vp, vp, vp]),
             "bgs_apply_vcycle": (i32, [vp, i32, vp, vp]),
             "bgs_full_spmv": (i32, [vp, vp, vp]),
@@ -78,6 +81,7 @@ def lib():
                                      C.POINTER(dbl)]),
             "bgs_level_copy": (i32, [vp, i32, i32, i32, vp, vp, vp]),
             "bgs_level_aggregates": (i32, [vp, i32, i32, vp]),
+            "bgs_level_strength": (i32, [vp, i32, i32, vp]),
             "bgs_level_format": (i32, [vp, i32, i32, i32, C.POINTER(C.c_int)]),
             "bgs_ilu_factors": (i32, [vp, i32, C.POINTER(C.c_int64), vp, vp, vp]),
             "bgs_level_ellipse": (i32, [vp, i32, i32, C.POINTER(C.c_double)]),
@@ -250,6 +254,16 @@ class Solver:
         _check(lib().bgs_grad_values(self.h, row_field, col_field, _ptr(lam), _ptr(x), _ptr(dvals)),
                "bgs_grad_values")
 
+    def bgs_grad_values_all(self, lam, x, dvals):
+        """dvals: F x F nested list of device tensors (nnz of each block) or None to skip a block."""
+        F = self.F
+        arr = (C.c_void_p * (F * F))()
+        for r in range(F):
+            for c in range(F):
+                if dvals[r][c] is not None:
+                    arr[r * F + c] = _ptr(dvals[r][c])
+        _check(lib().bgs_grad_values_all(self.h, _ptr(lam), _ptr(x), arr), "bgs_grad_values_all")
+
     def bgs_apply_preconditioner(self, v, z):
         _check(lib().bgs_apply_preconditioner(self.h, _ptr(v), _ptr(z)), "bgs_apply_preconditioner")
 
@@ -295,6 +309,13 @@ class Solver:
         agg = np.zeros(info["rows"], dtype=np.int32)
         _check(lib().bgs_level_aggregates(self.h, int(field), int(level), _ptr(agg)), "bgs_level_aggregates")
         return agg
+
+    def bgs_level_strength(self, field, level):
+        """Strength flag (uint8) of every stored entry of A_l, CSR order."""
+        info = self.bgs_level_info(field, level)
+        out = np.zeros(max(info["nnz"], 1), dtype=np.uint8)
+        _check(lib().bgs_level_strength(self.h, int(field), int(level), _ptr(out)), "bgs_level_strength")
+        return out[:info["nnz"]]
 
     def bgs_level_ellipse(self, field, level) -> float:
         im = C.c_double()

@@ -855,7 +855,7 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
     k_sg_ub<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, ub.p);
     CK_LAUNCH();
     // symbolic: short rows per thread, the rest per warp (shared table), then global tables
-    const int gl = grid_for(n, 128, kSMs * 32);
+    const int gl = grid_for(n, 128, num_sms() * 32);
     DBuf<int> lcols((size_t)n * SG_LOCAL, s);   // sorted columns of the short rows
     k_sg_local_sym<<<gl, 128, 0, s>>>(n, A.rp, A.ci, B.rp, B.ci, ub.p, C.rp.p, lcols.p);
     CK_LAUNCH();
@@ -868,7 +868,7 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
         CK_LAUNCH();
         const int nbA = collect_flag(n, flag.p, rows, sc, s);
         if (nbA) {
-            k_sg_sym<SG_SMALL_T><<<grid_for((int64_t)nbA * 32, SG_WARPS * 32, kSMs * 32), SG_WARPS * 32,
+            k_sg_sym<SG_SMALL_T><<<grid_for((int64_t)nbA * 32, SG_WARPS * 32, num_sms() * 32), SG_WARPS * 32,
                                    sizeof(int) * SG_WARPS * SG_SMALL_T, s>>>(nbA, rows.p, A.rp, A.ci, B.rp, B.ci,
                                                                              ub.p, C.rp.p);
             CK_LAUNCH();
@@ -878,14 +878,14 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
         DBuf<int> rowsM;
         const int nbM = collect_flag(n, flag.p, rowsM, sc, s);
         if (nbM) {
-            k_sg_sym<1024><<<grid_for((int64_t)nbM * 32, SG_WARPS * 32, kSMs * 16), SG_WARPS * 32,
+            k_sg_sym<1024><<<grid_for((int64_t)nbM * 32, SG_WARPS * 32, num_sms() * 16), SG_WARPS * 32,
                              sizeof(int) * SG_WARPS * 1024, s>>>(nbM, rowsM.p, A.rp, A.ci, B.rp, B.ci, ub.p, C.rp.p);
             CK_LAUNCH();
         }
         DBuf<int> rows1;
         const int nb1 = collect_big(n, C.rp.p, 1 << 30, rows1, sc, s);
         if (nb1) {
-            k_sg_sym<SG_SYM_T><<<grid_for((int64_t)nb1 * 32, SG_WARPS * 32, kSMs * 8), SG_WARPS * 32,
+            k_sg_sym<SG_SYM_T><<<grid_for((int64_t)nb1 * 32, SG_WARPS * 32, num_sms() * 8), SG_WARPS * 32,
                                  sizeof(int) * SG_WARPS * SG_SYM_T, s>>>(nb1, rows1.p, A.rp, A.ci, B.rp, B.ci, ub.p,
                                                                          C.rp.p);
             CK_LAUNCH();
@@ -929,18 +929,18 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
             const int nb = collect_flag(n, flag.p, rl, sc, s);
             if (!nb) continue;
             if (c == 0) {
-                k_sg_num<128><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, kSMs * 32), SG_WARPS * 32,
+                k_sg_num<128><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, num_sms() * 32), SG_WARPS * 32,
                                 sizeof(double) * SG_WARPS * (128 + 64) + sizeof(int) * SG_WARPS * 128,
                                 s>>>(nb, rl.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
                                      sc.flags.p + 8);
             } else if (c == 1) {
-                k_sg_num<SG_SMALL_T><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, kSMs * 32), SG_WARPS * 32,
+                k_sg_num<SG_SMALL_T><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, num_sms() * 32), SG_WARPS * 32,
                                        sizeof(double) * SG_WARPS * (SG_SMALL_T + 64) +
                                            sizeof(int) * SG_WARPS * SG_SMALL_T,
                                        s>>>(nb, rl.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
                                             sc.flags.p + 8);
             } else {
-                k_sg_num<SG_NUM_T><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, kSMs * 8), SG_WARPS * 32,
+                k_sg_num<SG_NUM_T><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, num_sms() * 8), SG_WARPS * 32,
                                      sizeof(double) * SG_WARPS * (SG_NUM_T + 64) + sizeof(int) * SG_WARPS * SG_NUM_T,
                                      s>>>(nb, rl.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
                                           sc.flags.p + 8);
@@ -1189,13 +1189,13 @@ static void dense_inverse_async(const DCsr &Ac, double *W, Scratch &sc, cudaStre
     DBuf<double> a((size_t)n * n, s), b((size_t)n * n, s);
     // about eight matrix entries per thread in each step: fewer blocks keep the pivot reduction
     // at the start of every step short
-    const int g = grid_for((int64_t)n * n, GJ_T * 8, kSMs);
+    const int g = grid_for((int64_t)n * n, GJ_T * 8, num_sms());
     DBuf<double> cv((size_t)2 * g, s);
     DBuf<int> cidx((size_t)2 * g, s), perm((size_t)n, s), tau((size_t)n, s);
     CK(cudaMemsetAsync(a.p, 0, sizeof(double) * (size_t)n * n, s));
     k_to_dense_rm<<<grid_for(n, 256), 256, 0, s>>>(n, Ac.rp.p, Ac.ci.p, Ac.v.p, a.p);
     CK_LAUNCH();
-    const int g0 = std::min(g, grid_for(n, GJ_T, kSMs));
+    const int g0 = std::min(g, grid_for(n, GJ_T, num_sms()));
     k_gj_first<<<g0, GJ_T, 0, s>>>(n, a.p, cv.p, cidx.p);
     CK_LAUNCH();
     double *S = a.p, *D = b.p;

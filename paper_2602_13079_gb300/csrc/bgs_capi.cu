@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <cstdlib>
 #include <memory>
@@ -33,7 +34,8 @@ struct EventPair {
 struct Krylov {
     int64_t n = 0, ld = 0;   // vector length, basis leading dimension (n rounded up to 64 entries)
     int m = 0;               // restart length
-    DBuf<double> V, Z, w, r, x, b, hdev;
+    DBuf<double> V, Z, w, r, x, b;
+    DBuf<FgState> st;        // the solver's scalar state on the device
     void alloc(int64_t n_, int m_, cudaStream_t s) {
         n = n_;
         m = m_;
@@ -44,8 +46,17 @@ struct Krylov {
         r.alloc((size_t)n, s);
         x.alloc((size_t)n, s);
         b.alloc((size_t)n, s);
-        hdev.alloc(256, s);
+        st.alloc(1, s);
     }
+};
+
+// One FGMRES restart cycle captured as a CUDA graph: a WHILE node whose body is one step (the
+// preconditioner sweep on the staging vectors, z_j stored, w = A z_j, Gram-Schmidt, the step kernel
+// that ends the loop).
+struct CycleGraph {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond{};
+    long long body_launches = 0;
 };
 
 // One group of the nested variant: order positions [p0, p1), fields with consecutive ids, so the
@@ -84,12 +95,10 @@ struct bgs_ctx {
     double t_setup_ms = 0.0;
     int last_reorth = 0;
     // profiling
-    // CUDA graph of one preconditioner sweep (forward, adjoint): captured once on an internal
-    // stream with fixed staging vectors gv -> gz, replayed every FGMRES iteration
+    // CUDA graph of one FGMRES restart cycle (forward, adjoint), captured once on an internal stream
+    // with fixed staging vectors gv -> gz for the sweep, replayed for every cycle of every solve
     cudaStream_t gs = nullptr;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    long long glaunches[2] = {0, 0};
-    cudaEvent_t gev[2] = {nullptr, nullptr};
+    CycleGraph cyc[2];
     DBuf<double> gv, gz;
     bool prof = false;
     std::vector<EventPair> ev;
@@ -352,61 +361,11 @@ void apply_prec(bgs_ctx *h, const double *v, double *z, bool transposed) {
 
 
 void drop_graphs(bgs_ctx *h) {
-    for (int a = 0; a < 2; a++)
-        if (h->gexec[a]) {
-            cudaGraphExecDestroy(h->gexec[a]);
-            h->gexec[a] = nullptr;
+    for (auto &c : h->cyc)
+        if (c.exec) {
+            cudaGraphExecDestroy(c.exec);
+            c.exec = nullptr;
         }
-}
-
-// z = M^-1 v through the captured graph (captured on first use for this direction)
-void apply_prec_graph(bgs_ctx *h, const double *v, double *z, bool adjoint) {
-    const int a = adjoint ? 1 : 0;
-    const int64_t n = total_n(h);
-    if (!h->gs) {
-        CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&h->gev[0], cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->gev[1], cudaEventDisableTiming));
-    }
-    if (!h->gv.p) {
-        h->gv.alloc((size_t)n, h->s);
-        h->gz.alloc((size_t)n, h->s);
-        CK(cudaStreamSynchronize(h->s));
-    }
-    if (!h->gexec[a]) {
-        cudaStream_t saved = h->s;
-        const bool saved_prof = h->prof;
-        h->s = h->gs;
-        h->prof = false;
-        const long long l0 = launch_count();
-        cudaGraph_t g = nullptr;
-        CK(cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal));
-        try {
-            apply_prec(h, h->gv.p, h->gz.p, adjoint);
-        } catch (...) {
-            cudaStreamEndCapture(h->gs, &g);
-            if (g) cudaGraphDestroy(g);
-            h->s = saved;
-            h->prof = saved_prof;
-            throw;
-        }
-        CK(cudaStreamEndCapture(h->gs, &g));
-        h->s = saved;
-        h->prof = saved_prof;
-        h->glaunches[a] = launch_count() - l0;
-        const cudaError_t e = cudaGraphInstantiate(&h->gexec[a], g, 0);
-        cudaGraphDestroy(g);
-        CK(e);
-    }
-    cudaStream_t s = h->s;
-    CK(cudaMemcpyAsync(h->gv.p, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    CK(cudaEventRecord(h->gev[0], s));
-    CK(cudaStreamWaitEvent(h->gs, h->gev[0], 0));
-    CK(cudaGraphLaunch(h->gexec[a], h->gs));
-    for (long long i = 0; i < h->glaunches[a]; i++) count_launch();
-    CK(cudaEventRecord(h->gev[1], h->gs));
-    CK(cudaStreamWaitEvent(s, h->gev[1], 0));
-    CK(cudaMemcpyAsync(z, h->gz.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
 }
 
 double host_dot(bgs_ctx *h, const double *a, const double *b, int64_t n) {
@@ -417,15 +376,86 @@ double host_dot(bgs_ctx *h, const double *a, const double *b, int64_t n) {
 }
 
 // ------------------------------------------------------------------ FGMRES(m)
+// The scalar fields at the head of the device state (read back after a step or a cycle).
+constexpr size_t kFgHead = offsetof(FgState, nw1);
+
+FgState read_state(bgs_ctx *h, const Krylov &K) {
+    double *buf = h->sc.h_scal + 16;   // pinned; slots 0..15 serve the other read-backs
+    CK(cudaMemcpyAsync(buf, K.st.p, kFgHead, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    FgState hs;
+    std::memcpy((void *)&hs, buf, kFgHead);
+    return hs;
+}
+
+// Captures one restart cycle of the outer solve as a CUDA graph (a WHILE node over one step).
+void build_cycle_graph(bgs_ctx *h, Krylov &K, const DCsr &A, int m, bool adjoint, CycleGraph &cg) {
+    const int64_t n = K.n;
+    if (!h->gs) CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
+    if (!h->gv.p) {
+        h->gv.alloc((size_t)n, h->s);
+        h->gz.alloc((size_t)n, h->s);
+        CK(cudaStreamSynchronize(h->s));
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaStream_t saved = h->s;
+    const bool saved_prof = h->prof;
+    bool capturing = false;
+    try {
+        CK(cudaGraphConditionalHandleCreate(&cg.cond, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cg.cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        h->s = h->gs;
+        h->prof = false;
+        const long long l0 = launch_count();
+        CK(cudaStreamBeginCaptureToGraph(h->gs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        capturing = true;
+        apply_prec(h, h->gv.p, h->gz.p, adjoint);
+        fg_store_z(K.st.p, h->gz.p, K.Z.p, K.ld, n, h->gs);
+        spmv_store<double, double>(A, h->gz.p, K.w.p, h->gs);
+        fg_orthogonalise(K.st.p, K.V.p, K.ld, m, K.w.p, n, h->opt.reorth_eta >= 1.0, h->sc, h->gs);
+        fg_step(K.st.p, cg.cond, true, K.w.p, K.V.p, K.ld, h->gv.p, n, h->gs);
+        cudaGraph_t out = nullptr;
+        capturing = false;
+        CK(cudaStreamEndCapture(h->gs, &out));
+        cg.body_launches = launch_count() - l0;
+        h->s = saved;
+        h->prof = saved_prof;
+        CK(cudaGraphInstantiate(&cg.exec, g, 0));
+        cudaGraphDestroy(g);
+    } catch (...) {
+        if (capturing) {
+            cudaGraph_t out = nullptr;
+            cudaStreamEndCapture(h->gs, &out);
+        }
+        h->s = saved;
+        h->prof = saved_prof;
+        cudaGraphDestroy(g);
+        cg.exec = nullptr;
+        throw;
+    }
+}
+
 // Restarted right-preconditioned flexible GMRES on the workspace K: solves A x = K.b from x = 0
 // into K.x.  prec(v, z) applies z = M^-1 v; A is the FP64 operator (w = A z and the true residual
-// at every restart).  Gram-Schmidt as described at the selective re-orthogonalisation below.
+// at every restart).  Gram-Schmidt with the selective re-orthogonalisation test of reorth_eta.
+// Every step's arithmetic runs in device kernels; with cg the whole cycle is one graph launch
+// (the preconditioner captured inside it), otherwise the host launches each step and reads the
+// stop decision back.  Both orders of launches run the same kernels on the same data.
 template <class Prec>
-int fgmres_run(bgs_ctx *h, Krylov &K, const DCsr &A, int m, int maxit, double rtol, Prec &&prec, bgs_info *info) {
+int fgmres_run(bgs_ctx *h, Krylov &K, const DCsr &A, int m, int maxit, double rtol, Prec &&prec, bgs_info *info,
+               CycleGraph *cg) {
     cudaStream_t s = h->s;
     const int64_t n = K.n;
     const int64_t ld = K.ld;
-    if (m > K.m) throw Error(BGS_INTERNAL, "restart longer than the Krylov workspace");
+    if (m > K.m || m > kMaxRestart) throw Error(BGS_INTERNAL, "restart longer than the Krylov workspace");
     double *V = K.V.p, *Z = K.Z.p, *w = K.w.p, *r = K.r.p, *x = K.x.p, *b = K.b.p;
     bgs_info inf{};
     CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
@@ -442,91 +472,40 @@ int fgmres_run(bgs_ctx *h, Krylov &K, const DCsr &A, int m, int maxit, double rt
         if (info) *info = inf;
         return BGS_OK;
     }
-    std::vector<double> Hm((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
+    const double eta = h->opt.reorth_eta;
+    fg_init(K.st.p, m, maxit, rtol, eta * eta, bnorm, s);
     CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    double beta = bnorm, rel = 1.0, est = 1.0;
-    int it = 0, status = BGS_NO_CONVERGENCE, restarts = 0, reorth = 0;
-    double *hd = K.hdev.p, *hh = h->sc.h_scal;
+    double beta = bnorm, rel = 1.0;
+    int status = BGS_NO_CONVERGENCE, restarts = 0;
+    FgState hs{};
     for (;;) {
-        scale_copy(r, 1.0 / beta, V, n, s);
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int jend = 0;
-        bool breakdown = false, nan = false;
-        for (int j = 0; j < m; j++) {
-            double *vj = V + (size_t)j * ld, *zj = Z + (size_t)j * ld;
-            prec((const double *)vj, zj);
-            {
-                Prof pf(h, 0, spmv_bytes(A, 8, 8, 0));
-                spmv_store<double, double>(A, zj, w, s);
+        fg_begin(K.st.p, r, beta, V, cg ? h->gv.p : nullptr, n, s);
+        if (cg) {
+            CK(cudaGraphLaunch(cg->exec, s));
+            hs = read_state(h, K);
+            for (long long i = 0; i < cg->body_launches * hs.jend; i++) count_launch();
+        } else {
+            for (int j = 0;; j++) {
+                double *vj = V + (size_t)j * ld, *zj = Z + (size_t)j * ld;
+                prec((const double *)vj, zj);
+                {
+                    Prof pf(h, 0, spmv_bytes(A, 8, 8, 0));
+                    spmv_store<double, double>(A, zj, w, s);
+                }
+                {
+                    Prof pf(h, 2, 8.0 * n * (2.0 * (j + 1) + 3.0));
+                    fg_orthogonalise(K.st.p, V, ld, m, w, n, eta >= 1.0, h->sc, s);
+                }
+                fg_step(K.st.p, cudaGraphConditionalHandle{}, false, w, V, ld, nullptr, n, s);
+                hs = read_state(h, K);
+                if (hs.stop) break;
             }
-            // classical Gram-Schmidt; the second pass runs when ||w1|| < eta ||w|| (eta = 1: always,
-            // i.e. CGS2; 1/sqrt(2): the Daniel-Gragg-Kaufman-Stewart test; 0: never)
-            {
-                Prof pf(h, 2, 8.0 * n * (2.0 * (j + 1) + 3.0));
-                arnoldi_dots(V, ld, j + 1, w, n, hd, h->sc, s);                     // h1, ||w||^2
-                arnoldi_update(V, ld, j + 1, hd, w, w, n, hd + 70, h->sc, s);      // w1, ||w1||^2
-            }
-            const double eta = h->opt.reorth_eta;
-            if (eta >= 1.0) {   // always: queue the second pass before the single read-back
-                Prof pf(h, 2, 8.0 * n * (2.0 * (j + 1) + 3.0));
-                arnoldi_dots(V, ld, j + 1, w, n, hd + 80, h->sc, s);
-                arnoldi_update(V, ld, j + 1, hd + 80, w, w, n, hd + 150, h->sc, s);
-            }
-            CK(cudaMemcpyAsync(hh, hd, sizeof(double) * 152, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            for (int i = 0; i <= j; i++) Hm[(size_t)i * m + j] = hh[i];
-            double nw2 = hh[70];
-            if (eta >= 1.0) {
-                for (int i = 0; i <= j; i++) Hm[(size_t)i * m + j] += hh[80 + i];
-                nw2 = hh[150];
-                reorth++;
-            } else if (nw2 < eta * eta * hh[j + 1]) {
-                Prof pf(h, 2, 8.0 * n * (2.0 * (j + 1) + 3.0));
-                arnoldi_dots(V, ld, j + 1, w, n, hd + 80, h->sc, s);
-                arnoldi_update(V, ld, j + 1, hd + 80, w, w, n, hd + 150, h->sc, s);
-                CK(cudaMemcpyAsync(hh + 80, hd + 80, sizeof(double) * 72, cudaMemcpyDeviceToHost, s));
-                CK(cudaStreamSynchronize(s));
-                for (int i = 0; i <= j; i++) Hm[(size_t)i * m + j] += hh[80 + i];
-                nw2 = hh[150];
-                reorth++;
-            }
-            const double hn = std::sqrt(nw2);
-            Hm[(size_t)(j + 1) * m + j] = hn;
-            it++;
-            if (hn == 0.0) breakdown = true;
-            else scale_copy(w, 1.0 / hn, V + (size_t)(j + 1) * ld, n, s);
-            for (int i = 0; i < j; i++) {
-                const double a = Hm[(size_t)i * m + j], c = Hm[(size_t)(i + 1) * m + j];
-                Hm[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
-                Hm[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
-            }
-            const double a = Hm[(size_t)j * m + j], c = Hm[(size_t)(j + 1) * m + j];
-            const double den = std::sqrt(a * a + c * c);
-            cs[j] = den == 0.0 ? 1.0 : a / den;
-            sn[j] = den == 0.0 ? 0.0 : c / den;
-            Hm[(size_t)j * m + j] = den;
-            Hm[(size_t)(j + 1) * m + j] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            est = std::fabs(g[j + 1]) / bnorm;
-            jend = j + 1;
-            if (!std::isfinite(est)) {
-                nan = true;
-                break;
-            }
-            if (est <= rtol || it >= maxit || breakdown) break;
         }
-        if (nan) {
+        if (hs.flag == 4) {
             status = BGS_NAN_INF;
             break;
         }
-        for (int i = jend - 1; i >= 0; i--) {
-            double t = g[i];
-            for (int k = i + 1; k < jend; k++) t -= Hm[(size_t)i * m + k] * y[k];
-            y[i] = t / Hm[(size_t)i * m + i];
-        }
-        multi_axpy(Z, ld, jend, y.data(), x, n, s);
+        fg_finish_cycle(K.st.p, Z, ld, x, n, s);
         spmv_resid<double, double>(A, b, x, r, s);
         beta = std::sqrt(host_dot(h, r, r, n));
         rel = beta / bnorm;
@@ -538,24 +517,19 @@ int fgmres_run(bgs_ctx *h, Krylov &K, const DCsr &A, int m, int maxit, double rt
             status = BGS_OK;
             break;
         }
-        if (it >= maxit) {
+        if (hs.it >= maxit) {
             status = BGS_NO_CONVERGENCE;
-            break;
-        }
-        if (breakdown && beta == 0.0) {
-            status = BGS_BREAKDOWN;
             break;
         }
         restarts++;
     }
-    inf.iters = it;
+    inf.iters = hs.it;
     inf.converged = status == BGS_OK;
     inf.status = status;
     inf.restarts = restarts;
-    inf.reorth = reorth;
-
+    inf.reorth = hs.reorth;
     inf.rel_true_resid = rel;
-    inf.rel_est_resid = est;
+    inf.rel_est_resid = hs.est;
     if (info) *info = inf;
     return status;
 }
@@ -613,7 +587,7 @@ void apply_nested(bgs_ctx *h, const double *v, double *z, bool adjoint) {
                        if (mixed) group_sweep<float, float, __nv_bfloat16>(h, g, vi, zi, adjoint);
                        else group_sweep<double, double, double>(h, g, vi, zi, adjoint);
                    },
-                   nullptr);
+                   nullptr, nullptr);
         CK(cudaMemcpyAsync(z + g.base, g.K.x.p, sizeof(double) * (size_t)g.n, cudaMemcpyDeviceToDevice, s));
     }
 }
@@ -713,13 +687,15 @@ void build_groups(bgs_ctx *h) {
 int fgmres(bgs_ctx *h, bool adjoint, bgs_info *info) {
     const DCsr &A = adjoint ? h->fullT : h->full;
     const bool nested = !h->groups.empty();
+    const bool graph = !nested && h->opt.graph && !h->prof;
+    CycleGraph *cg = graph ? &h->cyc[adjoint ? 1 : 0] : nullptr;
+    if (cg && !cg->exec) build_cycle_graph(h, h->K, A, h->opt.restart, adjoint, *cg);
     const int st = fgmres_run(h, h->K, A, h->opt.restart, h->opt.maxit, h->opt.rtol,
                               [&](const double *v, double *z) {
                                   if (nested) apply_nested(h, v, z, adjoint);
-                                  else if (h->opt.graph && !h->prof) apply_prec_graph(h, v, z, adjoint);
                                   else apply_prec(h, v, z, adjoint);
                               },
-                              info);
+                              info, cg);
     if (info) h->last_reorth = info->reorth;
     return st;
 }
@@ -1369,6 +1345,7 @@ static int solve_common(bgs_handle h, const double *b, double *x, bgs_info *info
         CK(cudaStreamSynchronize(s));
         inf.t_solve_ms = now_ms() - t0;
         inf.t_setup_ms = h->t_setup_ms;
+        for (int k = 0; k < h->F; k++) inf.nlevels[k] = (int)h->H[k].L.size();
         prof_collect(h);
         if (info) *info = inf;
         return st;
@@ -1381,6 +1358,21 @@ int bgs_solve(bgs_handle h, const double *b, double *x, bgs_info *info) {
 
 int bgs_solve_adjoint(bgs_handle h, const double *g, double *lambda, bgs_info *info) {
     return solve_common(h, g, lambda, info, true);
+}
+
+int bgs_grad_values_all(bgs_handle h, const double *lambda, const double *x, double *const *dvals) {
+    if (!h || !lambda || !x || !dvals) return BGS_INVALID_ARG;
+    return guarded([&]() -> int {
+        for (int r = 0; r < h->F; r++)
+            for (int c = 0; c < h->F; c++) {
+                DCsr &B = h->blk[(size_t)r * h->F + c];
+                double *d = dvals[r * h->F + c];
+                if (!d || B.nnz == 0) continue;
+                grad_outer(view(B), lambda + h->offs[r], x + h->offs[c], d, h->s);
+            }
+        CK(cudaStreamSynchronize(h->s));
+        return BGS_OK;
+    });
 }
 
 int bgs_grad_values(bgs_handle h, int rf, int cf, const double *lambda, const double *x, double *dvals) {
@@ -1525,6 +1517,20 @@ int bgs_level_aggregates(bgs_handle h, int field, int level, int32_t *agg) {
     });
 }
 
+int bgs_level_strength(bgs_handle h, int field, int level, uint8_t *strong) {
+    if (!h || field < 0 || field >= h->F || !strong) return BGS_INVALID_ARG;
+    if (!h->setup_done) return BGS_NOT_SETUP;
+    Hier &H = h->H[field];
+    if (level < 0 || level + 1 >= (int)H.L.size()) return BGS_INVALID_ARG;
+    return guarded([&]() -> int {
+        Level &L = H.L[level];
+        if (L.A.nnz)
+            CK(cudaMemcpyAsync(strong, L.strong.p, (size_t)L.A.nnz, cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        return BGS_OK;
+    });
+}
+
 int bgs_set_profiling(bgs_handle h, int on) {
     if (!h) return BGS_INVALID_ARG;
     h->prof = on != 0;
@@ -1554,10 +1560,11 @@ int bgs_csr_spmv(int64_t nrows, int64_t nnz, const int32_t *rowptr, const int32_
 
 int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, void *stream) {
     if (!V || !w || !h || n < 1 || cnt < 1 || cnt > 64 || ld < n || (ld & 1)) return BGS_INVALID_ARG;
+    if (((uintptr_t)V | (uintptr_t)w) & 15) return BGS_INVALID_ARG;   // read as 16-byte pairs
     return guarded([&]() -> int {
         cudaStream_t s = (cudaStream_t)stream;
-        DBuf<double> part(arnoldi_dots_scratch(cnt, n), s);
-        arnoldi_dots_into(V, ld, cnt, w, n, h, part.p, part.n, s);
+        DBuf<double> part(arnoldi_dots_scratch(cnt, n, 0), s);
+        arnoldi_dots_into(V, ld, cnt, w, n, h, part.p, part.n, 0, s);
         return BGS_OK;
     });
 }
@@ -1582,8 +1589,6 @@ void bgs_destroy(bgs_handle h) {
     }
     if (h->gs) cudaStreamSynchronize(h->gs);
     drop_graphs(h);
-    for (auto &e : h->gev)
-        if (e) cudaEventDestroy(e);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     for (auto &e : h->join_ev)
         if (e) cudaEventDestroy(e);

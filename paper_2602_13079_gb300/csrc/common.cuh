@@ -112,9 +112,13 @@ struct DCsr {
 // ------------------------------------------------------------------------------------------
 // Launch helpers
 // ------------------------------------------------------------------------------------------
-constexpr int kSMs = 152;
+// Multiprocessors of the current device (cudaDevAttrMultiProcessorCount, looked up once per
+// device): every grid cap below is a multiple of it (152 on a GB300).
+int num_sms();
 
-inline int grid_for(int64_t work, int block, int max_blocks = kSMs * 16) {
+// Blocks for `work` items of `block` each, capped at max_blocks (default: 16 per multiprocessor).
+inline int grid_for(int64_t work, int block, int max_blocks = 0) {
+    if (max_blocks <= 0) max_blocks = num_sms() * 16;
     int64_t g = (work + block - 1) / block;
     if (g < 1) g = 1;
     if (g > max_blocks) g = max_blocks;

@@ -104,23 +104,50 @@ void refresh_values(DCsr &A, cudaStream_t s);
 int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s);
 
 // ---------------------------------------------------------------- krylov.cu
-// h[k] = V_k . w for k < cnt and h[cnt] = w . w (V column-major, leading dimension ld, even)
-void arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, Scratch &sc,
-                  cudaStream_t s);
-// the same with a caller-provided partial-sum buffer of partial_cap doubles; the buffer needs
-// arnoldi_dots_scratch(cnt, n) doubles (at most 4 * 608 * 17) and need not be cleared
+// h[k] = V_k . w for k < cnt and h[cnt] = w . w (V column-major, leading dimension ld, even; V and w
+// 16-byte aligned), with a caller-provided partial-sum buffer of partial_cap doubles that needs
+// arnoldi_dots_scratch(cnt, n, max_blocks) doubles and need not be cleared; max_blocks caps the
+// grid (0: three blocks per multiprocessor).
 void arnoldi_dots_into(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, double *partial,
-                       size_t partial_cap, cudaStream_t s);
-size_t arnoldi_dots_scratch(int cnt, int64_t n);
-// w_out = w_in - V h (h on the device, cnt entries) and *nrm2 = ||w_out||^2; w_out may equal w_in
-void arnoldi_update(const double *V, int64_t ld, int cnt, const double *h, const double *w_in, double *w_out,
-                    int64_t n, double *nrm2, Scratch &sc, cudaStream_t s);
-// x += sum_k y_k Z_k (y host values)
-void multi_axpy(const double *Z, int64_t ld, int cnt, const double *y_host, double *x, int64_t n, cudaStream_t s);
-void scale_copy(const double *in, double alpha, double *out, int64_t n, cudaStream_t s);
-// out = in / *dev_scalar
-void scale_by_inv_dev(const double *in, const double *dev_scalar, double *out, int64_t n, bool sqrt_first,
-                      cudaStream_t s);
+                       size_t partial_cap, int max_blocks, cudaStream_t s);
+size_t arnoldi_dots_scratch(int cnt, int64_t n, int max_blocks);
+
+// FGMRES(m) state in device memory (one per Krylov workspace); m <= kMaxRestart.
+constexpr int kMaxRestart = 63;
+constexpr int kHld = kMaxRestart + 1;   // leading dimension of the Hessenberg matrix
+struct FgState {
+    int j;          // column of the current step within the cycle
+    int cnt;        // j + 1: basis vectors the step orthogonalises against
+    int it;         // iterations so far (all cycles)
+    int jend;       // columns done in this cycle
+    int stop;       // the cycle ends after this step
+    int flag;       // why: 1 estimate <= rtol, 2 maxit, 3 breakdown, 4 NaN/Inf, 5 restart length
+    int reorth;     // steps that ran the second Gram-Schmidt pass
+    int need2;      // this step runs the second pass
+    int m, maxit;
+    double rtol, eta2, bnorm, est, inv_hn;
+    double nw1, nw2;                 // ||w||^2 after the first / second pass
+    double h1[kHld + 8], h2[kHld + 8];   // dots of the passes (h[cnt] = ||w||^2 before the pass)
+    double cs[kHld], sn[kHld], g[kHld + 1], y[kHld];
+    double H[(kHld + 1) * kHld];     // rotated Hessenberg matrix, row-major [i * kHld + j]
+};
+// start of a solve: restart length, iteration limit, tolerance, eta^2 of the re-orthogonalisation
+// test, ||b||; iteration and re-orthogonalisation counts reset
+void fg_init(FgState *st, int m, int maxit, double rtol, double eta2, double bnorm, cudaStream_t s);
+// start of a cycle: state reset with g_0 = beta, V_0 = r / beta (and stage = V_0 when given)
+void fg_begin(FgState *st, const double *r, double beta, double *V, double *stage, int64_t n, cudaStream_t s);
+// column j of Z from the staging vector (j read on the device)
+void fg_store_z(const FgState *st, const double *src, double *Z, int64_t ld, int64_t n, cudaStream_t s);
+// the Gram-Schmidt passes of step j on w = A z_j (second pass by the re-orthogonalisation test, or
+// always); m = the restart length (the largest basis a step can see)
+void fg_orthogonalise(FgState *st, const double *V, int64_t ld, int m, double *w, int64_t n, bool always,
+                      Scratch &sc, cudaStream_t s);
+// the scalar part of the step and v_{j+1} = w / h_{j+1,j} (into stage too when given); with
+// use_loop the step sets the WHILE condition of the captured cycle (0 when the cycle ends)
+void fg_step(FgState *st, cudaGraphConditionalHandle loop, bool use_loop, const double *w, double *V, int64_t ld,
+             double *stage, int64_t n, cudaStream_t s);
+// after the cycle: y from the triangular system, x += Z y
+void fg_finish_cycle(FgState *st, const double *Z, int64_t ld, double *x, int64_t n, cudaStream_t s);
 
 // ---------------------------------------------------------------- amg_setup.cu
 struct Level {

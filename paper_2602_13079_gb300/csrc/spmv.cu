@@ -104,7 +104,7 @@ static void launch_csr(int lanes, int n, const int *rp, const int *ci, const VT 
                        cudaStream_t s) {
     if (n <= 0) return;
     int rows_per_block = 256 / lanes;
-    int g = grid_for(n, rows_per_block, kSMs * 32);
+    int g = grid_for(n, rows_per_block, num_sms() * 32);
     switch (lanes) {
         case 1: k_spmv<1, VT, XT, AT, Epi><<<g, 256, 0, s>>>(n, rp, ci, val, x, epi); break;
         case 2: k_spmv<2, VT, XT, AT, Epi><<<g, 256, 0, s>>>(n, rp, ci, val, x, epi); break;
@@ -191,7 +191,7 @@ __global__ void k_cheb_first(int n, const XT *__restrict__ b, const XT *__restri
 template <class XT>
 void cheb_first(int n, const XT *b, const XT *dinv, double inv_theta, XT *x, XT *e, cudaStream_t s) {
     if (n <= 0) return;
-    k_cheb_first<XT><<<grid_for(n, 256, kSMs * 32), 256, 0, s>>>(n, b, dinv, inv_theta, x, e);
+    k_cheb_first<XT><<<grid_for(n, 256, num_sms() * 32), 256, 0, s>>>(n, b, dinv, inv_theta, x, e);
     CK_LAUNCH();
 }
 
@@ -202,7 +202,7 @@ __global__ void k_dense_gemv(int n, const double *__restrict__ W, const XT *__re
 template <class XT>
 void dense_gemv(int n, const double *W, const XT *x, XT *y, cudaStream_t s) {
     if (n <= 0) return;
-    k_dense_gemv<XT><<<grid_for((int64_t)n * 32, 256, kSMs * 16), 256, 0, s>>>(n, W, x, y);
+    k_dense_gemv<XT><<<grid_for((int64_t)n * 32, 256, num_sms() * 16), 256, 0, s>>>(n, W, x, y);
     CK_LAUNCH();
 }
 

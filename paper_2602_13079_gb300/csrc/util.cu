@@ -42,10 +42,23 @@ bool plain_alloc() {
     return v;
 }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int num_sms() {
+    static std::atomic<int> cache[128] = {};
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) dev = 0;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    CK(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    if (v < 1) v = 1;
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void Scratch::init(cudaStream_t s) {
-    partial.alloc(kSMs * 8 * 72, s);
+    partial.alloc(num_sms() * 8 * 72, s);
     scal.alloc(256, s);
     flags.alloc(64, s);
     iscan.alloc(1 << 16, s);
@@ -228,7 +241,7 @@ __global__ void k_reduce_final_rsqrt(const double *part, int g, double *out) {
 }
 
 void dev_dot_rsqrt(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s) {
-    int g = grid_for(n, 256, kSMs * 4);
+    int g = grid_for(n, 256, num_sms() * 4);
     k_dot_partial<<<g, 256, 0, s>>>(a, b, n, sc.partial.p);
     CK_LAUNCH();
     k_reduce_final_rsqrt<<<1, 256, 0, s>>>(sc.partial.p, g, out);
@@ -236,7 +249,7 @@ void dev_dot_rsqrt(const double *a, const double *b, int64_t n, double *out, Scr
 }
 
 void dev_dot(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s) {
-    int g = grid_for(n, 256, kSMs * 4);
+    int g = grid_for(n, 256, num_sms() * 4);
     k_dot_partial<<<g, 256, 0, s>>>(a, b, n, sc.partial.p);
     CK_LAUNCH();
     k_reduce_final<<<1, 256, 0, s>>>(sc.partial.p, g, out);

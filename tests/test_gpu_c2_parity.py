@@ -1,0 +1,94 @@
+"""Parity on the 3D 64^3 five-field layered system (1.31M DOFs, seed 1) with the library defaults:
+the GPU set-up and solve against the CPU oracle on every block and every level.
+
+Bit-exact: the strength decision of every stored entry, the MIS-2 round counts, the aggregate maps,
+the level sizes and every sparsity pattern (A_l, P_l, R_l).  Within tolerances derived from the
+arithmetic (the same FP64 operations summed in another order): omega (1e-12), the Chebyshev bounds
+(1e-10), P_l and R_l values (1e-12 of the largest entry), A_l values (1e-11 of the largest entry).
+The FP64 solve reaches a true relative residual of 1e-8 (checked on the host with the oracle's
+SpMV) with ||x - x_oracle|| / ||x_oracle|| <= 1e-6 and an iteration count within 2 of the
+oracle's; the mixed-precision solve (FP32 hierarchy, BF16 couplings, FP64 Krylov) meets the same
+residual and error bounds, and its error against the oracle is printed."""
+import numpy as np
+import pytest
+
+import battery_system as bs
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bgs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_13079_gb300 import _build
+    _build.build()
+    import paper_2602_13079_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return bs.assemble("C2", seed=1)
+
+
+@pytest.fixture(scope="module")
+def ref(c2):
+    o = oracle.bgs_for_system(c2)          # oracle defaults = library defaults
+    x, info = o.solve(c2.b)
+    assert info.converged
+    return o, x, info
+
+
+def test_c2_every_block_and_level_matches_the_oracle(bgs, c2, ref):
+    o = ref[0]
+    g = bgs.solver_for_system(c2)
+    g.setup()
+    for k in range(5):
+        oa = o.amg(k)
+        nl = g.bgs_num_levels(k)
+        assert nl == oa.nlevels, (k, nl, oa.sizes())
+        for l in range(nl):
+            info = g.bgs_level_info(k, l)
+            assert info["rows"] == oa.sizes()[l], (k, l)
+            rp, ci, v = g.bgs_level_copy(k, l, 0)
+            A = oa.level_matrix(l)
+            assert np.array_equal(rp, A.rowptr) and np.array_equal(ci, A.col), (k, l)
+            assert np.abs(v - A.val).max() <= 1e-11 * np.abs(A.val).max(), (k, l)
+            if l + 1 == nl:
+                continue
+            assert np.array_equal(g.bgs_level_strength(k, l), oa.strong(l)), (k, l)
+            assert info["mis_rounds"] == oa.mis_rounds(l), (k, l)
+            assert info["nagg"] == oa.nagg(l), (k, l)
+            assert np.array_equal(g.bgs_level_aggregates(k, l), oa.aggregates(l)), (k, l)
+            assert abs(info["omega"] - oa.omega(l)) <= 1e-12 * abs(oa.omega(l)), (k, l)
+            lo, hi = oa.cheb_bounds(l)
+            assert abs(info["lmax"] - hi) <= 1e-10 * hi and abs(info["lmin"] - lo) <= 1e-10 * lo, (k, l)
+            for which, M in ((1, oa.prolongator(l)), (2, oa.restriction(l))):
+                prp, pci, pv = g.bgs_level_copy(k, l, which)
+                assert np.array_equal(prp, M.rowptr) and np.array_equal(pci, M.col), (k, l, which)
+                assert np.abs(pv - M.val).max() <= 1e-12 * max(1.0, np.abs(M.val).max()), (k, l, which)
+    g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c2_solve_matches_the_oracle(bgs, c2, ref, precision):
+    o, xr, ir = ref
+    g = bgs.solver_for_system(c2, precision=precision)
+    g.setup()
+    x = torch.zeros(c2.ndof, dtype=torch.float64, device="cuda")
+    info = g.bgs_solve(torch.from_numpy(c2.b).cuda(), x)
+    xh = x.cpu().numpy()
+    assert info.converged and info.status == 0
+    rel = np.linalg.norm(c2.b - o.full_matvec(xh)) / np.linalg.norm(c2.b)
+    err = np.linalg.norm(xh - xr) / np.linalg.norm(xr)
+    print(f"C2 precision={precision}: iters {info.iters} (oracle {ir.iters}), true rel. residual {rel:.3e}, "
+          f"||x - x_oracle|| / ||x_oracle|| = {err:.3e}")
+    assert rel <= 1e-8
+    assert err <= 1e-6
+    assert list(info.nlevels)[:5] == [o.amg(k).nlevels for k in range(5)]
+    if precision == 0:
+        assert abs(info.iters - ir.iters) <= 2
+    g.close()

@@ -112,3 +112,19 @@ OPTION_DEFECTS = [
 def test_malformed_options(bgs, bad):
     st, h = System(bgs).call(options=bgs.bgs_default_options(**bad))
     assert st == bgs.INVALID_ARG and not h.value
+
+
+@pytest.mark.parametrize("entry", ["bgs_arnoldi_dots", "bgs_arnoldi_dots_noalloc"])
+def test_arnoldi_dots_reject_misaligned_vectors_on_the_host(bgs, entry):
+    """The dot kernel reads V and w as 16-byte pairs: a pointer that is only 8-byte aligned (a view
+    such as x[1:]) is refused on the host with BGS_INVALID_ARG, before any CUDA call, so these
+    addresses (never dereferenced) are safe to pass without a GPU."""
+    f = getattr(bgs.lib(), entry)
+    base = 1 << 20                      # 16-byte aligned stand-in addresses, never dereferenced
+    n, cnt, ld = 1000, 3, 1000
+    for V, w in ((base + 8, base), (base, base + 8), (base + 8, base + 24)):
+        assert f(V, ld, cnt, w, n, base, None) == bgs.INVALID_ARG
+    # the other host checks, for completeness: odd leading dimension, basis size out of range
+    assert f(base, ld + 1, cnt, base, n, base, None) == bgs.INVALID_ARG
+    assert f(base, ld, 65, base, n, base, None) == bgs.INVALID_ARG
+    assert f(base, n - 2, cnt, base, n, base, None) == bgs.INVALID_ARG
