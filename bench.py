@@ -522,8 +522,8 @@ def gpu_arm(args, rank, world):
         # list, profiles/launch_list_c4_fp64_step.md), in the SpMV variant the autotuner chose for the
         # 128^3 diagonal blocks in this process
         fmt = prof.pop("_fine_format")
-        kname = ("k_sell<double,double,double,ECheb>" if fmt == 0 else
-                 f"k_spmv<{fmt},double,double,double,ECheb>")
+        kname = ("k_dia<double,double,double,ECheb>" if fmt == -1 else
+                 "k_sell<double,double,double,ECheb>" if fmt == 0 else f"k_spmv<{fmt},double,double,double,ECheb>")
         traffic, tsrc = CHEB_FINE_TRAFFIC.get(fmt, (None, "no ncu capture of this variant"))
         d = prof["chebyshev_fine"]
         ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
@@ -537,7 +537,8 @@ def gpu_arm(args, rank, world):
                             for k, v in prof.items()}}
         if prof_mx:
             fmx = prof_mx.pop("_fine_format")
-            roof["fine_kernel_mixed"] = ("k_sell<float,float,float,ECheb>" if fmx == 0 else
+            roof["fine_kernel_mixed"] = ("k_dia<float,float,float,ECheb>" if fmx == -1 else
+                                         "k_sell<float,float,float,ECheb>" if fmx == 0 else
                                          f"k_spmv<{fmx},float,float,float,ECheb>")
             roof["classes_mixed"] = {k: {"launches": v["launches"], "ms": v["ms"],
                                          "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}

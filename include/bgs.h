@@ -57,10 +57,13 @@ typedef struct {
     double rtol;            /* stop when ||b - A x|| / ||b|| <= rtol, true residual (default 1e-8) */
     int precision;          /* 0: FP64 hierarchy; 1: FP32 hierarchy + BF16 coupling values */
     int graph;              /* 1 (default): replay the preconditioner sweep as a captured CUDA graph */
-    int autotune;           /* 1 (default): pick SELL-32 or CSR (1..32 lanes per row) per stored operator by
-                               timing at setup, in the precision the solve uses; choices are cached per
-                               process by operator shape, and in the text file named by the environment
-                               variable BGS_AUTOTUNE_CACHE when it is set */
+    int autotune;           /* 1 (default): pick the SpMV form per stored operator by timing at setup, in the
+                               precision the solve uses: SELL-32 with diagonal offsets (structured
+                               operators), SELL-32, or CSR with 1..32 lanes per row, each at 128, 256 or
+                               512 threads per block; choices are cached per process by operator shape,
+                               and in the text file named by the environment variable BGS_AUTOTUNE_CACHE
+                               when it is set.  0: the diagonal-offset form where built, else SELL-32
+                               where built, else CSR with a lane count fixed by the row length */
     int cheb_degree[8];     /* Chebyshev degree per field id (Sec. 2.2.1: 2; voltage blocks 4, Sec. 3.1.5) */
     double theta[8];        /* strength drop tolerance per field id (Sec. 3.1.4: 0.04 for phi_s) */
     int max_coarse;         /* stop coarsening at this many rows (default 500; the paper uses 5000 with
@@ -194,9 +197,10 @@ int bgs_level_ellipse(bgs_handle h, int field, int level, double *imag);
  * (rows + 1), col and val (nnz each) are filled when not NULL (host or device).  BGS_INVALID_ARG for
  * a field on the V-cycle. */
 int bgs_ilu_factors(bgs_handle h, int field, int64_t *nnz, int32_t *rowptr, int32_t *col, double *val);
-/* SpMV kernel used for A_l (which 0), P_l (1) or R_l (2): 0 = SELL-32, k > 0 = CSR with k threads
- * per row (chosen by the autotuner when it is on). */
-int bgs_level_format(bgs_handle h, int field, int level, int which, int *format);
+/* SpMV kernel used for A_l (which 0), P_l (1) or R_l (2): -1 = SELL-32 with one diagonal offset per
+ * slice slot (structured operators), 0 = SELL-32, k > 0 = CSR with k threads per row (chosen by the
+ * autotuner when it is on); *threads_per_block (may be NULL) receives the block size of its launches. */
+int bgs_level_format(bgs_handle h, int field, int level, int which, int *format, int *threads_per_block);
 /* Aggregate id of every node of level `level` (host array of rows(level) entries). */
 int bgs_level_aggregates(bgs_handle h, int field, int level, int32_t *agg);
 /* Strength decision of every stored entry of A_l (Sec. 2.2.1 drop tolerance: 1 strong, 0 weak or the

@@ -82,7 +82,7 @@ def lib():
             "bgs_level_copy": (i32, [vp, i32, i32, i32, vp, vp, vp]),
             "bgs_level_aggregates": (i32, [vp, i32, i32, vp]),
             "bgs_level_strength": (i32, [vp, i32, i32, vp]),
-            "bgs_level_format": (i32, [vp, i32, i32, i32, C.POINTER(C.c_int)]),
+            "bgs_level_format": (i32, [vp, i32, i32, i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
             "bgs_ilu_factors": (i32, [vp, i32, C.POINTER(C.c_int64), vp, vp, vp]),
             "bgs_level_ellipse": (i32, [vp, i32, i32, C.POINTER(C.c_double)]),
             "bgs_set_profiling": (i32, [vp, i32]),
@@ -333,11 +333,13 @@ class Solver:
                "bgs_ilu_factors")
         return rp, ci[:nnz.value], v[:nnz.value]
 
-    def bgs_level_format(self, field, level, which=0) -> int:
-        """0 = SELL-32, k > 0 = CSR with k threads per row."""
-        f = C.c_int()
-        _check(lib().bgs_level_format(self.h, int(field), int(level), int(which), C.byref(f)), "bgs_level_format")
-        return f.value
+    def bgs_level_format(self, field, level, which=0, with_block=False):
+        """-1 = SELL-32 with diagonal offsets, 0 = SELL-32, k > 0 = CSR with k threads per row; with
+        with_block, (format, threads per block)."""
+        f, t = C.c_int(), C.c_int()
+        _check(lib().bgs_level_format(self.h, int(field), int(level), int(which), C.byref(f), C.byref(t)),
+               "bgs_level_format")
+        return (f.value, t.value) if with_block else f.value
 
     def bgs_set_profiling(self, on=True):
         _check(lib().bgs_set_profiling(self.h, 1 if on else 0), "bgs_set_profiling")

@@ -283,30 +283,38 @@ __global__ void k_mis_out(int n, const int *rp, const int *ci, int *state, const
     if (local) atomicAdd(undecided, local);
 }
 
+// Rounds are launched in batches with one read-back per batch (each round leaves its count of
+// undecided nodes in its own slot); a round after the last one changes nothing, so the round count
+// is the first round that left no node undecided.
 static int mis2(const DCsr &S, uint32_t salt, int *state, Scratch &sc, cudaStream_t s) {
     const int n = S.n;
     DBuf<unsigned long long> m1((size_t)n, s);
     DBuf<int> f1((size_t)n, s);
+    constexpr int kBatch = 4;
+    DBuf<int> left((size_t)kBatch, s);
     CK(cudaMemsetAsync(state, 0, sizeof(int) * (size_t)n, s));
     const int g = grid_for(n, 256);
     int rounds = 0;
     for (;;) {
-        rounds++;
-        k_mis_m1<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, salt, m1.p);
-        CK_LAUNCH();
-        k_mis_select<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, salt, m1.p);
-        CK_LAUNCH();
-        k_mis_f1<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, f1.p);
-        CK_LAUNCH();
-        CK(cudaMemsetAsync(sc.flags.p + 4, 0, sizeof(int), s));
-        k_mis_out<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, f1.p, sc.flags.p + 4);
-        CK_LAUNCH();
-        CK(cudaMemcpyAsync(sc.h_flags + 4, sc.flags.p + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemsetAsync(left.p, 0, sizeof(int) * kBatch, s));
+        for (int b = 0; b < kBatch; b++) {
+            k_mis_m1<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, salt, m1.p);
+            CK_LAUNCH();
+            k_mis_select<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, salt, m1.p);
+            CK_LAUNCH();
+            k_mis_f1<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, f1.p);
+            CK_LAUNCH();
+            k_mis_out<<<g, 256, 0, s>>>(n, S.rp.p, S.ci.p, state, f1.p, left.p + b);
+            CK_LAUNCH();
+        }
+        CK(cudaMemcpyAsync(sc.h_flags + 20, left.p, sizeof(int) * kBatch, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (sc.h_flags[4] == 0) break;
+        for (int b = 0; b < kBatch; b++) {
+            rounds++;
+            if (sc.h_flags[20 + b] == 0) return rounds;
+        }
         if (rounds > n + 1) throw Error(BGS_INTERNAL, "MIS-2 did not terminate");
     }
-    return rounds;
 }
 
 __global__ void k_root_flag(int n, const int *state, int *f) {
@@ -841,6 +849,41 @@ __global__ void __launch_bounds__(128) k_sg_local_num(int n, const int *__restri
     }
 }
 
+__global__ void k_iota(int n, int *a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
+}
+
+// Products with few rows (the coarse levels): every row through the warp-hash kernels, each with a
+// global-memory table sized for its product count, so no classing by row length; three read-backs
+// (table total, row counts, error flag) instead of one per class.
+constexpr int kSgSmallRows = 16384;
+static void spgemm_small(const CsrView &A, const CsrView &B, DCsr &C, const int *ub, Scratch &sc,
+                         cudaStream_t s) {
+    const int n = A.n;
+    DBuf<int> rows((size_t)n, s);
+    k_iota<<<grid_for(n, 256), 256, 0, s>>>(n, rows.p);
+    CK_LAUNCH();
+    DBuf<long long> toff((size_t)n + 1, s);
+    k_big_tsize<<<grid_for(n, 256), 256, 0, s>>>(n, rows.p, ub, toff.p);
+    CK_LAUNCH();
+    const long long tot = scan_ll_inplace(toff.p, n, s);
+    DBuf<int> gk((size_t)tot, s);
+    DBuf<double> gv((size_t)tot, s);
+    k_sg_sym_big<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, rows.p, toff.p, gk.p, A.rp, A.ci, B.rp, B.ci,
+                                                                 C.rp.p);
+    CK_LAUNCH();
+    C.nnz = scan_exclusive(C.rp.p, C.rp.p, n, sc, s);
+    C.ci.alloc((size_t)C.nnz, s);
+    C.v.alloc((size_t)C.nnz, s);
+    CK(cudaMemsetAsync(sc.flags.p + 8, 0, sizeof(int), s));
+    k_sg_num_big<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, rows.p, toff.p, gk.p, gv.p, A.rp, A.ci, A.v, B.rp,
+                                                                 B.ci, B.v, C.rp.p, C.ci.p, C.v.p, sc.flags.p + 8);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(sc.h_flags + 8, sc.flags.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (sc.h_flags[8]) throw Error(BGS_INTERNAL, "SpGEMM numeric count differs from the symbolic count");
+}
+
 static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cudaStream_t s) {
     const int n = A.n;
     C.n = n;
@@ -854,6 +897,10 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
     DBuf<int> ub((size_t)n, s);
     k_sg_ub<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, ub.p);
     CK_LAUNCH();
+    if (n <= kSgSmallRows) {
+        spgemm_small(A, B, C, ub.p, sc, s);
+        return;
+    }
     // symbolic: short rows per thread, the rest per warp (shared table), then global tables
     const int gl = grid_for(n, 128, num_sms() * 32);
     DBuf<int> lcols((size_t)n * SG_LOCAL, s);   // sorted columns of the short rows
@@ -1117,6 +1164,147 @@ __global__ void k_gj_unscramble(int n, const double *D, const int *tau, double *
     }
 }
 
+// Blocked form: GJB_R pivot steps per pair of launches.  The panel kernel (one block) takes the
+// columns K = [k, k+R) of the state before the steps, chooses the R pivots by partial pivoting on an
+// LU-eliminated working copy (the rows at and below each pivot hold, in R sequential Gauss-Jordan
+// steps, the same values as in LU, so the choices are the same), interchanges the rows, and
+// computes D = A_KK^-1 of the pivot rows (Gauss-Jordan on R x R, pivots on the diagonal) and
+// F = -A_IK D for the other rows.  The update kernel then writes the state after the R steps:
+// columns K: D (pivot rows) and F (others); other columns: D A_KJ (pivot rows) and A_IJ + F A_KJ
+// (others), A_KJ the interchanged pivot rows.  In exact arithmetic this is the state R sequential
+// steps leave; GB300's FP64 tensor path (mma.sync f64) runs at the FP64 FMA rate, so the small
+// products stay on the FP64 pipe.
+constexpr int GJB_R = 8;
+constexpr int GJB_T = 256;
+constexpr int GJB_MAXN = 1280;   // both panel copies (2 x n x R doubles) in shared memory
+
+__global__ void __launch_bounds__(GJB_T) k_gjb_panel(int n, int k, int R, const double *__restrict__ S, int *perm,
+                                                      double *Dk, double *F, int *status) {
+    extern __shared__ double gjb_sm[];
+    double *C0 = gjb_sm;          // n x R, row-major [i * R + t]: the panel, rows interchanged
+    double *Cw = gjb_sm + n * R;  // working copy, eliminated below each pivot
+    __shared__ double bv_s[GJB_T / 32];
+    __shared__ int bi_s[GJB_T / 32];
+    __shared__ int piv_s;
+    __shared__ double D[GJB_R * GJB_R];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < n * R; e += blockDim.x) {
+        const int i = e / R, t = e - i * R;
+        const double v = S[(size_t)i * n + k + t];
+        C0[e] = v;
+        Cw[e] = v;
+    }
+    __syncthreads();
+    for (int t = 0; t < R; t++) {
+        const int c = k + t;
+        double best = -1.0;
+        int bi = INT_MAX;
+        for (int i = c + threadIdx.x; i < n; i += blockDim.x) {
+            const double a = fabs(Cw[i * R + t]);
+            if (gj_better(a, i, best, bi)) { best = a; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (gj_better(ov, oi, best, bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { bv_s[w] = best; bi_s[w] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 1; q < GJB_T / 32; q++)
+                if (gj_better(bv_s[q], bi_s[q], best, bi)) { best = bv_s[q]; bi = bi_s[q]; }
+            if (!(best > 0.0) || bi >= n) {   // singular: keep row c, report (the results are not used)
+                bi = c;
+                *status = 1;
+            }
+            piv_s = bi;
+            perm[c] = bi;
+        }
+        __syncthreads();
+        const int p = piv_s;
+        if (p != c)
+            for (int e = threadIdx.x; e < R; e += blockDim.x) {
+                double a = C0[c * R + e];
+                C0[c * R + e] = C0[p * R + e];
+                C0[p * R + e] = a;
+                a = Cw[c * R + e];
+                Cw[c * R + e] = Cw[p * R + e];
+                Cw[p * R + e] = a;
+            }
+        __syncthreads();
+        const int rest = R - t - 1;
+        if (rest > 0) {
+            const double pv = Cw[c * R + t];
+            for (int e = threadIdx.x; e < (n - c - 1) * rest; e += blockDim.x) {
+                const int i = c + 1 + e / rest, u = t + 1 + e % rest;
+                Cw[i * R + u] -= (Cw[i * R + t] / pv) * Cw[c * R + u];
+            }
+        }
+        __syncthreads();
+    }
+    // D = A_KK^-1 by Gauss-Jordan on the R x R block (one thread; the pivots are its diagonal)
+    if (threadIdx.x == 0) {
+        double M[GJB_R * GJB_R];
+        for (int r = 0; r < R; r++)
+            for (int q = 0; q < R; q++) M[r * R + q] = C0[(k + r) * R + q];
+        for (int t = 0; t < R; t++) {
+            const double rp = 1.0 / M[t * R + t];
+            for (int q = 0; q < R; q++) M[t * R + q] = q == t ? rp : M[t * R + q] * rp;
+            for (int r = 0; r < R; r++) {
+                if (r == t) continue;
+                const double f = M[r * R + t];
+                for (int q = 0; q < R; q++) M[r * R + q] = q == t ? -f * rp : M[r * R + q] - f * M[t * R + q];
+            }
+        }
+        for (int e = 0; e < R * R; e++) D[e] = M[e];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) Dk[e] = D[e];
+    for (int e = threadIdx.x; e < n * R; e += blockDim.x) {
+        const int i = e / R, t = e - i * R;
+        double f = 0.0;
+        if (i < k || i >= k + R)
+            for (int q = 0; q < R; q++) f -= C0[i * R + q] * D[q * R + t];
+        F[e] = f;
+    }
+}
+
+// position q after the block's row interchanges holds row src(q) of the state before them
+__device__ __forceinline__ int gjb_src(int q, int k, int R, const int *perm) {
+    for (int t = R - 1; t >= 0; t--) {
+        const int p = perm[k + t];
+        if (q == k + t) q = p;
+        else if (q == p) q = k + t;
+    }
+    return q;
+}
+
+__global__ void __launch_bounds__(GJB_T) k_gjb_update(int n, int k, int R, const double *__restrict__ S,
+                                                       double *__restrict__ Dout, const int *perm,
+                                                       const double *__restrict__ Dk, const double *__restrict__ F) {
+    __shared__ int srck[GJB_R];
+    __shared__ double Ds[GJB_R * GJB_R];
+    if (threadIdx.x < R) srck[threadIdx.x] = gjb_src(k + threadIdx.x, k, R, perm);
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ds[e] = Dk[e];
+    __syncthreads();
+    const unsigned un = (unsigned)n, total = un * un;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int i = (int)(t / un), j = (int)(t - (unsigned)i * un);
+        const bool piv_row = i >= k && i < k + R;
+        double out;
+        if (j >= k && j < k + R) {
+            out = piv_row ? Ds[(i - k) * R + (j - k)] : F[(size_t)i * R + (j - k)];
+        } else if (piv_row) {
+            out = 0.0;
+            for (int q = 0; q < R; q++) out += Ds[(i - k) * R + q] * S[(size_t)srck[q] * n + j];
+        } else {
+            out = S[(size_t)gjb_src(i, k, R, perm) * n + j];
+            for (int q = 0; q < R; q++) out += F[(size_t)i * R + q] * S[(size_t)srck[q] * n + j];
+        }
+        Dout[t] = out;
+    }
+}
+
 // Radius of the skew-symmetric part S = (M - M^T)/2 of M = D^-1/2 A D^-1/2 (D = diag(A), all
 // positive, else 0): a Bendixson bound on |Im| of the eigenvalues of D^-1 A.  Power iteration on
 // S^T S = -S S from the hashed start, CSR kernels fixed by the shape, no host round trip until the
@@ -1195,18 +1383,32 @@ static void dense_inverse_async(const DCsr &Ac, double *W, Scratch &sc, cudaStre
     CK(cudaMemsetAsync(a.p, 0, sizeof(double) * (size_t)n * n, s));
     k_to_dense_rm<<<grid_for(n, 256), 256, 0, s>>>(n, Ac.rp.p, Ac.ci.p, Ac.v.p, a.p);
     CK_LAUNCH();
-    const int g0 = std::min(g, grid_for(n, GJ_T, num_sms()));
-    k_gj_first<<<g0, GJ_T, 0, s>>>(n, a.p, cv.p, cidx.p);
-    CK_LAUNCH();
     double *S = a.p, *D = b.p;
-    int gin = g0;
-    for (int k = 0; k < n; k++) {
-        const int in = k & 1, out = in ^ 1;
-        k_gj_step<<<g, GJ_T, 0, s>>>(n, k, S, D, cv.p + (size_t)in * g, cidx.p + (size_t)in * g, gin,
-                                     cv.p + (size_t)out * g, cidx.p + (size_t)out * g, perm.p, sc.flags.p + 6);
+    if (n <= GJB_MAXN) {
+        // blocked: GJB_R pivot steps per panel launch and update launch
+        DBuf<double> Dk((size_t)GJB_R * GJB_R, s), F((size_t)n * GJB_R, s);
+        const size_t smem = sizeof(double) * 2 * (size_t)n * GJB_R;
+        for (int k = 0; k < n; k += GJB_R) {
+            const int R = std::min(GJB_R, n - k);
+            k_gjb_panel<<<1, GJB_T, smem, s>>>(n, k, R, S, perm.p, Dk.p, F.p, sc.flags.p + 6);
+            CK_LAUNCH();
+            k_gjb_update<<<g, GJB_T, 0, s>>>(n, k, R, S, D, perm.p, Dk.p, F.p);
+            CK_LAUNCH();
+            std::swap(S, D);
+        }
+    } else {
+        const int g0 = std::min(g, grid_for(n, GJ_T, num_sms()));
+        k_gj_first<<<g0, GJ_T, 0, s>>>(n, a.p, cv.p, cidx.p);
         CK_LAUNCH();
-        std::swap(S, D);
-        gin = g;
+        int gin = g0;
+        for (int k = 0; k < n; k++) {
+            const int in = k & 1, out = in ^ 1;
+            k_gj_step<<<g, GJ_T, 0, s>>>(n, k, S, D, cv.p + (size_t)in * g, cidx.p + (size_t)in * g, gin,
+                                         cv.p + (size_t)out * g, cidx.p + (size_t)out * g, perm.p, sc.flags.p + 6);
+            CK_LAUNCH();
+            std::swap(S, D);
+            gin = g;
+        }
     }
     k_gj_tau<<<1, 1, 0, s>>>(n, perm.p, tau.p);
     CK_LAUNCH();
@@ -1241,6 +1443,8 @@ static void set_attributes() {
                                 (int)(sizeof(int) * SG_WARPS * SG_SYM_T)));
         CK(cudaFuncSetAttribute(k_sg_num<SG_NUM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(double) * SG_WARPS * (SG_NUM_T + 64) + sizeof(int) * SG_WARPS * SG_NUM_T)));
+        CK(cudaFuncSetAttribute(k_gjb_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(double) * 2 * GJB_MAXN * GJB_R)));
     });
 }
 

@@ -100,6 +100,7 @@ struct bgs_ctx {
     cudaStream_t gs = nullptr;
     CycleGraph cyc[2];
     DBuf<double> gv, gz;
+    DBuf<float> zf;                 // mixed precision: FP32 copy of the sweep output for the couplings
     bool prof = false;
     std::vector<EventPair> ev;
     size_t ev_used = 0;
@@ -147,8 +148,13 @@ void prof_collect(bgs_ctx *h) {
     h->ev_used = 0;
 }
 
+// Algorithmic bytes of one application: the stored values once, the index data of the form in use
+// (CSR / SELL-32: a column index per entry and the row pointers; diagonal-offset SELL-32: one offset
+// per slot of 32 rows and the slice pointers), x read and y written once, plus extra vectors.
 double spmv_bytes(const DCsr &A, int vbytes, int xbytes, int extra_vectors) {
-    return (double)A.nnz * (vbytes + 4) + 4.0 * (A.n + 1) + (double)xbytes * A.n * (2 + extra_vectors);
+    const double idx = A.dia ? 4.0 * (double)(A.dia_nnz / 32) + 4.0 * ((A.n + 31) / 32 + 1)
+                             : 4.0 * (double)A.nnz + 4.0 * (A.n + 1);
+    return (double)A.nnz * vbytes + idx + (double)xbytes * A.n * (2 + extra_vectors);
 }
 
 // ------------------------------------------------------------------ typed buffer access
@@ -336,6 +342,10 @@ void sweep(bgs_ctx *h, const double *v, double *z, bool transposed) {
         return;
     }
     cudaStream_t s = h->s;
+    // FP32 block solves: each block's output is also kept in FP32 (zf), and the couplings of the
+    // later blocks gather that copy (half the bytes of the FP64 z; the same values, since z holds
+    // the FP32 results widened)
+    float *zf = std::is_same<XT, float>::value ? h->zf.p : nullptr;
     for (int p = 0; p < h->F; p++) {
         const int k = transposed ? h->order[h->F - 1 - p] : h->order[p];
         Hier &H = h->H[k];
@@ -344,13 +354,23 @@ void sweep(bgs_ctx *h, const double *v, double *z, bool transposed) {
         XT *b0 = Buf<XT>::b(L0);
         const DCsr &C = transposed ? h->upperT[k] : h->lower[k];
         if (C.nnz > 0) {
-            Prof pf(h, 3, spmv_bytes(C, sizeof(CVT), 8, 1));
-            coupling_sub<CVT, XT>(C, v + h->offs[k], z, b0, s);
+            Prof pf(h, 3, spmv_bytes(C, sizeof(CVT), zf ? 4 : 8, 1));
+            if constexpr (std::is_same<XT, float>::value) {
+                if (zf) coupling_sub<CVT, XT, float>(C, v + h->offs[k], zf, b0, s);
+                else coupling_sub<CVT, XT, double>(C, v + h->offs[k], z, b0, s);
+            } else {
+                coupling_sub<CVT, XT, double>(C, v + h->offs[k], z, b0, s);
+            }
         } else {
             copy_in<XT>(v + h->offs[k], b0, nk, s);
         }
         XT *xk = block_solve<VT, XT>(h, H, transposed);
-        copy_out<XT>(xk, z + h->offs[k], nk, s);
+        if constexpr (std::is_same<XT, float>::value) {
+            if (zf) copy_f2d_keep(xk, z + h->offs[k], zf + h->offs[k], nk, s);
+            else copy_out<XT>(xk, z + h->offs[k], nk, s);
+        } else {
+            copy_out<XT>(xk, z + h->offs[k], nk, s);
+        }
     }
 }
 
@@ -551,7 +571,7 @@ void group_sweep(bgs_ctx *h, const Group &G, const double *v, double *z, bool tr
         const DCsr &C = transposed ? h->gi_upperT[k] : h->gi_lower[k];
         if (C.nnz > 0 && !h->opt.jacobi) {
             Prof pf(h, 3, spmv_bytes(C, sizeof(CVT), 8, 1));
-            coupling_sub<CVT, XT>(C, v + off, z, b0, s);
+            coupling_sub<CVT, XT, double>(C, v + off, z, b0, s);
         } else {
             copy_in<XT>(v + off, b0, nk, s);
         }
@@ -576,7 +596,7 @@ void apply_nested(bgs_ctx *h, const double *v, double *z, bool adjoint) {
             const DCsr &C = adjoint ? h->go_upperT[k] : h->go_lower[k];
             if (C.nnz > 0 && !h->opt.jacobi) {
                 Prof pf(h, 3, spmv_bytes(C, 8, 8, 1));
-                coupling_sub<double, double>(C, v + h->offs[k], z, rk, s);
+                coupling_sub<double, double, double>(C, v + h->offs[k], z, rk, s);
             } else {
                 CK(cudaMemcpyAsync(rk, v + h->offs[k], sizeof(double) * (size_t)h->sizes[k],
                                    cudaMemcpyDeviceToDevice, s));
@@ -660,8 +680,10 @@ void build_groups(bgs_ctx *h) {
         vstack(rb, (int)gr.n, gr.A, s);
         gr.A.m = (int)gr.n;
         build_sell(gr.A, kMaxPad, h->sc, s);
+        build_dia(gr.A, kMaxPadDia, h->sc, s);
         transpose_csr(view(gr.A), gr.AT, h->sc, s);
         build_sell(gr.AT, kMaxPad, h->sc, s);
+        build_dia(gr.AT, kMaxPadDia, h->sc, s);
         gr.K.alloc(gr.n, h->opt.inner_restart, s);
     }
     for (int k = 0; k < h->F; k++) {
@@ -718,11 +740,36 @@ void copy_block_data(const bgs_csr &in, DCsr &out, cudaStream_t s) {
     }
 }
 
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// BGS_TRACE=1: wall time of the phases of bgs_create (stream synchronised at each mark)
+struct CreateTrace {
+    bool on = getenv("BGS_TRACE") != nullptr;
+    cudaStream_t s;
+    double t;
+    explicit CreateTrace(cudaStream_t st) : s(st) {
+        if (on) {
+            cudaStreamSynchronize(s);
+            t = now_ms();
+        }
+    }
+    void mark(const char *what) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        const double n = now_ms();
+        fprintf(stderr, "bgs-trace create %-22s %8.3f ms\n", what, n - t);
+        t = n;
+    }
+};
+
 // The stored blocks' copies on two side streams (host buffers: more host-to-device bandwidth than
 // one stream; each block's validation on s overlaps the copies of the blocks after it), the
 // validation error bits one slot per block, read back once.
 int copy_and_validate(bgs_ctx *h, const int64_t *sizes, const bgs_csr *blocks, cudaStream_t s) {
     const int F = h->F;
+    CreateTrace tr(s);
     std::vector<int> todo;   // r * F + c of the stored blocks, largest first
     for (int r = 0; r < F; r++)
         for (int c = 0; c < F; c++) {
@@ -741,6 +788,7 @@ int copy_and_validate(bgs_ctx *h, const int64_t *sizes, const bgs_csr *blocks, c
         }
     std::stable_sort(todo.begin(), todo.end(), [&](int a, int b) { return blocks[a].nnz > blocks[b].nnz; });
     DBuf<int> flags(std::max<size_t>(todo.size(), 1), s);
+    tr.mark("  allocate block copies");
     cudaStream_t cs[2] = {nullptr, nullptr};
     cudaEvent_t ready = nullptr;
     std::vector<cudaEvent_t> done(todo.size(), nullptr);
@@ -758,6 +806,7 @@ int copy_and_validate(bgs_ctx *h, const int64_t *sizes, const bgs_csr *blocks, c
             CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
             CK(cudaStreamWaitEvent(q, ready, 0));
         }
+        tr.mark("  copy streams");
         int64_t load[2] = {0, 0};
         for (size_t i = 0; i < todo.size(); i++) {
             const int b = todo[i];
@@ -773,6 +822,7 @@ int copy_and_validate(bgs_ctx *h, const int64_t *sizes, const bgs_csr *blocks, c
         if (!todo.empty())
             CK(cudaMemcpyAsync(hf.data(), flags.p, sizeof(int) * todo.size(), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));   // s waited for every copy, so the side streams are idle
+        tr.mark("  copies + validation");
         cleanup();
         for (int f : hf)
             if (int st = validate_status(f)) return st;
@@ -870,6 +920,7 @@ void build_adjoint(bgs_ctx *h) {
     }
     transpose_csr(view(h->full), h->fullT, h->sc, s);
     build_sell(h->fullT, kMaxPad, h->sc, s);
+    build_dia(h->fullT, kMaxPadDia, h->sc, s);
     for (int k = 0; k < h->F; k++) {
         // rows of field k: sum over pos(j) > pos(k) of A_jk^T (global columns)
         std::vector<DCsr> tr;
@@ -908,6 +959,7 @@ void build_adjoint(bgs_ctx *h) {
         for (size_t l = 0; l + 1 < H.L.size(); l++) {
             transpose_csr(view(H.L[l].A), H.L[l].AT, h->sc, s);
             build_sell(H.L[l].AT, kMaxPad, h->sc, s);
+            if (l == 0) build_dia(H.L[l].AT, kMaxPadDia, h->sc, s);
             if (h->opt.precision == 1) {
                 H.L[l].AT.vf.alloc((size_t)H.L[l].AT.nnz, s);
                 convert_d2f(H.L[l].AT.v.p, H.L[l].AT.vf.p, H.L[l].AT.nnz, s);
@@ -977,29 +1029,6 @@ int guarded(F &&f) {
     }
 }
 
-double now_ms() {
-    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
-}
-
-// BGS_TRACE=1: wall time of the phases of bgs_create (stream synchronised at each mark)
-struct CreateTrace {
-    bool on = getenv("BGS_TRACE") != nullptr;
-    cudaStream_t s;
-    double t;
-    explicit CreateTrace(cudaStream_t st) : s(st) {
-        if (on) {
-            cudaStreamSynchronize(s);
-            t = now_ms();
-        }
-    }
-    void mark(const char *what) {
-        if (!on) return;
-        cudaStreamSynchronize(s);
-        const double n = now_ms();
-        fprintf(stderr, "bgs-trace create %-22s %8.3f ms\n", what, n - t);
-        t = n;
-    }
-};
 
 }  // namespace
 
@@ -1132,8 +1161,10 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
         tr.mark("copy+validate blocks");
         assemble_operators(h.get(), h->full, h->lower, s);
         tr.mark("full operator + couplings");
-        build_sell(h->full, kMaxPad, h->sc, s);
-        for (int k = 0; k < F; k++) build_sell(h->lower[k], kMaxPad, h->sc, s);
+        // the layouts the autotuner will choose from (only its cached choice when it has one)
+        const bool tune = o.autotune != 0;
+        build_formats(h->full, 8, true, tune, h->sc, s);
+        for (int k = 0; k < F; k++) build_formats(h->lower[k], o.precision == 1 ? 2 : 8, false, tune, h->sc, s);
         CK(cudaStreamSynchronize(s));
         tr.mark("sell");
         *out = h.release();
@@ -1208,8 +1239,11 @@ void build_block(bgs_ctx *h, int k, cudaStream_t sk, Scratch &sck) {
     }
     amg_build(H, params_for(h, k), sck, sk);
     if (H.status) throw Error(H.status, "coarsest-level factorisation");
+    // the SpMV layouts of the level operators (the diagonal-offset form for the level-0 stencil
+    // operator only, whose offsets repeat); only the autotuner's cached choice when it has one
     for (size_t l = 0; l + 1 < H.L.size(); l++)
-        for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R}) build_sell(*M, kMaxPad, sck, sk);
+        for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R})
+            build_formats(*M, mixed ? 4 : 8, M == &H.L[0].A, h->opt.autotune != 0, sck, sk);
     for (size_t l = 0; l < H.L.size(); l++) {
         Level &Lv = H.L[l];
         if (mixed) {
@@ -1259,6 +1293,7 @@ extern "C" int bgs_setup(bgs_handle h) {
             autotune_spmv(h->full, 8, h->sc, s);
         }
         h->K.alloc(total_n(h), h->opt.restart, s);
+        if (mixed) h->zf.alloc((size_t)total_n(h), s);
         build_groups(h);
         h->adjoint_ready = false;
         drop_graphs(h);
@@ -1493,14 +1528,15 @@ int bgs_ilu_factors(bgs_handle h, int field, int64_t *nnz, int32_t *rowptr, int3
     });
 }
 
-int bgs_level_format(bgs_handle h, int field, int level, int which, int *format) {
+int bgs_level_format(bgs_handle h, int field, int level, int which, int *format, int *threads_per_block) {
     if (!h || field < 0 || field >= h->F || which < 0 || which > 2 || !format) return BGS_INVALID_ARG;
     if (!h->setup_done) return BGS_NOT_SETUP;
     Hier &H = h->H[field];
     if (level < 0 || level >= (int)H.L.size()) return BGS_INVALID_ARG;
     if (which > 0 && level + 1 >= (int)H.L.size()) return BGS_INVALID_ARG;
     const DCsr &M = which == 0 ? H.L[level].A : (which == 1 ? H.L[level].P : H.L[level].R);
-    *format = M.sell ? 0 : (M.lanes ? M.lanes : choose_lanes(M.n, M.nnz));
+    *format = M.dia ? -1 : (M.sell ? 0 : (M.lanes ? M.lanes : choose_lanes(M.n, M.nnz)));
+    if (threads_per_block) *threads_per_block = M.tpb;
     return BGS_OK;
 }
 

@@ -99,6 +99,7 @@ struct DCsr {
     DBuf<float> vf;
     DBuf<__nv_bfloat16> vb;
     int lanes = 0;          // CSR SpMV threads per row chosen for this matrix
+    int tpb = 256;          // threads per block of its SpMV launches (autotuned: 128, 256 or 512)
     // SELL-32 copy (sell == true when built): slice offsets, columns (a padded slot repeats
     // its slice's first stored column, with value 0), CSR index of each slot (-1 pad)
     bool sell = false;
@@ -107,6 +108,17 @@ struct DCsr {
     DBuf<double> sv;
     DBuf<float> svf;
     DBuf<__nv_bfloat16> svb;
+    // SELL-32 with one diagonal offset per slot (dia == true when built): slice s of 32 rows holds
+    // w_s <= 32 slots, slot k one offset o for all its rows (entry column = row + o), so no column
+    // index is stored per entry; a row without an entry at that offset holds value 0 there.  Used for
+    // the structured operators (stencil blocks, the full operator), where the offsets repeat.
+    bool dia = false;
+    int64_t dia_nnz = 0;            // value slots (32 per slice and offset)
+    DBuf<int> dptr, doff, dperm;    // slot start per slice (multiple of 32); offsets at dptr[s]/32 + k;
+                                    // CSR index of each slot (-1: padding)
+    DBuf<double> dv;
+    DBuf<float> dvf;
+    DBuf<__nv_bfloat16> dvb;
 };
 
 // ------------------------------------------------------------------------------------------

@@ -36,6 +36,9 @@ void release_cached_memory();
 // out[0..n] = exclusive scan of in[0..n-1] (out[n] = total); in and out may alias.
 // Returns the total (synchronises the stream).  Throws if the total exceeds INT32_MAX.
 int64_t scan_exclusive(const int *in, int *out, int64_t n, Scratch &sc, cudaStream_t s);
+// a[0..n] = exclusive scan of a[0..n-1] in place (a has n + 1 entries; one block); returns a[n]
+// (synchronises the stream)
+long long scan_ll_inplace(long long *a, int n, cudaStream_t s);
 // sum of squares / dot products into a device scalar (deterministic two-pass reduction).
 void dev_dot(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s);
 // the same, and out[1] = 1/sqrt(out[0]) (0 when out[0] is 0)
@@ -57,6 +60,8 @@ void convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
 void convert_d2bf(const double *in, __nv_bfloat16 *out, int64_t n, cudaStream_t s);
 void copy_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
 void copy_f2d(const float *in, double *out, int64_t n, cudaStream_t s);
+// out = (double) in and out_f = in (an FP32 output kept beside its FP64 copy)
+void copy_f2d_keep(const float *in, double *out, float *out_f, int64_t n, cudaStream_t s);
 void extract_diag(const CsrView &A, double *diag, cudaStream_t s);
 void reciprocal(const double *in, double *out, int64_t n, cudaStream_t s);
 // dvals[e] = -lam[roff + i] * x[coff + j]
@@ -79,9 +84,9 @@ void cheb_step(const DCsr &A, const XT *b, const XT *dinv, const XT *xin, XT *xo
                double scale, bool first, cudaStream_t s);
 template <class XT>
 void cheb_first(int n, const XT *b, const XT *dinv, double inv_theta, XT *x, XT *e, cudaStream_t s);
-// r = v - L z (L with global columns into z), v/z FP64, output typed
-template <class VT, class XT>
-void coupling_sub(const DCsr &L, const double *v, const double *z, XT *r, cudaStream_t s);
+// r = v - L z (L with global columns into z), v FP64, z FP64 or its FP32 copy, output typed
+template <class VT, class XT, class ZT>
+void coupling_sub(const DCsr &L, const double *v, const ZT *z, XT *r, cudaStream_t s);
 // w_i = dinv_i * (A v)_i (FP64, power iteration)
 void spmv_scaled(const CsrView &A, const double *dinv, const double *v, double *w, cudaStream_t s);
 // w_i = dinv_i * (A v)_i * (*rnorm), rnorm = 1/||v|| on the device (power iteration step on a
@@ -94,14 +99,25 @@ void dense_gemv(int n, const double *W, const XT *x, XT *y, cudaStream_t s);
 // Builds the SELL-32 copy when its padding stays within max_pad * nnz (returns whether built);
 // sell_refresh re-gathers the FP32 / BF16 value copies after they are created.
 bool build_sell(DCsr &A, double max_pad, Scratch &sc, cudaStream_t s);
+// Builds the diagonal-offset SELL-32 copy when every slice has at most 32 distinct offsets and the
+// slots stay within max_pad * nnz (returns whether built).  Only for operators whose input vectors
+// are fully written when they are applied (a padded slot reads a neighbouring entry times 0).
+bool build_dia(DCsr &A, double max_pad, Scratch &sc, cudaStream_t s);
+void drop_dia(DCsr &A);
+// re-gathers the FP32 / BF16 value copies of the SELL forms after those copies are created
 void sell_refresh(DCsr &A, cudaStream_t s);
 // After A.v changed in place: re-derive the FP32 / BF16 copies that exist and re-gather every
 // SELL value copy (no allocation when the copies exist).
 void refresh_values(DCsr &A, cudaStream_t s);
-// Times SELL-32 (if built) against CSR with 1..32 lanes per row and keeps the fastest for A
-// (cached per shape); returns 0 for SELL or the lane count.
-// value_bytes selects the precision timed (8 FP64, 4 FP32 hierarchy, 2 BF16 couplings).
+// Times the diagonal-offset SELL-32 and SELL-32 (if built) and CSR with 1..32 lanes per row, each at
+// 128, 256 and 512 threads per block, and keeps the fastest for A (cached per shape); returns -1
+// (diagonal-offset SELL), 0 (SELL-32) or the lane count.  value_bytes selects the precision timed
+// (8 FP64, 4 FP32 hierarchy, 2 BF16 couplings).
 int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s);
+// Builds the SpMV layouts an operator may run: the one the autotuner's cached choice for its shape
+// names (use_cache), else SELL-32 and, with allow_dia, the diagonal-offset SELL-32 for the
+// autotuner to time.  value_bytes as for autotune_spmv.
+void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scratch &sc, cudaStream_t s);
 
 // ---------------------------------------------------------------- krylov.cu
 // h[k] = V_k . w for k < cnt and h[cnt] = w . w (V column-major, leading dimension ld, even; V and w
@@ -216,5 +232,7 @@ void take_values(DCsr &dst, const DCsr &src, Scratch &sc, cudaStream_t s);
 void transpose_csr(const CsrView &A, DCsr &T, Scratch &sc, cudaStream_t s);
 // SELL-32 is used for an operator when its padding adds at most this factor to the stored entries
 constexpr double kMaxPad = 2.0;
+// the diagonal-offset SELL-32 copy is built when its slots stay within this factor of the entries
+constexpr double kMaxPadDia = 1.5;
 
 }  // namespace bgs

@@ -1,32 +1,40 @@
 // SpMV with fused epilogues (K1, K2, K10, K11, K13).
 //
-// Two storage paths share every epilogue:
+// Three storage paths share every epilogue:
 //  * SELL-32 (the fine-level operators, the full operator, prolongators): one thread per row,
 //    a warp owns a slice of 32 rows stored column-major, so entry j of the 32 rows is one
 //    contiguous 256-byte (FP64) / 128-byte (index) run; no row-pointer round trip; the epilogue
 //    (residual, Chebyshev step, prolongation add, coupling subtraction) is fully coalesced.
+//  * SELL-32 with diagonal offsets (structured operators): the same slices, but slot k of a slice
+//    stores one offset o for its 32 rows (column = row + o) instead of 32 column indices, so the
+//    index stream (a third of the FP64 CSR bytes, half of the FP32 ones) shrinks 32-fold; rows
+//    missing an offset hold 0 there.  The entries of a row are still summed in column order.
 //  * CSR with L threads per row (coarse levels with long, irregular rows): rows are taken in
 //    warp-uniform strips of 32/L rows, the L lanes stride over the row and reduce by shuffles.
+// Every path is instantiated for 128, 256 and 512 threads per block (rows per block = threads / L
+// for CSR, = threads for the SELL forms); the autotuner picks the format and the block size.
 #include <cstdio>
 #include <cstdlib>
 #include <map>
 #include <mutex>
 #include <tuple>
 
+#include <climits>
+
 #include "spmv_dev.cuh"
 
 namespace bgs {
 
 // ------------------------------------------------------------------------------------------ CSR
-template <int L, class VT, class XT, class AT, class Epi>
-__global__ void __launch_bounds__(256) k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+template <int L, class VT, class XT, class AT, class Epi, int TPB>
+__global__ void __launch_bounds__(TPB) k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                               const VT *__restrict__ val, const XT *__restrict__ x, Epi epi) {
     spmv_rows<L, VT, XT, AT>(n, rp, ci, val, x, epi);
 }
 
 // ------------------------------------------------------------------------------------------ SELL-32
-template <class VT, class XT, class AT, class Epi>
-__global__ void __launch_bounds__(256) k_sell(int n, const int *__restrict__ sptr, const int *__restrict__ sci,
+template <class VT, class XT, class AT, class Epi, int TPB>
+__global__ void __launch_bounds__(TPB) k_sell(int n, const int *__restrict__ sptr, const int *__restrict__ sci,
                                               const VT *__restrict__ sv, const XT *__restrict__ x, Epi epi) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     const int slice = row >> 5;
@@ -80,40 +88,88 @@ __global__ void __launch_bounds__(256) k_sell(int n, const int *__restrict__ spt
     if (row < n) epi(row, acc);
 }
 
-// value arrays of a matrix by element type (CSR order / SELL order)
+// ------------------------------------------------------------------------------------------ SELL-32, diagonal offsets
+// Slice of 32 rows per warp; lane k holds the slice's k-th offset (w <= 32), broadcast by shuffle.
+// A padded slot's column is clamped into [0, m) (its value is 0).
+template <class VT, class XT, class AT, class Epi, int TPB>
+__global__ void __launch_bounds__(TPB) k_dia(int n, int m, const int *__restrict__ dptr, const int *__restrict__ doff,
+                                             const VT *__restrict__ dv, const XT *__restrict__ x, Epi epi) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = row >> 5;
+    if ((slice << 5) >= n) return;          // whole warp past the end
+    const int lane = row & 31;
+    const int s0 = __ldg(dptr + slice);
+    const int w = (__ldg(dptr + slice + 1) - s0) >> 5;
+    const int myo = lane < w ? __ldg(doff + (s0 >> 5) + lane) : 0;
+    const VT *v = dv + s0 + lane;
+    const int last = m - 1;
+    constexpr bool S = Epi::kSub;
+    AT acc = row < n ? epi.template start<AT>(row) : (AT)0;
+    // batches of U slots, all loads of a batch in flight together: a slot past the slice width
+    // re-reads the last one (a cached duplicate) and its product is skipped (w is warp-uniform)
+    constexpr int U = (sizeof(AT) == 4 && sizeof(VT) == 4) ? 8 : 4;
+#pragma unroll 1
+    for (int k = 0; k < w; k += U) {
+        AT a[U], xv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int kk = min(k + u, w - 1);
+            const int c = min(max(row + __shfl_sync(0xffffffffu, myo, kk), 0), last);
+            a[u] = Cvt<AT>::f(ldg(v + kk * 32));
+            xv[u] = Cvt<AT>::f(ldg(x + c));
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (k + u < w) acc = mac<S>(acc, a[u], xv[u]);
+    }
+    if (row < n) epi(row, acc);
+}
+
+// value arrays of a matrix by element type (CSR order / SELL order / diagonal-offset order)
 template <class VT>
 struct Vals;
 template <>
 struct Vals<double> {
     static const double *csr(const DCsr &A) { return A.v.p; }
     static const double *sell(const DCsr &A) { return A.sv.p; }
+    static const double *dia(const DCsr &A) { return A.dv.p; }
 };
 template <>
 struct Vals<float> {
     static const float *csr(const DCsr &A) { return A.vf.p; }
     static const float *sell(const DCsr &A) { return A.svf.p; }
+    static const float *dia(const DCsr &A) { return A.dvf.p; }
 };
 template <>
 struct Vals<__nv_bfloat16> {
     static const __nv_bfloat16 *csr(const DCsr &A) { return A.vb.p; }
     static const __nv_bfloat16 *sell(const DCsr &A) { return A.svb.p; }
+    static const __nv_bfloat16 *dia(const DCsr &A) { return A.dvb.p; }
 };
+
+template <class VT, class XT, class AT, class Epi, int TPB>
+static void launch_csr_tpb(int lanes, int n, const int *rp, const int *ci, const VT *val, const XT *x, Epi epi,
+                           cudaStream_t s) {
+    const int rows_per_block = TPB / lanes;
+    const int g = grid_for(n, rows_per_block, num_sms() * (8192 / TPB));
+    switch (lanes) {
+        case 1: k_spmv<1, VT, XT, AT, Epi, TPB><<<g, TPB, 0, s>>>(n, rp, ci, val, x, epi); break;
+        case 2: k_spmv<2, VT, XT, AT, Epi, TPB><<<g, TPB, 0, s>>>(n, rp, ci, val, x, epi); break;
+        case 4: k_spmv<4, VT, XT, AT, Epi, TPB><<<g, TPB, 0, s>>>(n, rp, ci, val, x, epi); break;
+        case 8: k_spmv<8, VT, XT, AT, Epi, TPB><<<g, TPB, 0, s>>>(n, rp, ci, val, x, epi); break;
+        case 16: k_spmv<16, VT, XT, AT, Epi, TPB><<<g, TPB, 0, s>>>(n, rp, ci, val, x, epi); break;
+        default: k_spmv<32, VT, XT, AT, Epi, TPB><<<g, TPB, 0, s>>>(n, rp, ci, val, x, epi); break;
+    }
+    CK_LAUNCH();
+}
 
 template <class VT, class XT, class AT, class Epi>
 static void launch_csr(int lanes, int n, const int *rp, const int *ci, const VT *val, const XT *x, Epi epi,
-                       cudaStream_t s) {
+                       cudaStream_t s, int tpb = 256) {
     if (n <= 0) return;
-    int rows_per_block = 256 / lanes;
-    int g = grid_for(n, rows_per_block, num_sms() * 32);
-    switch (lanes) {
-        case 1: k_spmv<1, VT, XT, AT, Epi><<<g, 256, 0, s>>>(n, rp, ci, val, x, epi); break;
-        case 2: k_spmv<2, VT, XT, AT, Epi><<<g, 256, 0, s>>>(n, rp, ci, val, x, epi); break;
-        case 4: k_spmv<4, VT, XT, AT, Epi><<<g, 256, 0, s>>>(n, rp, ci, val, x, epi); break;
-        case 8: k_spmv<8, VT, XT, AT, Epi><<<g, 256, 0, s>>>(n, rp, ci, val, x, epi); break;
-        case 16: k_spmv<16, VT, XT, AT, Epi><<<g, 256, 0, s>>>(n, rp, ci, val, x, epi); break;
-        default: k_spmv<32, VT, XT, AT, Epi><<<g, 256, 0, s>>>(n, rp, ci, val, x, epi); break;
-    }
-    CK_LAUNCH();
+    if (tpb == 128) launch_csr_tpb<VT, XT, AT, Epi, 128>(lanes, n, rp, ci, val, x, epi, s);
+    else if (tpb == 512) launch_csr_tpb<VT, XT, AT, Epi, 512>(lanes, n, rp, ci, val, x, epi, s);
+    else launch_csr_tpb<VT, XT, AT, Epi, 256>(lanes, n, rp, ci, val, x, epi, s);
 }
 
 int choose_lanes(int64_t nrows, int64_t nnz) {
@@ -129,16 +185,24 @@ static int lanes_of(const DCsr &A) { return A.lanes ? A.lanes : choose_lanes(A.n
 
 // dispatch: SELL when built, CSR otherwise
 
+template <class VT, class XT, class AT, class Epi, int TPB>
+static void launch_sliced(const DCsr &A, const XT *x, Epi epi, cudaStream_t s) {
+    const int g = (int)(((int64_t)A.n + TPB - 1) / TPB);
+    if (A.dia) k_dia<VT, XT, AT, Epi, TPB><<<g, TPB, 0, s>>>(A.n, A.m, A.dptr.p, A.doff.p, Vals<VT>::dia(A), x, epi);
+    else k_sell<VT, XT, AT, Epi, TPB><<<g, TPB, 0, s>>>(A.n, A.sptr.p, A.sci.p, Vals<VT>::sell(A), x, epi);
+    CK_LAUNCH();
+}
+
 template <class VT, class XT, class Epi>
 static void run(const DCsr &A, const XT *x, Epi epi, cudaStream_t s) {
     using AT = typename AccT<VT, XT>::T;
     if (A.n <= 0) return;
-    if (A.sell) {
-        const int g = (int)(((int64_t)A.n + 255) / 256);
-        k_sell<VT, XT, AT, Epi><<<g, 256, 0, s>>>(A.n, A.sptr.p, A.sci.p, Vals<VT>::sell(A), x, epi);
-        CK_LAUNCH();
+    if (A.dia || A.sell) {
+        if (A.tpb == 128) launch_sliced<VT, XT, AT, Epi, 128>(A, x, epi, s);
+        else if (A.tpb == 512) launch_sliced<VT, XT, AT, Epi, 512>(A, x, epi, s);
+        else launch_sliced<VT, XT, AT, Epi, 256>(A, x, epi, s);
     } else {
-        launch_csr<VT, XT, AT>(lanes_of(A), A.n, A.rp.p, A.ci.p, Vals<VT>::csr(A), x, epi, s);
+        launch_csr<VT, XT, AT>(lanes_of(A), A.n, A.rp.p, A.ci.p, Vals<VT>::csr(A), x, epi, s, A.tpb);
     }
 }
 
@@ -178,9 +242,9 @@ void cheb_step(const DCsr &A, const XT *b, const XT *dinv, const XT *xin, XT *xo
     using CT = typename AccOf<XT>::T;
     run<VT, XT>(A, xin, ECheb<XT, CT>{b, dinv, xin, xout, e, (CT)alpha, (CT)scale, first ? 1 : 0}, s);
 }
-template <class VT, class XT>
-void coupling_sub(const DCsr &L, const double *v, const double *z, XT *r, cudaStream_t s) {
-    run<VT, double>(L, z, ESub<XT>{v, r}, s);
+template <class VT, class XT, class ZT>
+void coupling_sub(const DCsr &L, const double *v, const ZT *z, XT *r, cudaStream_t s) {
+    run<VT, ZT>(L, z, ESub<XT>{v, r}, s);
 }
 
 template <class XT>
@@ -281,38 +345,140 @@ bool build_sell(DCsr &A, double max_pad, Scratch &sc, cudaStream_t s) {
     return true;
 }
 
+// ------------------------------------------------------------------------------------------ diagonal-offset SELL build
+// One warp per slice of 32 rows: the union of the rows' diagonal offsets (column - row), found by
+// merging the 32 sorted lists (each step takes the warp minimum of the lanes' next offsets).  The
+// width pass writes 32 * (union size), or -1 when a slice has more than 32 distinct offsets; the
+// fill pass writes the offsets and, per slot, the CSR index of the row's entry there (-1: none).
+__global__ void k_dia_width(int n, const int *rp, const int *ci, int *wslot) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = row >> 5;
+    if ((slice << 5) >= n) return;
+    int p = row < n ? rp[row] : 0;
+    const int e = row < n ? rp[row + 1] : 0;
+    int w = 0;
+    for (;;) {
+        const int cand = p < e ? ci[p] - row : INT_MAX;
+        const int mn = __reduce_min_sync(0xffffffffu, cand);
+        if (mn == INT_MAX) break;
+        if (cand == mn) p++;
+        if (++w > 32) break;
+    }
+    if ((row & 31) == 0) wslot[slice] = w > 32 ? -1 : w * 32;
+}
+__global__ void k_dia_fill(int n, const int *rp, const int *ci, const int *dptr, int *doff, int *dperm) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = row >> 5;
+    if ((slice << 5) >= n) return;
+    const int lane = row & 31;
+    const int s0 = dptr[slice];
+    int p = row < n ? rp[row] : 0;
+    const int e = row < n ? rp[row + 1] : 0;
+    for (int k = 0;; k++) {
+        const int cand = p < e ? ci[p] - row : INT_MAX;
+        const int mn = __reduce_min_sync(0xffffffffu, cand);
+        if (mn == INT_MAX) break;
+        if (lane == 0) doff[(s0 >> 5) + k] = mn;
+        dperm[s0 + k * 32 + lane] = cand == mn ? p : -1;
+        if (cand == mn) p++;
+    }
+}
+__global__ void k_min_int(int n, const int *a, int *out) {
+    int m = INT_MAX;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = min(m, a[i]);
+    m = __reduce_min_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) atomicMin(out, m);
+}
+
+template <class T>
+static void gather_dia(const DCsr &A, const T *src, DBuf<T> &dst, cudaStream_t s) {
+    if (dst.n != (size_t)A.dia_nnz || !dst.p) dst.alloc((size_t)A.dia_nnz, s);
+    k_gather_vals<T><<<grid_for(A.dia_nnz, 256), 256, 0, s>>>(A.dia_nnz, A.dperm.p, src, dst.p);
+    CK_LAUNCH();
+}
+
+bool build_dia(DCsr &A, double max_pad, Scratch &sc, cudaStream_t s) {
+    if (A.dia) return true;
+    if (A.n <= 0 || A.nnz <= 0 || A.m <= 0 || A.m > INT_MAX - 64) return false;
+    const int nsl = (A.n + 31) / 32;
+    const unsigned g = (unsigned)(((int64_t)nsl * 32 + 255) / 256);
+    DBuf<int> dptr((size_t)nsl + 1, s);
+    k_dia_width<<<g, 256, 0, s>>>(A.n, A.rp.p, A.ci.p, dptr.p);
+    CK_LAUNCH();
+    dev_fill_int(sc.flags.p + 14, INT_MAX, 1, s);
+    k_min_int<<<grid_for(nsl, 256), 256, 0, s>>>(nsl, dptr.p, sc.flags.p + 14);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(sc.h_flags + 14, sc.flags.p + 14, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (sc.h_flags[14] < 0) return false;                 // a slice with more than 32 offsets
+    const int64_t tot = scan_exclusive(dptr.p, dptr.p, nsl, sc, s);
+    if ((double)tot > max_pad * (double)A.nnz) return false;
+    A.dptr = std::move(dptr);
+    A.dia_nnz = tot;
+    A.doff.alloc((size_t)(tot / 32), s);
+    A.dperm.alloc((size_t)tot, s);
+    k_dia_fill<<<g, 256, 0, s>>>(A.n, A.rp.p, A.ci.p, A.dptr.p, A.doff.p, A.dperm.p);
+    CK_LAUNCH();
+    gather_dia(A, A.v.p, A.dv, s);
+    A.dia = true;
+    sell_refresh(A, s);
+    return true;
+}
+
+void drop_dia(DCsr &A) {
+    A.dia = false;
+    A.dia_nnz = 0;
+    A.dptr.release(); A.doff.release(); A.dperm.release(); A.dv.release(); A.dvf.release(); A.dvb.release();
+}
+
 void sell_refresh(DCsr &A, cudaStream_t s) {
-    if (!A.sell) return;
-    if (A.vf.p) gather_into(A, A.vf.p, A.svf, s);
-    if (A.vb.p) gather_into(A, A.vb.p, A.svb, s);
+    if (A.sell) {
+        if (A.vf.p) gather_into(A, A.vf.p, A.svf, s);
+        if (A.vb.p) gather_into(A, A.vb.p, A.svb, s);
+    }
+    if (A.dia) {
+        if (A.vf.p) gather_dia(A, A.vf.p, A.dvf, s);
+        if (A.vb.p) gather_dia(A, A.vb.p, A.dvb, s);
+    }
 }
 
 void refresh_values(DCsr &A, cudaStream_t s) {
     if (A.nnz <= 0) return;
     if (A.vf.p) convert_d2f(A.v.p, A.vf.p, A.nnz, s);
     if (A.vb.p) convert_d2bf(A.v.p, A.vb.p, A.nnz, s);
-    if (!A.sell) return;
-    gather_into(A, A.v.p, A.sv, s);
+    if (A.sell) gather_into(A, A.v.p, A.sv, s);
+    if (A.dia) gather_dia(A, A.v.p, A.dv, s);
     sell_refresh(A, s);
 }
 
 // ------------------------------------------------------------------------------------------ autotuner
-// Picks the SpMV kernel of one stored operator by timing it with every candidate: SELL-32 (when
-// built) and CSR with 1, 2, 4, 8, 16, 32 threads per row.  The timed launch is the fused Chebyshev
-// step (the epilogue most launches of a level operator run: b, D^-1, x and e read, e and x'
-// written), one warm-up and the fastest of five timed launches each, CUDA events on the stream.  The choice is cached for the process, keyed by
-// (rows, columns, stored entries, longest row, SELL slots), so repeated set-ups of operators
-// with the same shape reuse it without timing.
-__global__ void k_max_row(int n, const int *rp, int *out) {
-    int m = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        m = max(m, rp[i + 1] - rp[i]);
-    m = __reduce_max_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
-}
+// Picks the SpMV kernel of one stored operator by timing it with every candidate: the diagonal-
+// offset SELL-32 and SELL-32 (when built) and CSR with 1, 2, 4, 8, 16, 32 threads per row, each at
+// 128, 256 and 512 threads per block.  The timed launch is the fused Chebyshev step (the epilogue
+// most launches of a level operator run: b, D^-1, x and e read, e and x' written, five distinct
+// vectors), one warm-up and
+// the fastest of five timed launches each, CUDA events on the stream.  The choice is cached for the
+// process, keyed by (rows, columns, stored entries, value bytes), so repeated set-ups of operators
+// with the same shape reuse it without timing, and build only the layout the choice needs.
+// a choice: format (-1 diagonal-offset SELL, 0 SELL-32, k > 0 CSR with k threads per row) and block size
+struct Choice {
+    int format = 0, tpb = 256;
+    int code() const {
+        const int f = format < 0 ? 0 : (format == 0 ? 1 : 2 + __builtin_ctz((unsigned)format));
+        return f * 4 + (tpb == 128 ? 0 : (tpb == 512 ? 2 : 1));
+    }
+    static Choice from(int c) {
+        Choice ch;
+        const int f = c / 4, t = c % 4;
+        ch.format = f == 0 ? -1 : (f == 1 ? 0 : 1 << (f - 2));
+        ch.tpb = t == 0 ? 128 : (t == 2 ? 512 : 256);
+        return ch;
+    }
+};
 
+using TuneKey = std::tuple<int, int, int64_t, int>;
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int64_t, int, int64_t, int>, int> g_tune;   // -> 0 SELL, else lanes
+static std::map<TuneKey, int> g_tune;   // -> Choice::code()
 static bool g_tune_loaded = false;
 
 // BGS_AUTOTUNE_CACHE=<file>: choices are read from and appended to this text file, so another
@@ -324,95 +490,118 @@ static void tune_cache_load() {
     if (!path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    int n, m, r, vb, c;
-    long long nnz, snnz;
-    while (fscanf(f, "%d %d %lld %d %lld %d %d", &n, &m, &nnz, &r, &snnz, &vb, &c) == 7)
-        g_tune[std::make_tuple(n, m, (int64_t)nnz, r, (int64_t)snnz, vb)] = c;
+    int n, m, vb, c;
+    long long nnz;
+    while (fscanf(f, "%d %d %lld %d %d", &n, &m, &nnz, &vb, &c) == 5) g_tune[std::make_tuple(n, m, (int64_t)nnz, vb)] = c;
     fclose(f);
 }
 
-static void tune_cache_append(const std::tuple<int, int, int64_t, int, int64_t, int> &k, int c) {
+static void tune_cache_append(const TuneKey &k, int c) {
     const char *path = getenv("BGS_AUTOTUNE_CACHE");
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%d %d %lld %d %lld %d %d\n", std::get<0>(k), std::get<1>(k), (long long)std::get<2>(k),
-            std::get<3>(k), (long long)std::get<4>(k), std::get<5>(k), c);
+    fprintf(f, "%d %d %lld %d %d\n", std::get<0>(k), std::get<1>(k), (long long)std::get<2>(k), std::get<3>(k), c);
     fclose(f);
 }
 
 template <class VT, class XT>
-static float time_candidates(DCsr &A, int &choice, cudaStream_t s) {
+static Choice time_candidates(DCsr &A, cudaStream_t s) {
     using CT = typename AccOf<XT>::T;
+    // distinct vectors for b, D^-1, x, x' and e, as in a smoothing step (one shared vector would be
+    // read from L2 and favour the layouts with the fewest matrix bytes over what a step sees)
     const size_t nx = (size_t)std::max(A.m, A.n) + 1;
-    DBuf<XT> x(nx, s), y(nx, s), e(nx, s);
-    CK(cudaMemsetAsync(x.p, 0, sizeof(XT) * nx, s));
-    CK(cudaMemsetAsync(e.p, 0, sizeof(XT) * nx, s));
+    DBuf<XT> x(nx, s), y(nx, s), e(nx, s), bv(nx, s), dv(nx, s);
+    XT *const bufs[5] = {x.p, y.p, e.p, bv.p, dv.p};
+    for (XT *p : bufs) CK(cudaMemsetAsync(p, 0, sizeof(XT) * nx, s));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    const int cands[7] = {0, 1, 2, 4, 8, 16, 32};
-    for (int c : cands) {
-        if (c == 0 && !A.sell) continue;
-        const bool keep_sell = A.sell;
-        A.sell = (c == 0);
-        A.lanes = c;
-        float fastest = 1e30f;
-        for (int rep = 0; rep < 6; rep++) {
-            CK(cudaEventRecord(e0, s));
-            run<VT, XT>(A, x.p, ECheb<XT, CT>{x.p, x.p, x.p, y.p, e.p, (CT)0.5, (CT)0.5, 0}, s);
-            CK(cudaEventRecord(e1, s));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep) fastest = std::min(fastest, ms);
-        }
-        A.sell = keep_sell;
-        if (fastest < best) {
-            best = fastest;
-            choice = c;
+    Choice choice;
+    const bool had_sell = A.sell, had_dia = A.dia;
+    const int formats[8] = {-1, 0, 1, 2, 4, 8, 16, 32};
+    for (int f : formats) {
+        if ((f == -1 && !had_dia) || (f == 0 && !had_sell)) continue;
+        for (int tpb : {128, 256, 512}) {
+            A.dia = f == -1;
+            A.sell = f == 0;
+            A.lanes = f > 0 ? f : 0;
+            A.tpb = tpb;
+            float fastest = 1e30f;
+            for (int rep = 0; rep < 6; rep++) {
+                CK(cudaEventRecord(e0, s));
+                run<VT, XT>(A, x.p, ECheb<XT, CT>{bv.p, dv.p, x.p, y.p, e.p, (CT)0.5, (CT)0.5, 0}, s);
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep) fastest = std::min(fastest, ms);
+            }
+            if (fastest < best) {
+                best = fastest;
+                choice.format = f;
+                choice.tpb = tpb;
+            }
         }
     }
+    A.sell = had_sell;
+    A.dia = had_dia;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return best;
+    return choice;
+}
+
+static void apply_choice(DCsr &A, Choice c) {
+    A.tpb = c.tpb;
+    A.lanes = c.format > 0 ? c.format : 0;
+    if (c.format != -1 && A.dia) drop_dia(A);
+    if (c.format != 0 && A.sell) {
+        A.sell = false;
+        A.sptr.release(); A.sci.release(); A.sperm.release(); A.sv.release(); A.svf.release(); A.svb.release();
+    }
+}
+
+static int cached_code(const TuneKey &key) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_cache_load();
+    auto it = g_tune.find(key);
+    return it != g_tune.end() ? it->second : -1;
+}
+
+void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scratch &sc, cudaStream_t s) {
+    if (A.n <= 0 || A.nnz <= 0) return;
+    const int code = use_cache ? cached_code(std::make_tuple(A.n, A.m, A.nnz, value_bytes)) : -1;
+    if (code >= 0) {
+        const Choice c = Choice::from(code);
+        if (c.format == -1 && allow_dia && build_dia(A, kMaxPadDia, sc, s)) return;
+        if (c.format <= 0) build_sell(A, kMaxPad, sc, s);
+        return;
+    }
+    build_sell(A, kMaxPad, sc, s);
+    if (allow_dia) build_dia(A, kMaxPadDia, sc, s);
 }
 
 int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s) {
     if (A.n <= 0 || A.nnz <= 0) return 0;
-    CK(cudaMemsetAsync(sc.flags.p + 9, 0, sizeof(int), s));
-    k_max_row<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp.p, sc.flags.p + 9);
-    CK_LAUNCH();
-    CK(cudaMemcpyAsync(sc.h_flags + 9, sc.flags.p + 9, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const auto key = std::make_tuple(A.n, A.m, A.nnz, sc.h_flags[9], A.sell ? A.sell_nnz : (int64_t)0, value_bytes);
-    int choice = -1;
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        tune_cache_load();
-        auto it = g_tune.find(key);
-        if (it != g_tune.end()) choice = it->second;
-    }
-    if (choice < 0) {
-        // time the kernels in the precision the solve will use
-        if (value_bytes == 2 && A.vb.p) time_candidates<__nv_bfloat16, double>(A, choice, s);
-        else if (value_bytes == 4 && A.vf.p) time_candidates<float, float>(A, choice, s);
-        else time_candidates<double, double>(A, choice, s);
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune[key] = choice;
-        tune_cache_append(key, choice);
-    }
-    if (choice == 0) {
-        A.lanes = 0;
+    const TuneKey key = std::make_tuple(A.n, A.m, A.nnz, value_bytes);
+    const int code = cached_code(key);
+    Choice c;
+    if (code >= 0) {
+        c = Choice::from(code);
+        // the layout the choice names was not built for this operator: the fastest one that was
+        if ((c.format == -1 && !A.dia) || (c.format == 0 && !A.sell)) c = Choice{A.dia ? -1 : (A.sell ? 0 : 1), 256};
     } else {
-        A.lanes = choice;
-        if (A.sell) {   // CSR won: drop the SELL copy
-            A.sell = false;
-            A.sptr.release(); A.sci.release(); A.sperm.release(); A.sv.release(); A.svf.release(); A.svb.release();
-        }
+        // time the kernels in the precision the solve will use
+        if (value_bytes == 2 && A.vb.p) c = time_candidates<__nv_bfloat16, double>(A, s);
+        else if (value_bytes == 4 && A.vf.p) c = time_candidates<float, float>(A, s);
+        else c = time_candidates<double, double>(A, s);
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[key] = c.code();
+        tune_cache_append(key, c.code());
     }
-    return choice;
+    apply_choice(A, c);
+    return c.format;
 }
 
 // explicit instantiations
@@ -425,9 +614,12 @@ int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s) {
 BGS_INST(double, double)
 BGS_INST(float, float)
 #undef BGS_INST
-template void coupling_sub<double, double>(const DCsr &, const double *, const double *, double *, cudaStream_t);
-template void coupling_sub<__nv_bfloat16, float>(const DCsr &, const double *, const double *, float *,
-                                                 cudaStream_t);
+template void coupling_sub<double, double, double>(const DCsr &, const double *, const double *, double *,
+                                                   cudaStream_t);
+template void coupling_sub<__nv_bfloat16, float, double>(const DCsr &, const double *, const double *, float *,
+                                                         cudaStream_t);
+template void coupling_sub<__nv_bfloat16, float, float>(const DCsr &, const double *, const float *, float *,
+                                                        cudaStream_t);
 template void cheb_first<double>(int, const double *, const double *, double, double *, double *, cudaStream_t);
 template void cheb_first<float>(int, const float *, const float *, double, float *, float *, cudaStream_t);
 template void dense_gemv<double>(int, const double *, const double *, double *, cudaStream_t);

@@ -175,6 +175,15 @@ __global__ void k_scan_apply(const int *in, int *out, int64_t n, const long long
     }
 }
 
+long long scan_ll_inplace(long long *a, int n, cudaStream_t s) {
+    k_scan_ll_single<<<1, SCAN_T, 0, s>>>(a, n);
+    CK_LAUNCH();
+    long long h = 0;
+    CK(cudaMemcpyAsync(&h, a + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return h;
+}
+
 int64_t scan_exclusive(const int *in, int *out, int64_t n, Scratch &sc, cudaStream_t s) {
     if (n == 0) {
         CK(cudaMemsetAsync(out, 0, sizeof(int), s));
@@ -293,6 +302,18 @@ void copy_d2f(const double *in, float *out, int64_t n, cudaStream_t s) { convert
 void copy_f2d(const float *in, double *out, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
     k_convert<float, double><<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    CK_LAUNCH();
+}
+__global__ void k_copy_f2d_keep(const float *in, double *out, float *out_f, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = in[i];
+        out[i] = (double)v;
+        out_f[i] = v;
+    }
+}
+void copy_f2d_keep(const float *in, double *out, float *out_f, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_copy_f2d_keep<<<grid_for(n, 256), 256, 0, s>>>(in, out, out_f, n);
     CK_LAUNCH();
 }
 void convert_d2bf(const double *in, __nv_bfloat16 *out, int64_t n, cudaStream_t s) {

@@ -1,6 +1,7 @@
-"""SpMV autotuner: the choice per stored operator is visible through bgs_level_format, is written to
-the file named by BGS_AUTOTUNE_CACHE, and a later process obeys that file (here rewritten so that
-every operator uses CSR with one thread per row) and still solves to the same answer."""
+"""SpMV autotuner: the choice per stored operator (format and threads per block) is visible through
+bgs_level_format, is written to the file named by BGS_AUTOTUNE_CACHE, and a later process obeys that
+file (here rewritten so that every operator uses CSR with one thread per row at 256 threads per
+block) and still solves to the same answer."""
 import json
 import os
 import subprocess
@@ -28,7 +29,7 @@ for precision in (0, 1):
     for k in range(5):
         L = g.bgs_num_levels(k)
         for l in range(L - 1):    # the coarsest level is solved through its dense inverse
-            fmt += [g.bgs_level_format(k, l, w) for w in (0, 1, 2)]
+            fmt += [list(g.bgs_level_format(k, l, w, with_block=True)) for w in (0, 1, 2)]
     x = np.zeros(system.ndof)
     info = g.bgs_solve(system.b, x)
     out[precision] = {"fmt": fmt, "iters": info.iters, "converged": bool(info.converged), "x": x.tolist()}
@@ -56,21 +57,22 @@ def test_autotune_cache_written_and_obeyed(built, tmp_path):
     cache = tmp_path / "tune.txt"
     first = _run(tmp_path, cache, "first")
     lines = [ln.split() for ln in cache.read_text().splitlines() if ln.strip()]
-    assert lines and all(len(f) == 7 for f in lines)
+    assert lines and all(len(f) == 5 for f in lines)
     for p in ("0", "1"):
         assert first[p]["converged"]
-        assert all(f >= 0 for f in first[p]["fmt"])
+        assert all(f >= -1 and t in (128, 256, 512) for f, t in first[p]["fmt"])
     # a second process with the same file times nothing new and makes the same choices
     again = _run(tmp_path, cache, "again")
     assert len(cache.read_text().splitlines()) == len(lines)
     for p in ("0", "1"):
         assert again[p]["fmt"] == first[p]["fmt"]
         assert again[p]["x"] == first[p]["x"]          # same kernels, same order: bit-identical
-    # force CSR with one thread per row everywhere
-    cache.write_text("".join(" ".join(f[:6] + ["1"]) + "\n" for f in lines))
+    # force CSR with one thread per row at 256 threads per block everywhere (choice code 9: CSR with
+    # 2^(2 - 2) lanes, block-size code 1)
+    cache.write_text("".join(" ".join(f[:4] + ["9"]) + "\n" for f in lines))
     forced = _run(tmp_path, cache, "forced")
     for p in ("0", "1"):
         assert forced[p]["converged"]
-        assert all(f == 1 for f in forced[p]["fmt"])
+        assert all(f == 1 and t == 256 for f, t in forced[p]["fmt"])
         x0, x1 = np.array(first[p]["x"]), np.array(forced[p]["x"])
         assert np.linalg.norm(x1 - x0) <= 1e-6 * np.linalg.norm(x0)

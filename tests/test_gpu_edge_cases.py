@@ -89,3 +89,30 @@ def test_explicit_empty_coupling_and_zero_rhs(bgs):
     assert info.converged and np.linalg.norm(A @ x - b) <= 1e-8 * np.linalg.norm(b)
     x0, info0 = solve(bgs, nested, [n, n], [0, 1], np.zeros(2 * n), max_coarse=8)
     assert info0.converged and info0.iters == 0 and not np.any(x0)
+
+
+@pytest.mark.parametrize("n", [1, 7, 9, 483, 1000, 1281])
+def test_coarsest_direct_solve_sizes(bgs, n):
+    """A single-level hierarchy (max_coarse >= n): the V-cycle is the coarsest direct solve alone.
+    Sizes below and above the blocked Gauss-Jordan panel width (8) and its shared-memory limit
+    (1280 rows, beyond which the one-launch-per-pivot form runs), against a dense FP64 solve of a
+    nonsymmetric matrix whose pivots need row interchanges."""
+    rng = np.random.default_rng(n)
+    D = dd_matrix(n, rng)
+    # strong couplings to a few far rows, and a small diagonal on every third row: partial
+    # pivoting must interchange rows
+    for i in range(n):
+        for j in rng.choice(n, size=min(n, 3), replace=False):
+            D[i, j] += rng.uniform(-3.0, 3.0)
+    D[np.arange(0, n, 3), np.arange(0, n, 3)] = 1e-3
+    b = rng.standard_normal(n)
+    g = bgs.Solver([[csr(D)]], [n], [0], max_coarse=max(n, 1))
+    g.setup()
+    assert g.bgs_num_levels(0) == 1
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    g.bgs_apply_vcycle(0, torch.from_numpy(b).cuda(), x)
+    ref = np.linalg.solve(D, b)
+    cond = np.linalg.cond(D)
+    # backward-stable elimination: relative error within a small multiple of n eps cond
+    assert np.linalg.norm(x.cpu().numpy() - ref) <= 4 * n * np.finfo(float).eps * cond * np.linalg.norm(ref)
+    g.close()
