@@ -11,8 +11,10 @@
  *
  * Conventions for every entry point:
  *  - Return value: a status code (BGS_OK = 0, see below).  No C++ exception crosses the ABI.
- *  - Pointers marked "host or device" may point to either; the library copies them with
- *    cudaMemcpyDefault on the handle's stream.  Pointers marked "device" must be device memory.
+ *  - Pointers marked "host or device" may point to either, on the handle's stream: pinned host
+ *    memory (16-byte aligned) is read or written by the library's kernels over the host link, other
+ *    host memory and device memory are copied with cudaMemcpyAsync (cudaMemcpyDefault).  Pointers
+ *    marked "device" must be device memory.
  *  - Vectors over all fields are field-blocked: x = [x_0; x_1; ...; x_{F-1}], x_k of length
  *    field_sizes[k].
  *  - CSR: rowptr has nrows+1 int32 entries starting at 0; col/val have nnz entries; within a

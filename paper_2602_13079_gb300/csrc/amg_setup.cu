@@ -510,12 +510,18 @@ __device__ int sg_accumulate(int row, int *keys, double *vals, unsigned T, bool 
         const int len = has ? brp[k + 1] - bs : 0;
         const int maxlen = __reduce_max_sync(0xffffffffu, len);
         if (NUM) sv[lane] = a;   // read by the leaders after the first step's __syncwarp
+        // lane l walks its right-operand row starting at entry l mod len: the rows of neighbouring
+        // left entries share most of their columns in sorted order, so stepping them in lockstep
+        // from their first entries made most lanes of a step hit the same column (long serial
+        // group sums); the rotated walks spread a step's lanes over the row's columns
+        const int rot = len > 0 ? lane % len : 0;
         for (int q = 0; q < maxlen; q++) {
             const bool act = q < len;
-            const int j = act ? bci[bs + q] : -1;
+            const int qq = act ? (q + rot < len ? q + rot : q + rot - len) : 0;
+            const int j = act ? bci[bs + qq] : -1;
             const unsigned grp = __match_any_sync(0xffffffffu, j);
             const int leader = __ffs(grp) - 1;
-            if (NUM && act) sv[32 + lane] = bv[bs + q];
+            if (NUM && act) sv[32 + lane] = bv[bs + qq];
             __syncwarp();
             if (act && lane == leader) {
                 bool ins;
@@ -1167,33 +1173,40 @@ __global__ void k_gj_unscramble(int n, const double *D, const int *tau, double *
 // Blocked form: GJB_R pivot steps per pair of launches.  The panel kernel (one block) takes the
 // columns K = [k, k+R) of the state before the steps, chooses the R pivots by partial pivoting on an
 // LU-eliminated working copy (the rows at and below each pivot hold, in R sequential Gauss-Jordan
-// steps, the same values as in LU, so the choices are the same), interchanges the rows, and
-// computes D = A_KK^-1 of the pivot rows (Gauss-Jordan on R x R, pivots on the diagonal) and
-// F = -A_IK D for the other rows.  The update kernel then writes the state after the R steps:
-// columns K: D (pivot rows) and F (others); other columns: D A_KJ (pivot rows) and A_IJ + F A_KJ
-// (others), A_KJ the interchanged pivot rows.  In exact arithmetic this is the state R sequential
-// steps leave; GB300's FP64 tensor path (mma.sync f64) runs at the FP64 FMA rate, so the small
+// steps, the same values as in LU, so the choices are the same) and computes D = A_KK^-1 of the
+// interchanged pivot rows (Gauss-Jordan on R x R, one thread per entry, pivots on the diagonal).
+// The update kernel (one block per row) writes the state after the R steps: columns K: D (pivot
+// rows) and F = -A_IK D (other rows); other columns: D A_KJ (pivot rows) and A_IJ + F A_KJ (other
+// rows), A_KJ the interchanged pivot rows.  In exact arithmetic this is the state R sequential steps
+// leave.  GB300's FP64 tensor path (mma.sync f64) runs at the FP64 FMA rate, so these small
 // products stay on the FP64 pipe.
-constexpr int GJB_R = 8;
-constexpr int GJB_T = 256;
-constexpr int GJB_MAXN = 1280;   // both panel copies (2 x n x R doubles) in shared memory
+constexpr int GJB_R = 16;
+constexpr int GJB_T = 256;       // = GJB_R * GJB_R: one thread per entry of the pivot block
+constexpr int GJB_MAXN = 1280;   // the panel's working copy (n x R doubles) in shared memory
+
+// position q after the block's row interchanges (pk[t]: the row exchanged with row k + t) holds row
+// src(q) of the state before them
+__device__ __forceinline__ int gjb_src(int q, int k, int R, const int *pk) {
+    for (int t = R - 1; t >= 0; t--) {
+        const int p = pk[t];
+        if (q == k + t) q = p;
+        else if (q == p) q = k + t;
+    }
+    return q;
+}
 
 __global__ void __launch_bounds__(GJB_T) k_gjb_panel(int n, int k, int R, const double *__restrict__ S, int *perm,
-                                                      double *Dk, double *F, int *status) {
+                                                      double *Dk, int *status) {
     extern __shared__ double gjb_sm[];
-    double *C0 = gjb_sm;          // n x R, row-major [i * R + t]: the panel, rows interchanged
-    double *Cw = gjb_sm + n * R;  // working copy, eliminated below each pivot
+    double *Cw = gjb_sm;   // n x R, row-major [i * R + t]: the panel, rows interchanged, eliminated below pivots
     __shared__ double bv_s[GJB_T / 32];
     __shared__ int bi_s[GJB_T / 32];
-    __shared__ int piv_s;
-    __shared__ double D[GJB_R * GJB_R];
+    __shared__ int piv_s[GJB_R];
+    __shared__ double M[GJB_R * GJB_R];
+    __shared__ double prow[GJB_R], pcol[GJB_R];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int e = threadIdx.x; e < n * R; e += blockDim.x) {
-        const int i = e / R, t = e - i * R;
-        const double v = S[(size_t)i * n + k + t];
-        C0[e] = v;
-        Cw[e] = v;
-    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int t = 0; t < R; t++) Cw[i * R + t] = S[(size_t)i * n + k + t];
     __syncthreads();
     for (int t = 0; t < R; t++) {
         const int c = k + t;
@@ -1217,91 +1230,89 @@ __global__ void __launch_bounds__(GJB_T) k_gjb_panel(int n, int k, int R, const 
                 bi = c;
                 *status = 1;
             }
-            piv_s = bi;
+            piv_s[t] = bi;
             perm[c] = bi;
         }
         __syncthreads();
-        const int p = piv_s;
-        if (p != c)
-            for (int e = threadIdx.x; e < R; e += blockDim.x) {
-                double a = C0[c * R + e];
-                C0[c * R + e] = C0[p * R + e];
-                C0[p * R + e] = a;
-                a = Cw[c * R + e];
-                Cw[c * R + e] = Cw[p * R + e];
-                Cw[p * R + e] = a;
-            }
+        const int p = piv_s[t];
+        if (p != c && threadIdx.x < R) {
+            const double a = Cw[c * R + threadIdx.x];
+            Cw[c * R + threadIdx.x] = Cw[p * R + threadIdx.x];
+            Cw[p * R + threadIdx.x] = a;
+        }
         __syncthreads();
-        const int rest = R - t - 1;
-        if (rest > 0) {
+        if (t + 1 < R) {   // each thread eliminates its own rows below the pivot
             const double pv = Cw[c * R + t];
-            for (int e = threadIdx.x; e < (n - c - 1) * rest; e += blockDim.x) {
-                const int i = c + 1 + e / rest, u = t + 1 + e % rest;
-                Cw[i * R + u] -= (Cw[i * R + t] / pv) * Cw[c * R + u];
+            for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) {
+                const double l = Cw[i * R + t] / pv;
+                for (int u = t + 1; u < R; u++) Cw[i * R + u] -= l * Cw[c * R + u];
             }
         }
         __syncthreads();
     }
-    // D = A_KK^-1 by Gauss-Jordan on the R x R block (one thread; the pivots are its diagonal)
-    if (threadIdx.x == 0) {
-        double M[GJB_R * GJB_R];
-        for (int r = 0; r < R; r++)
-            for (int q = 0; q < R; q++) M[r * R + q] = C0[(k + r) * R + q];
-        for (int t = 0; t < R; t++) {
-            const double rp = 1.0 / M[t * R + t];
-            for (int q = 0; q < R; q++) M[t * R + q] = q == t ? rp : M[t * R + q] * rp;
-            for (int r = 0; r < R; r++) {
-                if (r == t) continue;
-                const double f = M[r * R + t];
-                for (int q = 0; q < R; q++) M[r * R + q] = q == t ? -f * rp : M[r * R + q] - f * M[t * R + q];
-            }
-        }
-        for (int e = 0; e < R * R; e++) D[e] = M[e];
+    // A_KK: the interchanged pivot rows of the state before the steps; D = A_KK^-1 in place
+    const int r = threadIdx.x / GJB_R, q = threadIdx.x % GJB_R;
+    if (r < R && q < R) {
+        M[r * GJB_R + q] = S[(size_t)gjb_src(k + r, k, R, piv_s) * n + k + q];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) Dk[e] = D[e];
-    for (int e = threadIdx.x; e < n * R; e += blockDim.x) {
-        const int i = e / R, t = e - i * R;
-        double f = 0.0;
-        if (i < k || i >= k + R)
-            for (int q = 0; q < R; q++) f -= C0[i * R + q] * D[q * R + t];
-        F[e] = f;
+    for (int t = 0; t < R; t++) {
+        // stage row t and column t: every thread then reads only staged values and its own entry
+        if (threadIdx.x < R) prow[threadIdx.x] = M[t * GJB_R + threadIdx.x];
+        else if (threadIdx.x < 2 * R) pcol[threadIdx.x - R] = M[(threadIdx.x - R) * GJB_R + t];
+        __syncthreads();
+        const double rp = 1.0 / prow[t];
+        if (r < R && q < R) {
+            const double f = pcol[r];
+            double v;
+            if (r == t) v = q == t ? rp : prow[q] * rp;
+            else v = q == t ? -f * rp : M[r * GJB_R + q] - f * (prow[q] * rp);
+            M[r * GJB_R + q] = v;
+        }
+        __syncthreads();
     }
-}
-
-// position q after the block's row interchanges holds row src(q) of the state before them
-__device__ __forceinline__ int gjb_src(int q, int k, int R, const int *perm) {
-    for (int t = R - 1; t >= 0; t--) {
-        const int p = perm[k + t];
-        if (q == k + t) q = p;
-        else if (q == p) q = k + t;
-    }
-    return q;
+    if (r < R && q < R) Dk[r * R + q] = M[r * GJB_R + q];
 }
 
 __global__ void __launch_bounds__(GJB_T) k_gjb_update(int n, int k, int R, const double *__restrict__ S,
                                                        double *__restrict__ Dout, const int *perm,
-                                                       const double *__restrict__ Dk, const double *__restrict__ F) {
-    __shared__ int srck[GJB_R];
+                                                       const double *__restrict__ Dk) {
+    __shared__ int pk[GJB_R], srck[GJB_R];
     __shared__ double Ds[GJB_R * GJB_R];
-    if (threadIdx.x < R) srck[threadIdx.x] = gjb_src(k + threadIdx.x, k, R, perm);
+    __shared__ double Fr[GJB_R], rowK[GJB_R];
+    if (threadIdx.x < R) pk[threadIdx.x] = perm[k + threadIdx.x];
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ds[e] = Dk[e];
     __syncthreads();
-    const unsigned un = (unsigned)n, total = un * un;
-    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int i = (int)(t / un), j = (int)(t - (unsigned)i * un);
+    if (threadIdx.x < R) srck[threadIdx.x] = gjb_src(k + threadIdx.x, k, R, pk);
+    __syncthreads();
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const bool piv_row = i >= k && i < k + R;
-        double out;
-        if (j >= k && j < k + R) {
-            out = piv_row ? Ds[(i - k) * R + (j - k)] : F[(size_t)i * R + (j - k)];
-        } else if (piv_row) {
-            out = 0.0;
-            for (int q = 0; q < R; q++) out += Ds[(i - k) * R + q] * S[(size_t)srck[q] * n + j];
-        } else {
-            out = S[(size_t)gjb_src(i, k, R, perm) * n + j];
-            for (int q = 0; q < R; q++) out += F[(size_t)i * R + q] * S[(size_t)srck[q] * n + j];
+        const int si = gjb_src(i, k, R, pk);   // every thread, from shared memory
+        if (threadIdx.x < R) rowK[threadIdx.x] = S[(size_t)si * n + k + threadIdx.x];
+        __syncthreads();
+        // this row's factors F = -A_iK D (other rows) or the row of D (pivot rows)
+        if (threadIdx.x < R) {
+            double f;
+            if (piv_row) {
+                f = Ds[(i - k) * R + threadIdx.x];
+            } else {
+                f = 0.0;
+                for (int q = 0; q < R; q++) f -= rowK[q] * Ds[q * R + threadIdx.x];
+            }
+            Fr[threadIdx.x] = f;
         }
-        Dout[t] = out;
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            double out;
+            if (j >= k && j < k + R) {
+                out = Fr[j - k];
+            } else {
+                out = piv_row ? 0.0 : S[(size_t)si * n + j];
+                for (int q = 0; q < R; q++) out += Fr[q] * S[(size_t)srck[q] * n + j];
+            }
+            Dout[(size_t)i * n + j] = out;
+        }
+        __syncthreads();
     }
 }
 
@@ -1386,13 +1397,14 @@ static void dense_inverse_async(const DCsr &Ac, double *W, Scratch &sc, cudaStre
     double *S = a.p, *D = b.p;
     if (n <= GJB_MAXN) {
         // blocked: GJB_R pivot steps per panel launch and update launch
-        DBuf<double> Dk((size_t)GJB_R * GJB_R, s), F((size_t)n * GJB_R, s);
-        const size_t smem = sizeof(double) * 2 * (size_t)n * GJB_R;
+        DBuf<double> Dk((size_t)GJB_R * GJB_R, s);
+        const size_t smem = sizeof(double) * (size_t)n * GJB_R;
+        const int gu = std::min(n, num_sms() * 4);
         for (int k = 0; k < n; k += GJB_R) {
             const int R = std::min(GJB_R, n - k);
-            k_gjb_panel<<<1, GJB_T, smem, s>>>(n, k, R, S, perm.p, Dk.p, F.p, sc.flags.p + 6);
+            k_gjb_panel<<<1, GJB_T, smem, s>>>(n, k, R, S, perm.p, Dk.p, sc.flags.p + 6);
             CK_LAUNCH();
-            k_gjb_update<<<g, GJB_T, 0, s>>>(n, k, R, S, D, perm.p, Dk.p, F.p);
+            k_gjb_update<<<gu, GJB_T, 0, s>>>(n, k, R, S, D, perm.p, Dk.p);
             CK_LAUNCH();
             std::swap(S, D);
         }
@@ -1444,7 +1456,7 @@ static void set_attributes() {
         CK(cudaFuncSetAttribute(k_sg_num<SG_NUM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(double) * SG_WARPS * (SG_NUM_T + 64) + sizeof(int) * SG_WARPS * SG_NUM_T)));
         CK(cudaFuncSetAttribute(k_gjb_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(double) * 2 * GJB_MAXN * GJB_R)));
+                                (int)(sizeof(double) * GJB_MAXN * GJB_R)));
     });
 }
 

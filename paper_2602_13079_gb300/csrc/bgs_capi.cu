@@ -732,14 +732,6 @@ void alloc_block(const bgs_csr &in, int64_t nr, int64_t nc, DCsr &out, cudaStrea
     out.v.alloc((size_t)in.nnz, s);
 }
 
-void copy_block_data(const bgs_csr &in, DCsr &out, cudaStream_t s) {
-    CK(cudaMemcpyAsync(out.rp.p, in.rowptr, sizeof(int) * ((size_t)out.n + 1), cudaMemcpyDefault, s));
-    if (in.nnz) {
-        CK(cudaMemcpyAsync(out.ci.p, in.col, sizeof(int) * (size_t)in.nnz, cudaMemcpyDefault, s));
-        CK(cudaMemcpyAsync(out.v.p, in.val, sizeof(double) * (size_t)in.nnz, cudaMemcpyDefault, s));
-    }
-}
-
 double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -764,13 +756,14 @@ struct CreateTrace {
     }
 };
 
-// The stored blocks' copies on two side streams (host buffers: more host-to-device bandwidth than
-// one stream; each block's validation on s overlaps the copies of the blocks after it), the
-// validation error bits one slot per block, read back once.
+// The stored blocks' copies (pinned host sources pulled by the SMs over the host link, device and
+// pageable sources by cudaMemcpyAsync), then each block's validation, the error bits one slot per
+// block, read back once.
 int copy_and_validate(bgs_ctx *h, const int64_t *sizes, const bgs_csr *blocks, cudaStream_t s) {
     const int F = h->F;
     CreateTrace tr(s);
-    std::vector<int> todo;   // r * F + c of the stored blocks, largest first
+    std::vector<int> todo;   // r * F + c of the stored blocks
+    std::vector<XferSeg> segs;
     for (int r = 0; r < F; r++)
         for (int c = 0; c < F; c++) {
             const bgs_csr &B = blocks[r * F + c];
@@ -785,55 +778,27 @@ int copy_and_validate(bgs_ctx *h, const int64_t *sizes, const bgs_csr *blocks, c
             }
             alloc_block(B, sizes[r], sizes[c], D, s);
             todo.push_back(r * F + c);
+            segs.push_back({B.rowptr, D.rp.p, sizeof(int) * ((size_t)D.n + 1)});
+            if (B.nnz) {
+                segs.push_back({B.col, D.ci.p, sizeof(int) * (size_t)B.nnz});
+                segs.push_back({B.val, D.v.p, sizeof(double) * (size_t)B.nnz});
+            }
         }
-    std::stable_sort(todo.begin(), todo.end(), [&](int a, int b) { return blocks[a].nnz > blocks[b].nnz; });
     DBuf<int> flags(std::max<size_t>(todo.size(), 1), s);
     tr.mark("  allocate block copies");
-    cudaStream_t cs[2] = {nullptr, nullptr};
-    cudaEvent_t ready = nullptr;
-    std::vector<cudaEvent_t> done(todo.size(), nullptr);
-    auto cleanup = [&]() {
-        for (cudaEvent_t e : done)
-            if (e) cudaEventDestroy(e);
-        if (ready) cudaEventDestroy(ready);
-        for (cudaStream_t q : cs)
-            if (q) cudaStreamDestroy(q);
-    };
-    try {
-        CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-        CK(cudaEventRecord(ready, s));   // the allocations above are ordered before the copies
-        for (cudaStream_t &q : cs) {
-            CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
-            CK(cudaStreamWaitEvent(q, ready, 0));
-        }
-        tr.mark("  copy streams");
-        int64_t load[2] = {0, 0};
-        for (size_t i = 0; i < todo.size(); i++) {
-            const int b = todo[i];
-            const int q = load[0] <= load[1] ? 0 : 1;
-            load[q] += blocks[b].nnz * 12 + blocks[b].nrows * 4;
-            copy_block_data(blocks[b], h->blk[(size_t)b], cs[q]);
-            CK(cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming));
-            CK(cudaEventRecord(done[i], cs[q]));
-            CK(cudaStreamWaitEvent(s, done[i], 0));
-            validate_csr_launch(view(h->blk[(size_t)b]), b / F == b % F, flags.p + i, s);
-        }
-        std::vector<int> hf(todo.size(), 0);
-        if (!todo.empty())
-            CK(cudaMemcpyAsync(hf.data(), flags.p, sizeof(int) * todo.size(), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));   // s waited for every copy, so the side streams are idle
-        tr.mark("  copies + validation");
-        cleanup();
-        for (int f : hf)
-            if (int st = validate_status(f)) return st;
-        return BGS_OK;
-    } catch (...) {
-        cudaStreamSynchronize(s);
-        for (cudaStream_t q : cs)
-            if (q) cudaStreamSynchronize(q);
-        cleanup();
-        throw;
+    transfer(segs, s);
+    for (size_t i = 0; i < todo.size(); i++) {
+        const int b = todo[i];
+        validate_csr_launch(view(h->blk[(size_t)b]), b / F == b % F, flags.p + i, s);
     }
+    std::vector<int> hf(todo.size(), 0);
+    if (!todo.empty())
+        CK(cudaMemcpyAsync(hf.data(), flags.p, sizeof(int) * todo.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    tr.mark("  copies + validation");
+    for (int f : hf)
+        if (int st = validate_status(f)) return st;
+    return BGS_OK;
 }
 
 __global__ void k_shift_rowptr(int n, const int *in, int off, int *out) {
@@ -1163,7 +1128,7 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
         tr.mark("full operator + couplings");
         // the layouts the autotuner will choose from (only its cached choice when it has one)
         const bool tune = o.autotune != 0;
-        build_formats(h->full, 8, true, tune, h->sc, s);
+        build_formats(h->full, 8, true, tune, h->sc, s, true);
         for (int k = 0; k < F; k++) build_formats(h->lower[k], o.precision == 1 ? 2 : 8, false, tune, h->sc, s);
         CK(cudaStreamSynchronize(s));
         tr.mark("sell");
@@ -1290,7 +1255,7 @@ extern "C" int bgs_setup(bgs_handle h) {
                     for (DCsr *M : {&H.L[l].A, &H.L[l].P, &H.L[l].R}) autotune_spmv(*M, hb, h->sc, s);
                 if (h->lower[k].nnz) autotune_spmv(h->lower[k], cb, h->sc, s);
             }
-            autotune_spmv(h->full, 8, h->sc, s);
+            autotune_spmv(h->full, 8, h->sc, s, true);   // applied only as a product
         }
         h->K.alloc(total_n(h), h->opt.restart, s);
         if (mixed) h->zf.alloc((size_t)total_n(h), s);
@@ -1313,10 +1278,10 @@ extern "C" int bgs_update_values(bgs_handle h, const double *const *values) {
         const double t0 = now_ms();
         const int F = h->F;
         const bool mixed = h->opt.precision == 1;
+        std::vector<XferSeg> segs;
         for (int b = 0; b < F * F; b++)
-            if (values[b] && h->blk[b].nnz)
-                CK(cudaMemcpyAsync(h->blk[b].v.p, values[b], sizeof(double) * (size_t)h->blk[b].nnz,
-                                   cudaMemcpyDefault, s));
+            if (values[b] && h->blk[b].nnz) segs.push_back({values[b], h->blk[b].v.p, sizeof(double) * (size_t)h->blk[b].nnz});
+        transfer(segs, s);
         {
             // the full operator and the couplings: re-assembled, then their values taken over so
             // that their SELL layouts and tuned kernels stay
@@ -1373,10 +1338,10 @@ static int solve_common(bgs_handle h, const double *b, double *x, bgs_info *info
         CK(cudaStreamSynchronize(s));
         const double t0 = now_ms();
         for (auto &k : h->stats) k = KStats();
-        CK(cudaMemcpyAsync(h->K.b.p, b, sizeof(double) * n, cudaMemcpyDefault, s));
+        transfer({{b, h->K.b.p, sizeof(double) * (size_t)n}}, s);
         bgs_info inf{};
         int st = fgmres(h, adjoint, &inf);
-        CK(cudaMemcpyAsync(x, h->K.x.p, sizeof(double) * n, cudaMemcpyDefault, s));
+        transfer({{h->K.x.p, x, sizeof(double) * (size_t)n}}, s);
         CK(cudaStreamSynchronize(s));
         inf.t_solve_ms = now_ms() - t0;
         inf.t_setup_ms = h->t_setup_ms;

@@ -31,6 +31,15 @@ struct Scratch {
 };
 
 // ---------------------------------------------------------------- util.cu
+// One piece of a host <-> device (or device <-> device) copy.
+struct XferSeg {
+    const void *src;
+    void *dst;
+    size_t bytes;
+};
+// Enqueues the copies on s: pieces to or from pinned host memory (16-byte aligned) are moved by one
+// kernel through the SMs over the host link; the others by cudaMemcpyAsync (cudaMemcpyDefault).
+void transfer(const std::vector<XferSeg> &segs, cudaStream_t s);
 long long launch_count();
 void release_cached_memory();
 // out[0..n] = exclusive scan of in[0..n-1] (out[n] = total); in and out may alias.
@@ -113,11 +122,13 @@ void refresh_values(DCsr &A, cudaStream_t s);
 // 128, 256 and 512 threads per block, and keeps the fastest for A (cached per shape); returns -1
 // (diagonal-offset SELL), 0 (SELL-32) or the lane count.  value_bytes selects the precision timed
 // (8 FP64, 4 FP32 hierarchy, 2 BF16 couplings).
-int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s);
+// product: time y = A x instead of the Chebyshev step (an operator only ever applied as a product).
+int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s, bool product = false);
 // Builds the SpMV layouts an operator may run: the one the autotuner's cached choice for its shape
 // names (use_cache), else SELL-32 and, with allow_dia, the diagonal-offset SELL-32 for the
 // autotuner to time.  value_bytes as for autotune_spmv.
-void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scratch &sc, cudaStream_t s);
+void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scratch &sc, cudaStream_t s,
+                   bool product = false);
 
 // ---------------------------------------------------------------- krylov.cu
 // h[k] = V_k . w for k < cnt and h[cnt] = w . w (V column-major, leading dimension ld, even; V and w

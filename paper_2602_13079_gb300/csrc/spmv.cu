@@ -456,9 +456,10 @@ void refresh_values(DCsr &A, cudaStream_t s) {
 // offset SELL-32 and SELL-32 (when built) and CSR with 1, 2, 4, 8, 16, 32 threads per row, each at
 // 128, 256 and 512 threads per block.  The timed launch is the fused Chebyshev step (the epilogue
 // most launches of a level operator run: b, D^-1, x and e read, e and x' written, five distinct
-// vectors), one warm-up and
+// vectors) or, for an operator applied only as a plain product (the full operator), y = A x; one
+// warm-up and
 // the fastest of five timed launches each, CUDA events on the stream.  The choice is cached for the
-// process, keyed by (rows, columns, stored entries, value bytes), so repeated set-ups of operators
+// process, keyed by (rows, columns, stored entries, value bytes, epilogue), so repeated set-ups of operators
 // with the same shape reuse it without timing, and build only the layout the choice needs.
 // a choice: format (-1 diagonal-offset SELL, 0 SELL-32, k > 0 CSR with k threads per row) and block size
 struct Choice {
@@ -476,7 +477,7 @@ struct Choice {
     }
 };
 
-using TuneKey = std::tuple<int, int, int64_t, int>;
+using TuneKey = std::tuple<int, int, int64_t, int, int>;   // rows, columns, entries, value bytes, epilogue
 static std::mutex g_tune_mu;
 static std::map<TuneKey, int> g_tune;   // -> Choice::code()
 static bool g_tune_loaded = false;
@@ -490,9 +491,10 @@ static void tune_cache_load() {
     if (!path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    int n, m, vb, c;
+    int n, m, vb, ep, c;
     long long nnz;
-    while (fscanf(f, "%d %d %lld %d %d", &n, &m, &nnz, &vb, &c) == 5) g_tune[std::make_tuple(n, m, (int64_t)nnz, vb)] = c;
+    while (fscanf(f, "%d %d %lld %d %d %d", &n, &m, &nnz, &vb, &ep, &c) == 6)
+        g_tune[std::make_tuple(n, m, (int64_t)nnz, vb, ep)] = c;
     fclose(f);
 }
 
@@ -501,12 +503,13 @@ static void tune_cache_append(const TuneKey &k, int c) {
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%d %d %lld %d %d\n", std::get<0>(k), std::get<1>(k), (long long)std::get<2>(k), std::get<3>(k), c);
+    fprintf(f, "%d %d %lld %d %d %d\n", std::get<0>(k), std::get<1>(k), (long long)std::get<2>(k), std::get<3>(k),
+            std::get<4>(k), c);
     fclose(f);
 }
 
 template <class VT, class XT>
-static Choice time_candidates(DCsr &A, cudaStream_t s) {
+static Choice time_candidates(DCsr &A, bool product, cudaStream_t s) {
     using CT = typename AccOf<XT>::T;
     // distinct vectors for b, D^-1, x, x' and e, as in a smoothing step (one shared vector would be
     // read from L2 and favour the layouts with the fewest matrix bytes over what a step sees)
@@ -531,7 +534,8 @@ static Choice time_candidates(DCsr &A, cudaStream_t s) {
             float fastest = 1e30f;
             for (int rep = 0; rep < 6; rep++) {
                 CK(cudaEventRecord(e0, s));
-                run<VT, XT>(A, x.p, ECheb<XT, CT>{bv.p, dv.p, x.p, y.p, e.p, (CT)0.5, (CT)0.5, 0}, s);
+                if (product) run<VT, XT>(A, x.p, EStore<XT>{y.p}, s);
+                else run<VT, XT>(A, x.p, ECheb<XT, CT>{bv.p, dv.p, x.p, y.p, e.p, (CT)0.5, (CT)0.5, 0}, s);
                 CK(cudaEventRecord(e1, s));
                 CK(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -569,9 +573,10 @@ static int cached_code(const TuneKey &key) {
     return it != g_tune.end() ? it->second : -1;
 }
 
-void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scratch &sc, cudaStream_t s) {
+void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scratch &sc, cudaStream_t s,
+                   bool product) {
     if (A.n <= 0 || A.nnz <= 0) return;
-    const int code = use_cache ? cached_code(std::make_tuple(A.n, A.m, A.nnz, value_bytes)) : -1;
+    const int code = use_cache ? cached_code(std::make_tuple(A.n, A.m, A.nnz, value_bytes, product ? 1 : 0)) : -1;
     if (code >= 0) {
         const Choice c = Choice::from(code);
         if (c.format == -1 && allow_dia && build_dia(A, kMaxPadDia, sc, s)) return;
@@ -582,9 +587,9 @@ void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scr
     if (allow_dia) build_dia(A, kMaxPadDia, sc, s);
 }
 
-int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s) {
+int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s, bool product) {
     if (A.n <= 0 || A.nnz <= 0) return 0;
-    const TuneKey key = std::make_tuple(A.n, A.m, A.nnz, value_bytes);
+    const TuneKey key = std::make_tuple(A.n, A.m, A.nnz, value_bytes, product ? 1 : 0);
     const int code = cached_code(key);
     Choice c;
     if (code >= 0) {
@@ -593,9 +598,9 @@ int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s) {
         if ((c.format == -1 && !A.dia) || (c.format == 0 && !A.sell)) c = Choice{A.dia ? -1 : (A.sell ? 0 : 1), 256};
     } else {
         // time the kernels in the precision the solve will use
-        if (value_bytes == 2 && A.vb.p) c = time_candidates<__nv_bfloat16, double>(A, s);
-        else if (value_bytes == 4 && A.vf.p) c = time_candidates<float, float>(A, s);
-        else c = time_candidates<double, double>(A, s);
+        if (value_bytes == 2 && A.vb.p) c = time_candidates<__nv_bfloat16, double>(A, product, s);
+        else if (value_bytes == 4 && A.vf.p) c = time_candidates<float, float>(A, product, s);
+        else c = time_candidates<double, double>(A, product, s);
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune[key] = c.code();
         tune_cache_append(key, c.code());

@@ -83,6 +83,73 @@ Scratch::~Scratch() {
 }
 
 // ------------------------------------------------------------------------------------------
+// Host transfers: pinned host memory is read or written by the SMs over the host link (one
+// kernel for every piece of a call) instead of by the copy engines, whose host transfers on this
+// platform ran at a fifth of the link rate on some calls; other memory goes through cudaMemcpyAsync.
+// ------------------------------------------------------------------------------------------
+constexpr int kXferMax = 96;
+struct XferParams {
+    int nseg;
+    uint64_t start[kXferMax + 1];   // first 16-byte unit of each piece, then the total
+    const uint4 *src[kXferMax];
+    uint4 *dst[kXferMax];
+};
+
+__global__ void k_xfer(XferParams p) {
+    const uint64_t total = p.start[p.nseg];
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total;
+         u += (uint64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = p.nseg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.start[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint64_t off = u - p.start[lo];
+        p.dst[lo][off] = p.src[lo][off];
+    }
+}
+
+// device-usable address of pinned host memory, or nullptr for device / pageable memory
+static void *pinned_device_address(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+void transfer(const std::vector<XferSeg> &segs, cudaStream_t s) {
+    XferParams prm{};
+    auto flush = [&]() {
+        if (prm.nseg == 0) return;
+        const uint64_t total = prm.start[prm.nseg];
+        k_xfer<<<grid_for((int64_t)total, 256, num_sms() * 8), 256, 0, s>>>(prm);
+        CK_LAUNCH();
+        prm.nseg = 0;
+    };
+    for (const XferSeg &g : segs) {
+        if (g.bytes == 0) continue;
+        const void *hs = pinned_device_address(g.src);
+        void *hd = pinned_device_address(g.dst);
+        const void *src = hs ? hs : g.src;
+        void *dst = hd ? hd : g.dst;
+        const bool aligned = (((uintptr_t)src | (uintptr_t)dst | (uintptr_t)g.bytes) & 15) == 0;
+        if ((hs || hd) && aligned) {
+            if (prm.nseg == kXferMax) flush();
+            prm.src[prm.nseg] = (const uint4 *)src;
+            prm.dst[prm.nseg] = (uint4 *)dst;
+            prm.start[prm.nseg + 1] = prm.start[prm.nseg] + g.bytes / 16;
+            prm.nseg++;
+        } else {
+            CK(cudaMemcpyAsync(g.dst, g.src, g.bytes, cudaMemcpyDefault, s));
+        }
+    }
+    flush();
+}
+
+// ------------------------------------------------------------------------------------------
 // Exclusive scan (int32 counts -> int32 offsets, int64 block totals)
 // ------------------------------------------------------------------------------------------
 constexpr int SCAN_T = 1024, SCAN_I = 4, SCAN_B = SCAN_T * SCAN_I;

@@ -57,7 +57,7 @@ def test_autotune_cache_written_and_obeyed(built, tmp_path):
     cache = tmp_path / "tune.txt"
     first = _run(tmp_path, cache, "first")
     lines = [ln.split() for ln in cache.read_text().splitlines() if ln.strip()]
-    assert lines and all(len(f) == 5 for f in lines)
+    assert lines and all(len(f) == 6 for f in lines)
     for p in ("0", "1"):
         assert first[p]["converged"]
         assert all(f >= -1 and t in (128, 256, 512) for f, t in first[p]["fmt"])
@@ -69,7 +69,7 @@ def test_autotune_cache_written_and_obeyed(built, tmp_path):
         assert again[p]["x"] == first[p]["x"]          # same kernels, same order: bit-identical
     # force CSR with one thread per row at 256 threads per block everywhere (choice code 9: CSR with
     # 2^(2 - 2) lanes, block-size code 1)
-    cache.write_text("".join(" ".join(f[:4] + ["9"]) + "\n" for f in lines))
+    cache.write_text("".join(" ".join(f[:5] + ["9"]) + "\n" for f in lines))
     forced = _run(tmp_path, cache, "forced")
     for p in ("0", "1"):
         assert forced[p]["converged"]
