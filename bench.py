@@ -36,6 +36,8 @@ CHEB_FINE_TRAFFIC = {
     1: (275.055616e6, "profiles/k_spmv1_cheb_phi_s_128cubed.md"),
 }
 WORKLOAD = "C4"
+# FP64 peak of one GB300 from its unit counts and clock: 152 SMs x 2 FMA/clock x 2 FLOP x 2.07 GHz
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def parse():
@@ -62,7 +64,7 @@ def parse():
     p.add_argument("--rtol", type=float, default=1e-8, help="relative tolerance for --theta-grid")
     p.add_argument("--sigma-means", default=None,
                    help="anode,separator,cathode conductivity means for --theta-grid (default: the workload's)")
-    p.add_argument("--profile-case", default=None, choices=["vcycle", "arnoldi", "spmv"],
+    p.add_argument("--profile-case", default=None, choices=["vcycle", "arnoldi", "spmv", "krylov"],
                    help="run one small kernel case for an ncu capture and exit")
     p.add_argument("--profile-precision", type=int, default=0, choices=[0, 1],
                    help="hierarchy precision of --profile-case vcycle (0 FP64, 1 FP32)")
@@ -307,6 +309,15 @@ def gpu_arm(args, rank, world):
         stats = {k: s.bgs_kernel_stats(v) for k, v in bgs.KERNEL_CLASSES.items()} if prof else None
         if prof:
             stats["_fine_format"] = s.bgs_level_format(spec.PHI_S, 0, 0)
+            # FP64 operations of the finest-level Chebyshev steps of one iteration: per step 2 nnz
+            # (row sum) + 5 per row (D^-1 r, e' = alpha e + D^-1 r, x' = x + c2 e'); steps per
+            # V-cycle 2 deg - 1 (the first pre-smoothing step from x = 0 has no SpMV)
+            flops = 0.0
+            for k in range(5):
+                li = s.bgs_level_info(k, 0)
+                deg = s.options.cheb_degree[k]
+                flops += (2 * deg - 1) * (2.0 * li["nnz"] + 5.0 * li["rows"])
+            stats["_fine_flops"] = flops * info.iters
         s.close()
         return info, stats
 
@@ -525,6 +536,7 @@ def gpu_arm(args, rank, world):
         kname = ("k_dia<double,double,double,ECheb>" if fmt == -1 else
                  "k_sell<double,double,double,ECheb>" if fmt == 0 else f"k_spmv<{fmt},double,double,double,ECheb>")
         traffic, tsrc = CHEB_FINE_TRAFFIC.get(fmt, (None, "no ncu capture of this variant"))
+        fine_flops = prof.pop("_fine_flops")
         d = prof["chebyshev_fine"]
         ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
         roof = {"bound": "hbm", "kernel": kname + " (Chebyshev step, finest level, FP64)",
@@ -532,11 +544,17 @@ def gpu_arm(args, rank, world):
                 "traffic": traffic, "traffic_source": tsrc,
                 "launches": d["launches"], "avg_launch_ms": d["ms"] / max(d["launches"], 1),
                 "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
+                # the same kernel against the FP64 pipe, the other limit of the FP64 step: 152 SMs x
+                # 2 FP64 FMA per clock x 2.07 GHz = 1.26 TFLOP/s nominal
+                "fp64_pipe": {"bound": "alu", "achieved": fine_flops / (d["ms"] * 1e-3) / 1e12,
+                              "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                              "frac": fine_flops / (d["ms"] * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS},
                 "classes": {k: {"launches": v["launches"], "ms": v["ms"],
                                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                             for k, v in prof.items()}}
         if prof_mx:
             fmx = prof_mx.pop("_fine_format")
+            prof_mx.pop("_fine_flops")
             roof["fine_kernel_mixed"] = ("k_dia<float,float,float,ECheb>" if fmx == -1 else
                                          "k_sell<float,float,float,ECheb>" if fmx == 0 else
                                          f"k_spmv<{fmx},float,float,float,ECheb>")
@@ -586,8 +604,9 @@ def gpu_arm(args, rank, world):
 
 def profile_case(args):
     """Small, self-contained cases for single-kernel ncu captures (inputs larger than L2, a few
-    GB on the device): one V-cycle on the 128^3 phi_s block alone; one Arnoldi dot/update pass
-    over 16 basis vectors of 10.5M entries; one SpMV with the 128^3 full operator."""
+    GB on the device): one V-cycle on the 128^3 phi_s block alone; one Arnoldi dot pass over 16
+    basis vectors of 10.5M entries; one SpMV with the 128^3 full operator; one FP64 solve of the
+    64^3 system launched step by step (the Arnoldi update kernels)."""
     import torch
     import battery_system as bs
     import paper_2602_13079_gb300 as bgs
@@ -603,6 +622,17 @@ def profile_case(args):
             assert bgs.bgs_arnoldi_dots(V, n, cnt, w, n, h) == 0
         torch.cuda.synchronize()
         print("arnoldi case done", float(h[-1]))
+        return
+    if args.profile_case == "krylov":
+        # one FP64 solve of the 3D 64^3 system (1.31M DOFs): the Arnoldi kernels of its later
+        # iterations read more basis than L2 holds (20 vectors of 10.5 MB)
+        system = bs.assemble("C2", seed=args.seed)
+        g = bgs.solver_for_system(system, graph=0)
+        g.setup()
+        x = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
+        info = g.bgs_solve(torch.from_numpy(system.b).cuda(), x)
+        torch.cuda.synchronize()
+        print("krylov case done", info.iters)
         return
     system = bs.assemble(args.config, seed=args.seed)
     if args.profile_case == "vcycle":
