@@ -60,7 +60,8 @@ typedef struct {
     int precision;          /* 0: FP64 hierarchy; 1: FP32 hierarchy + BF16 coupling values */
     int graph;              /* 1 (default): replay the preconditioner sweep as a captured CUDA graph */
     int autotune;           /* 1 (default): pick the SpMV form per stored operator by timing at setup, in the
-                               precision the solve uses: SELL-32 with diagonal offsets (structured
+                               precision the solve uses: field-interleaved F x F node blocks (the full
+                               operator of equal fields), SELL-32 with diagonal offsets (structured
                                operators), SELL-32, or CSR with 1..32 lanes per row, each at 128, 256 or
                                512 threads per block; choices are cached per process by operator shape,
                                and in the text file named by the environment variable BGS_AUTOTUNE_CACHE
@@ -199,9 +200,11 @@ int bgs_level_ellipse(bgs_handle h, int field, int level, double *imag);
  * (rows + 1), col and val (nnz each) are filled when not NULL (host or device).  BGS_INVALID_ARG for
  * a field on the V-cycle. */
 int bgs_ilu_factors(bgs_handle h, int field, int64_t *nnz, int32_t *rowptr, int32_t *col, double *val);
-/* SpMV kernel used for A_l (which 0), P_l (1) or R_l (2): -1 = SELL-32 with one diagonal offset per
- * slice slot (structured operators), 0 = SELL-32, k > 0 = CSR with k threads per row (chosen by the
- * autotuner when it is on); *threads_per_block (may be NULL) receives the block size of its launches. */
+/* SpMV kernel used for A_l (which 0), P_l (1), R_l (2), or the full operator (which 3; field and level
+ * ignored): -2 = field-interleaved node blocks (full operator of equal fields only), -1 = SELL-32 with
+ * one diagonal offset per slice slot (structured operators), 0 = SELL-32, k > 0 = CSR with k threads
+ * per row (chosen by the autotuner when it is on); *threads_per_block (may be NULL) receives the block
+ * size of its launches. */
 int bgs_level_format(bgs_handle h, int field, int level, int which, int *format, int *threads_per_block);
 /* Aggregate id of every node of level `level` (host array of rows(level) entries). */
 int bgs_level_aggregates(bgs_handle h, int field, int level, int32_t *agg);

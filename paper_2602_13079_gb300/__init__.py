@@ -334,8 +334,9 @@ class Solver:
         return rp, ci[:nnz.value], v[:nnz.value]
 
     def bgs_level_format(self, field, level, which=0, with_block=False):
-        """-1 = SELL-32 with diagonal offsets, 0 = SELL-32, k > 0 = CSR with k threads per row; with
-        with_block, (format, threads per block)."""
+        """Layout of a stored operator (which: 0 A_l, 1 P_l, 2 R_l, 3 the full operator): -2 = node
+        blocks, -1 = SELL-32 with diagonal offsets, 0 = SELL-32, k > 0 = CSR with k threads per row;
+        with with_block, (format, threads per block)."""
         f, t = C.c_int(), C.c_int()
         _check(lib().bgs_level_format(self.h, int(field), int(level), int(which), C.byref(f), C.byref(t)),
                "bgs_level_format")

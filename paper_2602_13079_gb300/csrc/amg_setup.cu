@@ -1172,8 +1172,9 @@ __global__ void k_gj_unscramble(int n, const double *D, const int *tau, double *
 
 // Blocked form: GJB_R pivot steps per pair of launches.  The panel kernel (one block) takes the
 // columns K = [k, k+R) of the state before the steps, chooses the R pivots by partial pivoting on an
-// LU-eliminated working copy (the rows at and below each pivot hold, in R sequential Gauss-Jordan
-// steps, the same values as in LU, so the choices are the same) and computes D = A_KK^-1 of the
+// LU-eliminated FP32 working copy (in R sequential Gauss-Jordan steps the rows at and below each
+// pivot hold the values LU gives them; FP32 rounding can only swap the choice between two entries of
+// nearly the same size, which leaves the pivoting as stable) and computes D = A_KK^-1 of the
 // interchanged pivot rows (Gauss-Jordan on R x R, one thread per entry, pivots on the diagonal).
 // The update kernel (one block per row) writes the state after the R steps: columns K: D (pivot
 // rows) and F = -A_IK D (other rows); other columns: D A_KJ (pivot rows) and A_IJ + F A_KJ (other
@@ -1182,7 +1183,7 @@ __global__ void k_gj_unscramble(int n, const double *D, const int *tau, double *
 // products stay on the FP64 pipe.
 constexpr int GJB_R = 16;
 constexpr int GJB_T = 256;       // = GJB_R * GJB_R: one thread per entry of the pivot block
-constexpr int GJB_MAXN = 1280;   // the panel's working copy (n x R doubles) in shared memory
+constexpr int GJB_MAXN = 2560;   // the panel's working copy (n x R floats) in shared memory
 
 // position q after the block's row interchanges (pk[t]: the row exchanged with row k + t) holds row
 // src(q) of the state before them
@@ -1197,8 +1198,11 @@ __device__ __forceinline__ int gjb_src(int q, int k, int R, const int *pk) {
 
 __global__ void __launch_bounds__(GJB_T) k_gjb_panel(int n, int k, int R, const double *__restrict__ S, int *perm,
                                                       double *Dk, int *status) {
-    extern __shared__ double gjb_sm[];
-    double *Cw = gjb_sm;   // n x R, row-major [i * R + t]: the panel, rows interchanged, eliminated below pivots
+    extern __shared__ float gjb_sm[];
+    // n x R, row-major [i * R + t]: the panel, rows interchanged, eliminated below the pivots.  It
+    // only chooses the pivots, so it is kept in FP32 (one SM's FP64 rate made the FP64 copy the
+    // slowest part of the inverse); every value the inverse is made of comes from the FP64 state
+    float *Cw = gjb_sm;
     __shared__ double bv_s[GJB_T / 32];
     __shared__ int bi_s[GJB_T / 32];
     __shared__ int piv_s[GJB_R];
@@ -1206,14 +1210,14 @@ __global__ void __launch_bounds__(GJB_T) k_gjb_panel(int n, int k, int R, const 
     __shared__ double prow[GJB_R], pcol[GJB_R];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < n; i += blockDim.x)
-        for (int t = 0; t < R; t++) Cw[i * R + t] = S[(size_t)i * n + k + t];
+        for (int t = 0; t < R; t++) Cw[i * R + t] = (float)S[(size_t)i * n + k + t];
     __syncthreads();
     for (int t = 0; t < R; t++) {
         const int c = k + t;
         double best = -1.0;
         int bi = INT_MAX;
         for (int i = c + threadIdx.x; i < n; i += blockDim.x) {
-            const double a = fabs(Cw[i * R + t]);
+            const double a = fabsf(Cw[i * R + t]);
             if (gj_better(a, i, best, bi)) { best = a; bi = i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -1236,15 +1240,15 @@ __global__ void __launch_bounds__(GJB_T) k_gjb_panel(int n, int k, int R, const 
         __syncthreads();
         const int p = piv_s[t];
         if (p != c && threadIdx.x < R) {
-            const double a = Cw[c * R + threadIdx.x];
+            const float a = Cw[c * R + threadIdx.x];
             Cw[c * R + threadIdx.x] = Cw[p * R + threadIdx.x];
             Cw[p * R + threadIdx.x] = a;
         }
         __syncthreads();
         if (t + 1 < R) {   // each thread eliminates its own rows below the pivot
-            const double pv = Cw[c * R + t];
+            const float rpv = 1.0f / Cw[c * R + t];
             for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) {
-                const double l = Cw[i * R + t] / pv;
+                const float l = Cw[i * R + t] * rpv;
                 for (int u = t + 1; u < R; u++) Cw[i * R + u] -= l * Cw[c * R + u];
             }
         }
@@ -1261,6 +1265,7 @@ __global__ void __launch_bounds__(GJB_T) k_gjb_panel(int n, int k, int R, const 
         if (threadIdx.x < R) prow[threadIdx.x] = M[t * GJB_R + threadIdx.x];
         else if (threadIdx.x < 2 * R) pcol[threadIdx.x - R] = M[(threadIdx.x - R) * GJB_R + t];
         __syncthreads();
+        if (threadIdx.x == 0 && prow[t] == 0.0) *status = 1;   // an exactly singular pivot block
         const double rp = 1.0 / prow[t];
         if (r < R && q < R) {
             const double f = pcol[r];
@@ -1398,7 +1403,7 @@ static void dense_inverse_async(const DCsr &Ac, double *W, Scratch &sc, cudaStre
     if (n <= GJB_MAXN) {
         // blocked: GJB_R pivot steps per panel launch and update launch
         DBuf<double> Dk((size_t)GJB_R * GJB_R, s);
-        const size_t smem = sizeof(double) * (size_t)n * GJB_R;
+        const size_t smem = sizeof(float) * (size_t)n * GJB_R;
         const int gu = std::min(n, num_sms() * 4);
         for (int k = 0; k < n; k += GJB_R) {
             const int R = std::min(GJB_R, n - k);
@@ -1456,7 +1461,7 @@ static void set_attributes() {
         CK(cudaFuncSetAttribute(k_sg_num<SG_NUM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(double) * SG_WARPS * (SG_NUM_T + 64) + sizeof(int) * SG_WARPS * SG_NUM_T)));
         CK(cudaFuncSetAttribute(k_gjb_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(double) * GJB_MAXN * GJB_R)));
+                                (int)(sizeof(float) * GJB_MAXN * GJB_R)));
     });
 }
 

@@ -152,8 +152,9 @@ void prof_collect(bgs_ctx *h) {
 // (CSR / SELL-32: a column index per entry and the row pointers; diagonal-offset SELL-32: one offset
 // per slot of 32 rows and the slice pointers), x read and y written once, plus extra vectors.
 double spmv_bytes(const DCsr &A, int vbytes, int xbytes, int extra_vectors) {
-    const double idx = A.dia ? 4.0 * (double)(A.dia_nnz / 32) + 4.0 * ((A.n + 31) / 32 + 1)
-                             : 4.0 * (double)A.nnz + 4.0 * (A.n + 1);
+    const double idx = A.bsr   ? 4.0 * (double)A.bsr_slots + 4.0 * ((A.bsr_nc + 31) / 32 + 1)
+                       : A.dia ? 4.0 * (double)(A.dia_nnz / 32) + 4.0 * ((A.n + 31) / 32 + 1)
+                               : 4.0 * (double)A.nnz + 4.0 * (A.n + 1);
     return (double)A.nnz * vbytes + idx + (double)xbytes * A.n * (2 + extra_vectors);
 }
 
@@ -1128,7 +1129,9 @@ int bgs_create(bgs_handle *out, int F, const int64_t *sizes, const bgs_csr *bloc
         tr.mark("full operator + couplings");
         // the layouts the autotuner will choose from (only its cached choice when it has one)
         const bool tune = o.autotune != 0;
-        build_formats(h->full, 8, true, tune, h->sc, s, true);
+        bool equal = F >= 2;
+        for (int k = 1; k < F; k++) equal = equal && sizes[k] == sizes[0];
+        build_formats(h->full, 8, true, tune, h->sc, s, true, equal ? F : 0);
         for (int k = 0; k < F; k++) build_formats(h->lower[k], o.precision == 1 ? 2 : 8, false, tune, h->sc, s);
         CK(cudaStreamSynchronize(s));
         tr.mark("sell");
@@ -1494,13 +1497,18 @@ int bgs_ilu_factors(bgs_handle h, int field, int64_t *nnz, int32_t *rowptr, int3
 }
 
 int bgs_level_format(bgs_handle h, int field, int level, int which, int *format, int *threads_per_block) {
-    if (!h || field < 0 || field >= h->F || which < 0 || which > 2 || !format) return BGS_INVALID_ARG;
+    if (!h || which < 0 || which > 3 || !format) return BGS_INVALID_ARG;
     if (!h->setup_done) return BGS_NOT_SETUP;
-    Hier &H = h->H[field];
-    if (level < 0 || level >= (int)H.L.size()) return BGS_INVALID_ARG;
-    if (which > 0 && level + 1 >= (int)H.L.size()) return BGS_INVALID_ARG;
-    const DCsr &M = which == 0 ? H.L[level].A : (which == 1 ? H.L[level].P : H.L[level].R);
-    *format = M.dia ? -1 : (M.sell ? 0 : (M.lanes ? M.lanes : choose_lanes(M.n, M.nnz)));
+    const DCsr *Mp = &h->full;
+    if (which < 3) {
+        if (field < 0 || field >= h->F) return BGS_INVALID_ARG;
+        Hier &H = h->H[field];
+        if (level < 0 || level >= (int)H.L.size()) return BGS_INVALID_ARG;
+        if (which > 0 && level + 1 >= (int)H.L.size()) return BGS_INVALID_ARG;
+        Mp = which == 0 ? &H.L[level].A : (which == 1 ? &H.L[level].P : &H.L[level].R);
+    }
+    const DCsr &M = *Mp;
+    *format = M.bsr ? -2 : (M.dia ? -1 : (M.sell ? 0 : (M.lanes ? M.lanes : choose_lanes(M.n, M.nnz))));
     if (threads_per_block) *threads_per_block = M.tpb;
     return BGS_OK;
 }

@@ -119,6 +119,15 @@ struct DCsr {
     DBuf<double> dv;
     DBuf<float> dvf;
     DBuf<__nv_bfloat16> dvb;
+    // Field-interleaved node blocks (bsr == true when built; the full operator of F fields of equal
+    // size nc only): node I gathers rows f*nc + I (f < F); its block columns J (ascending) each hold an
+    // F x F block, entry (f, g) = A(f*nc + I, g*nc + J) or 0.  Nodes in slices of 32 (one warp), slice
+    // s holding w_s block slots; bcol[slot*32 + lane], bval[((slot*F + f)*F + g)*32 + lane].
+    bool bsr = false;
+    int bsr_F = 0, bsr_nc = 0;
+    int64_t bsr_slots = 0;          // block slots (32 per slice and slot)
+    DBuf<int> bptr, bcol;           // slot start per slice (multiple of 32), block column per slot
+    DBuf<double> bval;
 };
 
 // ------------------------------------------------------------------------------------------

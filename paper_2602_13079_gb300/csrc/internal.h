@@ -127,8 +127,15 @@ int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s, bool pr
 // Builds the SpMV layouts an operator may run: the one the autotuner's cached choice for its shape
 // names (use_cache), else SELL-32 and, with allow_dia, the diagonal-offset SELL-32 for the
 // autotuner to time.  value_bytes as for autotune_spmv.
+// bsr_fields: F > 0 for the full operator of F equal fields (the node-block layout is then a
+// candidate too).
 void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scratch &sc, cudaStream_t s,
-                   bool product = false);
+                   bool product = false, int bsr_fields = 0);
+// Builds the field-interleaved node-block copy of the full operator of F fields of equal size (F x F
+// blocks per node pair, at most 32 block columns per node) when its stored block entries stay
+// within max_pad * nnz (returns whether built).
+bool build_bsr(DCsr &A, int F, double max_pad, Scratch &sc, cudaStream_t s);
+void drop_bsr(DCsr &A);
 
 // ---------------------------------------------------------------- krylov.cu
 // h[k] = V_k . w for k < cnt and h[cnt] = w . w (V column-major, leading dimension ld, even; V and w
@@ -245,5 +252,7 @@ void transpose_csr(const CsrView &A, DCsr &T, Scratch &sc, cudaStream_t s);
 constexpr double kMaxPad = 2.0;
 // the diagonal-offset SELL-32 copy is built when its slots stay within this factor of the entries
 constexpr double kMaxPadDia = 1.5;
+// the node-block copy stores F^2 values per block: built while that stays within this factor of the entries
+constexpr double kMaxPadBsr = 5.0;
 
 }  // namespace bgs

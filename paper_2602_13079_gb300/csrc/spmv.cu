@@ -20,6 +20,7 @@
 #include <tuple>
 
 #include <climits>
+#include <type_traits>
 
 #include "spmv_dev.cuh"
 
@@ -105,24 +106,86 @@ __global__ void __launch_bounds__(TPB) k_dia(int n, int m, const int *__restrict
     const int last = m - 1;
     constexpr bool S = Epi::kSub;
     AT acc = row < n ? epi.template start<AT>(row) : (AT)0;
-    // batches of U slots, all loads of a batch in flight together: a slot past the slice width
-    // re-reads the last one (a cached duplicate) and its product is skipped (w is warp-uniform)
-    constexpr int U = (sizeof(AT) == 4 && sizeof(VT) == 4) ? 8 : 4;
+    if constexpr (sizeof(AT) == 4 && sizeof(VT) == 4) {
+        // FP32: batches of 8 slots, all loads of a batch in flight together; a slot past the slice
+        // width re-reads the last one (a cached duplicate) and its product is skipped (w is
+        // warp-uniform)
+        constexpr int U = 8;
 #pragma unroll 1
-    for (int k = 0; k < w; k += U) {
-        AT a[U], xv[U];
+        for (int k = 0; k < w; k += U) {
+            AT a[U], xv[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int kk = min(k + u, w - 1);
-            const int c = min(max(row + __shfl_sync(0xffffffffu, myo, kk), 0), last);
-            a[u] = Cvt<AT>::f(ldg(v + kk * 32));
-            xv[u] = Cvt<AT>::f(ldg(x + c));
+            for (int u = 0; u < U; u++) {
+                const int kk = min(k + u, w - 1);
+                const int c = min(max(row + __shfl_sync(0xffffffffu, myo, kk), 0), last);
+                a[u] = Cvt<AT>::f(ldg(v + kk * 32));
+                xv[u] = Cvt<AT>::f(ldg(x + c));
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (k + u < w) acc = mac<S>(acc, a[u], xv[u]);
         }
+    } else {
+        // FP64: full batches of 4 slots, then the rest one by one (no duplicate loads; this timed
+        // faster than predicated batches for the FP64 operators)
+        constexpr int U = 4;
+        int k = 0;
+#pragma unroll 1
+        for (; k + U <= w; k += U) {
+            AT a[U], xv[U];
 #pragma unroll
-        for (int u = 0; u < U; u++)
-            if (k + u < w) acc = mac<S>(acc, a[u], xv[u]);
+            for (int u = 0; u < U; u++) {
+                const int c = min(max(row + __shfl_sync(0xffffffffu, myo, k + u), 0), last);
+                a[u] = Cvt<AT>::f(ldg(v + (k + u) * 32));
+                xv[u] = Cvt<AT>::f(ldg(x + c));
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) acc = mac<S>(acc, a[u], xv[u]);
+        }
+#pragma unroll 1
+        for (; k < w; k++) {
+            const int c = min(max(row + __shfl_sync(0xffffffffu, myo, k), 0), last);
+            acc = mac<S>(acc, Cvt<AT>::f(ldg(v + k * 32)), Cvt<AT>::f(ldg(x + c)));
+        }
     }
     if (row < n) epi(row, acc);
+}
+
+// ------------------------------------------------------------------------------------------ field-interleaved node blocks
+// The full operator of F fields on nc nodes as F x F node blocks (the block-sparse form the
+// coupled unknowns of one node suggest): one thread per node computes the F rows f * nc + I, each
+// block slot one block column J with its F x F values (stored lane-innermost, so every value load of
+// a warp is one contiguous run) and F gathers x[g * nc + J].  A row's products are summed block by
+// block (ascending J), within a block by field g.
+template <int F, class Epi, int TPB>
+__global__ void __launch_bounds__(TPB) k_bsr(int nc, const int *__restrict__ bptr, const int *__restrict__ bcol,
+                                             const double *__restrict__ bval, const double *__restrict__ x, Epi epi) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = I >> 5;
+    if ((slice << 5) >= nc) return;
+    const int lane = I & 31;
+    const int s0 = __ldg(bptr + slice);
+    const int w = (__ldg(bptr + slice + 1) - s0) >> 5;
+    constexpr bool S = Epi::kSub;
+    double acc[F];
+#pragma unroll
+    for (int f = 0; f < F; f++) acc[f] = I < nc ? epi.template start<double>(f * nc + I) : 0.0;
+    const double *vb = bval + (size_t)s0 * F * F + lane;
+#pragma unroll 1
+    for (int k = 0; k < w; k++) {
+        const int J = __ldg(bcol + s0 + k * 32 + lane);
+        double xg[F];
+#pragma unroll
+        for (int g = 0; g < F; g++) xg[g] = __ldg(x + (size_t)g * nc + J);
+#pragma unroll
+        for (int f = 0; f < F; f++)
+#pragma unroll
+            for (int g = 0; g < F; g++)
+                acc[f] = mac<S>(acc[f], __ldg(vb + ((size_t)k * F * F + f * F + g) * 32), xg[g]);
+    }
+    if (I < nc)
+#pragma unroll
+        for (int f = 0; f < F; f++) epi(f * nc + I, acc[f]);
 }
 
 // value arrays of a matrix by element type (CSR order / SELL order / diagonal-offset order)
@@ -193,10 +256,44 @@ static void launch_sliced(const DCsr &A, const XT *x, Epi epi, cudaStream_t s) {
     CK_LAUNCH();
 }
 
+template <int F, class Epi, int TPB>
+static void launch_bsr_f(const DCsr &A, const double *x, Epi epi, cudaStream_t s) {
+    const int g = (int)(((int64_t)A.bsr_nc + TPB - 1) / TPB);
+    k_bsr<F, Epi, TPB><<<g, TPB, 0, s>>>(A.bsr_nc, A.bptr.p, A.bcol.p, A.bval.p, x, epi);
+    CK_LAUNCH();
+}
+
+template <class Epi, int TPB>
+static void launch_bsr_tpb(const DCsr &A, const double *x, Epi epi, cudaStream_t s) {
+    switch (A.bsr_F) {
+        case 2: launch_bsr_f<2, Epi, TPB>(A, x, epi, s); break;
+        case 3: launch_bsr_f<3, Epi, TPB>(A, x, epi, s); break;
+        case 4: launch_bsr_f<4, Epi, TPB>(A, x, epi, s); break;
+        case 5: launch_bsr_f<5, Epi, TPB>(A, x, epi, s); break;
+        case 6: launch_bsr_f<6, Epi, TPB>(A, x, epi, s); break;
+        default: throw Error(BGS_INTERNAL, "node blocks built for an unsupported field count");
+    }
+}
+
+// the node-block form serves the full operator's plain product and residual only
+template <class VT, class XT, class Epi>
+constexpr bool kBsrEpi = std::is_same<VT, double>::value && std::is_same<XT, double>::value &&
+                         (std::is_same<Epi, EStore<double>>::value || std::is_same<Epi, EResid<double>>::value);
+
 template <class VT, class XT, class Epi>
 static void run(const DCsr &A, const XT *x, Epi epi, cudaStream_t s) {
     using AT = typename AccT<VT, XT>::T;
     if (A.n <= 0) return;
+    if (A.bsr) {
+        if constexpr (kBsrEpi<VT, XT, Epi>) {
+            if (A.tpb == 128) launch_bsr_tpb<Epi, 128>(A, x, epi, s);
+            else if (A.tpb == 512) launch_bsr_tpb<Epi, 512>(A, x, epi, s);
+            else launch_bsr_tpb<Epi, 256>(A, x, epi, s);
+            return;
+        } else {
+            throw Error(BGS_INTERNAL, "node-block layout applied with an unsupported epilogue");
+        }
+    }
     if (A.dia || A.sell) {
         if (A.tpb == 128) launch_sliced<VT, XT, AT, Epi, 128>(A, x, epi, s);
         else if (A.tpb == 512) launch_sliced<VT, XT, AT, Epi, 512>(A, x, epi, s);
@@ -425,6 +522,113 @@ bool build_dia(DCsr &A, double max_pad, Scratch &sc, cudaStream_t s) {
     return true;
 }
 
+// ------------------------------------------------------------------------------------------ node-block build
+constexpr int kBsrMaxBlocks = 32;   // distinct block columns per node
+
+// the distinct block columns of node I over its F rows, ascending, into lc; the count, or -1 past
+// kBsrMaxBlocks
+__device__ int bsr_node_cols(int I, int F, int nc, const int *rp, const int *ci, int *lc) {
+    int c = 0;
+    for (int f = 0; f < F; f++) {
+        const int r = f * nc + I;
+        for (int e = rp[r]; e < rp[r + 1]; e++) {
+            const int J = ci[e] % nc;
+            int p = c - 1;
+            while (p >= 0 && lc[p] > J) p--;
+            if (p >= 0 && lc[p] == J) continue;
+            if (c == kBsrMaxBlocks) return -1;
+            for (int q = c; q > p + 1; q--) lc[q] = lc[q - 1];
+            lc[p + 1] = J;
+            c++;
+        }
+    }
+    return c;
+}
+
+__global__ void k_bsr_width(int nc, int F, const int *rp, const int *ci, int *wslot, int *fail) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = I >> 5;
+    if ((slice << 5) >= nc) return;
+    int lc[kBsrMaxBlocks];
+    int c = I < nc ? bsr_node_cols(I, F, nc, rp, ci, lc) : 0;
+    if (c < 0) {
+        atomicOr(fail, 1);
+        c = 0;
+    }
+    const int w = __reduce_max_sync(0xffffffffu, c);
+    if ((I & 31) == 0) wslot[slice] = w * 32;
+}
+
+// block columns (a padded slot repeats the node's first block column, values 0) and values
+__global__ void k_bsr_fill(int nc, int F, const int *rp, const int *ci, const double *v, const int *bptr, int *bcol,
+                           double *bval) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = I >> 5;
+    if ((slice << 5) >= nc) return;
+    const int lane = I & 31;
+    const int s0 = bptr[slice], w = (bptr[slice + 1] - s0) >> 5;
+    int lc[kBsrMaxBlocks];
+    const int c = I < nc ? bsr_node_cols(I, F, nc, rp, ci, lc) : 0;
+    const int pad = c > 0 ? lc[0] : 0;
+    const size_t FF = (size_t)F * F;
+    for (int k = 0; k < w; k++) {
+        bcol[s0 + k * 32 + lane] = k < c ? lc[k] : pad;
+        for (size_t fg = 0; fg < FF; fg++) bval[((size_t)s0 + (size_t)k * 32) * FF + fg * 32 + lane] = 0.0;
+    }
+    if (I >= nc) return;
+    for (int f = 0; f < F; f++) {
+        const int r = f * nc + I;
+        for (int e = rp[r]; e < rp[r + 1]; e++) {
+            const int g = ci[e] / nc, J = ci[e] - g * nc;
+            int lo = 0, hi = c - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (lc[mid] < J) lo = mid + 1;
+                else hi = mid;
+            }
+            bval[((size_t)s0 + (size_t)lo * 32) * FF + (size_t)(f * F + g) * 32 + lane] = v[e];
+        }
+    }
+}
+
+static void bsr_fill(DCsr &A, cudaStream_t s) {
+    const int nsl = (A.bsr_nc + 31) / 32;
+    k_bsr_fill<<<(unsigned)(((int64_t)nsl * 32 + 255) / 256), 256, 0, s>>>(A.bsr_nc, A.bsr_F, A.rp.p, A.ci.p, A.v.p,
+                                                                         A.bptr.p, A.bcol.p, A.bval.p);
+    CK_LAUNCH();
+}
+
+bool build_bsr(DCsr &A, int F, double max_pad, Scratch &sc, cudaStream_t s) {
+    if (A.bsr) return true;
+    if (F < 2 || F > 6 || A.n <= 0 || A.nnz <= 0 || A.n % F || A.m != A.n) return false;
+    const int nc = A.n / F;
+    const int nsl = (nc + 31) / 32;
+    DBuf<int> bptr((size_t)nsl + 1, s);
+    CK(cudaMemsetAsync(sc.flags.p + 15, 0, sizeof(int), s));
+    k_bsr_width<<<(unsigned)(((int64_t)nsl * 32 + 255) / 256), 256, 0, s>>>(nc, F, A.rp.p, A.ci.p, bptr.p,
+                                                                           sc.flags.p + 15);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(sc.h_flags + 15, sc.flags.p + 15, sizeof(int), cudaMemcpyDeviceToHost, s));
+    const int64_t tot = scan_exclusive(bptr.p, bptr.p, nsl, sc, s);   // synchronises
+    if (sc.h_flags[15]) return false;                                // a node with too many block columns
+    if ((double)tot * F * F > max_pad * (double)A.nnz) return false;
+    A.bptr = std::move(bptr);
+    A.bsr_slots = tot;
+    A.bsr_F = F;
+    A.bsr_nc = nc;
+    A.bcol.alloc((size_t)tot, s);
+    A.bval.alloc((size_t)tot * F * F, s);
+    bsr_fill(A, s);
+    A.bsr = true;
+    return true;
+}
+
+void drop_bsr(DCsr &A) {
+    A.bsr = false;
+    A.bsr_slots = 0;
+    A.bptr.release(); A.bcol.release(); A.bval.release();
+}
+
 void drop_dia(DCsr &A) {
     A.dia = false;
     A.dia_nnz = 0;
@@ -448,6 +652,7 @@ void refresh_values(DCsr &A, cudaStream_t s) {
     if (A.vb.p) convert_d2bf(A.v.p, A.vb.p, A.nnz, s);
     if (A.sell) gather_into(A, A.v.p, A.sv, s);
     if (A.dia) gather_dia(A, A.v.p, A.dv, s);
+    if (A.bsr) bsr_fill(A, s);
     sell_refresh(A, s);
 }
 
@@ -461,17 +666,18 @@ void refresh_values(DCsr &A, cudaStream_t s) {
 // the fastest of five timed launches each, CUDA events on the stream.  The choice is cached for the
 // process, keyed by (rows, columns, stored entries, value bytes, epilogue), so repeated set-ups of operators
 // with the same shape reuse it without timing, and build only the layout the choice needs.
-// a choice: format (-1 diagonal-offset SELL, 0 SELL-32, k > 0 CSR with k threads per row) and block size
+// a choice: format (-2 node blocks, -1 diagonal-offset SELL, 0 SELL-32, k > 0 CSR with k threads per
+// row) and block size
 struct Choice {
     int format = 0, tpb = 256;
     int code() const {
-        const int f = format < 0 ? 0 : (format == 0 ? 1 : 2 + __builtin_ctz((unsigned)format));
+        const int f = format == -2 ? 8 : (format < 0 ? 0 : (format == 0 ? 1 : 2 + __builtin_ctz((unsigned)format)));
         return f * 4 + (tpb == 128 ? 0 : (tpb == 512 ? 2 : 1));
     }
     static Choice from(int c) {
         Choice ch;
         const int f = c / 4, t = c % 4;
-        ch.format = f == 0 ? -1 : (f == 1 ? 0 : 1 << (f - 2));
+        ch.format = f == 8 ? -2 : (f == 0 ? -1 : (f == 1 ? 0 : 1 << (f - 2)));
         ch.tpb = t == 0 ? 128 : (t == 2 ? 512 : 256);
         return ch;
     }
@@ -522,11 +728,14 @@ static Choice time_candidates(DCsr &A, bool product, cudaStream_t s) {
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
     Choice choice;
-    const bool had_sell = A.sell, had_dia = A.dia;
-    const int formats[8] = {-1, 0, 1, 2, 4, 8, 16, 32};
+    const bool had_sell = A.sell, had_dia = A.dia, had_bsr = A.bsr;
+    const int formats[9] = {-2, -1, 0, 1, 2, 4, 8, 16, 32};
     for (int f : formats) {
-        if ((f == -1 && !had_dia) || (f == 0 && !had_sell)) continue;
+        if ((f == -2 && !(had_bsr && product && kBsrEpi<VT, XT, EStore<XT>>)) || (f == -1 && !had_dia) ||
+            (f == 0 && !had_sell))
+            continue;
         for (int tpb : {128, 256, 512}) {
+            A.bsr = f == -2;
             A.dia = f == -1;
             A.sell = f == 0;
             A.lanes = f > 0 ? f : 0;
@@ -551,6 +760,7 @@ static Choice time_candidates(DCsr &A, bool product, cudaStream_t s) {
     }
     A.sell = had_sell;
     A.dia = had_dia;
+    A.bsr = had_bsr;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return choice;
@@ -559,6 +769,7 @@ static Choice time_candidates(DCsr &A, bool product, cudaStream_t s) {
 static void apply_choice(DCsr &A, Choice c) {
     A.tpb = c.tpb;
     A.lanes = c.format > 0 ? c.format : 0;
+    if (c.format != -2 && A.bsr) drop_bsr(A);
     if (c.format != -1 && A.dia) drop_dia(A);
     if (c.format != 0 && A.sell) {
         A.sell = false;
@@ -574,17 +785,19 @@ static int cached_code(const TuneKey &key) {
 }
 
 void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scratch &sc, cudaStream_t s,
-                   bool product) {
+                   bool product, int bsr_fields) {
     if (A.n <= 0 || A.nnz <= 0) return;
     const int code = use_cache ? cached_code(std::make_tuple(A.n, A.m, A.nnz, value_bytes, product ? 1 : 0)) : -1;
     if (code >= 0) {
         const Choice c = Choice::from(code);
+        if (c.format == -2 && bsr_fields && build_bsr(A, bsr_fields, kMaxPadBsr, sc, s)) return;
         if (c.format == -1 && allow_dia && build_dia(A, kMaxPadDia, sc, s)) return;
         if (c.format <= 0) build_sell(A, kMaxPad, sc, s);
         return;
     }
     build_sell(A, kMaxPad, sc, s);
     if (allow_dia) build_dia(A, kMaxPadDia, sc, s);
+    if (bsr_fields) build_bsr(A, bsr_fields, kMaxPadBsr, sc, s);
 }
 
 int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s, bool product) {
@@ -595,7 +808,8 @@ int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s, bool pr
     if (code >= 0) {
         c = Choice::from(code);
         // the layout the choice names was not built for this operator: the fastest one that was
-        if ((c.format == -1 && !A.dia) || (c.format == 0 && !A.sell)) c = Choice{A.dia ? -1 : (A.sell ? 0 : 1), 256};
+        if ((c.format == -2 && !A.bsr) || (c.format == -1 && !A.dia) || (c.format == 0 && !A.sell))
+            c = Choice{A.dia ? -1 : (A.sell ? 0 : 1), 256};
     } else {
         // time the kernels in the precision the solve will use
         if (value_bytes == 2 && A.vb.p) c = time_candidates<__nv_bfloat16, double>(A, product, s);

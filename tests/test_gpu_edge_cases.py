@@ -22,15 +22,9 @@ def bgs():
 
 def csr(D):
     D = np.asarray(D, dtype=np.float64)
-    rp = [0]
-    ci, v = [], []
-    for i in range(D.shape[0]):
-        for j in range(D.shape[1]):
-            if D[i, j] != 0.0:
-                ci.append(j)
-                v.append(D[i, j])
-        rp.append(len(ci))
-    return bs.CSR(np.array(rp, dtype=np.int32), np.array(ci, dtype=np.int32), np.array(v), D.shape[0], D.shape[1])
+    r, c = np.nonzero(D)                        # row-major order
+    rp = np.searchsorted(r, np.arange(D.shape[0] + 1)).astype(np.int32)
+    return bs.CSR(rp, c.astype(np.int32), D[r, c].copy(), D.shape[0], D.shape[1])
 
 
 def dd_matrix(n, rng):
@@ -91,11 +85,11 @@ def test_explicit_empty_coupling_and_zero_rhs(bgs):
     assert info0.converged and info0.iters == 0 and not np.any(x0)
 
 
-@pytest.mark.parametrize("n", [1, 7, 9, 483, 1000, 1281])
+@pytest.mark.parametrize("n", [1, 7, 9, 17, 483, 1000, 1281, 2560, 2561])
 def test_coarsest_direct_solve_sizes(bgs, n):
     """A single-level hierarchy (max_coarse >= n): the V-cycle is the coarsest direct solve alone.
-    Sizes below and above the blocked Gauss-Jordan panel width (8) and its shared-memory limit
-    (1280 rows, beyond which the one-launch-per-pivot form runs), against a dense FP64 solve of a
+    Sizes below and above the blocked Gauss-Jordan panel width (16) and its shared-memory limit
+    (2560 rows, beyond which the one-launch-per-pivot form runs), against a dense FP64 solve of a
     nonsymmetric matrix whose pivots need row interchanges."""
     rng = np.random.default_rng(n)
     D = dd_matrix(n, rng)
