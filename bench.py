@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--rtol", type=float, default=1e-8, help="relative tolerance for --theta-grid")
     p.add_argument("--sigma-means", default=None,
                    help="anode,separator,cathode conductivity means for --theta-grid (default: the workload's)")
-    p.add_argument("--profile-case", default=None, choices=["vcycle", "arnoldi", "spmv", "krylov"],
+    p.add_argument("--profile-case", default=None, choices=["vcycle", "arnoldi", "spmv", "krylov", "setup"],
                    help="run one small kernel case for an ncu capture and exit")
     p.add_argument("--profile-precision", type=int, default=0, choices=[0, 1],
                    help="hierarchy precision of --profile-case vcycle (0 FP64, 1 FP32)")
@@ -606,7 +606,8 @@ def profile_case(args):
     """Small, self-contained cases for single-kernel ncu captures (inputs larger than L2, a few
     GB on the device): one V-cycle on the 128^3 phi_s block alone; one Arnoldi dot pass over 16
     basis vectors of 10.5M entries; one SpMV with the 128^3 full operator; one FP64 solve of the
-    64^3 system launched step by step (the Arnoldi update kernels)."""
+    64^3 system launched step by step (the Arnoldi update kernels); and, not for ncu, the set-up's
+    phase timeline at 128^3 (stderr)."""
     import torch
     import battery_system as bs
     import paper_2602_13079_gb300 as bgs
@@ -635,6 +636,23 @@ def profile_case(args):
         print("krylov case done", info.iters)
         return
     system = bs.assemble(args.config, seed=args.seed)
+    if args.profile_case == "setup":
+        # the set-up's timeline (BGS_TRACE=async: host clock and stream of every phase mark, to
+        # stderr) for one set-up per precision after three untraced ones
+        blocks, _ = device_blocks(system, torch)
+        for precision in (0, 1):
+            for rep in range(4):
+                if rep == 3:
+                    os.environ["BGS_TRACE"] = "async"
+                    print(f"=== precision {precision}", file=sys.stderr, flush=True)
+                s = bgs.Solver(blocks, system.field_sizes, list(range(5)), precision=precision)
+                s.setup()
+                torch.cuda.synchronize()
+                sys.stderr.flush()
+                os.environ.pop("BGS_TRACE", None)
+                s.close()
+        print("setup case done")
+        return
     if args.profile_case == "vcycle":
         B = system.blocks[(0, 0)]
 

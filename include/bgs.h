@@ -65,7 +65,8 @@ typedef struct {
                                operators), SELL-32, or CSR with 1..32 lanes per row, each at 128, 256 or
                                512 threads per block; choices are cached per process by operator shape,
                                and in the text file named by the environment variable BGS_AUTOTUNE_CACHE
-                               when it is set.  0: the diagonal-offset form where built, else SELL-32
+                               when it is set (BGS_AUTOTUNE_LOG set: every candidate's time is printed
+                               to stderr).  0: the diagonal-offset form where built, else SELL-32
                                where built, else CSR with a lane count fixed by the row length */
     int cheb_degree[8];     /* Chebyshev degree per field id (Sec. 2.2.1: 2; voltage blocks 4, Sec. 3.1.5) */
     double theta[8];        /* strength drop tolerance per field id (Sec. 3.1.4: 0.04 for phi_s) */

@@ -13,6 +13,7 @@
 // products are summed in a fixed order (mul and add rounded separately).
 #include <algorithm>
 #include <chrono>
+#include <cstring>
 #include <cmath>
 #include <cstdlib>
 #include <mutex>
@@ -23,20 +24,37 @@
 
 namespace bgs {
 
-// Setup phase tracing (BGS_TRACE=1): synchronises the stream at phase boundaries and prints the
-// wall time of each phase to stderr.
+// Set-up phase tracing to stderr.  BGS_TRACE set: each phase's wall time, the stream synchronised
+// at every mark.  BGS_TRACE=async: no synchronisation; each mark prints the host clock since the
+// process's first mark and the stream, a timeline of the concurrent per-block set-ups (host-side,
+// so it runs ahead of the GPU between the set-up's own synchronisations).
+static std::chrono::steady_clock::time_point trace_origin() {
+    static const std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    return t0;
+}
+static void timeline_print(const char *what, cudaStream_t s, int level, long long n) {
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - trace_origin()).count();
+    fprintf(stderr, "bgs-timeline %10.3f ms stream %p level %d n %lld %s\n", ms, (void *)s, level, n, what);
+}
 struct Trace {
-    bool on;
+    bool on, async;
     cudaStream_t s;
     std::chrono::steady_clock::time_point t;
-    explicit Trace(cudaStream_t st) : on(getenv("BGS_TRACE") != nullptr), s(st) {
+    explicit Trace(cudaStream_t st) : on(getenv("BGS_TRACE") != nullptr), async(false), s(st) {
         if (on) {
-            cudaStreamSynchronize(s);
+            async = strcmp(getenv("BGS_TRACE"), "async") == 0;
+            if (!async) cudaStreamSynchronize(s);
             t = std::chrono::steady_clock::now();
+            trace_origin();
+            if (async) timeline_print("start", s, -1, 0);
         }
     }
     void mark(const char *what, int level, long long n) {
         if (!on) return;
+        if (async) {
+            timeline_print(what, s, level, n);
+            return;
+        }
         cudaStreamSynchronize(s);
         auto now = std::chrono::steady_clock::now();
         fprintf(stderr, "bgs-trace level %d n %lld %-18s %8.3f ms\n", level, n, what,
@@ -44,6 +62,11 @@ struct Trace {
         t = now;
     }
 };
+
+void timeline_mark(const char *what, cudaStream_t s) {
+    const char *t = getenv("BGS_TRACE");
+    if (t && strcmp(t, "async") == 0) timeline_print(what, s, -1, 0);
+}
 
 // ==========================================================================================
 // Strength of connection
@@ -429,28 +452,37 @@ __global__ void k_power_start(int n, double *v) {
 // from the last two, which equals ||D^-1 A v|| for the normalised v = u_k-1 / ||u_k-1|| of the
 // textbook iteration.  Every 8 steps (never on the last) the iterate is rescaled to unit norm, so
 // its size stays far from FP64's range limits however many steps are asked for.
-static double power_lambda(const DCsr &A, const double *dinv, int iters, Scratch &sc, cudaStream_t s) {
+// The steps, enqueued on s with no read-back: out[0] = ||u_k||^2, out[2] = ||u_k-1||^2 (out[0..1]
+// also hold (||v||^2, 1/||v||) for the rescaling steps); partial: num_sms() * 4 doubles.
+static void power_enqueue(const DCsr &A, const double *dinv, int iters, double *partial, double *out,
+                          cudaStream_t s) {
     const int n = A.n;
     DBuf<double> v((size_t)n, s), w((size_t)n, s);
     k_power_start<<<grid_for(n, 256), 256, 0, s>>>(n, v.p);
     CK_LAUNCH();
-    double *nv = sc.scal.p + 20, *nw = sc.scal.p + 22;
+    double *nv = out, *nw = out + 2;
     for (int it = 0; it < iters; it++) {
         if (it > 0 && it % 8 == 0 && it < iters - 1) {
-            dev_dot_rsqrt(v.p, v.p, n, nv, sc, s);           // (||v||^2, 1/||v||)
+            dev_dot_rsqrt(v.p, v.p, n, nv, partial, s);      // (||v||^2, 1/||v||)
             spmv_scaled_norm(A, dinv, v.p, nv + 1, w.p, s);  // w = D^-1 A (v / ||v||)
         } else {
             spmv_scaled_norm(A, dinv, v.p, nullptr, w.p, s); // w = D^-1 A v
         }
         std::swap(v.p, w.p);
     }
-    dev_dot(v.p, v.p, n, nv, sc, s);   // ||u_k||^2
-    dev_dot(w.p, w.p, n, nw, sc, s);   // ||u_k-1||^2
-    CK(cudaMemcpyAsync(sc.h_scal + 1, nv, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(sc.h_scal + 2, nw, sizeof(double), cudaMemcpyDeviceToHost, s));
+    dev_dot(v.p, v.p, n, nv, partial, s);   // ||u_k||^2
+    dev_dot(w.p, w.p, n, nw, partial, s);   // ||u_k-1||^2
+}
+
+static double power_estimate(double a, double b) { return b > 0.0 ? std::sqrt(a / b) : 0.0; }
+
+static double power_lambda(const DCsr &A, const double *dinv, int iters, Scratch &sc, cudaStream_t s) {
+    double *out = sc.scal.p + 20;
+    power_enqueue(A, dinv, iters, sc.partial.p, out, s);
+    CK(cudaMemcpyAsync(sc.h_scal + 1, out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(sc.h_scal + 2, out + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const double a = sc.h_scal[1], b = sc.h_scal[2];
-    return b > 0.0 ? std::sqrt(a / b) : 0.0;
+    return power_estimate(sc.h_scal[1], sc.h_scal[2]);
 }
 
 // ==========================================================================================
@@ -493,9 +525,12 @@ __device__ __forceinline__ int tbl_insert(int *keys, unsigned mask, int col, boo
 // doubles per warp: the lanes' left values (per chunk) and right values (per step).  Returns
 // this lane's count of new columns; sets over if the table's limit is passed (symbolic pass with
 // a capped shared table).
-template <bool NUM>
-__device__ int sg_accumulate(int row, int *keys, double *vals, unsigned T, bool capped, double *sv, const int *arp,
-                             const int *aci, const double *av, const int *brp, const int *bci, const double *bv,
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <bool NUM, class VT>
+__device__ int sg_accumulate(int row, int *keys, VT *vals, unsigned T, bool capped, VT *sv, const int *arp,
+                             const int *aci, const VT *av, const int *brp, const int *bci, const VT *bv,
                              bool &over) {
     const int lane = threadIdx.x & 31;
     const unsigned mask = T - 1;
@@ -505,7 +540,7 @@ __device__ int sg_accumulate(int row, int *keys, double *vals, unsigned T, bool 
         const int e = e0 + lane;
         const bool has = e < re;
         const int k = has ? aci[e] : 0;
-        const double a = (NUM && has) ? av[e] : 0.0;
+        const VT a = (NUM && has) ? av[e] : (VT)0;
         const int bs = has ? brp[k] : 0;
         const int len = has ? brp[k + 1] - bs : 0;
         const int maxlen = __reduce_max_sync(0xffffffffu, len);
@@ -529,10 +564,10 @@ __device__ int sg_accumulate(int row, int *keys, double *vals, unsigned T, bool 
                 if (sl < 0) over = true;
                 else {
                     if (NUM) {
-                        double v = vals[sl];
+                        VT v = vals[sl];
                         for (unsigned g = grp; g; g &= g - 1) {
                             const int m = __ffs(g) - 1;
-                            v = fma(sv[m], sv[32 + m], v);
+                            v = vfma(sv[m], sv[32 + m], v);
                         }
                         vals[sl] = v;
                     }
@@ -579,7 +614,7 @@ __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_sym(int n, const int *rows
         for (unsigned t = lane; t < T; t += 32) keys[t] = -1;
         __syncwarp();
         bool over = false;
-        const int mine = sg_accumulate<false>(row, keys, nullptr, T, T == (unsigned)TMAX && u > (int)(TMAX / 2),
+        const int mine = sg_accumulate<false, double>(row, keys, nullptr, T, T == (unsigned)TMAX && u > (int)(TMAX / 2),
                                               nullptr, arp, aci, nullptr, brp, bci, nullptr, over);
         const int total = __reduce_add_sync(0xffffffffu, mine);
         if (lane == 0) cnt[row] = over ? -1 : total;
@@ -598,7 +633,7 @@ __global__ void k_sg_sym_big(int nbig, const int *rows, const long long *toff, i
         for (unsigned t = lane; t < T; t += 32) keys[t] = -1;
         __syncwarp();
         bool over = false;
-        const int mine = sg_accumulate<false>(row, keys, nullptr, T, false, nullptr, arp, aci, nullptr, brp, bci,
+        const int mine = sg_accumulate<false, double>(row, keys, nullptr, T, false, nullptr, arp, aci, nullptr, brp, bci,
                                               nullptr, over);
         const int total = __reduce_add_sync(0xffffffffu, mine);
         if (lane == 0) cnt[row] = total;
@@ -606,17 +641,18 @@ __global__ void k_sg_sym_big(int nbig, const int *rows, const long long *toff, i
 }
 
 // numeric accumulate + in-place compaction + rank sort into the output row
-__device__ void sg_numeric_row(int row, int *keys, double *vals, unsigned T, double *sv, const int *arp,
-                               const int *aci, const double *av, const int *brp, const int *bci, const double *bv,
-                               const int *crp, int *cci, double *cv, int *err) {
+template <class VT>
+__device__ void sg_numeric_row(int row, int *keys, VT *vals, unsigned T, VT *sv, const int *arp, const int *aci,
+                               const VT *av, const int *brp, const int *bci, const VT *bv, const int *crp, int *cci,
+                               VT *cv, int *err) {
     const int lane = threadIdx.x & 31;
     for (unsigned t = lane; t < T; t += 32) {
         keys[t] = -1;
-        vals[t] = 0.0;
+        vals[t] = (VT)0;
     }
     __syncwarp();
     bool over = false;
-    sg_accumulate<true>(row, keys, vals, T, false, sv, arp, aci, av, brp, bci, bv, over);
+    sg_accumulate<true, VT>(row, keys, vals, T, false, sv, arp, aci, av, brp, bci, bv, over);
     if (over) {
         if (lane == 0) atomicOr(err, 1);
         return;
@@ -625,7 +661,7 @@ __device__ void sg_numeric_row(int row, int *keys, double *vals, unsigned T, dou
     for (unsigned base = 0; base < T; base += 32) {
         const unsigned sl = base + lane;
         const int k = sl < T ? keys[sl] : -1;
-        const double v = sl < T ? vals[sl] : 0.0;
+        const VT v = sl < T ? vals[sl] : (VT)0;
         const unsigned bal = __ballot_sync(0xffffffffu, k != -1);
         const int pos = wpos + __popc(bal & ((1u << lane) - 1u));
         __syncwarp();
@@ -652,15 +688,21 @@ __device__ void sg_numeric_row(int row, int *keys, double *vals, unsigned T, dou
     __syncwarp();
 }
 
-template <int TMAX>
+// shared memory of k_sg_num per block: SG_WARPS tables of TMAX values and keys, 64 staged values
+template <int TMAX, class VT>
+constexpr int sg_num_smem() {
+    return (int)(sizeof(VT) * SG_WARPS * (TMAX + 64) + sizeof(int) * SG_WARPS * TMAX);
+}
+
+template <int TMAX, class VT>
 __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *rows, const int *arp, const int *aci,
-                                                          const double *av, const int *brp, const int *bci,
-                                                          const double *bv, const int *crp, int *cci, double *cv,
-                                                          int *err) {
-    extern __shared__ double sg_nsm[];
+                                                          const VT *av, const int *brp, const int *bci, const VT *bv,
+                                                          const int *crp, int *cci, VT *cv, int *err) {
+    extern __shared__ __align__(16) unsigned char sg_nsm_raw[];
+    VT *sg_nsm = reinterpret_cast<VT *>(sg_nsm_raw);
     const int wib = threadIdx.x >> 5;
-    double *vals = sg_nsm + wib * TMAX;
-    double *sv = sg_nsm + SG_WARPS * TMAX + wib * 64;
+    VT *vals = sg_nsm + wib * TMAX;
+    VT *sv = sg_nsm + SG_WARPS * TMAX + wib * 64;
     int *keys = (int *)(sg_nsm + SG_WARPS * (TMAX + 64)) + wib * TMAX;
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n; it += (gridDim.x * blockDim.x) >> 5) {
         const int row = rows ? rows[it] : it;
@@ -671,10 +713,11 @@ __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *rows
     }
 }
 
-__global__ void k_sg_num_big(int nbig, const int *rows, const long long *toff, int *gkeys, double *gvals,
-                             const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
-                             const double *bv, const int *crp, int *cci, double *cv, int *err) {
-    __shared__ double svb[8][64];
+template <class VT>
+__global__ void k_sg_num_big(int nbig, const int *rows, const long long *toff, int *gkeys, VT *gvals, const int *arp,
+                             const int *aci, const VT *av, const int *brp, const int *bci, const VT *bv,
+                             const int *crp, int *cci, VT *cv, int *err) {
+    __shared__ VT svb[8][64];
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbig; b += (gridDim.x * blockDim.x) >> 5) {
         const unsigned T = (unsigned)(toff[b + 1] - toff[b]);
         sg_numeric_row(rows[b], gkeys + toff[b], gvals + toff[b], T, svb[(threadIdx.x >> 5) & 7], arp, aci, av, brp,
@@ -819,24 +862,29 @@ __global__ void __launch_bounds__(128) k_sg_local_sym(int n, const int *__restri
     }
 }
 
+// acc + a b with the product rounded on its own (no fused multiply-add), as the oracle sums
+__device__ __forceinline__ double add_mul_rn(double acc, double a, double b) { return __dadd_rn(acc, __dmul_rn(a, b)); }
+__device__ __forceinline__ float add_mul_rn(float acc, float a, float b) { return __fadd_rn(acc, __fmul_rn(a, b)); }
+
+template <class VT>
 __global__ void __launch_bounds__(128) k_sg_local_num(int n, const int *__restrict__ arp, const int *__restrict__ aci,
-                                                      const double *__restrict__ av, const int *__restrict__ brp,
-                                                      const int *__restrict__ bci, const double *__restrict__ bv,
+                                                      const VT *__restrict__ av, const int *__restrict__ brp,
+                                                      const int *__restrict__ bci, const VT *__restrict__ bv,
                                                       const int *__restrict__ ub, const int *__restrict__ cols,
-                                                      const int *__restrict__ crp, int *cci, double *cv, int *err) {
+                                                      const int *__restrict__ crp, int *cci, VT *cv, int *err) {
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
         const int o = crp[row], c = crp[row + 1] - o;
         if (ub[row] > SG_LOCAL_UB || c > SG_LOCAL) continue;   // handled by the hash path
         const int *in = cols + (size_t)row * SG_LOCAL;
         int *rc = cci + o;
-        double *rv = cv + o;
+        VT *rv = cv + o;
         for (int q = 0; q < c; q++) {
             rc[q] = in[q];
-            rv[q] = 0.0;
+            rv[q] = (VT)0;
         }
         for (int e = arp[row]; e < arp[row + 1]; e++) {
             const int k = aci[e];
-            const double a = av[e];
+            const VT a = av[e];
             for (int f = brp[k]; f < brp[k + 1]; f++) {
                 const int j = bci[f];
                 int lo = 0, hi = c;
@@ -849,7 +897,7 @@ __global__ void __launch_bounds__(128) k_sg_local_num(int n, const int *__restri
                     atomicOr(err, 1);
                     continue;
                 }
-                rv[lo] = __dadd_rn(rv[lo], __dmul_rn(a, bv[f]));
+                rv[lo] = add_mul_rn(rv[lo], a, bv[f]);
             }
         }
     }
@@ -863,8 +911,9 @@ __global__ void k_iota(int n, int *a) {
 // global-memory table sized for its product count, so no classing by row length; three read-backs
 // (table total, row counts, error flag) instead of one per class.
 constexpr int kSgSmallRows = 16384;
-static void spgemm_small(const CsrView &A, const CsrView &B, DCsr &C, const int *ub, Scratch &sc,
-                         cudaStream_t s) {
+template <class VT>
+static void spgemm_small(const CsrView &A, const VT *av, const CsrView &B, const VT *bv, DCsr &C, DBuf<VT> &cv,
+                         const int *ub, Scratch &sc, cudaStream_t s) {
     const int n = A.n;
     DBuf<int> rows((size_t)n, s);
     k_iota<<<grid_for(n, 256), 256, 0, s>>>(n, rows.p);
@@ -874,23 +923,27 @@ static void spgemm_small(const CsrView &A, const CsrView &B, DCsr &C, const int 
     CK_LAUNCH();
     const long long tot = scan_ll_inplace(toff.p, n, s);
     DBuf<int> gk((size_t)tot, s);
-    DBuf<double> gv((size_t)tot, s);
+    DBuf<VT> gv((size_t)tot, s);
     k_sg_sym_big<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, rows.p, toff.p, gk.p, A.rp, A.ci, B.rp, B.ci,
                                                                  C.rp.p);
     CK_LAUNCH();
     C.nnz = scan_exclusive(C.rp.p, C.rp.p, n, sc, s);
     C.ci.alloc((size_t)C.nnz, s);
-    C.v.alloc((size_t)C.nnz, s);
+    cv.alloc((size_t)C.nnz, s);
     CK(cudaMemsetAsync(sc.flags.p + 8, 0, sizeof(int), s));
-    k_sg_num_big<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, rows.p, toff.p, gk.p, gv.p, A.rp, A.ci, A.v, B.rp,
-                                                                 B.ci, B.v, C.rp.p, C.ci.p, C.v.p, sc.flags.p + 8);
+    k_sg_num_big<VT><<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, rows.p, toff.p, gk.p, gv.p, A.rp, A.ci, av,
+                                                                     B.rp, B.ci, bv, C.rp.p, C.ci.p, cv.p,
+                                                                     sc.flags.p + 8);
     CK_LAUNCH();
     CK(cudaMemcpyAsync(sc.h_flags + 8, sc.flags.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (sc.h_flags[8]) throw Error(BGS_INTERNAL, "SpGEMM numeric count differs from the symbolic count");
 }
 
-static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cudaStream_t s) {
+// C = A B with values of type VT (av, bv: the operands' values in that type; cv receives C's)
+template <class VT>
+static void spgemm_t(const CsrView &A, const VT *av, const CsrView &B, const VT *bv, DCsr &C, DBuf<VT> &cv,
+                     Scratch &sc, cudaStream_t s) {
     const int n = A.n;
     C.n = n;
     C.m = B.m;
@@ -904,7 +957,7 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
     k_sg_ub<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, ub.p);
     CK_LAUNCH();
     if (n <= kSgSmallRows) {
-        spgemm_small(A, B, C, ub.p, sc, s);
+        spgemm_small<VT>(A, av, B, bv, C, cv, ub.p, sc, s);
         return;
     }
     // symbolic: short rows per thread, the rest per warp (shared table), then global tables
@@ -956,11 +1009,11 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
     }
     C.nnz = scan_exclusive(C.rp.p, C.rp.p, n, sc, s);
     C.ci.alloc((size_t)C.nnz, s);
-    C.v.alloc((size_t)C.nnz, s);
+    cv.alloc((size_t)C.nnz, s);
     // numeric
     CK(cudaMemsetAsync(sc.flags.p + 8, 0, sizeof(int), s));
-    k_sg_local_num<<<gl, 128, 0, s>>>(n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, lcols.p, C.rp.p, C.ci.p, C.v.p,
-                                      sc.flags.p + 8);
+    k_sg_local_num<VT><<<gl, 128, 0, s>>>(n, A.rp, A.ci, av, B.rp, B.ci, bv, ub.p, lcols.p, C.rp.p, C.ci.p, cv.p,
+                                          sc.flags.p + 8);
     CK_LAUNCH();
     lcols.release();
     {
@@ -982,21 +1035,18 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
             const int nb = collect_flag(n, flag.p, rl, sc, s);
             if (!nb) continue;
             if (c == 0) {
-                k_sg_num<128><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, num_sms() * 32), SG_WARPS * 32,
-                                sizeof(double) * SG_WARPS * (128 + 64) + sizeof(int) * SG_WARPS * 128,
-                                s>>>(nb, rl.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
-                                     sc.flags.p + 8);
+                k_sg_num<128, VT><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, num_sms() * 32), SG_WARPS * 32,
+                                    sg_num_smem<128, VT>(), s>>>(nb, rl.p, A.rp, A.ci, av, B.rp, B.ci, bv, C.rp.p,
+                                                                 C.ci.p, cv.p, sc.flags.p + 8);
             } else if (c == 1) {
-                k_sg_num<SG_SMALL_T><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, num_sms() * 32), SG_WARPS * 32,
-                                       sizeof(double) * SG_WARPS * (SG_SMALL_T + 64) +
-                                           sizeof(int) * SG_WARPS * SG_SMALL_T,
-                                       s>>>(nb, rl.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
-                                            sc.flags.p + 8);
+                k_sg_num<SG_SMALL_T, VT><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, num_sms() * 32), SG_WARPS * 32,
+                                           sg_num_smem<SG_SMALL_T, VT>(), s>>>(nb, rl.p, A.rp, A.ci, av, B.rp, B.ci,
+                                                                               bv, C.rp.p, C.ci.p, cv.p,
+                                                                               sc.flags.p + 8);
             } else {
-                k_sg_num<SG_NUM_T><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, num_sms() * 8), SG_WARPS * 32,
-                                     sizeof(double) * SG_WARPS * (SG_NUM_T + 64) + sizeof(int) * SG_WARPS * SG_NUM_T,
-                                     s>>>(nb, rl.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
-                                          sc.flags.p + 8);
+                k_sg_num<SG_NUM_T, VT><<<grid_for((int64_t)nb * 32, SG_WARPS * 32, num_sms() * 8), SG_WARPS * 32,
+                                         sg_num_smem<SG_NUM_T, VT>(), s>>>(nb, rl.p, A.rp, A.ci, av, B.rp, B.ci, bv,
+                                                                           C.rp.p, C.ci.p, cv.p, sc.flags.p + 8);
             }
             CK_LAUNCH();
         }
@@ -1007,9 +1057,9 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
                 DBuf<long long> toff;
                 long long tot = big_tables(nb2, rows2.p, cnt.p, toff, s);
                 DBuf<int> gk((size_t)tot, s);
-                DBuf<double> gv((size_t)tot, s);
-                k_sg_num_big<<<grid_for((int64_t)nb2 * 32, 256), 256, 0, s>>>(
-                    nb2, rows2.p, toff.p, gk.p, gv.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp.p, C.ci.p, C.v.p,
+                DBuf<VT> gv((size_t)tot, s);
+                k_sg_num_big<VT><<<grid_for((int64_t)nb2 * 32, 256), 256, 0, s>>>(
+                    nb2, rows2.p, toff.p, gk.p, gv.p, A.rp, A.ci, av, B.rp, B.ci, bv, C.rp.p, C.ci.p, cv.p,
                     sc.flags.p + 8);
                 CK_LAUNCH();
             }
@@ -1018,6 +1068,10 @@ static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cud
     CK(cudaMemcpyAsync(sc.h_flags + 8, sc.flags.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (sc.h_flags[8]) throw Error(BGS_INTERNAL, "SpGEMM numeric count differs from the symbolic count");
+}
+
+static void spgemm(const CsrView &A, const CsrView &B, DCsr &C, Scratch &sc, cudaStream_t s) {
+    spgemm_t<double>(A, A.v, B, B.v, C, C.v, sc, s);
 }
 
 // ==========================================================================================
@@ -1458,8 +1512,10 @@ static void set_attributes() {
     std::call_once(attrs, [] {
         CK(cudaFuncSetAttribute(k_sg_sym<SG_SYM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(int) * SG_WARPS * SG_SYM_T)));
-        CK(cudaFuncSetAttribute(k_sg_num<SG_NUM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(double) * SG_WARPS * (SG_NUM_T + 64) + sizeof(int) * SG_WARPS * SG_NUM_T)));
+        CK(cudaFuncSetAttribute(k_sg_num<SG_NUM_T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                sg_num_smem<SG_NUM_T, double>()));
+        CK(cudaFuncSetAttribute(k_sg_num<SG_NUM_T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                sg_num_smem<SG_NUM_T, float>()));
         CK(cudaFuncSetAttribute(k_gjb_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(float) * GJB_MAXN * GJB_R)));
     });
@@ -1527,10 +1583,30 @@ static void level_numeric(Hier &H, int l, const AmgParams &p, Scratch &sc, cudaS
     tr.mark("prolongator", l, P.nnz);
     transpose_csr(view(P), R, sc, s);
     tr.mark("transpose", l, R.nnz);
-    spgemm(view(A), view(P), AP, sc, s);
-    tr.mark("spgemm AP", l, AP.nnz);
-    spgemm(view(R), view(AP), Ac, sc, s);
-    tr.mark("spgemm R(AP)", l, Ac.nnz);
+    if (p.fp32_galerkin) {
+        // the FP32 hierarchy's operator: A P and R (A P) in FP32 arithmetic from FP32 copies of A_l
+        // (kept from the previous level's product, or converted on the finest level), P_l and R_l
+        // (the copies the FP32 solve uses); A_l+1 keeps the FP32 product and its FP64 widening
+        if (A.vf.n != (size_t)A.nnz) {
+            A.vf.alloc((size_t)A.nnz, s);
+            convert_d2f(A.v.p, A.vf.p, A.nnz, s);
+        }
+        P.vf.alloc((size_t)P.nnz, s);
+        convert_d2f(P.v.p, P.vf.p, P.nnz, s);
+        R.vf.alloc((size_t)R.nnz, s);
+        convert_d2f(R.v.p, R.vf.p, R.nnz, s);
+        spgemm_t<float>(view(A), A.vf.p, view(P), P.vf.p, AP, AP.vf, sc, s);
+        tr.mark("spgemm AP", l, AP.nnz);
+        spgemm_t<float>(view(R), R.vf.p, view(AP), AP.vf.p, Ac, Ac.vf, sc, s);
+        Ac.v.alloc((size_t)Ac.nnz, s);
+        copy_f2d(Ac.vf.p, Ac.v.p, Ac.nnz, s);
+        tr.mark("spgemm R(AP)", l, Ac.nnz);
+    } else {
+        spgemm(view(A), view(P), AP, sc, s);
+        tr.mark("spgemm AP", l, AP.nnz);
+        spgemm(view(R), view(AP), Ac, sc, s);
+        tr.mark("spgemm R(AP)", l, Ac.nnz);
+    }
     Lv.omega = omega;
     if (update) {
         take_values(Lv.P, P, sc, s);
@@ -1543,9 +1619,44 @@ static void level_numeric(Hier &H, int l, const AmgParams &p, Scratch &sc, cudaS
     }
 }
 
+// Chebyshev power iterations started early: level l's estimate is enqueued on the scratch's side
+// stream as soon as A_l is final (and known not to be the coarsest), so it overlaps the coarsening
+// of the levels below it; the results are read back once, at the end of the build.  The same
+// kernels in the same order as power_lambda, so the same estimates.
+struct EarlyCheb {
+    std::vector<int> levels;   // levels whose estimate is enqueued
+    DBuf<double> partial;      // dot partials of the side stream
+    DBuf<double> out;          // 4 doubles per level (power_enqueue's out)
+};
+
+static void cheb_power_early(Hier &H, int l, const AmgParams &p, Scratch &sc, cudaStream_t s, EarlyCheb &ec) {
+    Level &Lv = H.L[l];
+    const int n = Lv.A.n;
+    cudaStream_t side = sc.side;
+    CK(cudaEventRecord(sc.fork, s));
+    CK(cudaStreamWaitEvent(side, sc.fork, 0));
+    DBuf<double> diag((size_t)n, side);
+    extract_diag(view(Lv.A), diag.p, side);
+    Lv.dinv.alloc((size_t)n, side);
+    reciprocal(diag.p, Lv.dinv.p, n, side);
+    power_enqueue(Lv.A, Lv.dinv.p, p.power_iters, ec.partial.p, ec.out.p + 4 * l, side);
+    ec.levels.push_back(l);
+}
+
+static void set_cheb_bounds(Level &Lv, double lam, const AmgParams &p, Scratch &sc, cudaStream_t s) {
+    Lv.lmax = p.cheb_boost * lam;
+    Lv.lmin = Lv.lmax / p.cheb_ratio;
+    Lv.lim = p.cheb_ellipse ? p.cheb_boost * skew_radius(Lv.A, p.power_iters, sc, s) : 0.0;
+    // below 1e-10 of lmax the skew part is rounding noise (e.g. a Galerkin product of a symmetric
+    // operator summed in two orders): keep the real interval
+    if (Lv.lim <= 1e-10 * Lv.lmax) Lv.lim = 0.0;
+}
+
 // Chebyshev bounds on every level above the coarsest and the coarsest dense inverse; the inverse
-// runs on the scratch's side stream while the power iterations run on s.
-static void smoothers_and_inverse(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s, Trace &tr) {
+// runs on the scratch's side stream (after the early estimates queued there, if any) while the
+// remaining power iterations run on s.
+static void smoothers_and_inverse(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s, Trace &tr,
+                                  EarlyCheb *ec) {
     H.nc = H.L.back().A.n;
     if (H.nc > 16384) throw Error(BGS_INTERNAL, "coarsest level too large for the dense direct solve");
     H.inv.alloc((size_t)H.nc * H.nc, s);
@@ -1553,23 +1664,30 @@ static void smoothers_and_inverse(Hier &H, const AmgParams &p, Scratch &sc, cuda
     CK(cudaEventRecord(sc.fork, s));
     CK(cudaStreamWaitEvent(sc.side, sc.fork, 0));
     dense_inverse_async(H.L.back().A, H.inv.p, sc, sc.side);
+    std::vector<char> early(H.L.size(), 0);
+    if (ec)
+        for (int l : ec->levels) early[(size_t)l] = 1;
     for (size_t k = 0; k + 1 < H.L.size(); k++) {
+        if (early[k]) continue;
         Level &Lv = H.L[k];
         const int n = Lv.A.n;
         DBuf<double> diag((size_t)n, s);
         extract_diag(view(Lv.A), diag.p, s);
         if (Lv.dinv.n != (size_t)n) Lv.dinv.alloc((size_t)n, s);
         reciprocal(diag.p, Lv.dinv.p, n, s);
-        const double lam = power_lambda(Lv.A, Lv.dinv.p, p.power_iters, sc, s);
-        Lv.lmax = p.cheb_boost * lam;
-        Lv.lmin = Lv.lmax / p.cheb_ratio;
-        Lv.lim = p.cheb_ellipse ? p.cheb_boost * skew_radius(Lv.A, p.power_iters, sc, s) : 0.0;
-        // below 1e-10 of lmax the skew part is rounding noise (e.g. a Galerkin product of a
-        // symmetric operator summed in two orders): keep the real interval
-        if (Lv.lim <= 1e-10 * Lv.lmax) Lv.lim = 0.0;
+        set_cheb_bounds(Lv, power_lambda(Lv.A, Lv.dinv.p, p.power_iters, sc, s), p, sc, s);
         tr.mark("power(cheb)", (int)k, n);
     }
     CK(cudaStreamSynchronize(sc.side));
+    if (ec && !ec->levels.empty()) {
+        std::vector<double> h(ec->out.n);
+        CK(cudaMemcpy(h.data(), ec->out.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+        for (int l : ec->levels) {
+            if (l + 1 >= (int)H.L.size()) continue;   // cannot happen: enqueued levels are not the coarsest
+            set_cheb_bounds(H.L[(size_t)l], power_estimate(h[4 * (size_t)l], h[4 * (size_t)l + 2]), p, sc, s);
+            tr.mark("power(cheb)", l, H.L[(size_t)l].A.n);
+        }
+    }
     // the inverse is used on s from here on
     CK(cudaEventRecord(sc.fork, sc.side));
     CK(cudaStreamWaitEvent(s, sc.fork, 0));
@@ -1583,6 +1701,15 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
     H.L.reserve(kMaxLevels + 1);
     const double t2 = p.theta * p.theta;
     Trace tr(s);
+    sc.ensure_side();
+    EarlyCheb ec;
+    ec.partial.alloc((size_t)num_sms() * 4, s);
+    ec.out.alloc(4 * (size_t)(kMaxLevels + 1), s);
+    // on every exit (an exception included), the side stream's work ends before ec's buffers go
+    struct SideJoin {
+        cudaStream_t st;
+        ~SideJoin() { cudaStreamSynchronize(st); }
+    } join{sc.side};
     for (int l = 0;; l++) {
         const int n = H.L[l].A.n;
         if (n <= p.max_coarse || l + 1 >= std::min(p.max_levels, kMaxLevels)) break;
@@ -1618,6 +1745,7 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
         }
         if ((long long)nagg * 10 > (long long)n * 9) break;   // coarsening stalled
         H.L.emplace_back();
+        cheb_power_early(H, l, p, sc, s, ec);   // level l is not the coarsest: its smoother's estimate
         Level &Lv = H.L[l];
         Lv.strong = std::move(strong);   // kept for the numeric re-set-up
         Lv.agg = std::move(agg);
@@ -1625,7 +1753,7 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
         Lv.mis_rounds = rounds;
         level_numeric(H, l, p, sc, s, tr, false);
     }
-    smoothers_and_inverse(H, p, sc, s, tr);
+    smoothers_and_inverse(H, p, sc, s, tr, &ec);
 }
 
 void amg_update(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
@@ -1633,7 +1761,7 @@ void amg_update(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
     Trace tr(s);
     CK(cudaMemsetAsync(sc.flags.p + 10, 0, sizeof(int), s));
     for (int l = 0; l + 1 < (int)H.L.size(); l++) level_numeric(H, l, p, sc, s, tr, true);
-    smoothers_and_inverse(H, p, sc, s, tr);
+    smoothers_and_inverse(H, p, sc, s, tr, nullptr);
     CK(cudaMemcpyAsync(sc.h_flags + 10, sc.flags.p + 10, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (sc.h_flags[10]) throw Error(BGS_INTERNAL, "numeric re-set-up produced a different operator pattern");

@@ -218,16 +218,38 @@ void cheb_coefs(const Level &Lv, int deg, double &inv_theta, double *alpha, doub
     }
 }
 
+// The first Chebyshev step of level l's pre-smoothing (of the diagonal solve for subsolver 2), to be
+// fused into the product that writes the level's right-hand side; false where there is none (the
+// coarsest level's dense solve, the DD(0)-ILU(0) sweep).  inv_theta is computed as cheb_coefs does.
+template <class XT>
+bool first_step_of(Hier &H, int l, FirstStep<XT> &f) {
+    if (H.solver == 1 || (H.solver == 2 && l != 0)) return false;
+    Level &Lv = H.L[l];
+    double inv_theta = 1.0;
+    if (H.solver == 0) {
+        if (l >= (int)H.L.size() - 1) return false;
+        const double theta = (Lv.lmax + Lv.lmin) / 2.0;
+        inv_theta = 1.0 / theta;
+    }
+    f = FirstStep<XT>{Buf<XT>::dinv(Lv), Buf<XT>::x0(Lv), Buf<XT>::d(Lv), inv_theta};
+    return true;
+}
+
+// One V-cycle on level l from x = 0.  first_done: the first pre-smoothing step was fused into the
+// product that wrote b (first_step_of).  out (finest level only, may be null): where the last
+// post-smoothing step writes, instead of the level's own x buffers.
 template <class VT, class XT>
-XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
+XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed, bool first_done = false, XT *out = nullptr) {
     cudaStream_t s = h->s;
     Level &Lv = H.L[l];
     const int n = Lv.A.n;
     XT *b = Buf<XT>::b(Lv), *x0 = Buf<XT>::x0(Lv), *x1 = Buf<XT>::x1(Lv), *d = Buf<XT>::d(Lv),
        *r = Buf<XT>::r(Lv);
+    if (l != 0) out = nullptr;
     if (l == (int)H.L.size() - 1) {
-        dense_gemv<XT>(n, transposed ? H.inv_T().p : H.inv.p, b, x0, s);
-        return x0;
+        XT *dst = out ? out : x0;
+        dense_gemv<XT>(n, transposed ? H.inv_T().p : H.inv.p, b, dst, s);
+        return dst;
     }
     const DCsr &A = transposed ? Lv.AT : Lv.A;
     const XT *dinv = Buf<XT>::dinv(Lv);
@@ -239,40 +261,44 @@ XT *vcycle(bgs_ctx *h, Hier &H, int l, bool transposed) {
     const double cbytes = spmv_bytes(A, vb, xb, 4);
     const int ccls = l == 0 ? 1 : 4;   // fine-level vs coarse-level Chebyshev steps
     // pre-smoothing from x = 0
-    cheb_first<XT>(n, b, dinv, inv_theta, x0, d, s);
+    if (!first_done) cheb_first<XT>(n, b, dinv, inv_theta, x0, d, s);
     XT *cur = x0, *oth = x1;
     for (int k = 1; k < deg; k++) {
         Prof pf(h, ccls, cbytes);
         cheb_step<VT, XT>(A, b, dinv, cur, oth, d, alpha[k - 1], scale[k - 1], false, s);
         std::swap(cur, oth);
     }
-    // residual, restriction, coarse correction, prolongation
+    // residual, restriction (with the coarse level's first smoothing step), coarse correction,
+    // prolongation
     spmv_resid<VT, XT>(A, b, cur, r, s);
     Level &C = H.L[l + 1];
-    spmv_store<VT, XT>(Lv.R, r, Buf<XT>::b(C), s);
-    XT *xc = vcycle<VT, XT>(h, H, l + 1, transposed);
+    FirstStep<XT> fc;
+    const bool fuse = first_step_of<XT>(H, l + 1, fc);
+    if (fuse) spmv_store_first<VT, XT>(Lv.R, r, Buf<XT>::b(C), fc, s);
+    else spmv_store<VT, XT>(Lv.R, r, Buf<XT>::b(C), s);
+    XT *xc = vcycle<VT, XT>(h, H, l + 1, transposed, fuse);
     spmv_addto<VT, XT>(Lv.P, xc, cur, s);
-    // post-smoothing
-    {
+    // post-smoothing (the first step with alpha = 0 from the corrected x)
+    for (int k = 0; k < deg; k++) {
+        XT *dst = (out && k == deg - 1) ? out : oth;
         Prof pf(h, ccls, cbytes);
-        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, 0.0, inv_theta, true, s);
-    }
-    std::swap(cur, oth);
-    for (int k = 1; k < deg; k++) {
-        Prof pf(h, ccls, cbytes);
-        cheb_step<VT, XT>(A, b, dinv, cur, oth, d, alpha[k - 1], scale[k - 1], false, s);
-        std::swap(cur, oth);
+        if (k == 0) cheb_step<VT, XT>(A, b, dinv, cur, dst, d, 0.0, inv_theta, true, s);
+        else cheb_step<VT, XT>(A, b, dinv, cur, dst, d, alpha[k - 1], scale[k - 1], false, s);
+        oth = cur;
+        cur = dst;
     }
     return cur;
 }
 
 // The block solve of one diagonal block on L[0].b: one V-cycle, the DD(0)-ILU(0) sweep, or the
-// diagonal solve x = D^-1 b (its own transpose).
+// diagonal solve x = D^-1 b (its own transpose).  first_done and out as for vcycle (first_done:
+// the first step of first_step_of(H, 0) has run).
 template <class VT, class XT>
-XT *block_solve(bgs_ctx *h, Hier &H, bool transposed) {
+XT *block_solve(bgs_ctx *h, Hier &H, bool transposed, bool first_done = false, XT *out = nullptr) {
     if (H.solver == 2) {
         Level &L0 = H.L[0];
-        cheb_first<XT>(L0.A.n, Buf<XT>::b(L0), Buf<XT>::dinv(L0), 1.0, Buf<XT>::x0(L0), Buf<XT>::d(L0), h->s);
+        if (!first_done)
+            cheb_first<XT>(L0.A.n, Buf<XT>::b(L0), Buf<XT>::dinv(L0), 1.0, Buf<XT>::x0(L0), Buf<XT>::d(L0), h->s);
         return Buf<XT>::x0(L0);
     }
     if (H.solver == 1) {
@@ -283,7 +309,7 @@ XT *block_solve(bgs_ctx *h, Hier &H, bool transposed) {
         ilu_apply<XT>(M, transposed, Buf<XT>::b(L0), Buf<XT>::x0(L0), h->s);
         return Buf<XT>::x0(L0);
     }
-    return vcycle<VT, XT>(h, H, 0, transposed);
+    return vcycle<VT, XT>(h, H, 0, transposed, first_done, out);
 }
 
 template <class XT>
@@ -321,9 +347,14 @@ void jacobi_sweep(bgs_ctx *h, const double *v, double *z, bool transposed) {
         h->s = sk;
         try {
             Hier &H = h->H[k];
-            copy_in<XT>(v + h->offs[k], Buf<XT>::b(H.L[0]), h->sizes[k], sk);
-            XT *xk = block_solve<VT, XT>(h, H, transposed);
-            copy_out<XT>(xk, z + h->offs[k], h->sizes[k], sk);
+            FirstStep<XT> f0;
+            const bool fuse0 = first_step_of<XT>(H, 0, f0);
+            if (fuse0) copy_in_first<XT>(v + h->offs[k], Buf<XT>::b(H.L[0]), h->sizes[k], f0, sk);
+            else copy_in<XT>(v + h->offs[k], Buf<XT>::b(H.L[0]), h->sizes[k], sk);
+            XT *out = nullptr;
+            if constexpr (std::is_same<XT, double>::value) out = z + h->offs[k];
+            XT *xk = block_solve<VT, XT>(h, H, transposed, fuse0, out);
+            if (xk != out) copy_out<XT>(xk, z + h->offs[k], h->sizes[k], sk);
         } catch (...) {
             h->s = s;
             throw;
@@ -354,23 +385,36 @@ void sweep(bgs_ctx *h, const double *v, double *z, bool transposed) {
         const int64_t nk = h->sizes[k];
         XT *b0 = Buf<XT>::b(L0);
         const DCsr &C = transposed ? h->upperT[k] : h->lower[k];
+        // the block's right-hand side with the first step of its solve fused in
+        FirstStep<XT> f0;
+        const bool fuse0 = first_step_of<XT>(H, 0, f0);
         if (C.nnz > 0) {
-            Prof pf(h, 3, spmv_bytes(C, sizeof(CVT), zf ? 4 : 8, 1));
+            Prof pf(h, 3, spmv_bytes(C, sizeof(CVT), zf ? 4 : 8, 1) + (fuse0 ? 3.0 * sizeof(XT) * nk : 0.0));
             if constexpr (std::is_same<XT, float>::value) {
-                if (zf) coupling_sub<CVT, XT, float>(C, v + h->offs[k], zf, b0, s);
-                else coupling_sub<CVT, XT, double>(C, v + h->offs[k], z, b0, s);
+                if (zf) {
+                    if (fuse0) coupling_sub_first<CVT, XT, float>(C, v + h->offs[k], zf, b0, f0, s);
+                    else coupling_sub<CVT, XT, float>(C, v + h->offs[k], zf, b0, s);
+                } else {
+                    if (fuse0) coupling_sub_first<CVT, XT, double>(C, v + h->offs[k], z, b0, f0, s);
+                    else coupling_sub<CVT, XT, double>(C, v + h->offs[k], z, b0, s);
+                }
             } else {
-                coupling_sub<CVT, XT, double>(C, v + h->offs[k], z, b0, s);
+                if (fuse0) coupling_sub_first<CVT, XT, double>(C, v + h->offs[k], z, b0, f0, s);
+                else coupling_sub<CVT, XT, double>(C, v + h->offs[k], z, b0, s);
             }
         } else {
-            copy_in<XT>(v + h->offs[k], b0, nk, s);
+            if (fuse0) copy_in_first<XT>(v + h->offs[k], b0, nk, f0, s);
+            else copy_in<XT>(v + h->offs[k], b0, nk, s);
         }
-        XT *xk = block_solve<VT, XT>(h, H, transposed);
+        // FP64: the last smoothing step writes the block's part of z itself
+        XT *out = nullptr;
+        if constexpr (std::is_same<XT, double>::value) out = z + h->offs[k];
+        XT *xk = block_solve<VT, XT>(h, H, transposed, fuse0, out);
         if constexpr (std::is_same<XT, float>::value) {
             if (zf) copy_f2d_keep(xk, z + h->offs[k], zf + h->offs[k], nk, s);
             else copy_out<XT>(xk, z + h->offs[k], nk, s);
         } else {
-            copy_out<XT>(xk, z + h->offs[k], nk, s);
+            if (xk != out) copy_out<XT>(xk, z + h->offs[k], nk, s);
         }
     }
 }
@@ -737,9 +781,10 @@ double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// BGS_TRACE=1: wall time of the phases of bgs_create (stream synchronised at each mark)
+// BGS_TRACE set (not "async"): wall time of the phases of bgs_create (stream synchronised at each
+// mark)
 struct CreateTrace {
-    bool on = getenv("BGS_TRACE") != nullptr;
+    bool on = getenv("BGS_TRACE") != nullptr && strcmp(getenv("BGS_TRACE"), "async") != 0;
     cudaStream_t s;
     double t;
     explicit CreateTrace(cudaStream_t st) : s(st) {
@@ -941,7 +986,7 @@ void build_adjoint(bgs_ctx *h) {
 AmgParams params_for(const bgs_ctx *h, int k) {
     return AmgParams{h->opt.theta[k], h->opt.cheb_degree[k], h->opt.max_coarse, h->opt.max_levels,
                      h->opt.power_iters, h->opt.filter_diag, h->opt.cheb_ratio, h->opt.cheb_boost,
-                     h->opt.cheb_ellipse};
+                     h->opt.cheb_ellipse, h->opt.precision == 1 ? 1 : 0};
 }
 
 // Runs fn(k, stream, scratch) for every diagonal block: the hierarchies are independent, so
@@ -1206,6 +1251,7 @@ void build_block(bgs_ctx *h, int k, cudaStream_t sk, Scratch &sck) {
         return;
     }
     amg_build(H, params_for(h, k), sck, sk);
+    timeline_mark("hierarchy built", sk);
     if (H.status) throw Error(H.status, "coarsest-level factorisation");
     // the SpMV layouts of the level operators (the diagonal-offset form for the level-0 stencil
     // operator only, whose offsets repeat); only the autotuner's cached choice when it has one
@@ -1218,8 +1264,10 @@ void build_block(bgs_ctx *h, int k, cudaStream_t sk, Scratch &sck) {
             Buf<float>::alloc(Lv, Lv.A.n, sk);
             if (l + 1 < H.L.size()) {
                 for (DCsr *M : {&Lv.A, &Lv.P, &Lv.R}) {
-                    M->vf.alloc((size_t)M->nnz, sk);
-                    convert_d2f(M->v.p, M->vf.p, M->nnz, sk);
+                    if (M->vf.n != (size_t)M->nnz) {   // the FP32 Galerkin products made most already
+                        M->vf.alloc((size_t)M->nnz, sk);
+                        convert_d2f(M->v.p, M->vf.p, M->nnz, sk);
+                    }
                     sell_refresh(*M, sk);
                 }
                 Lv.dinvf.alloc((size_t)Lv.A.n, sk);
@@ -1230,6 +1278,7 @@ void build_block(bgs_ctx *h, int k, cudaStream_t sk, Scratch &sck) {
         }
     }
     CK(cudaStreamSynchronize(sk));
+    timeline_mark("block done", sk);
 }
 
 }  // namespace
@@ -1243,6 +1292,7 @@ extern "C" int bgs_setup(bgs_handle h) {
         const bool mixed = h->opt.precision == 1;
         const int st = run_per_block(h, [&](int k, cudaStream_t sk, Scratch &sck) { build_block(h, k, sk, sck); });
         if (st) return st;
+        timeline_mark("all blocks built", s);
         // kernel choice by timing runs alone, after the concurrent build
         for (int k = 0; k < h->F; k++)
             if (mixed && h->lower[k].nnz) {
@@ -1268,6 +1318,7 @@ extern "C" int bgs_setup(bgs_handle h) {
         CK(cudaStreamSynchronize(s));
         h->t_setup_ms = now_ms() - t0;
         h->setup_done = true;
+        timeline_mark("setup done", s);
         return BGS_OK;
     });
 }

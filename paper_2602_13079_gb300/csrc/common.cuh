@@ -114,8 +114,9 @@ struct DCsr {
     // the structured operators (stencil blocks, the full operator), where the offsets repeat.
     bool dia = false;
     int64_t dia_nnz = 0;            // value slots (32 per slice and offset)
-    DBuf<int> dptr, doff, dperm;    // slot start per slice (multiple of 32); offsets at dptr[s]/32 + k;
-                                    // CSR index of each slot (-1: padding)
+    int dia_wmax = 0;               // the widest slice's offset count (the stride of doff)
+    DBuf<int> dptr, doff, dperm;    // slot start per slice (multiple of 32); offset k of slice s at
+                                    // doff[s * dia_wmax + k]; CSR index of each slot (-1: padding)
     DBuf<double> dv;
     DBuf<float> dvf;
     DBuf<__nv_bfloat16> dvb;

@@ -52,6 +52,10 @@ long long scan_ll_inplace(long long *a, int n, cudaStream_t s);
 void dev_dot(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s);
 // the same, and out[1] = 1/sqrt(out[0]) (0 when out[0] is 0)
 void dev_dot_rsqrt(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s);
+// both with a caller's partial-sum buffer (num_sms() * 4 doubles) instead of the scratch's, for a
+// second stream
+void dev_dot(const double *a, const double *b, int64_t n, double *out, double *partial, cudaStream_t s);
+void dev_dot_rsqrt(const double *a, const double *b, int64_t n, double *out, double *partial, cudaStream_t s);
 void dev_fill_int(int *p, int value, int64_t n, cudaStream_t s);
 void dev_fill_double(double *p, double value, int64_t n, cudaStream_t s);
 // Validation of one CSR (device arrays); returns 0 or BGS_INVALID_ARG.  Checks monotone rowptr,
@@ -96,6 +100,23 @@ void cheb_first(int n, const XT *b, const XT *dinv, double inv_theta, XT *x, XT 
 // r = v - L z (L with global columns into z), v FP64, z FP64 or its FP32 copy, output typed
 template <class VT, class XT, class ZT>
 void coupling_sub(const DCsr &L, const double *v, const ZT *z, XT *r, cudaStream_t s);
+// The same products with the first Chebyshev step from x = 0 of the level they write the right-hand
+// side of fused into the epilogue (e = D^-1 b, x = e / theta): the restriction y = R r onto a level,
+// the coupling subtraction onto a block's finest level, and a plain copy b = v for a block without
+// couplings.
+template <class XT>
+struct FirstStep {
+    const XT *dinv;   // the level's D^-1
+    XT *x, *e;        // the step's outputs
+    double inv_theta;
+};
+template <class VT, class XT>
+void spmv_store_first(const DCsr &A, const XT *x, XT *y, const FirstStep<XT> &f, cudaStream_t s);
+template <class VT, class XT, class ZT>
+void coupling_sub_first(const DCsr &L, const double *v, const ZT *z, XT *r, const FirstStep<XT> &f,
+                        cudaStream_t s);
+template <class XT>
+void copy_in_first(const double *v, XT *b, int64_t n, const FirstStep<XT> &f, cudaStream_t s);
 // w_i = dinv_i * (A v)_i (FP64, power iteration)
 void spmv_scaled(const CsrView &A, const double *dinv, const double *v, double *w, cudaStream_t s);
 // w_i = dinv_i * (A v)_i * (*rnorm), rnorm = 1/||v|| on the device (power iteration step on a
@@ -123,6 +144,8 @@ void refresh_values(DCsr &A, cudaStream_t s);
 // (diagonal-offset SELL), 0 (SELL-32) or the lane count.  value_bytes selects the precision timed
 // (8 FP64, 4 FP32 hierarchy, 2 BF16 couplings).
 // product: time y = A x instead of the Chebyshev step (an operator only ever applied as a product).
+// BGS_TRACE=async: one timeline line (host clock since the first mark, stream) to stderr
+void timeline_mark(const char *what, cudaStream_t s);
 int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s, bool product = false);
 // Builds the SpMV layouts an operator may run: the one the autotuner's cached choice for its shape
 // names (use_cache), else SELL-32 and, with allow_dia, the diagonal-offset SELL-32 for the
@@ -227,6 +250,7 @@ struct AmgParams {
     int degree, max_coarse, max_levels, power_iters, filter_diag;
     double cheb_ratio, cheb_boost;
     int cheb_ellipse;
+    int fp32_galerkin;   // mixed precision: A P and R (A P) in FP32 from FP32 copies of A_l, P_l, R_l
 };
 
 constexpr int kMaxLevels = 16;

@@ -68,7 +68,22 @@ __global__ void __launch_bounds__(TPB) k_sell(int n, const int *__restrict__ spt
         if (row < n) epi(row, acc);
         return;
     }
+    // FP64: batches of 8 slots (all index and value loads, then all gathers, in flight together:
+    // the long rows of the coarse levels wait on fewer dependent rounds), then of 4, then single
     int j = 0;
+#pragma unroll 1
+    for (; j + 8 <= w; j += 8) {
+        int cc[8];
+        AT a[8], xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) { cc[u] = __ldg(c + u * 32); a[u] = Cvt<AT>::f(ldg(v + u * 32)); }
+#pragma unroll
+        for (int u = 0; u < 8; u++) xv[u] = Cvt<AT>::f(ldg(x + cc[u]));
+#pragma unroll
+        for (int u = 0; u < 8; u++) acc = mac<S>(acc, a[u], xv[u]);
+        c += 8 * 32;
+        v += 8 * 32;
+    }
 #pragma unroll 1
     for (; j + 4 <= w; j += 4) {
         const int c0 = __ldg(c + 0 * 32), c1 = __ldg(c + 1 * 32), c2 = __ldg(c + 2 * 32), c3 = __ldg(c + 3 * 32);
@@ -90,27 +105,32 @@ __global__ void __launch_bounds__(TPB) k_sell(int n, const int *__restrict__ spt
 }
 
 // ------------------------------------------------------------------------------------------ SELL-32, diagonal offsets
-// Slice of 32 rows per warp; lane k holds the slice's k-th offset (w <= 32), broadcast by shuffle.
-// A padded slot's column is clamped into [0, m) (its value is 0).
+// Slice of 32 rows per warp; lane k holds the slice's k-th offset (w <= wmax <= 32), broadcast by
+// shuffle.  The offsets sit at a fixed stride of wmax per slice, so their load does not wait for the
+// slice's slot pointer: a warp's loads take two dependent rounds (pointers, offsets and the start
+// value; then values and x), not three.  A padded slot's column is clamped into [0, m) (its value
+// is 0).
 template <class VT, class XT, class AT, class Epi, int TPB>
-__global__ void __launch_bounds__(TPB) k_dia(int n, int m, const int *__restrict__ dptr, const int *__restrict__ doff,
-                                             const VT *__restrict__ dv, const XT *__restrict__ x, Epi epi) {
+__global__ void __launch_bounds__(TPB) k_dia(int n, int m, int wmax, const int *__restrict__ dptr,
+                                             const int *__restrict__ doff, const VT *__restrict__ dv,
+                                             const XT *__restrict__ x, Epi epi) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     const int slice = row >> 5;
     if ((slice << 5) >= n) return;          // whole warp past the end
     const int lane = row & 31;
     const int s0 = __ldg(dptr + slice);
     const int w = (__ldg(dptr + slice + 1) - s0) >> 5;
-    const int myo = lane < w ? __ldg(doff + (s0 >> 5) + lane) : 0;
+    const int myo = lane < wmax ? __ldg(doff + (int64_t)slice * wmax + lane) : 0;
     const VT *v = dv + s0 + lane;
     const int last = m - 1;
     constexpr bool S = Epi::kSub;
     AT acc = row < n ? epi.template start<AT>(row) : (AT)0;
     if constexpr (sizeof(AT) == 4 && sizeof(VT) == 4) {
-        // FP32: batches of 8 slots, all loads of a batch in flight together; a slot past the slice
+        // FP32: batches of 4 slots, all loads of a batch in flight together; a slot past the slice
         // width re-reads the last one (a cached duplicate) and its product is skipped (w is
-        // warp-uniform)
-        constexpr int U = 8;
+        // warp-uniform).  Batches of 8 took 40 registers (48 warps per SM) against 32 (64 warps)
+        // and timed 3% slower in the solve.
+        constexpr int U = 4;
 #pragma unroll 1
         for (int k = 0; k < w; k += U) {
             AT a[U], xv[U];
@@ -251,7 +271,8 @@ static int lanes_of(const DCsr &A) { return A.lanes ? A.lanes : choose_lanes(A.n
 template <class VT, class XT, class AT, class Epi, int TPB>
 static void launch_sliced(const DCsr &A, const XT *x, Epi epi, cudaStream_t s) {
     const int g = (int)(((int64_t)A.n + TPB - 1) / TPB);
-    if (A.dia) k_dia<VT, XT, AT, Epi, TPB><<<g, TPB, 0, s>>>(A.n, A.m, A.dptr.p, A.doff.p, Vals<VT>::dia(A), x, epi);
+    if (A.dia)
+        k_dia<VT, XT, AT, Epi, TPB><<<g, TPB, 0, s>>>(A.n, A.m, A.dia_wmax, A.dptr.p, A.doff.p, Vals<VT>::dia(A), x, epi);
     else k_sell<VT, XT, AT, Epi, TPB><<<g, TPB, 0, s>>>(A.n, A.sptr.p, A.sci.p, Vals<VT>::sell(A), x, epi);
     CK_LAUNCH();
 }
@@ -342,6 +363,37 @@ void cheb_step(const DCsr &A, const XT *b, const XT *dinv, const XT *xin, XT *xo
 template <class VT, class XT, class ZT>
 void coupling_sub(const DCsr &L, const double *v, const ZT *z, XT *r, cudaStream_t s) {
     run<VT, ZT>(L, z, ESub<XT>{v, r}, s);
+}
+template <class VT, class XT>
+void spmv_store_first(const DCsr &A, const XT *x, XT *y, const FirstStep<XT> &f, cudaStream_t s) {
+    using CT = typename AccOf<XT>::T;
+    run<VT, XT>(A, x, EThenFirst<EStore<XT>, XT, CT>{EStore<XT>{y}, f.dinv, f.x, f.e, (CT)f.inv_theta}, s);
+}
+template <class VT, class XT, class ZT>
+void coupling_sub_first(const DCsr &L, const double *v, const ZT *z, XT *r, const FirstStep<XT> &f,
+                        cudaStream_t s) {
+    using CT = typename AccOf<XT>::T;
+    run<VT, ZT>(L, z, EThenFirst<ESub<XT>, XT, CT>{ESub<XT>{v, r}, f.dinv, f.x, f.e, (CT)f.inv_theta}, s);
+}
+// b = v (converted to XT) and the first Chebyshev step from it, for a block without couplings
+template <class XT>
+__global__ void k_copy_first(int64_t n, const double *__restrict__ v, XT *__restrict__ b, const XT *__restrict__ dinv,
+                             double inv_theta, XT *__restrict__ x, XT *__restrict__ e) {
+    using CT = typename AccOf<XT>::T;
+    const CT it = (CT)inv_theta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const XT bi = (XT)v[i];
+        b[i] = bi;
+        const CT t = (CT)dinv[i] * (CT)bi;
+        e[i] = (XT)t;
+        x[i] = (XT)(it * t);
+    }
+}
+template <class XT>
+void copy_in_first(const double *v, XT *b, int64_t n, const FirstStep<XT> &f, cudaStream_t s) {
+    if (n <= 0) return;
+    k_copy_first<XT><<<grid_for(n, 256, num_sms() * 32), 256, 0, s>>>(n, v, b, f.dinv, f.inv_theta, f.x, f.e);
+    CK_LAUNCH();
 }
 
 template <class XT>
@@ -463,7 +515,7 @@ __global__ void k_dia_width(int n, const int *rp, const int *ci, int *wslot) {
     }
     if ((row & 31) == 0) wslot[slice] = w > 32 ? -1 : w * 32;
 }
-__global__ void k_dia_fill(int n, const int *rp, const int *ci, const int *dptr, int *doff, int *dperm) {
+__global__ void k_dia_fill(int n, int wmax, const int *rp, const int *ci, const int *dptr, int *doff, int *dperm) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     const int slice = row >> 5;
     if ((slice << 5) >= n) return;
@@ -471,20 +523,31 @@ __global__ void k_dia_fill(int n, const int *rp, const int *ci, const int *dptr,
     const int s0 = dptr[slice];
     int p = row < n ? rp[row] : 0;
     const int e = row < n ? rp[row + 1] : 0;
-    for (int k = 0;; k++) {
+    int k = 0;
+    for (;; k++) {
         const int cand = p < e ? ci[p] - row : INT_MAX;
         const int mn = __reduce_min_sync(0xffffffffu, cand);
         if (mn == INT_MAX) break;
-        if (lane == 0) doff[(s0 >> 5) + k] = mn;
+        if (lane == 0) doff[(int64_t)slice * wmax + k] = mn;
         dperm[s0 + k * 32 + lane] = cand == mn ? p : -1;
         if (cand == mn) p++;
     }
+    if (lane == 0)
+        for (; k < wmax; k++) doff[(int64_t)slice * wmax + k] = 0;   // past the slice's width: unused
 }
-__global__ void k_min_int(int n, const int *a, int *out) {
-    int m = INT_MAX;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = min(m, a[i]);
-    m = __reduce_min_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0) atomicMin(out, m);
+// min and max of a[0..n) into out[0], out[1] (out preset to INT_MAX, INT_MIN)
+__global__ void k_minmax_int(int n, const int *a, int *out) {
+    int lo = INT_MAX, hi = INT_MIN;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        lo = min(lo, a[i]);
+        hi = max(hi, a[i]);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(out, lo);
+        atomicMax(out + 1, hi);
+    }
 }
 
 template <class T>
@@ -502,19 +565,22 @@ bool build_dia(DCsr &A, double max_pad, Scratch &sc, cudaStream_t s) {
     DBuf<int> dptr((size_t)nsl + 1, s);
     k_dia_width<<<g, 256, 0, s>>>(A.n, A.rp.p, A.ci.p, dptr.p);
     CK_LAUNCH();
-    dev_fill_int(sc.flags.p + 14, INT_MAX, 1, s);
-    k_min_int<<<grid_for(nsl, 256), 256, 0, s>>>(nsl, dptr.p, sc.flags.p + 14);
+    dev_fill_int(sc.flags.p + 16, INT_MAX, 1, s);
+    dev_fill_int(sc.flags.p + 17, INT_MIN, 1, s);
+    k_minmax_int<<<grid_for(nsl, 256), 256, 0, s>>>(nsl, dptr.p, sc.flags.p + 16);
     CK_LAUNCH();
-    CK(cudaMemcpyAsync(sc.h_flags + 14, sc.flags.p + 14, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(sc.h_flags + 16, sc.flags.p + 16, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (sc.h_flags[14] < 0) return false;                 // a slice with more than 32 offsets
+    if (sc.h_flags[16] < 0) return false;                 // a slice with more than 32 offsets
+    const int wmax = std::max(sc.h_flags[17] / 32, 1);
     const int64_t tot = scan_exclusive(dptr.p, dptr.p, nsl, sc, s);
     if ((double)tot > max_pad * (double)A.nnz) return false;
     A.dptr = std::move(dptr);
     A.dia_nnz = tot;
-    A.doff.alloc((size_t)(tot / 32), s);
+    A.dia_wmax = wmax;
+    A.doff.alloc((size_t)nsl * wmax, s);
     A.dperm.alloc((size_t)tot, s);
-    k_dia_fill<<<g, 256, 0, s>>>(A.n, A.rp.p, A.ci.p, A.dptr.p, A.doff.p, A.dperm.p);
+    k_dia_fill<<<g, 256, 0, s>>>(A.n, wmax, A.rp.p, A.ci.p, A.dptr.p, A.doff.p, A.dperm.p);
     CK_LAUNCH();
     gather_dia(A, A.v.p, A.dv, s);
     A.dia = true;
@@ -632,6 +698,7 @@ void drop_bsr(DCsr &A) {
 void drop_dia(DCsr &A) {
     A.dia = false;
     A.dia_nnz = 0;
+    A.dia_wmax = 0;
     A.dptr.release(); A.doff.release(); A.dperm.release(); A.dv.release(); A.dvf.release(); A.dvb.release();
 }
 
@@ -729,6 +796,7 @@ static Choice time_candidates(DCsr &A, bool product, cudaStream_t s) {
     float best = 1e30f;
     Choice choice;
     const bool had_sell = A.sell, had_dia = A.dia, had_bsr = A.bsr;
+    const bool log = getenv("BGS_AUTOTUNE_LOG") != nullptr;   // every candidate's time to stderr
     const int formats[9] = {-2, -1, 0, 1, 2, 4, 8, 16, 32};
     for (int f : formats) {
         if ((f == -2 && !(had_bsr && product && kBsrEpi<VT, XT, EStore<XT>>)) || (f == -1 && !had_dia) ||
@@ -751,6 +819,8 @@ static Choice time_candidates(DCsr &A, bool product, cudaStream_t s) {
                 CK(cudaEventElapsedTime(&ms, e0, e1));
                 if (rep) fastest = std::min(fastest, ms);
             }
+            if (log) fprintf(stderr, "bgs-autotune n %d m %d nnz %lld vbytes %d product %d format %d tpb %d ms %.5f\n",
+                             A.n, A.m, (long long)A.nnz, (int)sizeof(VT), product ? 1 : 0, f, tpb, fastest);
             if (fastest < best) {
                 best = fastest;
                 choice.format = f;
@@ -826,6 +896,9 @@ int autotune_spmv(DCsr &A, int value_bytes, Scratch &sc, cudaStream_t s, bool pr
 // explicit instantiations
 #define BGS_INST(VT, XT)                                                                                    \
     template void spmv_store<VT, XT>(const DCsr &, const XT *, XT *, cudaStream_t);                       \
+    template void spmv_store_first<VT, XT>(const DCsr &, const XT *, XT *, const FirstStep<XT> &,         \
+                                           cudaStream_t);                                                 \
+    template void copy_in_first<XT>(const double *, XT *, int64_t, const FirstStep<XT> &, cudaStream_t);  \
     template void spmv_resid<VT, XT>(const DCsr &, const XT *, const XT *, XT *, cudaStream_t);           \
     template void spmv_addto<VT, XT>(const DCsr &, const XT *, XT *, cudaStream_t);                       \
     template void cheb_step<VT, XT>(const DCsr &, const XT *, const XT *, const XT *, XT *, XT *, double, \
@@ -839,6 +912,12 @@ template void coupling_sub<__nv_bfloat16, float, double>(const DCsr &, const dou
                                                          cudaStream_t);
 template void coupling_sub<__nv_bfloat16, float, float>(const DCsr &, const double *, const float *, float *,
                                                         cudaStream_t);
+template void coupling_sub_first<double, double, double>(const DCsr &, const double *, const double *, double *,
+                                                         const FirstStep<double> &, cudaStream_t);
+template void coupling_sub_first<__nv_bfloat16, float, double>(const DCsr &, const double *, const double *,
+                                                               float *, const FirstStep<float> &, cudaStream_t);
+template void coupling_sub_first<__nv_bfloat16, float, float>(const DCsr &, const double *, const float *, float *,
+                                                              const FirstStep<float> &, cudaStream_t);
 template void cheb_first<double>(int, const double *, const double *, double, double *, double *, cudaStream_t);
 template void cheb_first<float>(int, const float *, const float *, double, float *, float *, cudaStream_t);
 template void dense_gemv<double>(int, const double *, const double *, double *, cudaStream_t);

@@ -105,6 +105,28 @@ struct ECheb {
     }
 };
 
+// The first Chebyshev step from x = 0 of the level whose right-hand side b a product writes (the
+// restriction onto a level, or the coupling subtraction onto a block's finest level), fused into
+// that product's epilogue: after the base epilogue stores b_i, e_i = D^-1_i b_i and
+// x_i = e_i / theta, from the stored (rounded) b_i as the separate first-step kernel computes them.
+template <class Base, class XT, class CT>
+struct EThenFirst {
+    Base base;
+    const XT *dinv;
+    XT *x, *e;
+    CT inv_theta;
+    static constexpr bool kSub = Base::kSub;
+    template <class AT>
+    __device__ AT start(int i) const { return base.template start<AT>(i); }
+    template <class AT>
+    __device__ void operator()(int i, AT s) const {
+        base(i, s);
+        const CT t = (CT)dinv[i] * (CT)(XT)s;
+        e[i] = (XT)t;
+        x[i] = (XT)(inv_theta * t);
+    }
+};
+
 template <class XT>
 struct AccOf { using T = double; };
 template <>

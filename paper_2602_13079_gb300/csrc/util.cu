@@ -316,20 +316,26 @@ __global__ void k_reduce_final_rsqrt(const double *part, int g, double *out) {
     }
 }
 
-void dev_dot_rsqrt(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s) {
+void dev_dot_rsqrt(const double *a, const double *b, int64_t n, double *out, double *partial, cudaStream_t s) {
     int g = grid_for(n, 256, num_sms() * 4);
-    k_dot_partial<<<g, 256, 0, s>>>(a, b, n, sc.partial.p);
+    k_dot_partial<<<g, 256, 0, s>>>(a, b, n, partial);
     CK_LAUNCH();
-    k_reduce_final_rsqrt<<<1, 256, 0, s>>>(sc.partial.p, g, out);
+    k_reduce_final_rsqrt<<<1, 256, 0, s>>>(partial, g, out);
     CK_LAUNCH();
 }
+void dev_dot_rsqrt(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s) {
+    dev_dot_rsqrt(a, b, n, out, sc.partial.p, s);
+}
 
-void dev_dot(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s) {
+void dev_dot(const double *a, const double *b, int64_t n, double *out, double *partial, cudaStream_t s) {
     int g = grid_for(n, 256, num_sms() * 4);
-    k_dot_partial<<<g, 256, 0, s>>>(a, b, n, sc.partial.p);
+    k_dot_partial<<<g, 256, 0, s>>>(a, b, n, partial);
     CK_LAUNCH();
-    k_reduce_final<<<1, 256, 0, s>>>(sc.partial.p, g, out);
+    k_reduce_final<<<1, 256, 0, s>>>(partial, g, out);
     CK_LAUNCH();
+}
+void dev_dot(const double *a, const double *b, int64_t n, double *out, Scratch &sc, cudaStream_t s) {
+    dev_dot(a, b, n, out, sc.partial.p, s);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -8,7 +8,13 @@ arithmetic (the same FP64 operations summed in another order): omega (1e-12), th
 The FP64 solve reaches a true relative residual of 1e-8 (checked on the host with the oracle's
 SpMV) with ||x - x_oracle|| / ||x_oracle|| <= 1e-6 and an iteration count within 2 of the
 oracle's; the mixed-precision solve (FP32 hierarchy, BF16 couplings, FP64 Krylov) meets the same
-residual and error bounds, and its error against the oracle is printed."""
+residual and error bounds, and its error against the oracle is printed.
+
+Mixed precision builds the coarse operators by FP32 Galerkin products, so from level 1 on its
+operators differ from the oracle's by FP32 rounding and a strength decision near the threshold can
+flip: level 0 (strength, MIS-2 rounds, aggregates, omega, P_0, R_0) stays bit-exact or within the
+FP64 tolerances, A_1 within FP32 summation error, and the count of nodes whose aggregate differs
+on each coarser level is printed and bounded."""
 import numpy as np
 import pytest
 
@@ -88,7 +94,55 @@ def test_c2_solve_matches_the_oracle(bgs, c2, ref, precision):
           f"||x - x_oracle|| / ||x_oracle|| = {err:.3e}")
     assert rel <= 1e-8
     assert err <= 1e-6
-    assert list(info.nlevels)[:5] == [o.amg(k).nlevels for k in range(5)]
     if precision == 0:
+        assert list(info.nlevels)[:5] == [o.amg(k).nlevels for k in range(5)]
         assert abs(info.iters - ir.iters) <= 2
     g.close()
+
+
+def test_c2_mixed_hierarchy_against_the_oracle(bgs, c2, ref):
+    o = ref[0]
+    g = bgs.solver_for_system(c2, precision=1)
+    g.setup()
+    u = 2.0 ** -24
+    for k in range(5):
+        oa = o.amg(k)
+        # level 0: built from the FP64 input in FP64, as in the FP64 mode
+        info = g.bgs_level_info(k, 0)
+        assert np.array_equal(g.bgs_level_strength(k, 0), oa.strong(0)), k
+        assert info["mis_rounds"] == oa.mis_rounds(0) and info["nagg"] == oa.nagg(0), k
+        assert np.array_equal(g.bgs_level_aggregates(k, 0), oa.aggregates(0)), k
+        assert abs(info["omega"] - oa.omega(0)) <= 1e-12 * abs(oa.omega(0)), k
+        for which, M in ((1, oa.prolongator(0)), (2, oa.restriction(0))):
+            prp, pci, pv = g.bgs_level_copy(k, 0, which)
+            assert np.array_equal(prp, M.rowptr) and np.array_equal(pci, M.col), (k, which)
+            assert np.abs(pv - M.val).max() <= 1e-12 * max(1.0, np.abs(M.val).max()), (k, which)
+        # A_1 = R_0 (A_0 P_0) in FP32: the same pattern, values within the FP32 error of sums of
+        # products, |err| <= gamma (|R_0| |A_0| |P_0|) with gamma = 2 k u, k the longest product chain
+        rp, ci, v = g.bgs_level_copy(k, 1, 0)
+        A1 = oa.level_matrix(1)
+        assert np.array_equal(rp, A1.rowptr) and np.array_equal(ci, A1.col), k
+        R0, A0, P0 = (oracle_abs(M) for M in (oa.restriction(0), oa.level_matrix(0), oa.prolongator(0)))
+        bound = (R0 @ (A0 @ P0)).tocsr()
+        rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+        bvals = np.asarray(bound[rows, ci]).ravel()
+        chain = int(np.diff(R0.indptr).max() * np.diff(A0.indptr).max() * np.diff(P0.indptr).max())
+        dev = np.abs(v - A1.val)
+        assert np.all(dev <= 2 * chain * u * bvals + 1e-300), k
+        print(f"block {k}: A_1 max |dev| / max |A_1| = {dev.max() / np.abs(A1.val).max():.2e}")
+        # coarser levels: aggregates compared where the level sizes agree
+        nl = min(g.bgs_num_levels(k), oa.nlevels)
+        for l in range(1, nl - 1):
+            ga, oa_l = g.bgs_level_aggregates(k, l), oa.aggregates(l)
+            if ga.shape != oa_l.shape:
+                print(f"block {k} level {l}: {ga.size} nodes, oracle {oa_l.size}")
+                continue
+            diff = int(np.count_nonzero(ga != oa_l))
+            print(f"block {k} level {l}: {diff} of {ga.size} nodes in another aggregate than the oracle's")
+            assert diff <= 0.05 * ga.size, (k, l, diff)
+    g.close()
+
+
+def oracle_abs(M):
+    import scipy.sparse as sp
+    return sp.csr_matrix((np.abs(M.val), M.col, M.rowptr), shape=(M.nrows, M.ncols))

@@ -83,18 +83,29 @@ def test_update_matches_oracle_update(bgs, precision):
         assert g.bgs_num_levels(k) == oa.nlevels
         for l in range(oa.nlevels - 1):
             ag = g.bgs_level_aggregates(k, l)
-            assert np.array_equal(ag, agg_before[k][l]) and np.array_equal(ag, oa.aggregates(l))
+            assert np.array_equal(ag, agg_before[k][l])               # kept by the numeric re-set-up
+            # FP64 mode, and level 0 in mixed mode: the oracle's quantities up to summation order;
+            # mixed levels >= 1 hang off the FP32 Galerkin products (FP32 rounding)
+            fp64 = precision == 0 or l == 0
+            if fp64:
+                assert np.array_equal(ag, oa.aggregates(l))
+            else:
+                diff = int(np.count_nonzero(ag != oa.aggregates(l)))
+                print(f"block {k} level {l}: {diff} of {ag.size} nodes in another aggregate than the oracle's")
+                assert diff <= 0.05 * ag.size
+            t_om, t_lm, t_m = (1e-12, 1e-10, 1e-11) if fp64 else (1e-5, 1e-5, 1e-5)
             info = g.bgs_level_info(k, l)
-            assert abs(info["omega"] - oa.omega(l)) <= 1e-12 * abs(oa.omega(l))
+            assert abs(info["omega"] - oa.omega(l)) <= t_om * abs(oa.omega(l)), (k, l)
             lo, hi = oa.cheb_bounds(l)
-            assert abs(info["lmax"] - hi) <= 1e-10 * hi
+            assert abs(info["lmax"] - hi) <= t_lm * hi, (k, l)
             for which, ref in ((0, oa.level_matrix(l)), (1, oa.prolongator(l)), (2, oa.restriction(l))):
                 rp, ci, v = g.bgs_level_copy(k, l, which)
                 assert np.array_equal(rp, ref.rowptr) and np.array_equal(ci, ref.col)
-                assert np.abs(v - ref.val).max() <= 1e-11 * max(1.0, np.abs(ref.val).max()), (k, l, which)
+                assert np.abs(v - ref.val).max() <= t_m * max(1.0, np.abs(ref.val).max()), (k, l, which)
         rp, ci, v = g.bgs_level_copy(k, oa.nlevels - 1, 0)
         ref = oa.level_matrix(oa.nlevels - 1)
-        assert np.abs(v - ref.val).max() <= 1e-11 * np.abs(ref.val).max()
+        t_m = 1e-11 if precision == 0 or oa.nlevels == 1 else 1e-5
+        assert np.abs(v - ref.val).max() <= t_m * np.abs(ref.val).max()
     # the solve after the update: the new system's solution
     x = torch.zeros(system.ndof, dtype=torch.float64, device="cuda")
     info = g.bgs_solve(dev(system.b), x)
