@@ -29,10 +29,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "setup+solve sec to rtol 1e-8 at 10.5M DOFs, mixed vs FP64 on same GB300; SpMV HBM GB/s"
 # DRAM bytes (read + write) of one finest-level FP64 Chebyshev-step launch on the 128^3 phi_s block,
-# per SpMV variant the autotuner can pick for it (0 = SELL-32, k = CSR with k threads per row), from
-# the ncu captures named beside each; a variant without a capture reports null
+# per SpMV variant the autotuner can pick for it (-1 = SELL-32 with diagonal offsets, 0 = SELL-32,
+# k = CSR with k threads per row), from
+# the ncu captures named beside each; a variant without a capture of its current code (SELL-32's
+# FP64 loop changed after its capture) reports null
 CHEB_FINE_TRAFFIC = {
-    0: (264.967168e6, "profiles/k_sell_cheb_phi_s_128cubed.md"),
+    -1: (206.169856e6, "profiles/k_dia_cheb_phi_s_128cubed.md"),
     1: (275.055616e6, "profiles/k_spmv1_cheb_phi_s_128cubed.md"),
 }
 WORKLOAD = "C4"
@@ -443,11 +445,14 @@ def gpu_arm(args, rank, world):
         return statistics.median(out)
 
     spmv_csr_ms = time_spmv(lambda: bgs.bgs_csr_spmv(A.nrows, A.nnz, rp, ci, va, xs, ys, 0, stream))
-    spmv_sell_ms = time_spmv(lambda: op.bgs_full_spmv(xs, ys))
+    spmv_lib_ms = time_spmv(lambda: op.bgs_full_spmv(xs, ys))
+    spmv_layout = op.bgs_level_format(0, 0, 3, with_block=True)
     op.close()
-    spmv_bytes = A.nnz * 12 + 4 * (A.nrows + 1) + 8 * A.nrows * 2
-    spmv_gbs = spmv_bytes / (min(spmv_csr_ms, spmv_sell_ms) * 1e-3) / 1e9
-    spmv_ms = [min(spmv_csr_ms, spmv_sell_ms)]
+    # bytes every layout moves (values, x, y) and the CSR layout's (plus its column and row indices)
+    spmv_bytes = A.nnz * 8 + 8 * A.nrows * 2
+    spmv_bytes_csr = spmv_bytes + A.nnz * 4 + 4 * (A.nrows + 1)
+    spmv_gbs = spmv_bytes / (spmv_lib_ms * 1e-3) / 1e9
+    spmv_ms = [spmv_lib_ms]
     del rp, ci, va, xs, ys, flush
 
     # end to end through the C ABI from pinned host buffers (copies inside the timed region)
@@ -590,9 +595,14 @@ def gpu_arm(args, rank, world):
                            "graph": int(bgs.bgs_default_options(**extra).graph)},
                 "fp64": arm64, "mixed": armmx, "variants": variants,
                 "mixed_speedup_vs_fp64": (ms64 / msmx) if msmx else None,
-                "spmv_full_fp64": {"GBps": spmv_gbs, "ms": statistics.median(spmv_ms), "bytes": spmv_bytes,
+                "spmv_full_fp64": {"layout": {-2: "node blocks", -1: "diagonal-offset SELL-32",
+                                              0: "SELL-32"}.get(spmv_layout[0], f"CSR, {spmv_layout[0]} lanes"),
+                                   "threads_per_block": spmv_layout[1],
+                                   "ms": statistics.median(spmv_ms), "bytes": spmv_bytes, "GBps": spmv_gbs,
                                    "frac_of_measured_peak": spmv_gbs / peak,
-                                   "csr_ms": spmv_csr_ms, "sell32_ms": spmv_sell_ms},
+                                   "bytes_note": "values + x + y, the bytes every layout moves",
+                                   "csr_ms": spmv_csr_ms,
+                                   "csr_GBps": spmv_bytes_csr / (spmv_csr_ms * 1e-3) / 1e9},
                 "solves_per_s": world / (ms64 / 1e3),
                 "gpu_launches": int(launches64 // max(args.steps, 1)) * args.steps,
                 "gpu_launches_per_step": int(launches64 // max(args.steps, 1)),

@@ -152,7 +152,7 @@ void prof_collect(bgs_ctx *h) {
 // (CSR / SELL-32: a column index per entry and the row pointers; diagonal-offset SELL-32: one offset
 // per slot of 32 rows and the slice pointers), x read and y written once, plus extra vectors.
 double spmv_bytes(const DCsr &A, int vbytes, int xbytes, int extra_vectors) {
-    const double idx = A.bsr   ? 4.0 * (double)A.bsr_slots + 4.0 * ((A.bsr_nc + 31) / 32 + 1)
+    const double idx = A.bsr_active() ? 4.0 * (double)A.bsr_slots + 4.0 * ((A.bsr_nc + 31) / 32 + 1)
                        : A.dia ? 4.0 * (double)(A.dia_nnz / 32) + 4.0 * ((A.n + 31) / 32 + 1)
                                : 4.0 * (double)A.nnz + 4.0 * (A.n + 1);
     return (double)A.nnz * vbytes + idx + (double)xbytes * A.n * (2 + extra_vectors);
@@ -1559,7 +1559,7 @@ int bgs_level_format(bgs_handle h, int field, int level, int which, int *format,
         Mp = which == 0 ? &H.L[level].A : (which == 1 ? &H.L[level].P : &H.L[level].R);
     }
     const DCsr &M = *Mp;
-    *format = M.bsr ? -2 : (M.dia ? -1 : (M.sell ? 0 : (M.lanes ? M.lanes : choose_lanes(M.n, M.nnz))));
+    *format = M.bsr_active() ? -2 : (M.dia ? -1 : (M.sell ? 0 : (M.lanes ? M.lanes : choose_lanes(M.n, M.nnz))));
     if (threads_per_block) *threads_per_block = M.tpb;
     return BGS_OK;
 }

@@ -125,6 +125,9 @@ struct DCsr {
     // F x F block, entry (f, g) = A(f*nc + I, g*nc + J) or 0.  Nodes in slices of 32 (one warp), slice
     // s holding w_s block slots; bcol[slot*32 + lane], bval[((slot*F + f)*F + g)*32 + lane].
     bool bsr = false;
+    // the node-block kernel runs when it is the only sliced layout (the autotuner's choice, or the
+    // one built); untuned, the diagonal-offset and SELL-32 forms come first
+    bool bsr_active() const { return bsr && !dia && !sell; }
     int bsr_F = 0, bsr_nc = 0;
     int64_t bsr_slots = 0;          // block slots (32 per slice and slot)
     DBuf<int> bptr, bcol;           // slot start per slice (multiple of 32), block column per slot

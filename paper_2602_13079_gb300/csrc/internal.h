@@ -276,7 +276,12 @@ void transpose_csr(const CsrView &A, DCsr &T, Scratch &sc, cudaStream_t s);
 constexpr double kMaxPad = 2.0;
 // the diagonal-offset SELL-32 copy is built when its slots stay within this factor of the entries
 constexpr double kMaxPadDia = 1.5;
-// the node-block copy stores F^2 values per block: built while that stays within this factor of the entries
-constexpr double kMaxPadBsr = 5.0;
+// The node-block copy stores F^2 values per block, and its kernel multiplies every one of them: it is
+// built as an autotuner candidate while that stays within this factor of the stored entries (the
+// 128^3 workload's full operator, with 5 x 5 blocks of which the off-node ones hold their diagonal
+// only, is at 3.1x and timed 2.7x slower than the diagonal-offset SELL-32), and up to the larger
+// factor when a cached choice names it.
+constexpr double kMaxPadBsr = 1.5;
+constexpr double kMaxPadBsrForced = 8.0;
 
 }  // namespace bgs

@@ -305,7 +305,7 @@ template <class VT, class XT, class Epi>
 static void run(const DCsr &A, const XT *x, Epi epi, cudaStream_t s) {
     using AT = typename AccT<VT, XT>::T;
     if (A.n <= 0) return;
-    if (A.bsr) {
+    if (A.bsr_active()) {
         if constexpr (kBsrEpi<VT, XT, Epi>) {
             if (A.tpb == 128) launch_bsr_tpb<Epi, 128>(A, x, epi, s);
             else if (A.tpb == 512) launch_bsr_tpb<Epi, 512>(A, x, epi, s);
@@ -860,7 +860,7 @@ void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scr
     const int code = use_cache ? cached_code(std::make_tuple(A.n, A.m, A.nnz, value_bytes, product ? 1 : 0)) : -1;
     if (code >= 0) {
         const Choice c = Choice::from(code);
-        if (c.format == -2 && bsr_fields && build_bsr(A, bsr_fields, kMaxPadBsr, sc, s)) return;
+        if (c.format == -2 && bsr_fields && build_bsr(A, bsr_fields, kMaxPadBsrForced, sc, s)) return;
         if (c.format == -1 && allow_dia && build_dia(A, kMaxPadDia, sc, s)) return;
         if (c.format <= 0) build_sell(A, kMaxPad, sc, s);
         return;
