@@ -202,10 +202,10 @@ int bgs_level_ellipse(bgs_handle h, int field, int level, double *imag);
  * a field on the V-cycle. */
 int bgs_ilu_factors(bgs_handle h, int field, int64_t *nnz, int32_t *rowptr, int32_t *col, double *val);
 /* SpMV kernel used for A_l (which 0), P_l (1), R_l (2), or the full operator (which 3; field and level
- * ignored): -2 = field-interleaved node blocks (full operator of equal fields only), -1 = SELL-32 with
- * one diagonal offset per slice slot (structured operators), 0 = SELL-32, k > 0 = CSR with k threads
- * per row (chosen by the autotuner when it is on); *threads_per_block (may be NULL) receives the block
- * size of its launches. */
+ * ignored; available from bgs_create on, the others after bgs_setup): -2 = field-interleaved node
+ * blocks (full operator of equal fields only), -1 = SELL-32 with one diagonal offset per slice slot
+ * (structured operators), 0 = SELL-32, k > 0 = CSR with k threads per row (chosen by the autotuner
+ * when it is on); *threads_per_block (may be NULL) receives the block size of its launches. */
 int bgs_level_format(bgs_handle h, int field, int level, int which, int *format, int *threads_per_block);
 /* Aggregate id of every node of level `level` (host array of rows(level) entries). */
 int bgs_level_aggregates(bgs_handle h, int field, int level, int32_t *agg);

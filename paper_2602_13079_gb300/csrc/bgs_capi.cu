@@ -889,22 +889,28 @@ void vstack(const std::vector<DCsr *> &parts, int ncols, DCsr &C, cudaStream_t s
 void assemble_operators(bgs_ctx *h, DCsr &full, DCsr *lower, cudaStream_t s) {
     const int F = h->F;
     const int64_t tot = total_n(h);
-    std::vector<DCsr> rowblocks((size_t)F);
-    for (int r = 0; r < F; r++) {
-        std::vector<CsrView> parts;
-        std::vector<int> offs;
+    // the full operator in place: every block row's row lengths into its rows of the row
+    // pointer, one scan, then every block row's entries
+    std::vector<std::vector<CsrView>> parts((size_t)F);
+    std::vector<std::vector<int>> coffs((size_t)F);
+    for (int r = 0; r < F; r++)
         for (int c = 0; c < F; c++) {
             DCsr &B = h->blk[(size_t)r * F + c];
             if (B.nnz == 0) continue;
-            parts.push_back(view(B));
-            offs.push_back((int)h->offs[c]);
+            parts[r].push_back(view(B));
+            coffs[r].push_back((int)h->offs[c]);
         }
-        concat_rows((int)h->sizes[r], (int)parts.size(), parts.data(), offs.data(), rowblocks[r], h->sc, s);
-    }
-    std::vector<DCsr *> rb;
-    for (auto &x : rowblocks) rb.push_back(&x);
-    vstack(rb, (int)tot, full, s);
-    rowblocks.clear();
+    full.n = (int)tot;
+    full.m = (int)tot;
+    full.rp.alloc((size_t)tot + 1, s);
+    for (int r = 0; r < F; r++)
+        concat_count((int)h->sizes[r], (int)parts[r].size(), parts[r].data(), full.rp.p + h->offs[r], s);
+    full.nnz = scan_exclusive(full.rp.p, full.rp.p, tot, h->sc, s);   // throws past 2^31 - 1 entries
+    full.ci.alloc((size_t)full.nnz, s);
+    full.v.alloc((size_t)full.nnz, s);
+    for (int r = 0; r < F; r++)
+        concat_fill((int)h->sizes[r], (int)parts[r].size(), parts[r].data(), coffs[r].data(),
+                    full.rp.p + h->offs[r], full.ci.p, full.v.p, s);
     for (int k = 0; k < F; k++) {
         std::vector<CsrView> parts;
         std::vector<int> offs;
@@ -1549,7 +1555,7 @@ int bgs_ilu_factors(bgs_handle h, int field, int64_t *nnz, int32_t *rowptr, int3
 
 int bgs_level_format(bgs_handle h, int field, int level, int which, int *format, int *threads_per_block) {
     if (!h || which < 0 || which > 3 || !format) return BGS_INVALID_ARG;
-    if (!h->setup_done) return BGS_NOT_SETUP;
+    if (!h->setup_done && which != 3) return BGS_NOT_SETUP;   // the full operator exists from create on
     const DCsr *Mp = &h->full;
     if (which < 3) {
         if (field < 0 || field >= h->F) return BGS_INVALID_ARG;

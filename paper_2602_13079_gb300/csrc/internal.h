@@ -69,6 +69,11 @@ int validate_status(int flag);
 // row i of parts[1] ... (all parts have n rows; columns stay sorted if offsets increase).
 void concat_rows(int n, int nparts, const CsrView *parts, const int *col_offs, DCsr &C, Scratch &sc,
                  cudaStream_t s);
+// the two passes of concat_rows into caller-owned arrays: the row lengths into cnt[0..n), then,
+// given the row starts rp[0..n] (absolute positions in ci, v), the entries
+void concat_count(int n, int nparts, const CsrView *parts, int *cnt, cudaStream_t s);
+void concat_fill(int n, int nparts, const CsrView *parts, const int *col_offs, const int *rp, int *ci, double *v,
+                 cudaStream_t s);
 void convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
 void convert_d2bf(const double *in, __nv_bfloat16 *out, int64_t n, cudaStream_t s);
 void copy_d2f(const double *in, float *out, int64_t n, cudaStream_t s);

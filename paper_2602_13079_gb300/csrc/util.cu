@@ -500,21 +500,52 @@ __global__ void k_concat_count(int n, Parts P, int *cnt) {
     }
 }
 
-__global__ void k_concat_fill(int n, Parts P, const int *rp, int *ci, double *v) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int q = rp[i];
-        for (int p = 0; p < P.np; p++)
-            for (int e = P.rp[p][i]; e < P.rp[p][i + 1]; e++) {
-                ci[q] = P.ci[p][e] + P.off[p];
-                v[q] = P.v[p][e];
-                q++;
+// One warp per 32 consecutive rows: for each part the lanes walk the part's entries of those rows
+// (one contiguous range of the source) 32 apart, so the reads are coalesced and the writes land in
+// runs; an entry's row within the group comes from a search over the group's row starts in shared
+// memory, its destination from that row's start plus the row's entries of the earlier parts.
+constexpr int kConcatWarps = 8;
+__global__ void __launch_bounds__(kConcatWarps * 32) k_concat_fill(int n, Parts P, const int *rp, int *ci, double *v) {
+    __shared__ int sst[kConcatWarps][33], sdst[kConcatWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t g0 = ((int64_t)blockIdx.x * kConcatWarps + w) * 32; g0 < n;
+         g0 += (int64_t)gridDim.x * kConcatWarps * 32) {
+        const int rows = (int)min((int64_t)32, n - g0);
+        const int i = (int)g0 + lane;
+        int dst = lane < rows ? rp[i] : 0;   // where row i's entries of part p start
+        for (int p = 0; p < P.np; p++) {
+            const int *prp = P.rp[p];
+            const int st = lane < rows ? prp[i] : 0, en = lane < rows ? prp[i + 1] : 0;
+            if (lane < rows) {
+                sst[w][lane] = st;
+                sdst[w][lane] = dst;
             }
+            if (lane == rows - 1) sst[w][rows] = en;
+            __syncwarp();
+            const int e0 = sst[w][0], e1 = sst[w][rows];
+            const int *pci = P.ci[p];
+            const double *pv = P.v[p];
+            const int off = P.off[p];
+            for (int e = e0 + lane; e < e1; e += 32) {
+                int lo = 0, hi = rows - 1;   // the last row whose start is <= e (it holds e)
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sst[w][mid] <= e) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int q = sdst[w][lo] + (e - sst[w][lo]);
+                ci[q] = pci[e] + off;
+                v[q] = pv[e];
+            }
+            __syncwarp();
+            dst += en - st;
+        }
     }
 }
 
-void concat_rows(int n, int nparts, const CsrView *parts, const int *col_offs, DCsr &C, Scratch &sc,
-                 cudaStream_t s) {
+static Parts make_parts(int nparts, const CsrView *parts, const int *col_offs) {
     Parts P{};
+    if (nparts > 8) throw Error(BGS_INVALID_ARG, "more than 8 blocks in one block row");
     P.np = nparts;
     for (int p = 0; p < nparts; p++) {
         P.rp[p] = parts[p].rp;
@@ -522,6 +553,31 @@ void concat_rows(int n, int nparts, const CsrView *parts, const int *col_offs, D
         P.v[p] = parts[p].v;
         P.off[p] = col_offs[p];
     }
+    return P;
+}
+
+void concat_count(int n, int nparts, const CsrView *parts, int *cnt, cudaStream_t s) {
+    if (n <= 0) return;
+    if (nparts == 0) {
+        CK(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n, s));
+        return;
+    }
+    const int zero = 0;
+    k_concat_count<<<grid_for(n, 256), 256, 0, s>>>(n, make_parts(nparts, parts, &zero), cnt);
+    CK_LAUNCH();
+}
+
+void concat_fill(int n, int nparts, const CsrView *parts, const int *col_offs, const int *rp, int *ci, double *v,
+                 cudaStream_t s) {
+    if (n <= 0 || nparts == 0) return;
+    const int g = (int)std::min<int64_t>(((int64_t)n + kConcatWarps * 32 - 1) / (kConcatWarps * 32),
+                                         (int64_t)num_sms() * 16);
+    k_concat_fill<<<g, kConcatWarps * 32, 0, s>>>(n, make_parts(nparts, parts, col_offs), rp, ci, v);
+    CK_LAUNCH();
+}
+
+void concat_rows(int n, int nparts, const CsrView *parts, const int *col_offs, DCsr &C, Scratch &sc,
+                 cudaStream_t s) {
     C.n = n;
     C.rp.alloc((size_t)n + 1, s);
     if (nparts == 0 || n == 0) {
@@ -529,13 +585,11 @@ void concat_rows(int n, int nparts, const CsrView *parts, const int *col_offs, D
         C.nnz = 0;
         return;
     }
-    k_concat_count<<<grid_for(n, 256), 256, 0, s>>>(n, P, C.rp.p);
-    CK_LAUNCH();
+    concat_count(n, nparts, parts, C.rp.p, s);
     C.nnz = scan_exclusive(C.rp.p, C.rp.p, n, sc, s);
     C.ci.alloc((size_t)C.nnz, s);
     C.v.alloc((size_t)C.nnz, s);
-    k_concat_fill<<<grid_for(n, 256), 256, 0, s>>>(n, P, C.rp.p, C.ci.p, C.v.p);
-    CK_LAUNCH();
+    concat_fill(n, nparts, parts, col_offs, C.rp.p, C.ci.p, C.v.p, s);
 }
 
 }  // namespace bgs
