@@ -1001,9 +1001,21 @@ template <class Fn>
 int run_per_block(bgs_ctx *h, Fn &&fn) {
     int dev = 0;
     CK(cudaGetDevice(&dev));
+    // The blocks with the largest drop tolerance coarsen slowest (more levels: a longer chain of
+    // small, latency-bound steps after the shared level-0 work), so their streams get the greatest
+    // priority: where the blocks share the GPU, their work is scheduled first and their tail
+    // overlaps the others' bulk.  With equal tolerances every stream has the default priority.
+    double tmin = 1e300, tmax = -1e300;
+    for (int k = 0; k < h->F; k++) {
+        tmin = std::min(tmin, h->opt.theta[k]);
+        tmax = std::max(tmax, h->opt.theta[k]);
+    }
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
     for (int k = 0; k < h->F; k++)
         if (!h->bs[k]) {
-            CK(cudaStreamCreateWithFlags(&h->bs[k], cudaStreamNonBlocking));
+            const int prio = (tmax > tmin && h->opt.theta[k] == tmax) ? greatest : least;
+            CK(cudaStreamCreateWithPriority(&h->bs[k], cudaStreamNonBlocking, prio));
             h->bsc[k].init(h->bs[k]);
         }
     std::vector<int> st((size_t)h->F, BGS_OK);

@@ -22,7 +22,9 @@ struct Scratch {
     DBuf<double> pinned_dummy;
     double *h_scal = nullptr;  // pinned host mirror
     int *h_flags = nullptr;
-    // a second stream for work that overlaps the owner's stream (forked and joined by events)
+    // a second stream for work that overlaps the owner's stream (forked and joined by events), at
+    // the owner stream's priority
+    cudaStream_t owner = nullptr;
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr;
     void init(cudaStream_t s);

@@ -58,6 +58,7 @@ int num_sms() {
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void Scratch::init(cudaStream_t s) {
+    owner = s;
     partial.alloc(num_sms() * 8 * 72, s);
     scal.alloc(256, s);
     flags.alloc(64, s);
@@ -68,7 +69,9 @@ void Scratch::init(cudaStream_t s) {
 
 void Scratch::ensure_side() {
     if (side) return;
-    CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    int prio = 0;
+    if (owner) CK(cudaStreamGetPriority(owner, &prio));
+    CK(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio));
     CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
 }
 
