@@ -623,11 +623,13 @@ __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_sym(int n, const int *rows
 }
 
 // symbolic for big rows: global table per row
+// (open_only: rows whose count is already there, cnt[row] >= 0, are skipped)
 __global__ void k_sg_sym_big(int nbig, const int *rows, const long long *toff, int *gkeys, const int *arp,
-                             const int *aci, const int *brp, const int *bci, int *cnt) {
+                             const int *aci, const int *brp, const int *bci, int *cnt, int open_only) {
     const int lane = threadIdx.x & 31;
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbig; b += (gridDim.x * blockDim.x) >> 5) {
         const int row = rows[b];
+        if (open_only && cnt[row] >= 0) continue;
         int *keys = gkeys + toff[b];
         const unsigned T = (unsigned)(toff[b + 1] - toff[b]);
         for (unsigned t = lane; t < T; t += 32) keys[t] = -1;
@@ -714,11 +716,13 @@ __global__ void __launch_bounds__(SG_WARPS * 32) k_sg_num(int n, const int *rows
 }
 
 template <class VT>
+// (rows of at most min_c columns are skipped: a shared-table kernel made them)
 __global__ void k_sg_num_big(int nbig, const int *rows, const long long *toff, int *gkeys, VT *gvals, const int *arp,
                              const int *aci, const VT *av, const int *brp, const int *bci, const VT *bv,
-                             const int *crp, int *cci, VT *cv, int *err) {
+                             const int *crp, int *cci, VT *cv, int *err, int min_c) {
     __shared__ VT svb[8][64];
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbig; b += (gridDim.x * blockDim.x) >> 5) {
+        if (crp[rows[b] + 1] - crp[rows[b]] <= min_c) continue;
         const unsigned T = (unsigned)(toff[b + 1] - toff[b]);
         sg_numeric_row(rows[b], gkeys + toff[b], gvals + toff[b], T, svb[(threadIdx.x >> 5) & 7], arp, aci, av, brp,
                        bci, bv, crp, cci, cv, err);
@@ -907,9 +911,12 @@ __global__ void k_iota(int n, int *a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
 }
 
-// Products with few rows (the coarse levels): every row through the warp-hash kernels, each with a
-// global-memory table sized for its product count, so no classing by row length; three read-backs
-// (table total, row counts, error flag) instead of one per class.
+// Products with few rows (the coarse levels): every row first through the shared-memory hash
+// kernels (a symbolic table of SG_SYM_T slots, capped; a numeric table sized from the row's column
+// count, up to SG_NUM_T slots), and the rows that do not fit through global-memory tables sized
+// from their product counts, all launched over every row without classifying them first: three
+// read-backs in all (table total, row counts, error flag).  The coarsest products have few rows of
+// thousands of products but a few dozen columns, which the shared tables serve.
 constexpr int kSgSmallRows = 16384;
 template <class VT>
 static void spgemm_small(const CsrView &A, const VT *av, const CsrView &B, const VT *bv, DCsr &C, DBuf<VT> &cv,
@@ -924,16 +931,23 @@ static void spgemm_small(const CsrView &A, const VT *av, const CsrView &B, const
     const long long tot = scan_ll_inplace(toff.p, n, s);
     DBuf<int> gk((size_t)tot, s);
     DBuf<VT> gv((size_t)tot, s);
+    k_sg_sym<SG_SYM_T><<<grid_for((int64_t)n * 32, SG_WARPS * 32, num_sms() * 8), SG_WARPS * 32,
+                         sizeof(int) * SG_WARPS * SG_SYM_T, s>>>(n, nullptr, A.rp, A.ci, B.rp, B.ci, ub, C.rp.p);
+    CK_LAUNCH();
     k_sg_sym_big<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, rows.p, toff.p, gk.p, A.rp, A.ci, B.rp, B.ci,
-                                                                 C.rp.p);
+                                                                 C.rp.p, 1);
     CK_LAUNCH();
     C.nnz = scan_exclusive(C.rp.p, C.rp.p, n, sc, s);
     C.ci.alloc((size_t)C.nnz, s);
     cv.alloc((size_t)C.nnz, s);
     CK(cudaMemsetAsync(sc.flags.p + 8, 0, sizeof(int), s));
+    k_sg_num<SG_NUM_T, VT><<<grid_for((int64_t)n * 32, SG_WARPS * 32, num_sms() * 8), SG_WARPS * 32,
+                             sg_num_smem<SG_NUM_T, VT>(), s>>>(n, nullptr, A.rp, A.ci, av, B.rp, B.ci, bv, C.rp.p,
+                                                               C.ci.p, cv.p, sc.flags.p + 8);
+    CK_LAUNCH();
     k_sg_num_big<VT><<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, rows.p, toff.p, gk.p, gv.p, A.rp, A.ci, av,
                                                                      B.rp, B.ci, bv, C.rp.p, C.ci.p, cv.p,
-                                                                     sc.flags.p + 8);
+                                                                     sc.flags.p + 8, SG_NUM_T / 2);
     CK_LAUNCH();
     CK(cudaMemcpyAsync(sc.h_flags + 8, sc.flags.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1002,7 +1016,7 @@ static void spgemm_t(const CsrView &A, const VT *av, const CsrView &B, const VT 
                 long long tot = big_tables(nb2, rows2.p, ub.p, toff, s);
                 DBuf<int> gk((size_t)tot, s);
                 k_sg_sym_big<<<grid_for((int64_t)nb2 * 32, 256), 256, 0, s>>>(nb2, rows2.p, toff.p, gk.p, A.rp, A.ci,
-                                                                               B.rp, B.ci, C.rp.p);
+                                                                               B.rp, B.ci, C.rp.p, 0);
                 CK_LAUNCH();
             }
         }
@@ -1060,7 +1074,7 @@ static void spgemm_t(const CsrView &A, const VT *av, const CsrView &B, const VT 
                 DBuf<VT> gv((size_t)tot, s);
                 k_sg_num_big<VT><<<grid_for((int64_t)nb2 * 32, 256), 256, 0, s>>>(
                     nb2, rows2.p, toff.p, gk.p, gv.p, A.rp, A.ci, av, B.rp, B.ci, bv, C.rp.p, C.ci.p, cv.p,
-                    sc.flags.p + 8);
+                    sc.flags.p + 8, -1);
                 CK_LAUNCH();
             }
         }
@@ -1564,7 +1578,9 @@ static void level_numeric(Hier &H, int l, const AmgParams &p, Scratch &sc, cudaS
                                                    dinvF.p, p.filter_diag);
     CK_LAUNCH();
     tr.mark("filter", l, AF.nnz);
-    const double lamF = power_lambda(AF, dinvF.p, p.power_iters, sc, s);
+    // nothing filtered out (A_F has every entry of A_l, so the same values): the iteration runs on
+    // A_l and its layouts
+    const double lamF = power_lambda(AF.nnz == A.nnz ? A : AF, dinvF.p, p.power_iters, sc, s);
     const double omega = (4.0 / 3.0) / lamF;
     tr.mark("power(omega)", l, n);
     DCsr Pt;
@@ -1701,6 +1717,9 @@ void amg_build(Hier &H, const AmgParams &p, Scratch &sc, cudaStream_t s) {
     H.L.reserve(kMaxLevels + 1);
     const double t2 = p.theta * p.theta;
     Trace tr(s);
+    // the finest operator's diagonal-offset layout (the solve's likely choice) serves the
+    // set-up's power iterations on it already (spmv_scaled_norm)
+    build_dia(H.L[0].A, kMaxPadDia, sc, s);
     sc.ensure_side();
     EarlyCheb ec;
     ec.partial.alloc((size_t)num_sms() * 4, s);

@@ -335,10 +335,16 @@ void spmv_scaled(const CsrView &A, const double *dinv, const double *v, double *
 
 void spmv_scaled_norm(const DCsr &A, const double *dinv, const double *v, const double *rnorm, double *w,
                       cudaStream_t s) {
-    // a kernel fixed by the shape alone (not by the autotuned format), so that a set-up and a later
-    // numeric re-set-up sum in the same order: one thread per row for short rows, else L lanes
+    // a summation order fixed by the shape alone (not by the autotuned format), so that a set-up
+    // and a later numeric re-set-up sum alike: short rows left to right, one thread per row (from
+    // the diagonal-offset layout when the operator has one: its slots run in column order and its
+    // padded slots add exact zeros), longer rows over L lanes
     const double avg = A.n > 0 ? (double)A.nnz / (double)A.n : 0.0;
     const int lanes = avg <= 12.0 ? 1 : (avg <= 64.0 ? 4 : 8);
+    if (lanes == 1 && A.dia && A.n > 0) {
+        launch_sliced<double, double, double, EScaleNorm, 256>(A, v, EScaleNorm{dinv, rnorm, w}, s);
+        return;
+    }
     launch_csr<double, double, double>(lanes, A.n, A.rp.p, A.ci.p, A.v.p, v, EScaleNorm{dinv, rnorm, w}, s);
 }
 
@@ -860,6 +866,7 @@ void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scr
     const int code = use_cache ? cached_code(std::make_tuple(A.n, A.m, A.nnz, value_bytes, product ? 1 : 0)) : -1;
     if (code >= 0) {
         const Choice c = Choice::from(code);
+        if (c.format != -1 && A.dia) drop_dia(A);   // built earlier for the set-up's own products
         if (c.format == -2 && bsr_fields && build_bsr(A, bsr_fields, kMaxPadBsrForced, sc, s)) return;
         if (c.format == -1 && allow_dia && build_dia(A, kMaxPadDia, sc, s)) return;
         if (c.format <= 0) build_sell(A, kMaxPad, sc, s);
