@@ -105,26 +105,13 @@ __global__ void __launch_bounds__(TPB) k_sell(int n, const int *__restrict__ spt
 }
 
 // ------------------------------------------------------------------------------------------ SELL-32, diagonal offsets
-// Slice of 32 rows per warp; lane k holds the slice's k-th offset (w <= wmax <= 32), broadcast by
-// shuffle.  The offsets sit at a fixed stride of wmax per slice, so their load does not wait for the
-// slice's slot pointer: a warp's loads take two dependent rounds (pointers, offsets and the start
-// value; then values and x), not three.  A padded slot's column is clamped into [0, m) (its value
-// is 0).
-template <class VT, class XT, class AT, class Epi, int TPB>
-__global__ void __launch_bounds__(TPB) k_dia(int n, int m, int wmax, const int *__restrict__ dptr,
-                                             const int *__restrict__ doff, const VT *__restrict__ dv,
-                                             const XT *__restrict__ x, Epi epi) {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    const int slice = row >> 5;
-    if ((slice << 5) >= n) return;          // whole warp past the end
-    const int lane = row & 31;
-    const int s0 = __ldg(dptr + slice);
-    const int w = (__ldg(dptr + slice + 1) - s0) >> 5;
-    const int myo = lane < wmax ? __ldg(doff + (int64_t)slice * wmax + lane) : 0;
-    const VT *v = dv + s0 + lane;
-    const int last = m - 1;
-    constexpr bool S = Epi::kSub;
-    AT acc = row < n ? epi.template start<AT>(row) : (AT)0;
+// The row sum of one row over its slice's w slots (offsets in myo across the warp's lanes), added
+// to acc.  CLAMP: the column row + offset is clamped into [0, last] (a padded slot may point
+// outside; its value is 0); a slice whose rows all stay inside for every offset skips it.
+template <bool CLAMP, class VT, class XT, class AT, bool S>
+__device__ __forceinline__ AT dia_row_sum(AT acc, int row, int w, int myo, int last, const VT *__restrict__ v,
+                                          const XT *__restrict__ x) {
+    auto col = [&](int o) { return CLAMP ? min(max(row + o, 0), last) : row + o; };
     if constexpr (sizeof(AT) == 4 && sizeof(VT) == 4) {
         // FP32: batches of 4 slots, all loads of a batch in flight together; a slot past the slice
         // width re-reads the last one (a cached duplicate) and its product is skipped (w is
@@ -137,7 +124,7 @@ __global__ void __launch_bounds__(TPB) k_dia(int n, int m, int wmax, const int *
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int kk = min(k + u, w - 1);
-                const int c = min(max(row + __shfl_sync(0xffffffffu, myo, kk), 0), last);
+                const int c = col(__shfl_sync(0xffffffffu, myo, kk));
                 a[u] = Cvt<AT>::f(ldg(v + kk * 32));
                 xv[u] = Cvt<AT>::f(ldg(x + c));
             }
@@ -155,7 +142,7 @@ __global__ void __launch_bounds__(TPB) k_dia(int n, int m, int wmax, const int *
             AT a[U], xv[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                const int c = min(max(row + __shfl_sync(0xffffffffu, myo, k + u), 0), last);
+                const int c = col(__shfl_sync(0xffffffffu, myo, k + u));
                 a[u] = Cvt<AT>::f(ldg(v + (k + u) * 32));
                 xv[u] = Cvt<AT>::f(ldg(x + c));
             }
@@ -164,10 +151,38 @@ __global__ void __launch_bounds__(TPB) k_dia(int n, int m, int wmax, const int *
         }
 #pragma unroll 1
         for (; k < w; k++) {
-            const int c = min(max(row + __shfl_sync(0xffffffffu, myo, k), 0), last);
+            const int c = col(__shfl_sync(0xffffffffu, myo, k));
             acc = mac<S>(acc, Cvt<AT>::f(ldg(v + k * 32)), Cvt<AT>::f(ldg(x + c)));
         }
     }
+    return acc;
+}
+
+// Slice of 32 rows per warp; lane k holds the slice's k-th offset (w <= wmax <= 32), broadcast by
+// shuffle.  The offsets sit at a fixed stride of wmax per slice, so their load does not wait for the
+// slice's slot pointer: a warp's loads take two dependent rounds (pointers, offsets and the start
+// value; then values and x), not three.
+template <class VT, class XT, class AT, class Epi, int TPB>
+__global__ void __launch_bounds__(TPB) k_dia(int n, int m, int wmax, const int *__restrict__ dptr,
+                                             const int *__restrict__ doff, const VT *__restrict__ dv,
+                                             const XT *__restrict__ x, Epi epi) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = row >> 5;
+    if ((slice << 5) >= n) return;          // whole warp past the end
+    const int lane = row & 31;
+    const int s0 = __ldg(dptr + slice);
+    const int w = (__ldg(dptr + slice + 1) - s0) >> 5;
+    const int myo = lane < wmax ? __ldg(doff + (int64_t)slice * wmax + lane) : 0;
+    const VT *v = dv + s0 + lane;
+    const int last = m - 1;
+    AT acc = row < n ? epi.template start<AT>(row) : (AT)0;
+    // every row of the slice, shifted by every offset it stores (and 0), inside [0, m): no clamping
+    const int omin = __reduce_min_sync(0xffffffffu, myo), omax = __reduce_max_sync(0xffffffffu, myo);
+    const int64_t first = (int64_t)slice << 5;
+    if (first + omin >= 0 && first + 31 + omax <= (int64_t)last)
+        acc = dia_row_sum<false, VT, XT, AT, Epi::kSub>(acc, row, w, myo, last, v, x);
+    else
+        acc = dia_row_sum<true, VT, XT, AT, Epi::kSub>(acc, row, w, myo, last, v, x);
     if (row < n) epi(row, acc);
 }
 
