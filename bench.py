@@ -34,7 +34,7 @@ METRIC = "setup+solve sec to rtol 1e-8 at 10.5M DOFs, mixed vs FP64 on same GB30
 # the ncu captures named beside each; a variant without a capture of its current code (SELL-32's
 # FP64 loop changed after its capture) reports null
 CHEB_FINE_TRAFFIC = {
-    -1: (206.169856e6, "profiles/k_dia_cheb_phi_s_128cubed.md"),
+    -1: (206.510592e6, "profiles/k_dia_cheb_phi_s_128cubed.md"),
     1: (275.055616e6, "profiles/k_spmv1_cheb_phi_s_128cubed.md"),
 }
 WORKLOAD = "C4"

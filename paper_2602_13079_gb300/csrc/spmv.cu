@@ -882,6 +882,8 @@ void build_formats(DCsr &A, int value_bytes, bool allow_dia, bool use_cache, Scr
     if (code >= 0) {
         const Choice c = Choice::from(code);
         if (c.format != -1 && A.dia) drop_dia(A);   // built earlier for the set-up's own products
+        A.tpb = c.tpb;
+        A.lanes = c.format > 0 ? c.format : 0;
         if (c.format == -2 && bsr_fields && build_bsr(A, bsr_fields, kMaxPadBsrForced, sc, s)) return;
         if (c.format == -1 && allow_dia && build_dia(A, kMaxPadDia, sc, s)) return;
         if (c.format <= 0) build_sell(A, kMaxPad, sc, s);
