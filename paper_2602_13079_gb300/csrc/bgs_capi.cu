@@ -832,11 +832,24 @@ int copy_and_validate(bgs_ctx *h, const int64_t *sizes, const bgs_csr *blocks, c
         }
     DBuf<int> flags(std::max<size_t>(todo.size(), 1), s);
     tr.mark("  allocate block copies");
-    transfer(segs, s);
+    // block by block: each block's copy on s, its validation on the side stream once the copy is
+    // done, so a block's validation runs under the next block's copy (bound by the host link)
+    h->sc.ensure_side();
+    cudaStream_t vs = h->sc.side;
+    CK(cudaEventRecord(h->sc.fork, s));
+    CK(cudaStreamWaitEvent(vs, h->sc.fork, 0));   // the flags' allocation and the empty blocks
+    size_t seg0 = 0;
     for (size_t i = 0; i < todo.size(); i++) {
         const int b = todo[i];
-        validate_csr_launch(view(h->blk[(size_t)b]), b / F == b % F, flags.p + i, s);
+        const size_t nseg = h->blk[(size_t)b].nnz ? 3 : 1;
+        transfer(std::vector<XferSeg>(segs.begin() + seg0, segs.begin() + seg0 + nseg), s);
+        seg0 += nseg;
+        CK(cudaEventRecord(h->sc.fork, s));
+        CK(cudaStreamWaitEvent(vs, h->sc.fork, 0));
+        validate_csr_launch(view(h->blk[(size_t)b]), b / F == b % F, flags.p + i, vs);
     }
+    CK(cudaEventRecord(h->sc.fork, vs));
+    CK(cudaStreamWaitEvent(s, h->sc.fork, 0));
     std::vector<int> hf(todo.size(), 0);
     if (!todo.empty())
         CK(cudaMemcpyAsync(hf.data(), flags.p, sizeof(int) * todo.size(), cudaMemcpyDeviceToHost, s));
