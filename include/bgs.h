@@ -237,6 +237,24 @@ int bgs_csr_spmv(int64_t nrows, int64_t nnz, const int32_t *rowptr, const int32_
 int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h,
                      void *cuda_stream);
 
+/* One classical Gram-Schmidt pass of the FGMRES orthogonalisation exactly as the solver runs it
+ * (K14, Sec. 2.2 flexible GMRES): h[k] = V_k . w for k < cnt and h[cnt] = w . w, then
+ * w <- w - sum_k h[k] V_k in place and *nw = w . w after the update.  On GB300 the FP64 pipe alone
+ * caps these passes below the HBM rate, so the solver splits the products: in the dots, vectors
+ * 0..2 of every group of 8 in FP64 and 3..7 in exact fixed point on the integer pipes; in the
+ * update, the even rows in FP64 and the odd rows in fixed point.  A fixed-point sum truncates each
+ * basis entry to a multiple of 2^-62 and each entry of the other factor to 56 bits below the
+ * largest exponent among those one accumulator sees, sums exactly and rounds once to FP64.  This
+ * needs |V_ik| < 2, as for the solver's unit basis vectors: a larger, infinite or NaN entry makes
+ * its vector's fixed-point dot NaN (and with it the whole update), and an infinite or NaN w makes
+ * every fixed-point dot NaN.  V: device, column-major, vector k
+ * at V + k*ld, ld even and >= n; w: device, n entries; V and w 16-byte aligned; h: device, cnt + 1
+ * entries; nw: device, 1 entry; 1 <= cnt <= 64 (anything else returns BGS_INVALID_ARG before any
+ * GPU work).  Scratch is allocated and freed on the stream (stream-ordered); results are
+ * run-to-run reproducible. */
+int bgs_gram_schmidt_pass(const double *V, int64_t ld, int cnt, double *w, int64_t n, double *h, double *nw,
+                          void *cuda_stream);
+
 /* bgs_arnoldi_dots without any device allocation (the paper has no counterpart: this is a
  * library convenience).  For callers that cannot allocate device memory when they need the dots:
  * applications whose device memory is fully pre-reserved by their own pool manager, and embedded or

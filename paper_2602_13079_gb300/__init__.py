@@ -90,6 +90,7 @@ def lib():
             "bgs_csr_spmv": (i32, [i64, i64, vp, vp, vp, vp, vp, i32, vp]),
             "bgs_arnoldi_dots": (i32, [vp, i64, i32, vp, i64, vp, vp]),
             "bgs_arnoldi_dots_noalloc": (i32, [vp, i64, i32, vp, i64, vp, vp]),
+            "bgs_gram_schmidt_pass": (i32, [vp, i64, i32, vp, i64, vp, vp, vp]),
             "bgs_launch_count": (C.c_int64, []),
             "bgs_release_cached_memory": (i32, []),
             "bgs_destroy": (None, [vp]),
@@ -152,6 +153,14 @@ def bgs_csr_spmv(nrows, nnz, rowptr, col, val, x, y, lanes=0, stream=None) -> in
 def bgs_arnoldi_dots(V, ld, cnt, w, n, h, stream=None) -> int:
     """h[k] = V_k . w (k < cnt), h[cnt] = w . w; device tensors, V column-major with leading dim ld."""
     return lib().bgs_arnoldi_dots(_ptr(V), int(ld), int(cnt), _ptr(w), int(n), _ptr(h), _stream_ptr(stream))
+
+
+def bgs_gram_schmidt_pass(V, ld, cnt, w, n, h, nw, stream=None) -> int:
+    """One Gram-Schmidt pass of the FGMRES orthogonalisation with the solver's kernels: h = V^T w
+    (h[cnt] = ||w||^2), w -= V h in place, nw[0] = ||w||^2 after (device tensors; basis entries
+    below 2 in magnitude)."""
+    return lib().bgs_gram_schmidt_pass(_ptr(V), int(ld), int(cnt), _ptr(w), int(n), _ptr(h), _ptr(nw),
+                                       _stream_ptr(stream))
 
 
 def bgs_arnoldi_dots_noalloc(V, ld, cnt, w, n, h, stream=None) -> int:

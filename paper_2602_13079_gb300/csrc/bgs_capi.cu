@@ -1660,6 +1660,18 @@ int bgs_arnoldi_dots(const double *V, int64_t ld, int cnt, const double *w, int6
     });
 }
 
+int bgs_gram_schmidt_pass(const double *V, int64_t ld, int cnt, double *w, int64_t n, double *h, double *nw,
+                          void *stream) {
+    if (!V || !w || !h || !nw || n < 1 || cnt < 1 || cnt > 64 || ld < n || (ld & 1)) return BGS_INVALID_ARG;
+    if (((uintptr_t)V | (uintptr_t)w) & 15) return BGS_INVALID_ARG;   // read as 16-byte pairs
+    return guarded([&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        DBuf<double> part(gs_pass_scratch(cnt, n), s);
+        gs_pass(V, ld, cnt, w, n, h, nw, part.p, part.n, s);
+        return BGS_OK;
+    });
+}
+
 int64_t bgs_launch_count(void) { return (int64_t)launch_count(); }
 
 int bgs_release_cached_memory(void) {

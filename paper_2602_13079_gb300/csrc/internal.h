@@ -175,6 +175,12 @@ void drop_bsr(DCsr &A);
 void arnoldi_dots_into(const double *V, int64_t ld, int cnt, const double *w, int64_t n, double *h, double *partial,
                        size_t partial_cap, int max_blocks, cudaStream_t s);
 size_t arnoldi_dots_scratch(int cnt, int64_t n, int max_blocks);
+// One Gram-Schmidt pass of the FGMRES orthogonalisation with the solver's kernels (the FP64 /
+// fixed-point split; basis entries below 2 in magnitude): h = V^T w (cnt + 1 entries, h[cnt] =
+// ||w||^2), w -= V h, *nw = ||w||^2 after; partial holds gs_pass_scratch(cnt, n) doubles.
+size_t gs_pass_scratch(int cnt, int64_t n);
+void gs_pass(const double *V, int64_t ld, int cnt, double *w, int64_t n, double *h, double *nw, double *partial,
+             size_t partial_cap, cudaStream_t s);
 
 // FGMRES(m) state in device memory (one per Krylov workspace); m <= kMaxRestart.
 constexpr int kMaxRestart = 63;

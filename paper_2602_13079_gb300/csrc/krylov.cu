@@ -4,16 +4,41 @@
 // Orthogonalisation: classical Gram-Schmidt with selective re-orthogonalisation (Daniel-Gragg-
 // Kaufman-Stewart test, "twice is enough").
 //   dots:   h = V^T w and ||w||^2 in one pass over V (column-major, leading dimension ld);
-//           the basis is split over gridDim.y in chunks of KC vectors so a thread keeps KC + 1
-//           accumulators, and each thread reads two rows per load (16-byte loads along a column).
-//   update: w_out = w_in - V h and ||w_out||^2 in one pass (one accumulator per row pair).
+//           the basis is split over gridDim.y in chunks of vectors so a thread keeps one
+//           accumulator per vector of its chunk, and each thread reads two rows per load (16-byte
+//           loads along a column).
+//   update: w_out = w_in - V h and ||w_out||^2 in one pass (one accumulator per row).
 // Every reduction goes through per-block partials summed in a fixed order, so the results do not
 // depend on scheduling.
+//
+// The FGMRES passes split their products between two kinds of arithmetic.  On GB300 the FP64 pipe
+// retires about 1.6 fused multiply-adds per clock per multiprocessor, fewer than the basis entries
+// HBM delivers (about 2.7 per clock), so a pass done wholly in FP64 is bound by that pipe; the
+// integer pipes sit idle meanwhile.  So a share of the products runs as exact integer arithmetic:
+//  * a basis entry v, |v| < 2 (the basis vectors have unit norm), becomes the integer
+//    trunc(|v| 2^62) (at most 63 bits) and a sign;
+//  * the other factor x (w in the dots, h in the update) is taken relative to the largest exponent
+//    field S among the values one accumulator sees: |x| = M 2^(S - 1078) with M a 56-bit integer
+//    (an entry 2^k below the largest drops its k lowest mantissa bits);
+//  * each integer product, floor(product / 2^32) formed from 32-bit partial products (less than one
+//    unit, 2^-85 of the largest possible product, cut off), is summed into a 96-bit two's-complement
+//    accumulator: a thread's sum is exact up to those truncations and independent of order; it is
+//    rounded to FP64 once (value = accumulator * 2^(S - 1108)) and the thread sums go through the
+//    same fixed-order FP64 tree as the FP64 sums.
+// The terms of a dot of a unit vector v with w thus carry less than 2^-62 ||w||_1 + 2^-55 max|w|
+// ||v||_1 + n 2^-84 max|w| of truncation in all, and only the tree's roundings on top, where an FP64
+// sum rounds at every term.  The dots take vectors
+// 0..2 of each chunk of 8 in FP64 and 3..7 in fixed point; the update takes the first row of each
+// pair in FP64 and the second in fixed point (measured on the 10.5M-row workload with 16 basis
+// vectors: dots 0.415 -> 0.326 ms, update 0.340 -> 0.236 ms).  The general-purpose dots of the C
+// interface (any V) stay in FP64.
 //
 // The step kernels read the basis size (cnt = j + 1) from the solver state in device memory, and
 // the scalar work of a step (Hessenberg column, rotations, estimate, stop decision) runs in one
 // single-thread kernel, so a whole restart cycle can be replayed as one CUDA graph whose WHILE
 // node the step kernel ends; launched one by one, the same kernels give the same bits.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace bgs {
@@ -46,6 +71,78 @@ __device__ void block_reduce_to(const double (&acc)[NACC], int nvalid, double *o
         for (int q = 0; q < KT / 32; q++) t += sm[q][k];
         out[k] = t;
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// Fixed-point products (the scheme in the header comment)
+// ------------------------------------------------------------------------------------------
+struct Fx96 {
+    uint32_t w0, w1, w2;   // two's complement, w0 least significant
+};
+
+// exponent field of a double for scaling: at least 1, so that zeros and subnormals share the
+// smallest normal exponent
+__device__ __forceinline__ uint32_t fx_exp(uint64_t bits) { return max((uint32_t)(bits >> 52) & 0x7ffu, 1u); }
+
+// trunc(|v| 2^62) for |v| < 2; bad is set for |v| >= 2, Inf and NaN (the value is then 0)
+__device__ __forceinline__ uint64_t fx_basis(uint64_t bits, bool &bad) {
+    const uint32_t e = (uint32_t)(bits >> 52) & 0x7ffu;
+    bad |= e >= 1024u;
+    const uint64_t m = ((bits & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 10;
+    return m >> min(1023u - e, 63u);   // e >= 1024 wraps to a shift of 63: 0
+}
+
+// |x| = M 2^(S - 1078) with M < 2^56, for S >= fx_exp(x)
+__device__ __forceinline__ uint64_t fx_scaled(uint64_t bits, uint32_t S) {
+    const uint32_t e = (uint32_t)(bits >> 52) & 0x7ffu;
+    const uint64_t m = ((bits & 0x000FFFFFFFFFFFFFull) | ((uint64_t)(e != 0) << 52)) << 3;
+    return m >> min(S - max(e, 1u), 63u);
+}
+
+// acc += (-1)^s floor(a b / 2^32) for a = a1 2^32 + a0 < 2^63, b = b1 2^32 + b0 < 2^56, formed as
+// hi(a0 b0) + a0 b1 + a1 b0 + a1 b1 2^32; each term is below 2^88, so 127 of them fit the
+// accumulator's 2^95
+__device__ __forceinline__ void fx_mac(Fx96 &acc, uint64_t a, uint64_t b, uint32_t s) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    uint64_t t = (uint64_t)__umulhi(a0, b0);
+    t += (uint64_t)a0 * b1;
+    t += (uint64_t)a1 * b0;                 // < 2^32 + 2^56 + 2^63
+    const uint64_t u = (uint64_t)a1 * b1;   // < 2^55
+    uint32_t x0 = (uint32_t)t, x1, x2;
+    asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;"
+        : "=r"(x1), "=r"(x2)
+        : "r"((uint32_t)(t >> 32)), "r"((uint32_t)u), "r"((uint32_t)(u >> 32)));
+    const uint32_t mask = 0u - s;   // negation as (x ^ mask) + s
+    x0 ^= mask;
+    x1 ^= mask;
+    x2 ^= mask;
+    asm("{\n\t.reg .u32 c;\n\tadd.cc.u32 c, %3, 0xffffffff;\n\t"
+        "addc.cc.u32 %0, %0, %4;\n\taddc.cc.u32 %1, %1, %5;\n\taddc.u32 %2, %2, %6;\n\t}"
+        : "+r"(acc.w0), "+r"(acc.w1), "+r"(acc.w2)
+        : "r"(s), "r"(x0), "r"(x1), "r"(x2));
+}
+
+// the accumulator times 2^E, rounded to nearest once: the magnitude's leading 64 bits with the
+// rest as a sticky bit, converted with round-to-nearest-even, then scaled exactly by 2^E
+__device__ double fx_to_double(Fx96 a, int E) {
+    const bool neg = (int32_t)a.w2 < 0;
+    if (neg)
+        asm("{\n\tnot.b32 %0, %0;\n\tnot.b32 %1, %1;\n\tnot.b32 %2, %2;\n\t"
+            "add.cc.u32 %0, %0, 1;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.u32 %2, %2, 0;\n\t}"
+            : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2));
+    double d;
+    if (a.w2 == 0) {
+        d = __ull2double_rn(((uint64_t)a.w1 << 32) | a.w0);
+    } else {
+        const int lz = __clz((int)a.w2);   // 0..31
+        const uint64_t hi = ((uint64_t)a.w2 << 32) | a.w1;
+        const uint64_t top = lz ? (hi << lz) | (a.w0 >> (32 - lz)) : hi;
+        const uint32_t rest = a.w0 << lz;
+        d = __ull2double_rn(top | (uint64_t)(rest != 0));
+        E += 32 - lz;
+    }
+    d = (E >= -1022 && E <= 1023) ? d * __longlong_as_double((long long)(E + 1023) << 52) : ldexp(d, E);
+    return neg ? -d : d;
 }
 
 // part layout: [chunk][block][KC + 1]; slot KC holds ||w||^2 (chunk 0 only).  A launch whose gate
@@ -85,7 +182,8 @@ __global__ void __launch_bounds__(KT, 3) k_mdot(const double *__restrict__ V, in
 }
 
 // one warp per output: out[t] = sum over blocks of the partials (fixed order per lane, then a
-// fixed shuffle tree); out[cnt] = ||w||^2
+// fixed shuffle tree); out[cnt] = ||w||^2.  Partials laid out [chunk][block][CH + 1].
+template <int CH>
 __global__ void k_mdot_reduce(const double *part, int g, int cnt0, const int *cntp, const int *gate, double *out) {
     if (gate && !*gate) return;
     const int cnt = basis_count(cnt0, cntp);
@@ -93,36 +191,157 @@ __global__ void k_mdot_reduce(const double *part, int g, int cnt0, const int *cn
     if (t > cnt) return;
     double s = 0.0;
     if (t < cnt) {
-        const int c = t / KC, k = t % KC;
-        for (int b = lane; b < g; b += 32) s += part[((size_t)c * g + b) * (KC + 1) + k];
+        const int c = t / CH, k = t % CH;
+        for (int b = lane; b < g; b += 32) s += part[((size_t)c * g + b) * (CH + 1) + k];
     } else {
-        for (int b = lane; b < g; b += 32) s += part[(size_t)b * (KC + 1) + KC];
+        for (int b = lane; b < g; b += 32) s += part[(size_t)b * (CH + 1) + CH];
     }
     s = warp_sum(s);
     if (lane == 0) out[t] = s;
 }
 
-// w_out = w_in - V h ; partial ||w_out||^2 per block
+// FGMRES dots: chunks of OC basis vectors, the first OF of a chunk on the FP64 pipe and the rest in
+// fixed point; ||w||^2 (FP64) in chunk 0.  A thread's fixed-point sums are rounded into FP64 after
+// every kFxBatch row pairs (at most 2 kFxBatch < 127 terms per accumulator), added in order.
+constexpr int OC = 8, OF = 3, OI = OC - OF, kFxBatch = 60;
+static int kg_odots() { return num_sms() * 4; }
+
+__global__ void __launch_bounds__(KT, 4) k_odot(const double *__restrict__ V, int64_t ld, int cnt0, const int *cntp,
+                                             const int *gate, const double *__restrict__ w, int64_t n, double *part) {
+    if (gate && !*gate) return;
+    const int cnt = basis_count(cnt0, cntp);
+    const int k0 = blockIdx.y * OC;
+    if (k0 >= cnt) return;                 // chunk past the basis (launched for the largest count)
+    const int kc = min(OC, cnt - k0);
+    const bool first = blockIdx.y == 0;
+    __shared__ double fsum[OI][KT];
+    const int64_t npair = n >> 1;
+    const double2 *w2 = reinterpret_cast<const double2 *>(w);
+    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ps = (int64_t)gridDim.x * blockDim.x;
+    // the thread's scale: the largest exponent field among its rows of w (eight loads in flight)
+    uint32_t S = 1;
+    {
+        int64_t p = p0;
+        for (; p + 7 * ps < npair; p += 8 * ps) {
+            uint64_t t[16];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const double2 v = w2[p + u * ps];
+                t[2 * u] = __double_as_longlong(v.x);
+                t[2 * u + 1] = __double_as_longlong(v.y);
+            }
+#pragma unroll
+            for (int u = 0; u < 16; u++) S = max(S, fx_exp(t[u]));
+        }
+        for (; p < npair; p += ps) {
+            const double2 v = w2[p];
+            S = max(S, max(fx_exp(__double_as_longlong(v.x)), fx_exp(__double_as_longlong(v.y))));
+        }
+    }
+    const bool wbad = S == 2047u;   // w holds an Inf or NaN
+    uint32_t badm = 0;              // bit i: vector OF + i has an entry outside (-2, 2)
+    const int E = (int)S - 1108;
+    double accd[OF], nrm = 0.0;
+#pragma unroll
+    for (int i = 0; i < OF; i++) accd[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < OI; i++) fsum[i][threadIdx.x] = 0.0;
+    for (int64_t p = p0; p < npair;) {
+        Fx96 acc[OI];
+#pragma unroll
+        for (int i = 0; i < OI; i++) acc[i] = Fx96{0, 0, 0};
+        for (int b = 0; b < kFxBatch && p < npair; b++, p += ps) {
+            const double2 wi = w2[p];
+            const uint64_t bx = __double_as_longlong(wi.x), by = __double_as_longlong(wi.y);
+            const uint64_t Wx = fx_scaled(bx, S), Wy = fx_scaled(by, S);
+            const uint32_t sx = (uint32_t)(bx >> 63), sy = (uint32_t)(by >> 63);
+#pragma unroll
+            for (int i = 0; i < OF; i++)
+                if (i < kc) {
+                    const double2 v = __ldcs(reinterpret_cast<const double2 *>(V + (int64_t)(k0 + i) * ld) + p);
+                    accd[i] = fma(v.x, wi.x, accd[i]);
+                    accd[i] = fma(v.y, wi.y, accd[i]);
+                }
+#pragma unroll
+            for (int i = 0; i < OI; i++)
+                if (OF + i < kc) {
+                    const double2 v =
+                        __ldcs(reinterpret_cast<const double2 *>(V + (int64_t)(k0 + OF + i) * ld) + p);
+                    const uint64_t vx = __double_as_longlong(v.x), vy = __double_as_longlong(v.y);
+                    bool bi = false;
+                    fx_mac(acc[i], fx_basis(vx, bi), Wx, sx ^ (uint32_t)(vx >> 63));
+                    fx_mac(acc[i], fx_basis(vy, bi), Wy, sy ^ (uint32_t)(vy >> 63));
+                    badm |= (uint32_t)bi << i;
+                }
+            if (first) {
+                nrm = fma(wi.x, wi.x, nrm);
+                nrm = fma(wi.y, wi.y, nrm);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < OI; i++) fsum[i][threadIdx.x] += fx_to_double(acc[i], E);
+    }
+    double out[OC + 1];
+#pragma unroll
+    for (int i = 0; i < OF; i++) out[i] = accd[i];
+#pragma unroll
+    for (int i = 0; i < OI; i++)
+        out[OF + i] = wbad || ((badm >> i) & 1u) ? __longlong_as_double(0x7ff8000000000000ll) : fsum[i][threadIdx.x];
+    out[OC] = nrm;
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {   // odd tail row, in FP64
+        const int64_t r = n - 1;
+        const double wr = w[r];
+        for (int k = 0; k < kc; k++) out[k] += V[(int64_t)(k0 + k) * ld + r] * wr;
+        if (first) out[OC] += wr * wr;
+    }
+    block_reduce_to<OC + 1>(out, OC + 1, part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (OC + 1));
+}
+
+// w_out = w_in - V h; partial ||w_out||^2 per block.  The first row of each pair on the FP64 pipe,
+// the second in fixed point (h scaled by its largest exponent field; at most 64 terms per row).
 __global__ void __launch_bounds__(KT) k_mupdate(const double *__restrict__ V, int64_t ld, int cnt0, const int *cntp,
                                                 const int *gate, const double *__restrict__ h, const double *w_in,
                                                 double *w_out, int64_t n, double *part) {
     if (gate && !*gate) return;
     const int cnt = basis_count(cnt0, cntp);
     __shared__ double hs[64];
-    for (int k = threadIdx.x; k < 64; k += blockDim.x) hs[k] = k < cnt ? h[k] : 0.0;
+    __shared__ uint64_t hm[64];
+    __shared__ uint32_t hsg[64];
+    __shared__ uint32_t Sh;
+    if (threadIdx.x < 32) {
+        uint32_t e = 1;
+        for (int k = threadIdx.x; k < cnt; k += 32) e = max(e, fx_exp(__double_as_longlong(h[k])));
+        for (int o = 16; o; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        if (threadIdx.x == 0) Sh = e;
+    }
     __syncthreads();
+    const uint32_t S = Sh;
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) {
+        const double hk = k < cnt ? h[k] : 0.0;
+        const uint64_t b = __double_as_longlong(hk);
+        hs[k] = hk;
+        hm[k] = fx_scaled(b, S);
+        hsg[k] = (uint32_t)(b >> 63);
+    }
+    __syncthreads();
+    const bool hbad = S == 2047u;   // h holds an Inf or NaN
+    const int E = (int)S - 1108;
     double nrm = 0.0;
     const int64_t npair = n >> 1;
     const double2 *wi2 = reinterpret_cast<const double2 *>(w_in);
     double2 *wo2 = reinterpret_cast<double2 *>(w_out);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npair; p += (int64_t)gridDim.x * blockDim.x) {
         double2 a = wi2[p];
-#pragma unroll 8
+        Fx96 ay{0, 0, 0};
+        bool bad = hbad;   // per row: an entry of this row outside (-2, 2)
+#pragma unroll 4
         for (int k = 0; k < cnt; k++) {
-            const double2 v = reinterpret_cast<const double2 *>(V + (int64_t)k * ld)[p];
+            const double2 v = __ldcs(reinterpret_cast<const double2 *>(V + (int64_t)k * ld) + p);
             a.x -= v.x * hs[k];
-            a.y -= v.y * hs[k];
+            const uint64_t vy = __double_as_longlong(v.y);
+            fx_mac(ay, fx_basis(vy, bad), hm[k], hsg[k] ^ (uint32_t)(vy >> 63));
         }
+        a.y = bad ? __longlong_as_double(0x7ff8000000000000ll) : a.y - fx_to_double(ay, E);
         wo2[p] = a;
         nrm = fma(a.x, a.x, nrm);
         nrm = fma(a.y, a.y, nrm);
@@ -160,7 +379,7 @@ static void dots_launch(const double *V, int64_t ld, int cnt, const int *cntp, i
     if ((size_t)nchunk * g * (KC + 1) > partial_cap) throw Error(BGS_INTERNAL, "partial scratch too small");
     k_mdot<<<dim3(g, nchunk), KT, 0, s>>>(V, ld, cnt, cntp, gate, w, n, partial);
     CK_LAUNCH();
-    k_mdot_reduce<<<(cnt_max + 1 + 7) / 8, 256, 0, s>>>(partial, g, cnt, cntp, gate, h);
+    k_mdot_reduce<KC><<<(cnt_max + 1 + 7) / 8, 256, 0, s>>>(partial, g, cnt, cntp, gate, h);
     CK_LAUNCH();
 }
 
@@ -169,6 +388,36 @@ void arnoldi_dots_into(const double *V, int64_t ld, int cnt, const double *w, in
     if (cnt < 1 || cnt > 64) throw Error(BGS_INVALID_ARG, "basis size outside 1..64");
     if (ld & 1) throw Error(BGS_INVALID_ARG, "basis leading dimension must be even");
     dots_launch(V, ld, cnt, nullptr, cnt, nullptr, w, n, h, partial, partial_cap, max_blocks, s);
+}
+
+// the FGMRES dots (basis of unit vectors): k_odot, then the same fixed-order reduction
+static void odots_launch(const double *V, int64_t ld, int cnt0, const int *cntp, int cnt_max, const int *gate,
+                         const double *w, int64_t n, double *h, double *partial, size_t partial_cap, cudaStream_t s) {
+    const int nchunk = (cnt_max + OC - 1) / OC;
+    const int g = grid_for(n / 2 + 1, KT, kg_odots());
+    if ((size_t)nchunk * g * (OC + 1) > partial_cap) throw Error(BGS_INTERNAL, "partial scratch too small");
+    k_odot<<<dim3(g, nchunk), KT, 0, s>>>(V, ld, cnt0, cntp, gate, w, n, partial);
+    CK_LAUNCH();
+    k_mdot_reduce<OC><<<(cnt_max + 1 + 7) / 8, 256, 0, s>>>(partial, g, cnt0, cntp, gate, h);
+    CK_LAUNCH();
+}
+
+size_t gs_pass_scratch(int cnt, int64_t n) {
+    const size_t dots = (size_t)((cnt + OC - 1) / OC) * grid_for(n / 2 + 1, KT, kg_odots()) * (OC + 1);
+    return std::max(dots, (size_t)grid_for(n / 2 + 1, KT, kg_update()));
+}
+
+void gs_pass(const double *V, int64_t ld, int cnt, double *w, int64_t n, double *h, double *nw, double *partial,
+             size_t partial_cap, cudaStream_t s) {
+    if (cnt < 1 || cnt > 64) throw Error(BGS_INVALID_ARG, "basis size outside 1..64");
+    if (ld & 1) throw Error(BGS_INVALID_ARG, "basis leading dimension must be even");
+    odots_launch(V, ld, cnt, nullptr, cnt, nullptr, w, n, h, partial, partial_cap, s);
+    const int gu = grid_for(n / 2 + 1, KT, kg_update());
+    if ((size_t)gu > partial_cap) throw Error(BGS_INTERNAL, "partial scratch too small");
+    k_mupdate<<<gu, KT, 0, s>>>(V, ld, cnt, nullptr, nullptr, h, w, w, n, partial);
+    CK_LAUNCH();
+    k_sum_partials<<<1, 32, 0, s>>>(partial, gu, nullptr, nw);
+    CK_LAUNCH();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -328,7 +577,7 @@ void fg_orthogonalise(FgState *st, const double *V, int64_t ld, int m, double *w
     const int cnt_max = m;   // the step of column j orthogonalises against j + 1 <= m vectors
     const int gu = grid_for(n / 2 + 1, KT, kg_update());
     // first pass: h1 = V^T w, ||w||^2; w1 = w - V h1, ||w1||^2
-    dots_launch(V, ld, 0, &st->cnt, cnt_max, nullptr, w, n, st->h1, sc.partial.p, sc.partial.n, 0, s);
+    odots_launch(V, ld, 0, &st->cnt, cnt_max, nullptr, w, n, st->h1, sc.partial.p, sc.partial.n, s);
     k_mupdate<<<gu, KT, 0, s>>>(V, ld, 0, &st->cnt, nullptr, st->h1, w, w, n, sc.partial.p);
     CK_LAUNCH();
     k_sum_partials<<<1, 32, 0, s>>>(sc.partial.p, gu, nullptr, &st->nw1);
@@ -336,7 +585,7 @@ void fg_orthogonalise(FgState *st, const double *V, int64_t ld, int m, double *w
     k_fg_check<<<1, 32, 0, s>>>(st, always ? 1 : 0);
     CK_LAUNCH();
     // second pass when the test asks for it (the kernels read the decision on the device)
-    dots_launch(V, ld, 0, &st->cnt, cnt_max, &st->need2, w, n, st->h2, sc.partial.p, sc.partial.n, 0, s);
+    odots_launch(V, ld, 0, &st->cnt, cnt_max, &st->need2, w, n, st->h2, sc.partial.p, sc.partial.n, s);
     k_mupdate<<<gu, KT, 0, s>>>(V, ld, 0, &st->cnt, &st->need2, st->h2, w, w, n, sc.partial.p);
     CK_LAUNCH();
     k_sum_partials<<<1, 32, 0, s>>>(sc.partial.p, gu, &st->need2, &st->nw2);
