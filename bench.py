@@ -66,7 +66,8 @@ def parse():
     p.add_argument("--rtol", type=float, default=1e-8, help="relative tolerance for --theta-grid")
     p.add_argument("--sigma-means", default=None,
                    help="anode,separator,cathode conductivity means for --theta-grid (default: the workload's)")
-    p.add_argument("--profile-case", default=None, choices=["vcycle", "arnoldi", "spmv", "krylov", "setup"],
+    p.add_argument("--profile-case", default=None,
+                   choices=["vcycle", "arnoldi", "spmv", "krylov", "setup", "gram_schmidt"],
                    help="run one small kernel case for an ncu capture and exit")
     p.add_argument("--profile-precision", type=int, default=0, choices=[0, 1],
                    help="hierarchy precision of --profile-case vcycle (0 FP64, 1 FP32)")
@@ -633,6 +634,21 @@ def profile_case(args):
             assert bgs.bgs_arnoldi_dots(V, n, cnt, w, n, h) == 0
         torch.cuda.synchronize()
         print("arnoldi case done", float(h[-1]))
+        return
+    if args.profile_case == "gram_schmidt":
+        # the FGMRES Gram-Schmidt pass (dots and update, FP64 / fixed-point split) at 128^3 rows with
+        # 16 unit basis vectors, as in a mid-cycle Arnoldi step
+        n, cnt = 5 * 128 ** 3, 16
+        V = torch.randn((cnt, n), dtype=torch.float64, device="cuda")
+        V /= V.norm(dim=1, keepdim=True)
+        w0 = torch.randn(n, dtype=torch.float64, device="cuda")
+        h = torch.zeros(cnt + 1, dtype=torch.float64, device="cuda")
+        nw = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            w = w0.clone()
+            assert bgs.bgs_gram_schmidt_pass(V, n, cnt, w, n, h, nw) == 0
+        torch.cuda.synchronize()
+        print("gram_schmidt case done", float(nw[0]))
         return
     if args.profile_case == "krylov":
         # one FP64 solve of the 3D 64^3 system (1.31M DOFs): the Arnoldi kernels of its later
