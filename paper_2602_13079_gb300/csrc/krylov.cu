@@ -37,6 +37,7 @@
 // single-thread kernel, so a whole restart cycle can be replayed as one CUDA graph whose WHILE
 // node the step kernel ends; launched one by one, the same kernels give the same bits.
 #include <algorithm>
+#include <atomic>
 
 #include "internal.h"
 
@@ -202,10 +203,29 @@ __global__ void k_mdot_reduce(const double *part, int g, int cnt0, const int *cn
 // FGMRES dots: chunks of OC basis vectors, the first OF of a chunk on the FP64 pipe and the rest in
 // fixed point; ||w||^2 (FP64) in chunk 0.  A thread's fixed-point sums are rounded into FP64 after
 // every kFxBatch row pairs (at most 2 kFxBatch < 127 terms per accumulator), added in order.
+// The loads run two row pairs ahead of the arithmetic: each thread copies its next pair's chunk
+// entries and w with cp.async into its own column of a two-stage shared buffer (basis entries
+// marked evict-first in L2, so that w stays there for the other chunks), then computes on the
+// current stage; a thread only reads what it copied, so no block barrier is needed.
 constexpr int OC = 8, OF = 3, OI = OC - OF, kFxBatch = 60;
-static int kg_odots() { return num_sms() * 4; }
+static int kg_odots() { return num_sms() * 2; }
+static size_t odot_smem() { return sizeof(double2) * 2 * (OC + 1) * KT; }
 
-__global__ void __launch_bounds__(KT, 4) k_odot(const double *__restrict__ V, int64_t ld, int cnt0, const int *cntp,
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16_first(void *sdst, const void *gsrc, uint64_t pol) {
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(KT, 2) k_odot(const double *__restrict__ V, int64_t ld, int cnt0, const int *cntp,
                                              const int *gate, const double *__restrict__ w, int64_t n, double *part) {
     if (gate && !*gate) return;
     const int cnt = basis_count(cnt0, cntp);
@@ -213,10 +233,22 @@ __global__ void __launch_bounds__(KT, 4) k_odot(const double *__restrict__ V, in
     if (k0 >= cnt) return;                 // chunk past the basis (launched for the largest count)
     const int kc = min(OC, cnt - k0);
     const bool first = blockIdx.y == 0;
+    extern __shared__ double2 ostage[];    // [2][OC + 1][KT]: chunk entries, then w
     __shared__ double fsum[OI][KT];
     const int64_t npair = n >> 1;
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
     const int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ps = (int64_t)gridDim.x * blockDim.x;
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    auto issue = [&](int st, int64_t p) {
+        double2 *b = ostage + (size_t)st * (OC + 1) * KT + threadIdx.x;
+        cp_async16(b + OC * KT, w2 + p);
+#pragma unroll
+        for (int i = 0; i < OC; i++)
+            if (i < kc) cp_async16_first(b + i * KT, reinterpret_cast<const double2 *>(V + (int64_t)(k0 + i) * ld) + p, pol);
+    };
+    if (p0 < npair) issue(0, p0);
+    cp_async_commit();
     // the thread's scale: the largest exponent field among its rows of w (eight loads in flight)
     uint32_t S = 1;
     {
@@ -245,41 +277,52 @@ __global__ void __launch_bounds__(KT, 4) k_odot(const double *__restrict__ V, in
     for (int i = 0; i < OF; i++) accd[i] = 0.0;
 #pragma unroll
     for (int i = 0; i < OI; i++) fsum[i][threadIdx.x] = 0.0;
-    for (int64_t p = p0; p < npair;) {
-        Fx96 acc[OI];
+    Fx96 acc[OI];
 #pragma unroll
-        for (int i = 0; i < OI; i++) acc[i] = Fx96{0, 0, 0};
-        for (int b = 0; b < kFxBatch && p < npair; b++, p += ps) {
-            const double2 wi = w2[p];
-            const uint64_t bx = __double_as_longlong(wi.x), by = __double_as_longlong(wi.y);
-            const uint64_t Wx = fx_scaled(bx, S), Wy = fx_scaled(by, S);
-            const uint32_t sx = (uint32_t)(bx >> 63), sy = (uint32_t)(by >> 63);
+    for (int i = 0; i < OI; i++) acc[i] = Fx96{0, 0, 0};
+    int st = 0, inbatch = 0;
+    for (int64_t p = p0; p < npair; p += ps) {
+        if (p + ps < npair) issue(st ^ 1, p + ps);
+        cp_async_commit();
+        cp_async_wait1();   // this pair's copies are complete
+        const double2 *b = ostage + (size_t)st * (OC + 1) * KT + threadIdx.x;
+        const double2 wi = b[OC * KT];
+        const uint64_t bx = __double_as_longlong(wi.x), by = __double_as_longlong(wi.y);
+        const uint64_t Wx = fx_scaled(bx, S), Wy = fx_scaled(by, S);
+        const uint32_t sx = (uint32_t)(bx >> 63), sy = (uint32_t)(by >> 63);
 #pragma unroll
-            for (int i = 0; i < OF; i++)
-                if (i < kc) {
-                    const double2 v = __ldcs(reinterpret_cast<const double2 *>(V + (int64_t)(k0 + i) * ld) + p);
-                    accd[i] = fma(v.x, wi.x, accd[i]);
-                    accd[i] = fma(v.y, wi.y, accd[i]);
-                }
+        for (int i = 0; i < OF; i++)
+            if (i < kc) {
+                const double2 v = b[i * KT];
+                accd[i] = fma(v.x, wi.x, accd[i]);
+                accd[i] = fma(v.y, wi.y, accd[i]);
+            }
 #pragma unroll
-            for (int i = 0; i < OI; i++)
-                if (OF + i < kc) {
-                    const double2 v =
-                        __ldcs(reinterpret_cast<const double2 *>(V + (int64_t)(k0 + OF + i) * ld) + p);
-                    const uint64_t vx = __double_as_longlong(v.x), vy = __double_as_longlong(v.y);
-                    bool bi = false;
-                    fx_mac(acc[i], fx_basis(vx, bi), Wx, sx ^ (uint32_t)(vx >> 63));
-                    fx_mac(acc[i], fx_basis(vy, bi), Wy, sy ^ (uint32_t)(vy >> 63));
-                    badm |= (uint32_t)bi << i;
-                }
-            if (first) {
-                nrm = fma(wi.x, wi.x, nrm);
-                nrm = fma(wi.y, wi.y, nrm);
+        for (int i = 0; i < OI; i++)
+            if (OF + i < kc) {
+                const double2 v = b[(OF + i) * KT];
+                const uint64_t vx = __double_as_longlong(v.x), vy = __double_as_longlong(v.y);
+                bool bi = false;
+                fx_mac(acc[i], fx_basis(vx, bi), Wx, sx ^ (uint32_t)(vx >> 63));
+                fx_mac(acc[i], fx_basis(vy, bi), Wy, sy ^ (uint32_t)(vy >> 63));
+                badm |= (uint32_t)bi << i;
+            }
+        if (first) {
+            nrm = fma(wi.x, wi.x, nrm);
+            nrm = fma(wi.y, wi.y, nrm);
+        }
+        st ^= 1;
+        if (++inbatch == kFxBatch) {
+            inbatch = 0;
+#pragma unroll
+            for (int i = 0; i < OI; i++) {
+                fsum[i][threadIdx.x] += fx_to_double(acc[i], E);
+                acc[i] = Fx96{0, 0, 0};
             }
         }
-#pragma unroll
-        for (int i = 0; i < OI; i++) fsum[i][threadIdx.x] += fx_to_double(acc[i], E);
     }
+#pragma unroll
+    for (int i = 0; i < OI; i++) fsum[i][threadIdx.x] += fx_to_double(acc[i], E);
     double out[OC + 1];
 #pragma unroll
     for (int i = 0; i < OF; i++) out[i] = accd[i];
@@ -294,6 +337,17 @@ __global__ void __launch_bounds__(KT, 4) k_odot(const double *__restrict__ V, in
         if (first) out[OC] += wr * wr;
     }
     block_reduce_to<OC + 1>(out, OC + 1, part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (OC + 1));
+}
+
+// k_odot's dynamic shared memory above the default limit, once per device
+static void odot_attributes() {
+    static std::atomic<bool> done[128] = {};
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) dev = 0;
+    if (done[dev].load(std::memory_order_acquire)) return;
+    CK(cudaFuncSetAttribute(k_odot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)odot_smem()));
+    done[dev].store(true, std::memory_order_release);
 }
 
 // w_out = w_in - V h; partial ||w_out||^2 per block.  The first row of each pair on the FP64 pipe,
@@ -395,7 +449,8 @@ static void odots_launch(const double *V, int64_t ld, int cnt0, const int *cntp,
     const int nchunk = (cnt_max + OC - 1) / OC;
     const int g = grid_for(n / 2 + 1, KT, kg_odots());
     if ((size_t)nchunk * g * (OC + 1) > partial_cap) throw Error(BGS_INTERNAL, "partial scratch too small");
-    k_odot<<<dim3(g, nchunk), KT, 0, s>>>(V, ld, cnt0, cntp, gate, w, n, partial);
+    odot_attributes();
+    k_odot<<<dim3(g, nchunk), KT, odot_smem(), s>>>(V, ld, cnt0, cntp, gate, w, n, partial);
     CK_LAUNCH();
     k_mdot_reduce<OC><<<(cnt_max + 1 + 7) / 8, 256, 0, s>>>(partial, g, cnt0, cntp, gate, h);
     CK_LAUNCH();
