@@ -44,11 +44,11 @@
 namespace bgs {
 
 constexpr int KT = 256;   // threads per block
-constexpr int KC = 16;    // basis vectors per dot chunk
-// blocks along x: the dots run one wave at the 3 blocks per multiprocessor that k_mdot's
-// registers allow (so no multiprocessor runs a lone fourth block); the update 4 per multiprocessor
+constexpr int KC = 16;    // basis vectors per dot chunk of the C interface's FP64 dots
+// blocks along x: one wave at the 3 blocks per multiprocessor that k_mdot's and k_mupdate's
+// registers allow (so no multiprocessor runs a lone fourth block)
 static int kg_dots() { return num_sms() * 3; }
-static int kg_update() { return num_sms() * 4; }
+static int kg_update() { return num_sms() * 3; }
 
 // basis size of a launch: the fixed value, or the solver state's (device) count
 __device__ __forceinline__ int basis_count(int cnt, const int *cntp) { return cntp ? *cntp : cnt; }
@@ -352,7 +352,8 @@ static void odot_attributes() {
 
 // w_out = w_in - V h; partial ||w_out||^2 per block.  The first row of each pair on the FP64 pipe,
 // the second in fixed point (h scaled by its largest exponent field; at most 64 terms per row).
-__global__ void __launch_bounds__(KT) k_mupdate(const double *__restrict__ V, int64_t ld, int cnt0, const int *cntp,
+// Eight basis vectors' loads in flight per thread, three blocks per multiprocessor.
+__global__ void __launch_bounds__(KT, 3) k_mupdate(const double *__restrict__ V, int64_t ld, int cnt0, const int *cntp,
                                                 const int *gate, const double *__restrict__ h, const double *w_in,
                                                 double *w_out, int64_t n, double *part) {
     if (gate && !*gate) return;
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double *__restrict__ V, in
         double2 a = wi2[p];
         Fx96 ay{0, 0, 0};
         bool bad = hbad;   // per row: an entry of this row outside (-2, 2)
-#pragma unroll 4
+#pragma unroll 8
         for (int k = 0; k < cnt; k++) {
             const double2 v = __ldcs(reinterpret_cast<const double2 *>(V + (int64_t)k * ld) + p);
             a.x -= v.x * hs[k];
