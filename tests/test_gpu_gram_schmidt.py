@@ -15,7 +15,6 @@ A systematic slip in the integer arithmetic (a dropped partial product, a wrong 
 fixed-point results by far more than these bounds.  A second case runs enough rows that every thread
 rounds its fixed-point sums more than once (batches of 60 row pairs) and compares with the FP64-only
 dots of bgs_arnoldi_dots."""
-import math
 from fractions import Fraction
 
 import numpy as np
@@ -65,15 +64,17 @@ def _run(bgs, V, w, ld):
     return h.cpu().numpy(), wd.cpu().numpy(), float(nw.item())
 
 
-def test_gram_schmidt_pass_against_exact_arithmetic(bgs):
-    rng = np.random.default_rng(13)
-    n, cnt = 4099, 19                     # odd n: the last row goes through the FP64 tail
-    ld = n + 1
+@pytest.mark.parametrize("n,cnt", [(4099, 19), (1030, 64), (513, 1)])
+def test_gram_schmidt_pass_against_exact_arithmetic(bgs, n, cnt):
+    # odd n: the last row goes through the FP64 tail; 64 vectors: eight full chunks; one vector:
+    # no fixed-point dot at all (vector 0 of a chunk is on the FP64 side)
+    rng = np.random.default_rng(13 + cnt)
+    ld = n + (n & 1)
     V, w = _basis(rng, n, cnt), _w(rng, n)
     h, wout, nw = _run(bgs, V, w, ld)
     wf = [Fraction(float(x)) for x in w]
     absw = np.abs(w)
-    threads = 256 * min(-(-(n // 2 + 1) // 256), 4 * torch.cuda.get_device_properties(0).multi_processor_count)
+    threads = 256 * min(-(-(n // 2 + 1) // 256), 2 * torch.cuda.get_device_properties(0).multi_processor_count)
     m = 2 * -(-(n // 2) // threads) + 1
     for k in range(cnt):
         exact = sum(Fraction(float(V[k, i])) * wf[i] for i in range(n))
@@ -120,7 +121,8 @@ def test_gram_schmidt_pass_out_of_range_basis_gives_nan(bgs):
 
 
 def test_gram_schmidt_pass_many_batches_matches_fp64_dots(bgs):
-    # 2 * 60 * (4 * SMs * 256) rows and more: every thread rounds its fixed-point sums several times
+    # the dots run 2 * SMs blocks of 256 threads: 180 row pairs per thread, so every thread rounds
+    # its fixed-point sums three times (batches of 60 pairs)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     n = 2 * 60 * 4 * sms * 256 * 3 // 2 + 2
     cnt = 9
@@ -136,7 +138,7 @@ def test_gram_schmidt_pass_many_batches_matches_fp64_dots(bgs):
     nw = torch.zeros(1, dtype=torch.float64, device="cuda")
     assert bgs.bgs_gram_schmidt_pass(V, n, cnt, w2, n, h, nw) == 0
     s_abs = (V.abs() * w.abs()).sum(dim=1)
-    m = 2 * -(-(n // 2) // (3 * sms * 256)) + 80
+    m = 2 * -(-(n // 2) // (2 * sms * 256)) + 80
     bound = 2 * (m + 40) * U * s_abs + 2.0 ** -62 * w.abs().sum() + 2.0 ** -55 * w.abs().max() * V.abs().sum(dim=1)
     assert torch.all((h[:cnt] - h_fp[:cnt]).abs() <= bound)
     assert abs(float(h[cnt] - h_fp[cnt])) <= 2 * (m + 40) * U * float(h_fp[cnt])
