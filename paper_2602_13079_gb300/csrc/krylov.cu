@@ -21,7 +21,7 @@
 //    field S among the values one accumulator sees: |x| = M 2^(S - 1078) with M a 56-bit integer
 //    (an entry 2^k below the largest drops its k lowest mantissa bits);
 //  * each integer product, floor(product / 2^32) formed from 32-bit partial products (less than one
-//    unit, 2^-85 of the largest possible product, cut off), is summed into a 96-bit two's-complement
+//    unit, 2^-87 of the largest possible product, cut off), is summed into a 96-bit two's-complement
 //    accumulator: a thread's sum is exact up to those truncations and independent of order; it is
 //    rounded to FP64 once (value = accumulator * 2^(S - 1108)) and the thread sums go through the
 //    same fixed-order FP64 tree as the FP64 sums.
@@ -29,7 +29,8 @@
 // ||v||_1 + n 2^-84 max|w| of truncation in all, and only the tree's roundings on top, where an FP64
 // sum rounds at every term.  The dots take vectors 0..2 of each chunk of 8 in FP64 and 3..7 in
 // fixed point; the update takes the first row of each pair in FP64 and the second in fixed point
-// (both passes of the 27 iterations of the 128^3 FP64 solve: 21.6 -> 16.5 ms).  The
+// (both passes of the 27 iterations of the 128^3 FP64 solve: 21.6 -> 16.5 ms, and 14.4 ms with the
+// dots' loads staged through shared memory and the update's eight loads in flight).  The
 // general-purpose dots of the C interface (any V) stay in FP64.
 //
 // The step kernels read the basis size (cnt = j + 1) from the solver state in device memory, and
