@@ -128,3 +128,21 @@ def test_arnoldi_dots_reject_misaligned_vectors_on_the_host(bgs, entry):
     assert f(base, ld + 1, cnt, base, n, base, None) == bgs.INVALID_ARG
     assert f(base, ld, 65, base, n, base, None) == bgs.INVALID_ARG
     assert f(base, n - 2, cnt, base, n, base, None) == bgs.INVALID_ARG
+
+
+def test_gram_schmidt_pass_rejects_bad_arguments_on_the_host(bgs):
+    """bgs_gram_schmidt_pass reads V and w as 16-byte pairs and takes 1..64 basis vectors: every
+    malformed call returns BGS_INVALID_ARG on the host, before any CUDA call (these stand-in
+    addresses are never dereferenced)."""
+    f = bgs.lib().bgs_gram_schmidt_pass
+    base = 1 << 20
+    n, cnt, ld = 1000, 3, 1000
+    ok = dict(V=base, ld=ld, cnt=cnt, w=base, n=n, h=base, nw=base)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return f(a["V"], a["ld"], a["cnt"], a["w"], a["n"], a["h"], a["nw"], None)
+
+    for kw in ({"V": base + 8}, {"w": base + 8}, {"V": None}, {"w": None}, {"h": None}, {"nw": None},
+               {"cnt": 0}, {"cnt": 65}, {"ld": ld + 1}, {"ld": n - 2}, {"n": 0}):
+        assert call(**kw) == bgs.INVALID_ARG, kw
